@@ -1,0 +1,161 @@
+"""FP64 CPU oracle for the electron scattering self-energy of Eq. (3).
+
+TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA path is
+checked against. Only the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package. It shares no code with
+the CUDA path (``paper_1912_10024_gb300``) and imports nothing from it.
+
+The arithmetic lives in ``sse_oracle.c`` (plain C99 complex loops, pthreads
+over output blocks); this module only compiles it with gcc and marshals
+numpy / CPU torch arrays through ctypes.
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sse_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Dims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("NA", "NB", "Norb", "NE", "Nkz", "Nqz", "Nw", "a_begin", "a_end", "E_begin", "E_end")]
+
+
+def compile_source(src: str, so: str) -> str:
+    """gcc flags shared by every build of the oracle (IEEE double, no FMA contraction)."""
+    tmp = so + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+                           "-fcx-limited-range", "-o", tmp, src, "-lm"])
+    os.replace(tmp, so)
+    return so
+
+
+def build() -> str:
+    """Compile sse_oracle.c into a shared library (cached by source hash)."""
+    with open(_SRC, "rb") as f:
+        tag = hashlib.sha1(f.read()).hexdigest()[:12]
+    so = os.path.join(_BUILD, f"libsse_oracle_{tag}.so")
+    if not os.path.exists(so):
+        os.makedirs(_BUILD, exist_ok=True)
+        compile_source(_SRC, so)
+    return so
+
+
+def _open(path):
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.sse_oracle_fwd.argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp,
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+    lib.sse_oracle_fwd.restype = ctypes.c_int
+    lib.sse_oracle_bwd.argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp,
+                                   vp, vp, vp, ctypes.c_int]
+    lib.sse_oracle_bwd.restype = ctypes.c_int
+    return lib
+
+
+@contextlib.contextmanager
+def _library(path):
+    """Temporarily route calls to another build of the oracle (used by the
+    test that plants mistakes in a copy of sse_oracle.c)."""
+    global _lib
+    old = _load()
+    _lib = _open(path)
+    try:
+        yield
+    finally:
+        _lib = old
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _open(build())
+    return _lib
+
+
+def _np(x, dtype):
+    """numpy view of a CPU torch tensor or array, C-contiguous, given dtype."""
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
+
+
+def _dims(G, D, dH, a_range, E_range):
+    Nkz, NE, NA, Norb, _ = G.shape
+    Nqz, Nw = D.shape[0], D.shape[1]
+    NB = dH.shape[1]
+    a0, a1 = a_range if a_range is not None else (0, NA)
+    e0, e1 = E_range if E_range is not None else (0, NE)
+    return _Dims(NA, NB, Norb, NE, Nkz, Nqz, Nw, a0, a1, e0, e1)
+
+
+def sigma(nbr, dH, D_less, D_greater, G_less, G_greater, scale, a_range=None, E_range=None, nthreads=None,
+          out=None, count_terms=False):
+    """Sigma^<, Sigma^> of Eq. (3) in FP64 on the host.
+
+    Arrays may be numpy arrays or CPU torch tensors with the layouts of the
+    C-ABI (G/Sigma [Nkz,NE,NA,Norb,Norb], dH [NA,NB,3,Norb,Norb],
+    D [Nqz,Nw,NA,NB,3,3], nbr [NA,NB] int32). Only blocks of atoms in
+    ``a_range`` and energies in ``E_range`` are computed; the rest of the
+    outputs stay zero (or keep the contents of ``out``).
+    Returns (S_less, S_greater) as complex128 numpy arrays, plus the number of
+    in-range terms if ``count_terms``.
+    """
+    lib = _load()
+    G_l, G_g = _np(G_less, np.complex128), _np(G_greater, np.complex128)
+    D_l, D_g = _np(D_less, np.complex128), _np(D_greater, np.complex128)
+    dH_, nbr_ = _np(dH, np.complex128), _np(nbr, np.int32)
+    d = _dims(G_l, D_l, dH_, a_range, E_range)
+    if out is None:
+        S_l, S_g = np.zeros_like(G_l), np.zeros_like(G_l)
+    else:
+        S_l, S_g = out
+    n = ctypes.c_longlong(0)
+    rc = lib.sse_oracle_fwd(ctypes.byref(d), nbr_.ctypes.data, dH_.ctypes.data, D_l.ctypes.data, D_g.ctypes.data,
+                            G_l.ctypes.data, G_g.ctypes.data, float(scale), S_l.ctypes.data, S_g.ctypes.data,
+                            int(nthreads or default_threads()), ctypes.byref(n))
+    if rc != 0:
+        raise ValueError(f"sse_oracle_fwd failed with status {rc}")
+    if count_terms:
+        return S_l, S_g, int(n.value)
+    return S_l, S_g
+
+
+def sigma_grad(nbr, dH, D_less, D_greater, G_less, G_greater, scale, W_less, W_greater, a_range=None,
+               nthreads=None):
+    """Gradients of L = sum_t Re tr(W^t^H Sigma^t) w.r.t. dH, Dc^<, Dc^>.
+
+    PyTorch convention for complex leaves (grad = dL/dRe + i dL/dIm).
+    Returns (g_dH, g_D_less, g_D_greater); blocks of atoms outside
+    ``a_range`` are zero.
+    """
+    lib = _load()
+    G_l, G_g = _np(G_less, np.complex128), _np(G_greater, np.complex128)
+    D_l, D_g = _np(D_less, np.complex128), _np(D_greater, np.complex128)
+    dH_, nbr_ = _np(dH, np.complex128), _np(nbr, np.int32)
+    W_l, W_g = _np(W_less, np.complex128), _np(W_greater, np.complex128)
+    d = _dims(G_l, D_l, dH_, a_range, None)
+    g_dH = np.zeros_like(dH_)
+    g_Dl, g_Dg = np.zeros_like(D_l), np.zeros_like(D_g)
+    rc = lib.sse_oracle_bwd(ctypes.byref(d), nbr_.ctypes.data, dH_.ctypes.data, D_l.ctypes.data, D_g.ctypes.data,
+                            G_l.ctypes.data, G_g.ctypes.data, float(scale), W_l.ctypes.data, W_g.ctypes.data,
+                            g_dH.ctypes.data, g_Dl.ctypes.data, g_Dg.ctypes.data, int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError(f"sse_oracle_bwd failed with status {rc}")
+    return g_dH, g_Dl, g_Dg

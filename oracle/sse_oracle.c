@@ -1,0 +1,392 @@
+/*
+ * FP64 CPU oracle for the electron scattering self-energy (SSE) of
+ * Ziogas et al., "A Data-Centric Approach to Extreme-Scale Ab initio
+ * Dissipative Quantum Transport Simulations" (SC'19), Eq. (3).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference that the
+ * CUDA path is checked against. Only the test suite, the package smoke check
+ * and the benchmark's CPU-baseline leg may build, load or call it. It shares
+ * no code with the CUDA path and includes none of its headers.
+ *
+ * Notation (Sec. 2, Eq. 3 and the tensor description that follows it):
+ *   G^t   [Nkz][NE][NA][Norb][Norb]   diagonal blocks G^t_bb(E, kz), t in {<,>}
+ *   dH    [NA][NB][3][Norb][Norb]     grad_i H_ab for b = nbr[a][s]
+ *   Dc^t  [Nqz][Nw][NA][NB][3][3]     phonon weight of the bond (a, slot s):
+ *                                     the combination D_ba - D_bb - D_aa + D_ab
+ *   Sigma [Nkz][NE][NA][Norb][Norb]   diagonal blocks Sigma^t_aa(E, kz)
+ *
+ * Eq. (3), with the readings used throughout this project:
+ *   Sigma^t_aa(E,k) = i*scale * sum_q sum_{s} sum_{w,sigma} sum_{i,j}
+ *        dH_i(a,s) . G^t_bb(E - sigma*(w+1), (k - q) mod Nkz) . dH_j(a,s)^H
+ *        * Dc^{tau(t,sigma)}_ij(q, w, a, s)
+ *   - b = nbr[a][s]; the l in the printed sum index is the neighbour b.
+ *   - grad_j H_ba = (grad_j H_ab)^H.
+ *   - sigma = +1 (emission): G at E - (w+1), weight Dc^t;
+ *     sigma = -1 (absorption): G at E + (w+1), weight Dc^{other type}.
+ *   - energies outside [0, NE) contribute zero (no wrap); kz wraps.
+ *   - the integral d(hbar omega)/2pi over the uniform phonon grid is the sum
+ *     over w times `scale` (= grid step / 2pi).
+ *
+ * All arithmetic is IEEE double / double complex, built with
+ * -ffp-contract=off so x86 and Arm hosts round identically.
+ */
+#include <complex.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+typedef struct {
+    int32_t NA, NB, Norb, NE, Nkz, Nqz, Nw;
+    int32_t a_begin, a_end; /* atoms whose Sigma (or gradients) are computed */
+    int32_t E_begin, E_end; /* energies whose Sigma is computed (forward only) */
+} sse_oracle_dims;
+
+#define ORACLE_OK 0
+#define ORACLE_BAD_ARG 1
+#define ORACLE_NO_MEM 2
+
+static int check_dims(const sse_oracle_dims* d) {
+    if (!d) return 0;
+    if (d->NA < 1 || d->NB < 1 || d->Norb < 1 || d->NE < 1 || d->Nkz < 1 || d->Nqz < 1 || d->Nw < 1) return 0;
+    if (d->Nqz > d->Nkz) return 0;
+    if (d->a_begin < 0 || d->a_end > d->NA || d->a_begin > d->a_end) return 0;
+    if (d->E_begin < 0 || d->E_end > d->NE || d->E_begin > d->E_end) return 0;
+    return 1;
+}
+
+static size_t off_G(const sse_oracle_dims* d, int k, int E, int a) {
+    return (((size_t)k * d->NE + E) * d->NA + a) * (size_t)d->Norb * d->Norb;
+}
+static size_t off_dH(const sse_oracle_dims* d, int a, int s, int i) {
+    return (((size_t)a * d->NB + s) * 3 + i) * (size_t)d->Norb * d->Norb;
+}
+static size_t off_D(const sse_oracle_dims* d, int q, int w, int a, int s) {
+    return ((((size_t)q * d->Nw + w) * d->NA + a) * d->NB + s) * 9;
+}
+
+/* C = A B */
+static void mm(int n, const cplx* A, const cplx* B, cplx* C) {
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            cplx acc = 0;
+            for (int l = 0; l < n; ++l) acc += A[r * n + l] * B[l * n + c];
+            C[r * n + c] = acc;
+        }
+}
+/* C = A B^H */
+static void mm_bh(int n, const cplx* A, const cplx* B, cplx* C) {
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            cplx acc = 0;
+            for (int l = 0; l < n; ++l) acc += A[r * n + l] * conj(B[c * n + l]);
+            C[r * n + c] = acc;
+        }
+}
+/* C = A^H B */
+static void mm_ah(int n, const cplx* A, const cplx* B, cplx* C) {
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            cplx acc = 0;
+            for (int l = 0; l < n; ++l) acc += conj(A[l * n + r]) * B[l * n + c];
+            C[r * n + c] = acc;
+        }
+}
+/* sum_{mn} conj(X[mn]) Y[mn] = tr(X^H Y) */
+static cplx frob(int n, const cplx* X, const cplx* Y) {
+    cplx acc = 0;
+    for (int e = 0; e < n * n; ++e) acc += conj(X[e]) * Y[e];
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* forward                                                              */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const sse_oracle_dims* d;
+    const int32_t* nbr;
+    const cplx* dH;
+    const cplx* D[2]; /* [0] = Dc^<, [1] = Dc^> */
+    const cplx* G[2];
+    cplx* S[2];
+    cplx c; /* i * scale */
+    long long n_out, next;
+    pthread_mutex_t lock;
+    long long terms; /* number of (t,a,E,k,q,s,w,sigma) terms that were in range */
+    int fail;
+} fwd_job;
+
+/* Sigma^t_aa(E,k) for one output block, following Eq. (3) term by term. */
+static long long fwd_one(fwd_job* J, int t, int a, int E, int k, cplx* P, cplx* Q, cplx* S) {
+    const sse_oracle_dims* d = J->d;
+    const int n = d->Norb, nn = n * n;
+    long long terms = 0;
+    memset(S, 0, sizeof(cplx) * nn);
+    for (int q = 0; q < d->Nqz; ++q) {
+        const int kp = ((k - q) % d->Nkz + d->Nkz) % d->Nkz; /* kz - qz, periodic */
+        for (int s = 0; s < d->NB; ++s) {
+            const int b = J->nbr[(size_t)a * d->NB + s];
+            for (int w = 0; w < d->Nw; ++w) {
+                for (int sg = 0; sg < 2; ++sg) {
+                    const int sigma = sg == 0 ? +1 : -1;
+                    const int Ep = E - sigma * (w + 1);
+                    if (Ep < 0 || Ep >= d->NE) continue; /* out of range: zero */
+                    ++terms;
+                    const int tau = sigma == +1 ? t : 1 - t;
+                    const cplx* Gp = J->G[t] + off_G(d, kp, Ep, b);
+                    const cplx* Dc = J->D[tau] + off_D(d, q, w, a, s);
+                    for (int i = 0; i < 3; ++i) {
+                        mm(n, J->dH + off_dH(d, a, s, i), Gp, P); /* dH_i(a,b) G_bb */
+                        for (int j = 0; j < 3; ++j) {
+                            mm_bh(n, P, J->dH + off_dH(d, a, s, j), Q); /* ... dH_j(b,a) */
+                            const cplx dij = Dc[i * 3 + j];
+                            for (int e = 0; e < nn; ++e) S[e] += dij * Q[e];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    cplx* out = J->S[t] + off_G(d, k, E, a);
+    for (int e = 0; e < nn; ++e) out[e] = J->c * S[e];
+    return terms;
+}
+
+static void* fwd_worker(void* arg) {
+    fwd_job* J = (fwd_job*)arg;
+    const sse_oracle_dims* d = J->d;
+    const int nn = d->Norb * d->Norb;
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * nn * 3);
+    if (!buf) {
+        pthread_mutex_lock(&J->lock);
+        J->fail = 1;
+        pthread_mutex_unlock(&J->lock);
+        return NULL;
+    }
+    const int nA = d->a_end - d->a_begin, nE = d->E_end - d->E_begin;
+    long long terms = 0;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        long long o = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (o >= J->n_out) break;
+        /* output index -> (t, a, E, k) */
+        const int k = (int)(o % d->Nkz);
+        long long r = o / d->Nkz;
+        const int E = d->E_begin + (int)(r % nE);
+        r /= nE;
+        const int a = d->a_begin + (int)(r % nA);
+        const int t = (int)(r / nA);
+        terms += fwd_one(J, t, a, E, k, buf, buf + nn, buf + 2 * nn);
+    }
+    free(buf);
+    pthread_mutex_lock(&J->lock);
+    J->terms += terms;
+    pthread_mutex_unlock(&J->lock);
+    return NULL;
+}
+
+static int run_threads(void* (*fn)(void*), void* job, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        if (pthread_create(&th[i], NULL, fn, job) != 0) break;
+        ++started;
+    }
+    if (started == 0) fn(job);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/*
+ * Sigma^<, Sigma^> of Eq. (3) for atoms [a_begin, a_end) and energies
+ * [E_begin, E_end), all kz. Other blocks of S_less / S_greater are untouched.
+ * Host pointers, complex128 interleaved. Returns 0 on success. If n_terms is
+ * not NULL it receives the number of in-range (t,a,E,k,q,s,w,sigma) terms.
+ */
+int sse_oracle_fwd(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH, const cplx* D_less,
+                   const cplx* D_greater, const cplx* G_less, const cplx* G_greater, double scale,
+                   cplx* S_less, cplx* S_greater, int nthreads, long long* n_terms) {
+    if (!check_dims(d) || !nbr || !dH || !D_less || !D_greater || !G_less || !G_greater || !S_less || !S_greater)
+        return ORACLE_BAD_ARG;
+    for (size_t e = 0; e < (size_t)d->NA * d->NB; ++e)
+        if (nbr[e] < 0 || nbr[e] >= d->NA) return ORACLE_BAD_ARG;
+    fwd_job J;
+    memset(&J, 0, sizeof J);
+    J.d = d;
+    J.nbr = nbr;
+    J.dH = dH;
+    J.D[0] = D_less;
+    J.D[1] = D_greater;
+    J.G[0] = G_less;
+    J.G[1] = G_greater;
+    J.S[0] = S_less;
+    J.S[1] = S_greater;
+    J.c = I * scale;
+    J.n_out = 2LL * (d->a_end - d->a_begin) * (d->E_end - d->E_begin) * d->Nkz;
+    pthread_mutex_init(&J.lock, NULL);
+    run_threads(fwd_worker, &J, nthreads);
+    pthread_mutex_destroy(&J.lock);
+    if (n_terms) *n_terms = J.terms;
+    return J.fail ? ORACLE_NO_MEM : ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* adjoint                                                              */
+/* ------------------------------------------------------------------ */
+/*
+ * Loss L = sum_t sum_{a,E,k} Re tr( W^t_a(E,k)^H Sigma^t_a(E,k) ).
+ * Gradients follow the PyTorch convention for complex leaves,
+ * grad z = dL/dRe z + i dL/dIm z, so for L = Re(alpha z) grad z = conj(alpha)
+ * and for L = Re tr(B^H X) grad X = B. With c = i*scale each term
+ * c * Dc_ij * dH_i G dH_j^H of Eq. (3) gives
+ *   grad Dc_ij     += conj( c * tr(W^H dH_i G dH_j^H) )
+ *   grad dH_m      += sum_j conj(c * Dc_mj) * W dH_j G^H      (dH_m on the left)
+ *                   + sum_i c * Dc_im * W^H dH_i G            (dH_m^H on the right)
+ */
+
+typedef struct {
+    const sse_oracle_dims* d;
+    const int32_t* nbr;
+    const cplx* dH;
+    const cplx* D[2];
+    const cplx* G[2];
+    const cplx* W[2];
+    cplx* gdH;
+    cplx* gD[2];
+    cplx c;
+    int next;
+    pthread_mutex_t lock;
+    int fail;
+} bwd_job;
+
+static void bwd_atom(bwd_job* J, int a, cplx* buf) {
+    const sse_oracle_dims* d = J->d;
+    const int n = d->Norb, nn = n * n;
+    cplx* P = buf;           /* dH_i G          */
+    cplx* T = buf + nn;      /* scratch         */
+    cplx* U = buf + 2 * nn;  /* scratch         */
+    cplx* AG = buf + 3 * nn; /* 3 x (dH_i G) or 3 x (W dH_j) */
+    for (int s = 0; s < d->NB; ++s) {
+        for (int i = 0; i < 3; ++i) memset(J->gdH + off_dH(d, a, s, i), 0, sizeof(cplx) * nn);
+        for (int q = 0; q < d->Nqz; ++q)
+            for (int w = 0; w < d->Nw; ++w) {
+                memset(J->gD[0] + off_D(d, q, w, a, s), 0, sizeof(cplx) * 9);
+                memset(J->gD[1] + off_D(d, q, w, a, s), 0, sizeof(cplx) * 9);
+            }
+    }
+    for (int t = 0; t < 2; ++t)
+        for (int E = 0; E < d->NE; ++E)
+            for (int k = 0; k < d->Nkz; ++k) {
+                const cplx* W = J->W[t] + off_G(d, k, E, a);
+                for (int q = 0; q < d->Nqz; ++q) {
+                    const int kp = ((k - q) % d->Nkz + d->Nkz) % d->Nkz;
+                    for (int s = 0; s < d->NB; ++s) {
+                        const int b = J->nbr[(size_t)a * d->NB + s];
+                        const cplx* A0 = J->dH + off_dH(d, a, s, 0);
+                        cplx* gA = J->gdH + off_dH(d, a, s, 0);
+                        for (int w = 0; w < d->Nw; ++w)
+                            for (int sg = 0; sg < 2; ++sg) {
+                                const int sigma = sg == 0 ? +1 : -1;
+                                const int Ep = E - sigma * (w + 1);
+                                if (Ep < 0 || Ep >= d->NE) continue;
+                                const int tau = sigma == +1 ? t : 1 - t;
+                                const cplx* Gp = J->G[t] + off_G(d, kp, Ep, b);
+                                const cplx* Dc = J->D[tau] + off_D(d, q, w, a, s);
+                                cplx* gDc = J->gD[tau] + off_D(d, q, w, a, s);
+                                /* grad Dc_ij += conj(c tr(W^H dH_i G dH_j^H)) */
+                                for (int i = 0; i < 3; ++i) {
+                                    mm(n, A0 + (size_t)i * nn, Gp, P);
+                                    for (int j = 0; j < 3; ++j) {
+                                        mm_bh(n, P, A0 + (size_t)j * nn, T);
+                                        gDc[i * 3 + j] += conj(J->c * frob(n, W, T));
+                                    }
+                                }
+                                /* grad dH_m, left occurrences: conj(c Dc_mj) W dH_j G^H */
+                                for (int j = 0; j < 3; ++j) {
+                                    mm(n, W, A0 + (size_t)j * nn, T); /* W dH_j */
+                                    mm_bh(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */
+                                }
+                                for (int m = 0; m < 3; ++m)
+                                    for (int j = 0; j < 3; ++j) {
+                                        const cplx f = conj(J->c * Dc[m * 3 + j]);
+                                        for (int e = 0; e < nn; ++e) gA[(size_t)m * nn + e] += f * AG[(size_t)j * nn + e];
+                                    }
+                                /* grad dH_m, right occurrences: c Dc_im W^H dH_i G */
+                                for (int i = 0; i < 3; ++i) {
+                                    mm_ah(n, W, A0 + (size_t)i * nn, T); /* W^H dH_i */
+                                    mm(n, T, Gp, U);                      /* W^H dH_i G */
+                                    memcpy(AG + (size_t)i * nn, U, sizeof(cplx) * nn);
+                                }
+                                for (int m = 0; m < 3; ++m)
+                                    for (int i = 0; i < 3; ++i) {
+                                        const cplx f = J->c * Dc[i * 3 + m];
+                                        for (int e = 0; e < nn; ++e) gA[(size_t)m * nn + e] += f * AG[(size_t)i * nn + e];
+                                    }
+                            }
+                    }
+                }
+            }
+}
+
+static void* bwd_worker(void* arg) {
+    bwd_job* J = (bwd_job*)arg;
+    const int nn = J->d->Norb * J->d->Norb;
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * nn * 6);
+    if (!buf) {
+        pthread_mutex_lock(&J->lock);
+        J->fail = 1;
+        pthread_mutex_unlock(&J->lock);
+        return NULL;
+    }
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int a = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (a >= J->d->a_end) break;
+        bwd_atom(J, a, buf);
+    }
+    free(buf);
+    return NULL;
+}
+
+/*
+ * Gradients of L = sum_t Re tr(W^t^H Sigma^t) w.r.t. dH and Dc^<, Dc^> for the
+ * atoms [a_begin, a_end) (all energies; E_begin/E_end are ignored). Blocks of
+ * other atoms are untouched. W_less / W_greater have the shape of Sigma.
+ */
+int sse_oracle_bwd(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH, const cplx* D_less,
+                   const cplx* D_greater, const cplx* G_less, const cplx* G_greater, double scale,
+                   const cplx* W_less, const cplx* W_greater, cplx* g_dH, cplx* g_D_less, cplx* g_D_greater,
+                   int nthreads) {
+    if (!check_dims(d) || !nbr || !dH || !D_less || !D_greater || !G_less || !G_greater || !W_less || !W_greater ||
+        !g_dH || !g_D_less || !g_D_greater)
+        return ORACLE_BAD_ARG;
+    for (size_t e = 0; e < (size_t)d->NA * d->NB; ++e)
+        if (nbr[e] < 0 || nbr[e] >= d->NA) return ORACLE_BAD_ARG;
+    bwd_job J;
+    memset(&J, 0, sizeof J);
+    J.d = d;
+    J.nbr = nbr;
+    J.dH = dH;
+    J.D[0] = D_less;
+    J.D[1] = D_greater;
+    J.G[0] = G_less;
+    J.G[1] = G_greater;
+    J.W[0] = W_less;
+    J.W[1] = W_greater;
+    J.gdH = g_dH;
+    J.gD[0] = g_D_less;
+    J.gD[1] = g_D_greater;
+    J.c = I * scale;
+    J.next = d->a_begin;
+    pthread_mutex_init(&J.lock, NULL);
+    run_threads(bwd_worker, &J, nthreads);
+    pthread_mutex_destroy(&J.lock);
+    return J.fail ? ORACLE_NO_MEM : ORACLE_OK;
+}

@@ -1,0 +1,98 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/sse_oracle.c (on the CPU),
+builds it, and checks that at least one pin of tests/test_oracle_pins.py or
+tests/test_oracle_adjoint.py fails against the mutated build.
+"""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_adjoint as adj
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "sse_oracle.c")
+
+# (name, original text, mutated text, which pins to run)
+FWD = [
+    ("emission/absorption types swapped", "const int tau = sigma == +1 ? t : 1 - t;\n                    const cplx* Gp",
+     "const int tau = sigma == +1 ? 1 - t : t;\n                    const cplx* Gp"),
+    ("energy shift sign", "const int Ep = E - sigma * (w + 1);\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out",
+     "const int Ep = E + sigma * (w + 1);\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out"),
+    ("frequency offset off by one", "const int Ep = E - sigma * (w + 1);\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out",
+     "const int Ep = E - sigma * (w + 0);\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out"),
+    ("kz shift sign", "const int kp = ((k - q) % d->Nkz + d->Nkz) % d->Nkz; /* kz - qz",
+     "const int kp = ((k + q) % d->Nkz + d->Nkz) % d->Nkz; /* kz - qz"),
+    ("absorption term dropped", "for (int sg = 0; sg < 2; ++sg) {\n                    const int sigma = sg == 0 ? +1 : -1;\n                    const int Ep = E - sigma",
+     "for (int sg = 0; sg < 1; ++sg) {\n                    const int sigma = sg == 0 ? +1 : -1;\n                    const int Ep = E - sigma"),
+    ("right factor not conjugate-transposed", "mm_bh(n, P, J->dH + off_dH(d, a, s, j), Q);",
+     "mm(n, P, J->dH + off_dH(d, a, s, j), Q);"),
+    ("factor order G dH_i", "mm(n, J->dH + off_dH(d, a, s, i), Gp, P);", "mm(n, Gp, J->dH + off_dH(d, a, s, i), P);"),
+    ("weight indices transposed", "const cplx dij = Dc[i * 3 + j];", "const cplx dij = Dc[j * 3 + i];"),
+    ("prefactor i dropped", "J.c = I * scale;\n    J.n_out", "J.c = scale;\n    J.n_out"),
+    ("neighbour G replaced by own atom", "const cplx* Gp = J->G[t] + off_G(d, kp, Ep, b);\n                    const cplx* Dc = J->D[tau]",
+     "const cplx* Gp = J->G[t] + off_G(d, kp, Ep, a);\n                    const cplx* Dc = J->D[tau]"),
+    ("edge terms wrapped instead of dropped",
+     "const int Ep = E - sigma * (w + 1);\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out",
+     "const int Ep = ((E - sigma * (w + 1)) % d->NE + d->NE) % d->NE;\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out"),
+]
+BWD = [
+    ("grad D not conjugated", "gDc[i * 3 + j] += conj(J->c * frob(n, W, T));", "gDc[i * 3 + j] += J->c * frob(n, W, T);"),
+    ("grad dH right term uses D_mi", "const cplx f = J->c * Dc[i * 3 + m];", "const cplx f = J->c * Dc[m * 3 + i];"),
+    ("grad dH left term not conjugated", "const cplx f = conj(J->c * Dc[m * 3 + j]);", "const cplx f = J->c * Dc[m * 3 + j];"),
+    ("grad dH left term misses G^H", "mm_bh(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */",
+     "mm(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */"),
+]
+
+def _fwd_pins():
+    yield pins.test_scalar_worked_example
+    yield pins.test_closed_form_constant_G
+    for args in [(0, 1, 5, 0), (2, 2, 3, 1), (1, 0, 0, 2)]:
+        yield lambda a=args: pins.test_delta_response(*a)
+    yield pins.test_anti_hermitian
+    yield pins.test_sesquilinear_in_dH
+    yield pins.test_term_count_matches_paper_flop_model
+
+
+def _bwd_pins():
+    def run():
+        problem = adj.make_problem()
+        adj.test_gradient_central_differences(problem)
+        adj.test_dot_product_in_D(problem)
+        adj.test_dot_product_in_dH(problem)
+    yield run
+
+
+def _build(tmp_path, old, new):
+    with open(SRC) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation anchor not found exactly once: {old!r}"
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    return oracle.compile_source(str(path), str(tmp_path / "libmut.so"))
+
+
+def _caught(so, tests):
+    with oracle._library(so):
+        for t in tests:
+            try:
+                t()
+            except AssertionError:
+                return True
+    return False
+
+
+@pytest.mark.parametrize("name,old,new", FWD, ids=[m[0] for m in FWD])
+def test_forward_mutation_is_caught(tmp_path, name, old, new):
+    assert _caught(_build(tmp_path, old, new), _fwd_pins()), f"no pin caught: {name}"
+
+
+@pytest.mark.parametrize("name,old,new", BWD, ids=[m[0] for m in BWD])
+def test_adjoint_mutation_is_caught(tmp_path, name, old, new):
+    assert _caught(_build(tmp_path, old, new), _bwd_pins()), f"no pin caught: {name}"
+
+
+def test_unmutated_source_passes(tmp_path):
+    so = _build(tmp_path, "#include <complex.h>", "#include <complex.h>")
+    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()))
