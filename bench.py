@@ -1,0 +1,296 @@
+#!/usr/bin/env python3
+"""Benchmark of the electron scattering self-energy (Eq. 3) on GB300.
+
+One step = one sse_sigma_fwd call: Sigma^< and Sigma^> for every atom,
+energy and kz of the workload (default: the Si-FinFET-shaped problem,
+NA=1024, NB=4, Norb=10, NE=512, Nkz=Nqz=7, Nw=32, FP64), inputs resident in
+HBM. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--mode fp64|tf32|bf16x3]
+
+Metric: useful TFLOP/s of the paper-equivalent (regrouped, Sec. 5.1) flop
+count, plus (E,kz) points/s. Multi-GPU (torchrun): every rank solves its own
+independent problem of the same size (atom-tile sharding, no collective on
+the data path), value = all ranks' useful flops / max time ("weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1912_10024_gb300 import binding as B  # noqa: E402
+from paper_1912_10024_gb300.inputs import WORKLOADS, make_inputs  # noqa: E402
+
+SCALE = 1.0 / (2.0 * math.pi)
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2070 MHz (derivation in the design doc).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def n_valid(NE: int, Nw: int):
+    """Number of in-range (w, sigma) terms for each energy."""
+    return [sum(1 for w in range(Nw) if E - (w + 1) >= 0) + sum(1 for w in range(Nw) if E + (w + 1) < NE)
+            for E in range(NE)]
+
+
+def useful_flops(d, atoms=None, energies=None) -> float:
+    """Paper-equivalent flops (Sec. 5.1 model after regrouping, exact in-range count):
+    per (a, s, t, k, E): 24 Norb^3 per in-range (q, w, sigma) term + 24 Norb^3 final multiply."""
+    nv = n_valid(d.NE, d.Nw)
+    Es = range(d.NE) if energies is None else energies
+    nA = d.NA if atoms is None else atoms
+    per = sum(24 * d.Norb ** 3 * (d.Nqz * nv[E] + 1) for E in Es)
+    return 2.0 * nA * d.NB * d.Nkz * per
+
+
+def fp64_kernel_flops(d) -> float:
+    """Real FP64 flops the FP64 kernel's algorithm performs (no zero taps counted):
+    per (a, s, t, k, E): 9 Norb^2 complex MACs per in-range term at 3 FMA (6 flop) each,
+    plus 12 Norb^3 complex MACs (8 flop) of block products."""
+    nv = n_valid(d.NE, d.Nw)
+    per = sum(54 * d.Norb ** 2 * d.Nqz * nv[E] + 96 * d.Norb ** 3 for E in range(d.NE))
+    return 2.0 * d.NA * d.NB * d.Nkz * per
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        if shutil.which("nvidia-smi"):
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(d, seconds: float, inp=None, seed: int = 0):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded sample:
+    atom 0 and a growing block of energies around the middle, all kz, both types."""
+    import oracle
+    from oracle.subproblem import oracle_blocks
+    if inp is None:
+        # only atom 0's neighbourhood is copied to the host by oracle_blocks
+        inp = make_inputs(d, seed=seed, device="cuda" if torch.cuda.is_available() else "cpu")
+    threads = oracle.default_threads()
+    nE, spent, flops, a = 1, 0.0, 0.0, 0
+    E0 = d.NE // 2
+    while spent < seconds and nE <= d.NE:
+        lo = max(0, min(E0, d.NE - nE))
+        t0 = time.perf_counter()
+        oracle_blocks(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, a, lo, lo + nE,
+                      nthreads=threads)
+        dt = time.perf_counter() - t0
+        spent += dt
+        flops += useful_flops(d, atoms=1, energies=range(lo, lo + nE))
+        last = (nE, dt)
+        nE *= 2
+    return {"value": flops / spent / 1e12, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"atom 0, energies around NE/2 in blocks of 1,2,...,{last[0]} ({spent:.1f} s total), "
+                      f"all kz, Sigma^< and Sigma^>; FP64 C loops (pthreads)"}
+
+
+def run_reference(args, d, rank, world):
+    if rank != 0:
+        return 0
+    inp = make_inputs(d, seed=0, device="cuda" if torch.cuda.is_available() else "cpu")
+    cb = cpu_baseline(d, args.cpu_seconds, inp)
+    steps = []
+    for _ in range(args.warmup + args.steps):
+        steps.append(cpu_baseline(d, args.cpu_seconds / 4, inp))
+    vals = [s["value"] for s in steps[args.warmup:]]
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": v,
+           "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, **d.__dict__, "mode": "fp64"},
+           "cpu_baseline": {**cb, "value": v},
+           "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="finfet", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="fp64", choices=sorted(B.MODES))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    d = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, d, rank, world)
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    inp = make_inputs(d, seed=rank, device=dev)
+    mode = B.MODES[args.mode]
+    dims = B.dims_of(inp.G_less, inp.D_less, inp.dH)
+    ws = B.workspace(dims, mode, 0, dev)
+    Sl = torch.empty_like(inp.G_less)
+    Sg = torch.empty_like(inp.G_greater)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rc = B.sse_sigma_fwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                             mode, 0, Sl, Sg, ws, ws.numel(), stream)
+        if rc != 0:
+            raise B.SseError(rc, "sse_sigma_fwd")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    uf = useful_flops(d)
+    value = world * uf * args.steps / (total_ms * 1e-3) / 1e12
+    pts = world * d.NE * d.Nkz * args.steps / (total_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host = {n: getattr(inp, n).cpu().pin_memory() for n in ("nbr", "dH", "D_less", "D_greater", "G_less",
+                                                                  "G_greater")}
+        hSl = torch.empty(Sl.shape, dtype=Sl.dtype).pin_memory()
+        hSg = torch.empty(Sg.shape, dtype=Sg.dtype).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = 2 * Sl.numel() * Sl.element_size()
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            for n, t in host.items():
+                getattr(inp, n).copy_(t, non_blocking=True)
+            step()
+            hSl.copy_(Sl, non_blocking=True)
+            hSg.copy_(Sg, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * uf * args.steps / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+        del host, hSl, hSg
+
+    out = None
+    if rank == 0:
+        kflops = fp64_kernel_flops(d)
+        avg_launch_s = statistics.mean(launch_ms) * 1e-3
+        achieved = kflops / avg_launch_s / 1e12
+        out = {"metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": value, "unit": "TFLOP/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic (seeded; Si-FinFET-shaped)",
+               "config": {"workload": args.workload, **d.__dict__, "mode": args.mode,
+                          "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (2 * inp.G_less.numel() * 16 / 1e9)},
+               "pts_per_s": pts,
+               "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                            "kernel": "sigma_fp64_fwd_kernel", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz"},
+               "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps}
+        if world == 1 and not args.no_cpu:
+            del Sl, Sg
+            torch.cuda.empty_cache()
+            out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds, inp)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

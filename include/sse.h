@@ -1,0 +1,133 @@
+/*
+ * sse.h -- C ABI of the GB300 (sm_103a) electron scattering self-energy library.
+ *
+ * The library evaluates the electron-phonon scattering self-energies
+ * Sigma^<, Sigma^> of Eq. (3) of Ziogas et al., "A Data-Centric Approach to
+ * Extreme-Scale Ab initio Dissipative Quantum Transport Simulations"
+ * (SC'19, Sec. 2), and the adjoint of that map.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Complex numbers are complex128: two consecutive doubles (re, im), the
+ * layout of C99 `double complex`, std::complex<double> and torch.complex128.
+ * All tensors are dense, C-contiguous (row-major), in DEVICE memory of the
+ * current CUDA device unless stated otherwise:
+ *
+ *   nbr   int32      [NA][NB]                    neighbour b = nbr[a][s] of atom a
+ *   dH    complex128 [NA][NB][3][Norb][Norb]     grad_i H_ab for b = nbr[a][s]
+ *                                                (grad_j H_ba is its conjugate transpose)
+ *   D^t   complex128 [Nqz][Nw][NA][NB][3][3]     phonon weight of the bond (a,s) at
+ *                                                momentum qz and frequency w: the
+ *                                                combination D_ba - D_bb - D_aa + D_ab
+ *                                                of Eq. (3), t in {<, >}
+ *   G^t   complex128 [Nkz][NE][NA][Norb][Norb]   diagonal blocks G^t_bb(E, kz)
+ *   S^t   complex128 [Nkz][NE][NA][Norb][Norb]   diagonal blocks Sigma^t_aa(E, kz)
+ *
+ * Eq. (3) as evaluated (readings of the printed formula):
+ *   Sigma^t_aa(E,k) = i*scale * sum_{q<Nqz} sum_{s<NB} sum_{w<Nw} sum_{sigma=+-1} sum_{i,j<3}
+ *        dH_i(a,s) G^t_bb(E - sigma*(w+1), (k-q) mod Nkz) dH_j(a,s)^H  D^{tau}_ij(q,w,a,s)
+ *   with b = nbr[a][s], tau = t for sigma = +1 (emission) and the other type
+ *   for sigma = -1 (absorption). Energies outside [0, NE) contribute zero;
+ *   kz is periodic. `scale` is the frequency-integration weight
+ *   (grid step / 2 pi; 1/(2 pi) with energies in units of the grid step).
+ *
+ * Every entry point is asynchronous on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream), validates its arguments on the host before
+ * launching anything, and returns an sse_status. No entry point throws,
+ * exits, prints, allocates device memory or frees caller memory: the caller
+ * owns every buffer, including the workspace. The caller keeps all buffers
+ * alive until the work queued on `stream` has finished. Calls that share a
+ * workspace must be ordered on one stream.
+ */
+#ifndef SSE_H
+#define SSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSE_API __attribute__((visibility("default")))
+#else
+#define SSE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Problem sizes. Atoms [a_begin, a_end) are computed; [0, NA) = all. */
+typedef struct sse_dims {
+    int32_t NA, NB, Norb, NE, Nkz, Nqz, Nw;
+    int32_t a_begin, a_end;
+} sse_dims;
+
+/* Arithmetic of the contraction.
+ *   FP64   : IEEE double throughout (CUDA-core DFMA).
+ *   TF32   : G and the frequency weights rounded to TF32 split-complex planes,
+ *            products on the tcgen05 tensor cores with FP32 accumulation over
+ *            one qz slice, FP64 sums over qz, neighbours and the final
+ *            multiply by dH (Sec. 4.4 adapted to TF32).
+ *   BF16X3 : like TF32 but each operand split into bf16 hi + lo parts and the
+ *            three products hi*hi + hi*lo + lo*hi accumulated in FP32. */
+typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 2 } sse_mode;
+
+/* SYMMETRIZE: replace each output block S by (S - S^H)/2 in FP64 before the
+ *             store (exact Sigma is anti-Hermitian when G and D are; this
+ *             removes round-off asymmetry). In the adjoint it projects the
+ *             upstream gradient the same way.
+ * CHECK     : after the launches, synchronise `stream` and report device-side
+ *             input checks (neighbour indices outside [0, NA)) as
+ *             SSE_ERR_DEVICE_CHECK. Without CHECK such entries contribute zero
+ *             and the call stays asynchronous. */
+enum { SSE_FLAG_SYMMETRIZE = 1u << 0, SSE_FLAG_CHECK = 1u << 1 };
+
+typedef enum sse_status {
+    SSE_OK = 0,
+    SSE_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, bad size or range     */
+    SSE_ERR_UNSUPPORTED = 2,  /* valid but unsupported mode, flag or size       */
+    SSE_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed           */
+    SSE_ERR_TIMEOUT = 4,      /* a bounded device wait gave up                  */
+    SSE_ERR_DEVICE_CHECK = 5, /* device-side input check failed (with CHECK)    */
+    SSE_ERR_WORKSPACE = 6     /* workspace missing, misaligned or too small     */
+} sse_status;
+
+/* Bytes of device workspace that sse_sigma_fwd and sse_sigma_bwd need for
+ * these sizes, mode and flags (the larger of the two). Returns 0 if the
+ * arguments are invalid. The workspace must be 256-byte aligned. */
+SSE_API size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
+
+/* Sigma^< and Sigma^> of Eq. (3) (Sec. 2) for atoms [a_begin, a_end).
+ * Inputs as in the header comment; S_less / S_greater are fully overwritten
+ * for atoms in range (all E, kz) and untouched elsewhere.
+ * Host checks: non-null, 16-byte aligned complex arrays (4-byte nbr),
+ * NA,NB,NE,Nkz,Nqz,Nw >= 1, 1 <= Norb <= 16, Nqz <= Nkz, Nw < NE,
+ * 0 <= a_begin <= a_end <= NA, NA <= 32767, finite scale, known mode and flags. */
+SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                  const double* D_greater, const double* G_less, const double* G_greater, double scale, int mode,
+                  uint32_t flags, double* S_less, double* S_greater, void* workspace, size_t ws_bytes,
+                  void* stream);
+
+/* Adjoint of sse_sigma_fwd (FP64 mode only). For the loss
+ *   L = sum_t sum_{a in range, E, k} Re tr( gS^t_a(E,k)^H Sigma^t_a(E,k) )
+ * it writes the gradients w.r.t. dH, D^< and D^> in the PyTorch convention
+ * for complex tensors (grad z = dL/dRe z + i dL/dIm z):
+ *   g_D^tau_ij(q,w,a,s) = sum over (t,sigma) with type tau and (E,k) in range of
+ *                         conj( i*scale * tr(gS^H dH_i G dH_j^H) )
+ *   g_dH_m(a,s)         = sum_{t,E,k,q,w,sigma} sum_j conj(i*scale*D_mj) gS dH_j G^H
+ *                                              + sum_i i*scale*D_im gS^H dH_i G
+ * gS_less / gS_greater have the layout of S^t. Gradient blocks of atoms in
+ * [a_begin, a_end) are fully overwritten; others are untouched. G is not
+ * differentiated. The gathered G tiles are recomputed, not stored. */
+SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                  const double* D_greater, const double* G_less, const double* G_greater, double scale, int mode,
+                  uint32_t flags, const double* gS_less, const double* gS_greater, double* g_dH, double* g_D_less,
+                  double* g_D_greater, void* workspace, size_t ws_bytes, void* stream);
+
+/* Static, NUL-terminated description of a status code (never NULL). */
+SSE_API const char* sse_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSE_H */

@@ -1,0 +1,220 @@
+"""Thin ctypes binding of libsse (include/sse.h).
+
+The functions named like the C entry points only marshal arguments: every
+step of the computation runs in the CUDA kernels of libsse. There is no CPU
+fallback: if the library cannot be built or loaded, or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import threading
+from typing import Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3 = 0, 1, 2
+SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK = 1, 2
+MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3}
+EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_strerror")
+
+
+class sse_dims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("NA", "NB", "Norb", "NE", "Nkz", "Nqz", "Nw", "a_begin", "a_end")]
+
+
+class SseError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {sse_strerror(status)} (status {status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Build (if the sources changed) and load libsse.so from the package tree."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(_build.build())
+            vp, i32, u32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_double
+            pd = ctypes.POINTER(sse_dims)
+            lib.sse_workspace_bytes.argtypes = [pd, i32, u32]
+            lib.sse_workspace_bytes.restype = ctypes.c_size_t
+            lib.sse_sigma_fwd.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, ctypes.c_size_t, vp]
+            lib.sse_sigma_fwd.restype = i32
+            lib.sse_sigma_bwd.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, vp, vp, vp,
+                                          ctypes.c_size_t, vp]
+            lib.sse_sigma_bwd.restype = i32
+            lib.sse_strerror.argtypes = [i32]
+            lib.sse_strerror.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _p(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---- the C entry points, one to one -------------------------------------
+
+def sse_workspace_bytes(d: sse_dims, mode: int, flags: int) -> int:
+    return int(load().sse_workspace_bytes(ctypes.byref(d), int(mode), int(flags)))
+
+
+def sse_sigma_fwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int, flags: int,
+                  S_less, S_greater, workspace, ws_bytes: int, stream=None) -> int:
+    return int(load().sse_sigma_fwd(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater), _p(G_less),
+                                    _p(G_greater), float(scale), int(mode), int(flags), _p(S_less), _p(S_greater),
+                                    _p(workspace), int(ws_bytes), _stream(stream)))
+
+
+def sse_sigma_bwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int, flags: int,
+                  gS_less, gS_greater, g_dH, g_D_less, g_D_greater, workspace, ws_bytes: int, stream=None) -> int:
+    return int(load().sse_sigma_bwd(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater), _p(G_less),
+                                    _p(G_greater), float(scale), int(mode), int(flags), _p(gS_less), _p(gS_greater),
+                                    _p(g_dH), _p(g_D_less), _p(g_D_greater), _p(workspace), int(ws_bytes),
+                                    _stream(stream)))
+
+
+def sse_strerror(status: int) -> str:
+    return load().sse_strerror(int(status)).decode()
+
+
+# ---- tensor-level helpers ------------------------------------------------
+
+def dims_of(G: torch.Tensor, D: torch.Tensor, dH: torch.Tensor, atoms: Optional[Sequence[int]] = None) -> sse_dims:
+    Nkz, NE, NA, Norb, _ = G.shape
+    a0, a1 = (0, NA) if atoms is None else atoms
+    return sse_dims(NA, dH.shape[1], Norb, NE, Nkz, D.shape[0], D.shape[1], a0, a1)
+
+
+def _check_tensor(name, x, dtype, shape):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def check_inputs(G_less, G_greater, dH, D_less, D_greater, nbr):
+    Nkz, NE, NA, Norb, _ = G_less.shape
+    NB = dH.shape[1]
+    Nqz, Nw = D_less.shape[0], D_less.shape[1]
+    c128 = torch.complex128
+    _check_tensor("G_less", G_less, c128, (Nkz, NE, NA, Norb, Norb))
+    _check_tensor("G_greater", G_greater, c128, (Nkz, NE, NA, Norb, Norb))
+    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb))
+    _check_tensor("D_less", D_less, c128, (Nqz, Nw, NA, NB, 3, 3))
+    _check_tensor("D_greater", D_greater, c128, (Nqz, Nw, NA, NB, 3, 3))
+    _check_tensor("nbr", nbr, torch.int32, (NA, NB))
+
+
+def workspace(d: sse_dims, mode: int, flags: int, device) -> torch.Tensor:
+    n = sse_workspace_bytes(d, mode, flags)
+    if n == 0:
+        raise ValueError("invalid or unsupported problem sizes for libsse")
+    # torch's caching allocator returns >= 512-byte aligned blocks
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2.0 * math.pi), mode: str = "fp64",
+          symmetrize: bool = False, check: bool = False, atoms=None, out=None, ws: Optional[torch.Tensor] = None,
+          stream=None):
+    """Sigma^<, Sigma^> of Eq. (3) on the current CUDA device via sse_sigma_fwd.
+
+    Returns (S_less, S_greater), complex128 tensors shaped like G. With
+    ``atoms=(a0, a1)`` only those atoms are written (the rest of ``out``, or
+    of the freshly allocated zero outputs, is left as is).
+    """
+    check_inputs(G_less, G_greater, dH, D_less, D_greater, nbr)
+    d = dims_of(G_less, D_less, dH, atoms)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    if out is None:
+        alloc = torch.empty if atoms is None else torch.zeros
+        out = (alloc(G_less.shape, dtype=torch.complex128, device=G_less.device),
+               alloc(G_less.shape, dtype=torch.complex128, device=G_less.device))
+    if ws is None:
+        ws = workspace(d, m, flags, G_less.device)
+    rc = sse_sigma_fwd(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, out[0], out[1], ws,
+                       ws.numel(), stream)
+    if rc != 0:
+        raise SseError(rc, "sse_sigma_fwd")
+    return out
+
+
+def sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greater,
+               scale: float = 1.0 / (2.0 * math.pi), mode: str = "fp64", symmetrize: bool = False,
+               check: bool = False, atoms=None, ws: Optional[torch.Tensor] = None, stream=None):
+    """Gradients (g_dH, g_D_less, g_D_greater) of sum_t Re tr(gS^t^H Sigma^t) via sse_sigma_bwd."""
+    check_inputs(G_less, G_greater, dH, D_less, D_greater, nbr)
+    d = dims_of(G_less, D_less, dH, atoms)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    gSl, gSg = gS_less.contiguous(), gS_greater.contiguous()
+    alloc = torch.empty if atoms is None else torch.zeros
+    g_dH = alloc(dH.shape, dtype=torch.complex128, device=dH.device)
+    g_Dl = alloc(D_less.shape, dtype=torch.complex128, device=dH.device)
+    g_Dg = alloc(D_greater.shape, dtype=torch.complex128, device=dH.device)
+    if ws is None:
+        ws = workspace(d, m, flags, dH.device)
+    rc = sse_sigma_bwd(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, gSl, gSg, g_dH, g_Dl,
+                       g_Dg, ws, ws.numel(), stream)
+    if rc != 0:
+        raise SseError(rc, "sse_sigma_bwd")
+    return g_dH, g_Dl, g_Dg
+
+
+class SigmaFunction(torch.autograd.Function):
+    """(dH, D^<, D^>) -> (Sigma^<, Sigma^>) with the hand-written adjoint.
+
+    G^<, G^>, nbr and the scalar options are not differentiated.
+    """
+
+    @staticmethod
+    def forward(ctx, dH, D_less, D_greater, G_less, G_greater, nbr, scale, mode, symmetrize):
+        S = sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale=scale, mode=mode, symmetrize=symmetrize)
+        ctx.save_for_backward(dH, D_less, D_greater, G_less, G_greater, nbr)
+        ctx.scale, ctx.symmetrize = scale, symmetrize
+        return S
+
+    @staticmethod
+    def backward(ctx, gSl, gSg):
+        dH, D_less, D_greater, G_less, G_greater, nbr = ctx.saved_tensors
+        if gSl is None:
+            gSl = torch.zeros_like(G_less)
+        if gSg is None:
+            gSg = torch.zeros_like(G_greater)
+        g = sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gSl, gSg, scale=ctx.scale,
+                       symmetrize=ctx.symmetrize)
+        return g[0], g[1], g[2], None, None, None, None, None, None
+
+
+def sigma_autograd(dH, D_less, D_greater, G_less, G_greater, nbr, scale=1.0 / (2.0 * math.pi), mode="fp64",
+                   symmetrize=False):
+    return SigmaFunction.apply(dH, D_less, D_greater, G_less, G_greater, nbr, scale, mode, symmetrize)

@@ -1,0 +1,151 @@
+// C ABI entry points of libsse: host-side validation, workspace bookkeeping,
+// dispatch to the kernels and status reporting. Declarations and contracts
+// are in include/sse.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sse.h"
+#include "sse_internal.h"
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool valid_dims(const sse_dims* d) {
+    if (!d) return false;
+    if (d->NA < 1 || d->NB < 1 || d->Norb < 1 || d->NE < 1 || d->Nkz < 1 || d->Nqz < 1 || d->Nw < 1) return false;
+    if (d->Nqz > d->Nkz || d->Nw >= d->NE) return false;
+    if (d->a_begin < 0 || d->a_end > d->NA || d->a_begin > d->a_end) return false;
+    return true;
+}
+
+// Sizes that are valid but outside what the kernels are built for.
+bool supported_dims(const sse_dims* d) {
+    if (d->Norb > 16 || d->NA > 32767 || d->Nkz > 65535) return false;
+    // element counts of the largest tensors must fit comfortably in 63 bits
+    const double g = (double)d->Nkz * d->NE * d->NA * d->Norb * d->Norb;
+    const double dd = (double)d->Nqz * d->Nw * d->NA * d->NB * 9.0;
+    return g < 4e18 && dd < 4e18;
+}
+
+bool valid_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3; }
+bool valid_flags(uint32_t f) { return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK)) == 0; }
+
+size_t fwd_ws(const sse_dims& d, int mode) {
+    if (mode == SSE_MODE_FP64) return sse::fp64_fwd_workspace(d);
+    return sse::mixed_fwd_workspace(d, mode);
+}
+
+int finish(cudaError_t launch, unsigned* status, uint32_t flags, cudaStream_t st) {
+    if (launch != cudaSuccess) return SSE_ERR_CUDA;
+    if (!(flags & SSE_FLAG_CHECK)) return SSE_OK;
+    unsigned h = 0;
+    if (cudaMemcpyAsync(&h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SSE_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SSE_ERR_CUDA;
+    if (h & sse::DEV_TIMEOUT) return SSE_ERR_TIMEOUT;
+    if (h & sse::DEV_BAD_NEIGHBOUR) return SSE_ERR_DEVICE_CHECK;
+    return SSE_OK;
+}
+
+int common_checks(const sse_dims* d, const int32_t* nbr, const double* dH, const double* Dl, const double* Dg,
+                  const double* Gl, const double* Gg, double scale, int mode, uint32_t flags) {
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags)) return SSE_ERR_INVALID_ARG;
+    if (!isfinite(scale)) return SSE_ERR_INVALID_ARG;
+    if (!nbr || !dH || !Dl || !Dg || !Gl || !Gg) return SSE_ERR_INVALID_ARG;
+    if (!aligned(nbr, 4) || !aligned(dH, 16) || !aligned(Dl, 16) || !aligned(Dg, 16) || !aligned(Gl, 16) ||
+        !aligned(Gg, 16))
+        return SSE_ERR_INVALID_ARG;
+    if (!supported_dims(d)) return SSE_ERR_UNSUPPORTED;
+    return SSE_OK;
+}
+
+sse::Problem make_problem(const sse_dims* d, const int32_t* nbr, const double* dH, const double* Dl,
+                          const double* Dg, const double* Gl, const double* Gg, double scale, uint32_t flags) {
+    sse::Problem p;
+    p.d = *d;
+    p.nbr = nbr;
+    p.dH = reinterpret_cast<const double2*>(dH);
+    p.D[0] = reinterpret_cast<const double2*>(Dl);
+    p.D[1] = reinterpret_cast<const double2*>(Dg);
+    p.G[0] = reinterpret_cast<const double2*>(Gl);
+    p.G[1] = reinterpret_cast<const double2*>(Gg);
+    p.scale = scale;
+    p.flags = flags;
+    return p;
+}
+
+}  // namespace
+
+extern "C" const char* sse_strerror(int status) {
+    switch (status) {
+        case SSE_OK: return "success";
+        case SSE_ERR_INVALID_ARG: return "invalid argument (null or misaligned pointer, bad size or range)";
+        case SSE_ERR_UNSUPPORTED: return "unsupported mode, flag or problem size";
+        case SSE_ERR_CUDA: return "a CUDA runtime call or kernel launch failed";
+        case SSE_ERR_TIMEOUT: return "a bounded device-side wait gave up";
+        case SSE_ERR_DEVICE_CHECK: return "device-side input check failed (neighbour index out of range)";
+        case SSE_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        default: return "unknown status";
+    }
+}
+
+extern "C" size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
+    size_t f = fwd_ws(*d, mode);
+    size_t b = mode == SSE_MODE_FP64 ? sse::fp64_bwd_workspace(*d) : 0;
+    return sse::kStatusBytes + (f > b ? f : b);
+}
+
+extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                             const double* D_greater, const double* G_less, const double* G_greater, double scale,
+                             int mode, uint32_t flags, double* S_less, double* S_greater, void* workspace,
+                             size_t ws_bytes, void* stream) {
+    int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    if (rc != SSE_OK) return rc;
+    if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + fwd_ws(*d, mode))
+        return SSE_ERR_WORKSPACE;
+    if (d->a_begin == d->a_end) return SSE_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(workspace);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
+    void* ws = static_cast<char*>(workspace) + sse::kStatusBytes;
+    const size_t wsb = ws_bytes - sse::kStatusBytes;
+    const sse::Problem p = make_problem(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, flags);
+    double2* Sl = reinterpret_cast<double2*>(S_less);
+    double2* Sg = reinterpret_cast<double2*>(S_greater);
+    cudaError_t e = mode == SSE_MODE_FP64 ? sse::fp64_fwd(p, Sl, Sg, status, ws, wsb, st)
+                                          : sse::mixed_fwd(p, mode, Sl, Sg, status, ws, wsb, st);
+    if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
+    return finish(e, status, flags, st);
+}
+
+extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                             const double* D_greater, const double* G_less, const double* G_greater, double scale,
+                             int mode, uint32_t flags, const double* gS_less, const double* gS_greater,
+                             double* g_dH, double* g_D_less, double* g_D_greater, void* workspace, size_t ws_bytes,
+                             void* stream) {
+    int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    if (rc != SSE_OK) return rc;
+    if (!gS_less || !gS_greater || !g_dH || !g_D_less || !g_D_greater) return SSE_ERR_INVALID_ARG;
+    if (!aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_dH, 16) || !aligned(g_D_less, 16) ||
+        !aligned(g_D_greater, 16))
+        return SSE_ERR_INVALID_ARG;
+    if (mode != SSE_MODE_FP64) return SSE_ERR_UNSUPPORTED;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::fp64_bwd_workspace(*d))
+        return SSE_ERR_WORKSPACE;
+    if (d->a_begin == d->a_end) return SSE_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(workspace);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
+    void* ws = static_cast<char*>(workspace) + sse::kStatusBytes;
+    const size_t wsb = ws_bytes - sse::kStatusBytes;
+    const sse::Problem p = make_problem(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, flags);
+    cudaError_t e = sse::fp64_bwd(p, reinterpret_cast<const double2*>(gS_less),
+                                  reinterpret_cast<const double2*>(gS_greater), reinterpret_cast<double2*>(g_dH),
+                                  reinterpret_cast<double2*>(g_D_less), reinterpret_cast<double2*>(g_D_greater),
+                                  status, ws, wsb, st);
+    if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
+    return finish(e, status, flags, st);
+}

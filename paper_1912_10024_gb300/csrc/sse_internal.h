@@ -1,0 +1,47 @@
+// Internal declarations shared by the translation units of libsse (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sse.h"
+
+namespace sse {
+
+// Bits of the device status word (first word of the workspace).
+enum : unsigned {
+    DEV_BAD_NEIGHBOUR = 1u,  // nbr[a][s] outside [0, NA): that bond contributed zero
+    DEV_TIMEOUT = 2u,        // a bounded mbarrier / flag wait gave up
+};
+
+// Device views of the inputs of Eq. (3). Complex tensors are double2 (re, im).
+struct Problem {
+    sse_dims d;
+    const int32_t* nbr;
+    const double2* dH;
+    const double2* D[2];  // [0] = D^<, [1] = D^>
+    const double2* G[2];  // [0] = G^<, [1] = G^>
+    double scale;
+    uint32_t flags;
+};
+
+// Workspace layout: [0, 256) status word + padding; the rest per mode.
+constexpr size_t kStatusBytes = 256;
+
+// FP64 forward (sse_fp64.cu).
+size_t fp64_fwd_workspace(const sse_dims& d);
+cudaError_t fp64_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                     size_t ws_bytes, cudaStream_t st);
+
+// FP64 adjoint (sse_fp64_bwd.cu).
+size_t fp64_bwd_workspace(const sse_dims& d);
+cudaError_t fp64_bwd(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
+                     double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
+                     cudaStream_t st);
+
+// Mixed-precision forward (sse_mixed.cu).
+size_t mixed_fwd_workspace(const sse_dims& d, int mode);
+cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status,
+                      void* ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace sse

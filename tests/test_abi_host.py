@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI (no GPU needed: nothing here launches work).
+
+The library must load, export every symbol include/sse.h declares, and
+reject invalid arguments before touching the device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1912_10024_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                names |= set(re.findall(r"SSE_API\s+[\w\s\*]+?\b(sse_\w+)\s*\(", f.read()))
+    return names
+
+
+def test_header_declares_the_entry_points():
+    assert {"sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_strerror"} <= declared_symbols()
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(B.EXPORTED) <= declared_symbols()
+
+
+def good_dims():
+    return B.sse_dims(16, 4, 4, 32, 3, 3, 4, 0, 16)
+
+
+def test_strerror_covers_all_codes():
+    for s in range(7):
+        assert B.sse_strerror(s) and B.sse_strerror(s) != "unknown status"
+    assert B.sse_strerror(99) == "unknown status"
+
+
+def test_workspace_bytes_validation():
+    d = good_dims()
+    assert B.sse_workspace_bytes(d, B.SSE_MODE_FP64, 0) >= 256
+    for field, value in (("NA", 0), ("Nqz", 4), ("Nw", 32), ("a_end", 17), ("a_begin", 5), ("Norb", 0)):
+        bad = good_dims()
+        setattr(bad, field, value)
+        if field == "a_begin":
+            bad.a_end = 4
+        assert B.sse_workspace_bytes(bad, B.SSE_MODE_FP64, 0) == 0, field
+    assert B.sse_workspace_bytes(d, 7, 0) == 0
+    assert B.sse_workspace_bytes(d, 0, 1 << 7) == 0
+    big = good_dims()
+    big.Norb = 17
+    assert B.sse_workspace_bytes(big, 0, 0) == 0
+
+
+FAKE = 1 << 20  # 16-byte aligned fake device address: never dereferenced on these paths
+
+
+def call_fwd(d, **over):
+    args = dict(nbr=FAKE, dH=FAKE, D_less=FAKE, D_greater=FAKE, G_less=FAKE, G_greater=FAKE, scale=0.1, mode=0,
+                flags=0, S_less=FAKE, S_greater=FAKE, workspace=FAKE, ws_bytes=1 << 20)
+    args.update(over)
+    return B.sse_sigma_fwd(d, stream=0, **args)
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(G_less=0), 1), (dict(S_greater=0), 1), (dict(dH=FAKE + 8), 1), (dict(nbr=FAKE + 2), 1),
+    (dict(scale=float("nan")), 1), (dict(mode=3), 1), (dict(flags=4), 1),
+    (dict(workspace=0), 6), (dict(workspace=FAKE + 16), 6), (dict(ws_bytes=16), 6),
+])
+def test_fwd_rejects_bad_arguments_on_host(over, status):
+    assert call_fwd(good_dims(), **over) == status
+
+
+@pytest.mark.parametrize("field,value,status", [("Nqz", 4, 1), ("Nw", 32, 1), ("a_end", 17, 1), ("NB", 0, 1),
+                                                ("Norb", 17, 2), ("NA", 40000, 1)])
+def test_fwd_rejects_bad_dims_on_host(field, value, status):
+    d = good_dims()
+    setattr(d, field, value)
+    if field == "NA":
+        d.a_end = 16
+        status = 2  # valid but larger than the kernels support
+    assert call_fwd(d) == status
+
+
+def test_empty_atom_range_is_a_noop():
+    d = good_dims()
+    d.a_begin = d.a_end = 3
+    assert call_fwd(d) == 0
+
+
+def test_bwd_rejects_non_fp64_and_nulls():
+    d = good_dims()
+    args = [FAKE] * 6
+    assert B.sse_sigma_bwd(d, *args, 0.1, 1, 0, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 20, 0) == 2
+    assert B.sse_sigma_bwd(d, *args, 0.1, 0, 0, 0, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 20, 0) == 1
