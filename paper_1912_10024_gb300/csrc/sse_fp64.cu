@@ -110,8 +110,11 @@ sigma_fp64_fwd_kernel(Problem p, FwdCfg c, double2* __restrict__ S_less, double2
             for (int sg = 0; sg < 2; ++sg) {
                 const int sigma = sg == 0 ? +1 : -1;
                 const double2* Dt = p.D[sg == 0 ? t : 1 - t];
-                for (int w0 = 0; w0 < d.Nw; w0 += c.wc) {
-                    const int wn = min(c.wc, d.Nw - w0);
+                // frequencies whose shifted energy is off the grid for every energy of the tile
+                // contribute nothing: emission needs E0+TE-1-(w+1) >= 0, absorption E0+w+1 < NE
+                const int wend = min(d.Nw, sigma > 0 ? E0 + TE - 1 : d.NE - 1 - E0);
+                for (int w0 = 0; w0 < wend; w0 += c.wc) {
+                    const int wn = min(c.wc, wend - w0);
                     const int rows = TE + wn - 1;
                     const int Elo = sigma > 0 ? E0 - w0 - wn : E0 + w0 + 1;
                     __syncthreads();  // previous chunk is done with the window and weights
