@@ -64,6 +64,29 @@ def fp64_kernel_flops(d) -> float:
     return 2.0 * d.NA * d.NB * d.Nkz * per
 
 
+def mixed_tensor_flops(d, mode: str) -> float:
+    """Tensor-pipe flops one sse_sigma_fwd launch issues in a mixed mode (padding included):
+    per (atom, slot, type, kz, 128-row tile) and in-range (q, w, sigma) tap, kpad/kstep MMAs of
+    128 x npad x kstep (the tile layout of the tcgen05 kernel)."""
+    TE = 128 // d.Norb
+    kstep = 16 if mode == "bf16x3" else 8
+    kraw = 6 * d.Norb if mode == "bf16x3" else 2 * d.Norb
+    kpad = -(-kraw // kstep) * kstep
+    npad = -(-6 * d.Norb // 16) * 16
+    taps = 0
+    for E0 in range(0, d.NE, TE):
+        taps += max(0, min(d.Nw, E0 + TE - 1)) + max(0, min(d.Nw, d.NE - 1 - E0))
+    return 2.0 * 128 * npad * kpad * taps * d.Nqz * d.NB * d.Nkz * 2 * d.NA
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
 
@@ -268,20 +291,30 @@ def main():
 
     out = None
     if rank == 0:
-        kflops = fp64_kernel_flops(d)
         avg_launch_s = statistics.mean(launch_ms) * 1e-3
-        achieved = kflops / avg_launch_s / 1e12
+        if args.mode == "fp64":
+            achieved = fp64_kernel_flops(d) / avg_launch_s / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sigma_fp64_fwd_kernel",
+                    "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
+        else:
+            peaks, src = load_peaks()
+            key = "bf16_tflops_sustained" if avg_launch_s > 1.0 else "bf16_tflops"
+            peak = peaks[key] * (1.0 if args.mode == "bf16x3" else 1.1 / 2.25)
+            achieved = mixed_tensor_flops(d, args.mode) / avg_launch_s / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "sigma_mixed_kernel (timed with its staging kernels)",
+                    "peak_source": f"{src} {key}" + ("" if args.mode == "bf16x3" else " x 1.1/2.25 (tf32/bf16 nominal)")}
         out = {"metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": value, "unit": "TFLOP/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": {"fp64": "f64", "tf32": "tf32+f64", "bf16x3": "bf16x3+f64"}[args.mode],
                "data": "synthetic (seeded; Si-FinFET-shaped)",
                "config": {"workload": args.workload, **d.__dict__, "mode": args.mode,
                           "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (2 * inp.G_less.numel() * 16 / 1e9)},
-               "pts_per_s": pts,
-               "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                            "kernel": "sigma_fp64_fwd_kernel", "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz"},
-               "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps}
+               "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+               "gpu_launches": args.steps * (1 if args.mode == "fp64" else 3)}
         if world == 1 and not args.no_cpu:
             del Sl, Sg
             torch.cuda.empty_cache()

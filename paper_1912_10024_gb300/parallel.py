@@ -1,0 +1,101 @@
+"""Atom-tile sharding of Eq. (3) across ranks with a halo exchange of G.
+
+The communication-avoiding decomposition of Sec. 4.2 tiles the atoms of the
+device: a rank that owns atoms [a0, a1) computes Sigma_a for exactly those
+atoms and needs, besides its own G blocks, the G blocks of the neighbours of
+its atoms that other ranks own (the "+N_b atom halo"). One exchange step
+brings those blocks in; Sigma needs no reduction afterwards.
+
+On one GPU the shard primitive is sse_sigma_fwd's atom range; across GPUs the
+exchange below runs over torch.distributed (NCCL for CUDA tensors, gloo for
+CPU tensors). Every transfer is a point-to-point send/recv of whole
+[Nkz, NE, Norb, Norb] blocks; nothing else crosses ranks.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Sequence, Tuple
+
+import torch
+import torch.distributed as dist
+
+
+def atom_range(NA: int, world: int, rank: int) -> Tuple[int, int]:
+    """Balanced contiguous atom range of ``rank``."""
+    base, rem = divmod(NA, world)
+    a0 = rank * base + min(rank, rem)
+    return a0, a0 + base + (1 if rank < rem else 0)
+
+
+def owner(a: int, NA: int, world: int) -> int:
+    for r in range(world):
+        a0, a1 = atom_range(NA, world, r)
+        if a0 <= a < a1:
+            return r
+    raise ValueError(a)
+
+
+def halo_atoms(nbr: torch.Tensor, a0: int, a1: int) -> List[int]:
+    """Neighbours of atoms [a0, a1) that lie outside the range (sorted)."""
+    need = set(int(b) for b in nbr[a0:a1].reshape(-1).tolist())
+    return sorted(b for b in need if not a0 <= b < a1)
+
+
+def exchange_halo(G_owned: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int, group=None) -> Dict[int, List[torch.Tensor]]:
+    """Fetch the G blocks of this rank's halo atoms from their owners.
+
+    G_owned: the owned slices [Nkz, NE, a1-a0, Norb, Norb] of G^< and G^>.
+    Returns {atom: [G^< block, G^> block]} for every halo atom.
+    """
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    a0, a1 = atom_range(NA, world, rank)
+    mine = halo_atoms(nbr, a0, a1)
+    wants: List[List[int]] = [None] * world  # type: ignore[list-item]
+    dist.all_gather_object(wants, mine, group=group)
+    ops, recv = [], {}
+    for peer in range(world):
+        if peer == rank:
+            continue
+        # blocks the peer needs from me, in the peer's (sorted) order
+        give = [b for b in wants[peer] if a0 <= b < a1]
+        for b in give:
+            for G in G_owned:
+                ops.append(dist.P2POp(dist.isend, G[:, :, b - a0].contiguous(), peer, group))
+        for b in mine:
+            if owner(b, NA, world) == peer:
+                bufs = [torch.empty_like(G[:, :, 0]) for G in G_owned]
+                recv[b] = bufs
+                for buf in bufs:
+                    ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    return recv
+
+
+def local_problem(nbr: torch.Tensor, a0: int, a1: int, G_owned: Sequence[torch.Tensor],
+                  halo: Dict[int, List[torch.Tensor]], dH_owned: torch.Tensor, D_owned: Sequence[torch.Tensor]):
+    """Rank-local problem: atoms [a0, a1) first, then the halo atoms.
+
+    Returns (nbr_local, dH_local, D_less_local, D_greater_local, G_less_local,
+    G_greater_local); Sigma of local atoms [0, a1-a0) equals Sigma of global
+    atoms [a0, a1). Halo atoms get zero dH/D and point at themselves.
+    """
+    order = list(range(a0, a1)) + sorted(halo)
+    index = {b: i for i, b in enumerate(order)}
+    n_own, n_loc = a1 - a0, len(order)
+    NB = nbr.shape[1]
+    nbr_l = torch.arange(n_loc, dtype=torch.int32).unsqueeze(1).repeat(1, NB)
+    nbr_l[:n_own] = torch.tensor([[index[int(b)] for b in row] for row in nbr[a0:a1].tolist()], dtype=torch.int32)
+    Gs = []
+    for t, G in enumerate(G_owned):
+        blocks = [G] + [halo[b][t].unsqueeze(2) for b in sorted(halo)]
+        Gs.append(torch.cat(blocks, dim=2).contiguous())
+    dH_l = torch.zeros((n_loc,) + tuple(dH_owned.shape[1:]), dtype=dH_owned.dtype, device=dH_owned.device)
+    dH_l[:n_own] = dH_owned
+    Ds = []
+    for D in D_owned:
+        Dl = torch.zeros(D.shape[:2] + (n_loc,) + D.shape[3:], dtype=D.dtype, device=D.device)
+        Dl[:, :, :n_own] = D
+        Ds.append(Dl)
+    return nbr_l.to(dH_owned.device), dH_l, Ds[0], Ds[1], Gs[0], Gs[1]

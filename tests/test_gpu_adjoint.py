@@ -36,7 +36,7 @@ def gpu_grad(inp, W, V, **kw):
     TINY,
     Dims(NA=6, NB=3, Norb=3, NE=29, Nkz=4, Nqz=3, Nw=5),
     Dims(NA=5, NB=2, Norb=10, NE=23, Nkz=3, Nqz=2, Nw=7),
-    Dims(NA=3, NB=2, Norb=16, NE=19, Nkz=2, Nqz=2, Nw=37),   # frequency chunks in both kernels
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=37),   # frequency chunks in both kernels
 ], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}")
 def test_gradients_match_oracle(dims):
     nbr = None if dims is TINY else ring_neighbours(dims.NA, dims.NB)
