@@ -257,31 +257,23 @@ typedef struct {
     const cplx* D[2];
     const cplx* G[2];
     const cplx* W[2];
-    cplx* gdH;
-    cplx* gD[2];
     cplx c;
-    int next;
     pthread_mutex_t lock;
     int fail;
 } bwd_job;
 
-static void bwd_atom(bwd_job* J, int a, cplx* buf) {
+/* Adds the contributions of energies [E0, E1) of atom a to gdH_a [NB][3][nn] and
+ * gD_a[tau] [Nqz][Nw][NB][9] (per-atom packed gradient buffers). */
+static void bwd_atom(bwd_job* J, int a, int E0, int E1, cplx* gdH_a, cplx* gD_a0, cplx* gD_a1, cplx* buf) {
     const sse_oracle_dims* d = J->d;
     const int n = d->Norb, nn = n * n;
+    cplx* gD_a[2] = {gD_a0, gD_a1};
     cplx* P = buf;           /* dH_i G          */
     cplx* T = buf + nn;      /* scratch         */
     cplx* U = buf + 2 * nn;  /* scratch         */
     cplx* AG = buf + 3 * nn; /* 3 x (dH_i G) or 3 x (W dH_j) */
-    for (int s = 0; s < d->NB; ++s) {
-        for (int i = 0; i < 3; ++i) memset(J->gdH + off_dH(d, a, s, i), 0, sizeof(cplx) * nn);
-        for (int q = 0; q < d->Nqz; ++q)
-            for (int w = 0; w < d->Nw; ++w) {
-                memset(J->gD[0] + off_D(d, q, w, a, s), 0, sizeof(cplx) * 9);
-                memset(J->gD[1] + off_D(d, q, w, a, s), 0, sizeof(cplx) * 9);
-            }
-    }
     for (int t = 0; t < 2; ++t)
-        for (int E = 0; E < d->NE; ++E)
+        for (int E = E0; E < E1; ++E)
             for (int k = 0; k < d->Nkz; ++k) {
                 const cplx* W = J->W[t] + off_G(d, k, E, a);
                 for (int q = 0; q < d->Nqz; ++q) {
@@ -289,7 +281,7 @@ static void bwd_atom(bwd_job* J, int a, cplx* buf) {
                     for (int s = 0; s < d->NB; ++s) {
                         const int b = J->nbr[(size_t)a * d->NB + s];
                         const cplx* A0 = J->dH + off_dH(d, a, s, 0);
-                        cplx* gA = J->gdH + off_dH(d, a, s, 0);
+                        cplx* gA = gdH_a + (size_t)s * 3 * nn;
                         for (int w = 0; w < d->Nw; ++w)
                             for (int sg = 0; sg < 2; ++sg) {
                                 const int sigma = sg == 0 ? +1 : -1;
@@ -298,7 +290,7 @@ static void bwd_atom(bwd_job* J, int a, cplx* buf) {
                                 const int tau = sigma == +1 ? t : 1 - t;
                                 const cplx* Gp = J->G[t] + off_G(d, kp, Ep, b);
                                 const cplx* Dc = J->D[tau] + off_D(d, q, w, a, s);
-                                cplx* gDc = J->gD[tau] + off_D(d, q, w, a, s);
+                                cplx* gDc = gD_a[tau] + (((size_t)q * d->Nw + w) * d->NB + s) * 9;
                                 /* grad Dc_ij += conj(c tr(W^H dH_i G dH_j^H)) */
                                 for (int i = 0; i < 3; ++i) {
                                     mm(n, A0 + (size_t)i * nn, Gp, P);
@@ -334,9 +326,21 @@ static void bwd_atom(bwd_job* J, int a, cplx* buf) {
             }
 }
 
+/* Thread `id` of `nthreads` takes the energy chunk [id*NE/n, (id+1)*NE/n) of every atom and
+ * accumulates into its own buffers; the chunks are added in thread order afterwards, so the
+ * result does not depend on scheduling. */
+typedef struct {
+    bwd_job* J;
+    int id, nthreads;
+    cplx *gdH, *gD0, *gD1; /* [atoms][...] private partial sums */
+} bwd_part;
+
 static void* bwd_worker(void* arg) {
-    bwd_job* J = (bwd_job*)arg;
-    const int nn = J->d->Norb * J->d->Norb;
+    bwd_part* P = (bwd_part*)arg;
+    bwd_job* J = P->J;
+    const sse_oracle_dims* d = J->d;
+    const int nn = d->Norb * d->Norb;
+    const size_t per_dH = (size_t)d->NB * 3 * nn, per_D = (size_t)d->Nqz * d->Nw * d->NB * 9;
     cplx* buf = (cplx*)malloc(sizeof(cplx) * nn * 6);
     if (!buf) {
         pthread_mutex_lock(&J->lock);
@@ -344,12 +348,11 @@ static void* bwd_worker(void* arg) {
         pthread_mutex_unlock(&J->lock);
         return NULL;
     }
-    for (;;) {
-        pthread_mutex_lock(&J->lock);
-        int a = J->next++;
-        pthread_mutex_unlock(&J->lock);
-        if (a >= J->d->a_end) break;
-        bwd_atom(J, a, buf);
+    const int E0 = (int)((long long)P->id * d->NE / P->nthreads);
+    const int E1 = (int)((long long)(P->id + 1) * d->NE / P->nthreads);
+    for (int a = d->a_begin; a < d->a_end; ++a) {
+        const size_t ai = (size_t)(a - d->a_begin);
+        bwd_atom(J, a, E0, E1, P->gdH + ai * per_dH, P->gD0 + ai * per_D, P->gD1 + ai * per_D, buf);
     }
     free(buf);
     return NULL;
@@ -380,13 +383,59 @@ int sse_oracle_bwd(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH,
     J.G[1] = G_greater;
     J.W[0] = W_less;
     J.W[1] = W_greater;
-    J.gdH = g_dH;
-    J.gD[0] = g_D_less;
-    J.gD[1] = g_D_greater;
     J.c = I * scale;
-    J.next = d->a_begin;
     pthread_mutex_init(&J.lock, NULL);
-    run_threads(bwd_worker, &J, nthreads);
+    int nt = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
+    if (nt > d->NE) nt = d->NE;
+    const int nA = d->a_end - d->a_begin, nn = d->Norb * d->Norb;
+    const size_t per_dH = (size_t)d->NB * 3 * nn, per_D = (size_t)d->Nqz * d->Nw * d->NB * 9;
+    const size_t part = (size_t)nA * (per_dH + 2 * per_D);
+    cplx* parts = (cplx*)calloc((size_t)nt * part + 1, sizeof(cplx));
+    bwd_part P[256];
+    pthread_t th[256];
+    if (!parts) {
+        pthread_mutex_destroy(&J.lock);
+        return ORACLE_NO_MEM;
+    }
+    for (int i = 0; i < nt; ++i) {
+        P[i].J = &J;
+        P[i].id = i;
+        P[i].nthreads = nt;
+        P[i].gdH = parts + (size_t)i * part;
+        P[i].gD0 = P[i].gdH + (size_t)nA * per_dH;
+        P[i].gD1 = P[i].gD0 + (size_t)nA * per_D;
+    }
+    int started = 0;
+    for (int i = 0; i < nt; ++i) {
+        if (pthread_create(&th[i], NULL, bwd_worker, &P[i]) != 0) break;
+        ++started;
+    }
+    for (int i = started; i < nt; ++i) bwd_worker(&P[i]);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    /* add the energy chunks in thread order and scatter into the caller's layout */
+    for (int a = d->a_begin; a < d->a_end; ++a) {
+        const size_t ai = (size_t)(a - d->a_begin);
+        for (int s = 0; s < d->NB; ++s)
+            for (int e = 0; e < 3 * nn; ++e) {
+                cplx acc = 0;
+                for (int i = 0; i < nt; ++i) acc += P[i].gdH[ai * per_dH + (size_t)s * 3 * nn + e];
+                g_dH[off_dH(d, a, s, 0) + e] = acc;
+            }
+        for (int q = 0; q < d->Nqz; ++q)
+            for (int w = 0; w < d->Nw; ++w)
+                for (int s = 0; s < d->NB; ++s)
+                    for (int e = 0; e < 9; ++e) {
+                        const size_t o = ai * per_D + (((size_t)q * d->Nw + w) * d->NB + s) * 9 + e;
+                        cplx a0 = 0, a1 = 0;
+                        for (int i = 0; i < nt; ++i) {
+                            a0 += P[i].gD0[o];
+                            a1 += P[i].gD1[o];
+                        }
+                        g_D_less[off_D(d, q, w, a, s) + e] = a0;
+                        g_D_greater[off_D(d, q, w, a, s) + e] = a1;
+                    }
+    }
+    free(parts);
     pthread_mutex_destroy(&J.lock);
     return J.fail ? ORACLE_NO_MEM : ORACLE_OK;
 }
