@@ -156,27 +156,39 @@ __global__ void grad_dh_reduce_kernel(sse_dims d, const double2* __restrict__ pa
 // ---------------------------------------------------------------------------
 // kernel 2: grad D per bond (a, s)
 // ---------------------------------------------------------------------------
-constexpr int kTEd = 4;      // energies per Q tile
 constexpr int kThreadsD = 256;
+constexpr int kSmemBudgetD = 200 * 1024;
 
 struct DCfg {
-    int nel, wc, groups;
+    int nel, te, wc, groups;  // energies per Q tile, frequencies per window chunk, element groups
     int off_A, off_W, off_P, off_Q, off_G, off_part, smem;
 };
 
-DCfg make_dcfg(const sse_dims& d) {
+DCfg layout_dcfg(const sse_dims& d, int te, int wc) {
     DCfg c{};
     c.nel = d.Norb * d.Norb;
-    c.wc = d.Nw < 32 ? d.Nw : 32;
+    c.te = te;
+    c.wc = wc;
     c.groups = kThreadsD / c.wc;
     const int blk = c.nel * 16;
     c.off_A = 0;
     c.off_W = c.off_A + 3 * blk;
-    c.off_P = c.off_W + kTEd * blk;
-    c.off_Q = c.off_P + kTEd * 3 * blk;
-    c.off_G = c.off_Q + kTEd * 9 * blk;
-    c.off_part = c.off_G + (kTEd + c.wc - 1) * blk;
+    c.off_P = c.off_W + te * blk;
+    c.off_Q = c.off_P + te * 3 * blk;
+    c.off_G = c.off_Q + te * 9 * blk;
+    c.off_part = c.off_G + (te + c.wc - 1) * blk;
     c.smem = c.off_part + c.groups * c.wc * 9 * 16;
+    return c;
+}
+
+// Largest energy tile (4, 2, 1) and frequency chunk (<= 32) whose buffers fit the budget.
+DCfg make_dcfg(const sse_dims& d) {
+    DCfg c{};
+    for (int te = 4; te >= 1; te /= 2)
+        for (int wc = d.Nw < 32 ? d.Nw : 32; wc >= 1; --wc) {
+            c = layout_dcfg(d, te, wc);
+            if (c.smem <= kSmemBudgetD) return c;
+        }
     return c;
 }
 
@@ -217,9 +229,9 @@ grad_d_kernel(Problem p, DCfg c, const double2* __restrict__ gS_less, const doub
     for (int t = 0; t < 2; ++t) {
         const double2* W = t == 0 ? gS_less : gS_greater;
         for (int k = 0; k < d.Nkz; ++k) {
-            for (int E0 = 0; E0 < d.NE; E0 += kTEd) {
+            for (int E0 = 0; E0 < d.NE; E0 += c.te) {
                 __syncthreads();  // previous tile is done with sW / sP / sQ
-                for (int i = tid; i < kTEd * nel; i += kThreadsD) {
+                for (int i = tid; i < c.te * nel; i += kThreadsD) {
                     const int le = i / nel, mn = i - le * nel;
                     const int E = E0 + le;
                     double2 v = make_double2(0.0, 0.0);
@@ -228,7 +240,7 @@ grad_d_kernel(Problem p, DCfg c, const double2* __restrict__ gS_less, const doub
                     sW[i] = v;
                 }
                 __syncthreads();
-                for (int it = tid; it < kTEd * 3 * nel; it += kThreadsD) {  // P_i = dH_i^H W
+                for (int it = tid; it < c.te * 3 * nel; it += kThreadsD) {  // P_i = dH_i^H W
                     const int le = it / (3 * nel), rem = it - le * 3 * nel;
                     const int i = rem / nel, mn = rem - i * nel;
                     const int m = mn / Norb, n = mn - m * Norb;
@@ -238,7 +250,7 @@ grad_d_kernel(Problem p, DCfg c, const double2* __restrict__ gS_less, const doub
                     sP[it] = acc;
                 }
                 __syncthreads();
-                for (int it = tid; it < kTEd * 9 * nel; it += kThreadsD) {  // Q_ij = conj(c) P_i dH_j
+                for (int it = tid; it < c.te * 9 * nel; it += kThreadsD) {  // Q_ij = conj(c) P_i dH_j
                     const int le = it / (9 * nel), rem = it - le * 9 * nel;
                     const int ij = rem / nel, mn = rem - ij * nel;
                     const int i = ij / 3, j = ij - 3 * i;
@@ -254,10 +266,10 @@ grad_d_kernel(Problem p, DCfg c, const double2* __restrict__ gS_less, const doub
                     for (int sg = 0; sg < 2; ++sg) {
                         const int sigma = sg == 0 ? +1 : -1;
                         const int tau = sg == 0 ? t : 1 - t;
-                        const int wend = min(d.Nw, sigma > 0 ? E0 + kTEd - 1 : d.NE - 1 - E0);
+                        const int wend = min(d.Nw, sigma > 0 ? E0 + c.te - 1 : d.NE - 1 - E0);
                         for (int w0 = 0; w0 < wend; w0 += c.wc) {
                             const int wn = min(c.wc, wend - w0);
-                            const int rows = kTEd + wn - 1;
+                            const int rows = c.te + wn - 1;
                             const int Elo = sigma > 0 ? E0 - w0 - wn : E0 + w0 + 1;
                             __syncthreads();  // sQ complete; previous chunk done with sG / sPart
                             for (int i = tid; i < rows * nel; i += kThreadsD) {
@@ -272,7 +284,7 @@ grad_d_kernel(Problem p, DCfg c, const double2* __restrict__ gS_less, const doub
 #pragma unroll
                             for (int ij = 0; ij < 9; ++ij) acc[ij] = make_double2(0.0, 0.0);
                             if (active && wi < wn) {
-                                for (int le = 0; le < kTEd; ++le) {
+                                for (int le = 0; le < c.te; ++le) {
                                     const int row = sigma > 0 ? le + (wn - 1) - wi : le + wi;
                                     const double2* Gr = sG + (size_t)row * nel;
                                     const double2* Qr = sQ + (size_t)le * 9 * nel;
