@@ -123,6 +123,34 @@ SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* d
                   uint32_t flags, const double* gS_less, const double* gS_greater, double* g_dH, double* g_D_less,
                   double* g_D_greater, void* workspace, size_t ws_bytes, void* stream);
 
+/* Size of the library's static device scratch array used by sse_sigma_bwd_static. */
+#define SSE_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* sse_sigma_bwd_static -- sse_sigma_bwd for callers that cannot allocate device memory.
+ * (The paper has no counterpart: this is an interface convenience.)
+ * Callers such as a host application whose device memory belongs to its own allocator
+ * or pool, code that must not allocate on its hot path, or a foreign-language host that
+ * only passes through pointers it was given cannot call cudaMalloc to create the
+ * workspace sse_sigma_bwd needs. This entry point takes the same inputs and outputs
+ * (and writes the same gradients, FP64 mode only) but no workspace: its scratch (status
+ * word and per-bond partial gradients) lives in one static device array of
+ * SSE_STATIC_SCRATCH_BYTES that the library holds on every GPU that loads it, until the
+ * process exits. It calls no allocation routine.
+ * - Sizes whose sse_workspace_bytes(d, SSE_MODE_FP64, flags) exceeds
+ *   SSE_STATIC_SCRATCH_BYTES are rejected with SSE_ERR_WORKSPACE before any device work
+ *   (the array holds e.g. NA*NB*Nkz*6*Norb^2*16 bytes of partials + 256: NA=256, NB=4,
+ *   Norb=10, Nkz=5 fits; NA=1024, Nkz=7 does not).
+ * - The first call on a device looks up the array's device address on that device
+ *   (the current device); make that first call before any stream capture.
+ * - All calls share the one array and it keeps the last call's contents; the status
+ *   word is cleared by each call. Calls that overlap on the GPU (different streams,
+ *   different host threads) race on the array: order them on one stream. */
+SSE_API int sse_sigma_bwd_static(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                                 const double* D_greater, const double* G_less, const double* G_greater,
+                                 double scale, int mode, uint32_t flags, const double* gS_less,
+                                 const double* gS_greater, double* g_dH, double* g_D_less, double* g_D_greater,
+                                 void* stream);
+
 /* Static, NUL-terminated description of a status code (never NULL). */
 SSE_API const char* sse_strerror(int status);
 

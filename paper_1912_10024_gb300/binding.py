@@ -19,7 +19,8 @@ from . import build as _build
 SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3 = 0, 1, 2
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK = 1, 2
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3}
-EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_strerror")
+EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_strerror")
+SSE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class sse_dims(ctypes.Structure):
@@ -55,6 +56,8 @@ def load() -> ctypes.CDLL:
             lib.sse_sigma_bwd.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, vp, vp, vp,
                                           ctypes.c_size_t, vp]
             lib.sse_sigma_bwd.restype = i32
+            lib.sse_sigma_bwd_static.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, vp, vp, vp]
+            lib.sse_sigma_bwd_static.restype = i32
             lib.sse_strerror.argtypes = [i32]
             lib.sse_strerror.restype = ctypes.c_char_p
             _lib = lib
@@ -96,6 +99,16 @@ def sse_sigma_bwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, sc
                                     _p(G_greater), float(scale), int(mode), int(flags), _p(gS_less), _p(gS_greater),
                                     _p(g_dH), _p(g_D_less), _p(g_D_greater), _p(workspace), int(ws_bytes),
                                     _stream(stream)))
+
+
+def sse_sigma_bwd_static(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int,
+                         flags: int, gS_less, gS_greater, g_dH, g_D_less, g_D_greater, stream=None) -> int:
+    """sse_sigma_bwd without a workspace, for callers that cannot allocate device memory
+    (scratch in the library's static device array; see include/sse.h)."""
+    return int(load().sse_sigma_bwd_static(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater),
+                                           _p(G_less), _p(G_greater), float(scale), int(mode), int(flags),
+                                           _p(gS_less), _p(gS_greater), _p(g_dH), _p(g_D_less), _p(g_D_greater),
+                                           _stream(stream)))
 
 
 def sse_strerror(status: int) -> str:
