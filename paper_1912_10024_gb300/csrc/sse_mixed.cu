@@ -21,17 +21,26 @@
 //   BF16X3: x = hi + lo with hi = bf16(x), lo = bf16(x - hi); the K dimension
 //           holds three segments [G_hi | G_lo | G_hi] x [W_hi ; W_hi ; W_lo],
 //           so one accumulation gives hi*hi + lo*hi + hi*lo (lo*lo dropped).
-//   FP32 accumulation in TMEM within one qz slice; the slice is drained into
-//   FP64 registers (sum over qz in FP64), and the final multiply by dH_i and
-//   the sums over i and neighbours run in FP64.
+//   FP32 accumulation in TMEM within one qz slice; each slice is drained into
+//   FP64 registers (the sum over qz is FP64), and the final multiply by dH_i
+//   and the sums over i and neighbours run in FP64.
 //
 // Kernels: (1) per-(t,b) max |G| for the scale, (2) staging of G into split
 // planes laid out [t][kz][b][16-byte K chunk][row = E*Norb + m], (3) the
-// tcgen05 kernel: CTA = (tile of TE energies = TE*Norb <= 128 rows, kz, atom,
-// type); TMA (cp.async.bulk.tensor) loads each shifted window, out-of-range
-// rows are zero-filled by the TMA unit (energies outside [0, NE) contribute
-// nothing); the W tiles are formed in FP32 on the CUDA cores into shared
-// memory; one thread issues the MMAs; every wait is bounded.
+// tcgen05 kernel, persistent (one CTA per SM) and warp-specialised:
+//   warp 0     TMA producer: each (qz, sigma, 16-frequency) window of
+//              128 + 15*Norb rows, cp.async.bulk.tensor into a 2-stage ring;
+//              rows outside [0, NE*Norb) are zero-filled by the TMA unit
+//              (energies outside [0, NE) contribute nothing);
+//   warp 1     MMA issuer (one thread): tcgen05.mma M=128, N=64 into a
+//              2-buffer TMEM accumulator (one buffer per qz slice);
+//   warps 2-5  W producers: form each (sigma, qz, w) weight tile in FP32 from
+//              D and dH, split it, and write it K-major into a 4-stage ring;
+//   warps 6-9  epilogue: drain each slice with tcgen05.ld into FP64, then the
+//              FP64 final multiply and store, overlapping the next slice's MMAs.
+// The rings are mbarrier pipelines. Every wait is bounded: a wait that gives
+// up sets SSE_ERR_TIMEOUT's status bit and all later waits return at once, so
+// the kernel always terminates.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -44,17 +53,22 @@
 namespace sse {
 namespace {
 
-constexpr int kThreads = 128;  // 4 warps: TMEM lanes 0..127 = tile rows
-constexpr int kMaxNorb = 10;   // 6*Norb accumulator columns kept in registers
+constexpr int kMaxNorb = 10;   // 6*Norb accumulator columns kept in epilogue registers
 constexpr int kMaxCols = 6 * kMaxNorb;
-constexpr uint32_t kWaitIters = 1u << 26;  // bounded waits (about a second)
+constexpr int kYStride = kMaxCols + 1;  // doubles per FP64 accumulator row (odd: conflict-free rows)
+constexpr uint32_t kWaitIters = 1u << 22;  // bounded waits (well under a second of polling)
+constexpr int kThreads = 320;              // 10 warps
+constexpr int kBThread0 = 64, kEThread0 = 192, kRole = 128;
+constexpr int kBStages = 4;  // W-tile ring: stages of up to `tg` consecutive taps
+constexpr int kMaxItems = 5;   // W-tile items per producer thread and stage, TF32 (tg * 3 Norb^2 <= 5 * 128)
+constexpr int kItemsBf16 = 3;  // the same for BF16X3 (tg * 3 Norb ceil(Norb/2) <= 3 * 128)
 
 struct MixCfg {
-    int mode, Norb, nel, TE;
+    int mode, Norb, nel, TE, ntiles;
     int esz, kpad, nch, npad, kmma;  // element bytes, K per term, 16-B chunks per row, N, MMAs per term
-    int wc, wr, rb, nblk, wb;        // window: frequencies, rows (alloc), rows per TMA box, boxes, B tiles per batch
-    int tmem_cols, btile;
-    int off_B, off_D, off_Ah, off_A64, off_red, smem;
+    int wc, wr, rb, nblk;            // window: frequencies, rows (alloc), rows per TMA box, boxes per plane
+    int tmem_cols, acc_stride, btile, tg;  // TMEM columns, offset of the 2nd accumulator, W tile bytes, taps per W stage
+    int off_B, off_D, off_Ah, off_A64, off_Y, off_bar, smem;
     int nrows;                       // NE * Norb
 };
 
@@ -64,6 +78,7 @@ MixCfg make_cfg(const sse_dims& d, int mode) {
     c.Norb = d.Norb;
     c.nel = d.Norb * d.Norb;
     c.TE = 128 / d.Norb;
+    c.ntiles = (d.NE + c.TE - 1) / c.TE;
     c.esz = mode == SSE_MODE_BF16X3 ? 2 : 4;
     const int kraw = mode == SSE_MODE_BF16X3 ? 6 * d.Norb : 2 * d.Norb;
     const int kstep = mode == SSE_MODE_BF16X3 ? 16 : 8;  // K per tcgen05.mma
@@ -71,25 +86,28 @@ MixCfg make_cfg(const sse_dims& d, int mode) {
     c.kmma = c.kpad / kstep;
     c.nch = c.kpad * c.esz / 16;
     c.npad = (6 * d.Norb + 15) / 16 * 16;
-    c.tmem_cols = c.npad <= 32 ? 32 : (c.npad <= 64 ? 64 : 128);
+    c.tmem_cols = 2 * c.npad <= 32 ? 32 : (2 * c.npad <= 64 ? 64 : 128);
+    c.acc_stride = c.tmem_cols / 2;
     c.btile = c.npad * c.kpad * c.esz;
     c.nrows = d.NE * d.Norb;
-    c.wc = d.Nw < 32 ? d.Nw : 32;
+    c.wc = d.Nw < 16 ? d.Nw : 16;
     const int need = 128 + (c.wc - 1) * d.Norb;
     c.nblk = (need + 255) / 256;
     c.rb = ((need + c.nblk - 1) / c.nblk + 7) / 8 * 8;
     c.wr = c.rb * c.nblk;
-    c.wb = 4;
     const int win = c.nch * c.wr * 16;
-    const int bb = c.wb * c.btile;
-    const int yx = 128 * kMaxCols * 8;  // FP64 accumulator exchange for the final multiply (aliases win + B)
-    c.off_B = win;
-    const int reg0 = (win + bb > yx ? win + bb : yx);
-    c.off_D = (reg0 + 127) / 128 * 128;
-    c.off_Ah = c.off_D + 2 * d.Nw * 9 * 8;
-    c.off_A64 = (c.off_Ah + 3 * c.nel * 8 + 15) / 16 * 16;
-    c.off_red = c.off_A64 + 3 * c.nel * 16;
-    c.smem = c.off_red + 64 + 128;  // + alignment slack of the dynamic base
+    for (c.tg = 2; c.tg >= 1; c.tg /= 2) {  // largest W stage that fits next to the other buffers
+        c.off_B = 2 * win;
+        c.off_D = c.off_B + kBStages * c.tg * c.btile;
+        c.off_Ah = c.off_D + 2 * (2 * d.Nw * 9 * 8);  // two qz buffers of [2 sigma][Nw][9] float2
+        c.off_A64 = (c.off_Ah + 3 * c.nel * 8 + 15) / 16 * 16;
+        c.off_Y = c.off_A64 + 3 * c.nel * 16;
+        c.off_bar = (c.off_Y + 128 * kYStride * 8 + 7) / 8 * 8;
+        const int per_tile = mode == SSE_MODE_BF16X3 ? 3 * d.Norb * ((d.Norb + 1) / 2) : 3 * c.nel;
+        const int items = mode == SSE_MODE_BF16X3 ? kItemsBf16 : kMaxItems;
+        if (c.off_bar + 256 + 128 <= 227 * 1024 && c.tg * per_tile <= items * kRole) break;
+    }
+    c.smem = c.off_bar + 256 + 128;  // barriers and flags, + alignment slack of the dynamic base
     return c;
 }
 
@@ -122,11 +140,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
         : "r"(bar), "r"(phase)
         : "memory");
     return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (uint32_t it = 0; it < kWaitIters; ++it)
-        if (mbar_try_wait(bar, phase)) return true;
-    return false;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -178,6 +191,77 @@ __device__ __forceinline__ int floor_log2(float m) {
     int ex;
     frexpf(m, &ex);
     return ex - 1;
+}
+
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// Bounded wait; after any wait of the CTA has given up, waits return at once (results are then
+// discarded: the host reports SSE_ERR_TIMEOUT), so every role still runs its loops to the end.
+__device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned* status) {
+    if (*abort_flag) return;
+    for (uint32_t it = 0; it < kWaitIters; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    *abort_flag = 1;
+    atomicOr(status, DEV_TIMEOUT);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+struct Item {
+    int tile, k, a, t, E0, wend_p, wend_m;
+};
+__device__ __forceinline__ Item decode(int item, const sse_dims& d, const MixCfg& c) {
+    Item it;
+    it.tile = item % c.ntiles;
+    int r = item / c.ntiles;
+    it.k = r % d.Nkz;
+    r /= d.Nkz;
+    it.t = r & 1;
+    it.a = d.a_begin + (r >> 1);
+    it.E0 = it.tile * c.TE;
+    // frequencies whose shifted energy is off the grid for the whole tile contribute nothing
+    it.wend_p = max(0, min(d.Nw, it.E0 + c.TE - 1));
+    it.wend_m = max(0, min(d.Nw, d.NE - 1 - it.E0));
+    return it;
+}
+
+// Weight-scale exponent of every bond (a, s): one warp per bond takes max |Re|, |Im| over
+// dH(a,s) and D^<, D^>(., ., a, s); |Re W|, |Im W| <= sum_j |D_ij| |dH_j| <= 2 * 3 * dmax * amax.
+__global__ void wexp_kernel(Problem p, int* __restrict__ ew) {
+    const sse_dims& d = p.d;
+    const int nel = d.Norb * d.Norb;
+    const int nb = (d.a_end - d.a_begin) * d.NB;
+    const int lane = threadIdx.x & 31;
+    for (int bond = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; bond < nb; bond += (gridDim.x * blockDim.x) >> 5) {
+        const int a = d.a_begin + bond / d.NB, s = bond % d.NB;
+        const double2* Ag = p.dH + ((size_t)a * d.NB + s) * 3 * nel;
+        float amax = 0.f, dmax = 0.f;
+        for (int i = lane; i < 3 * nel; i += 32) {
+            const double2 v = Ag[i];
+            amax = fmaxf(amax, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
+        }
+        for (int i = lane; i < 2 * d.Nqz * d.Nw * 9; i += 32) {
+            const int tau = i / (d.Nqz * d.Nw * 9), r = i - tau * d.Nqz * d.Nw * 9;
+            const int qw = r / 9, ij = r - qw * 9;
+            const double2 v = p.D[tau][(((size_t)qw * d.NA + a) * d.NB + s) * 9 + ij];
+            dmax = fmaxf(dmax, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        }
+        if (lane == 0) ew[bond] = floor_log2(6.f * amax * dmax) + 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -251,284 +335,475 @@ __global__ void stage_kernel(sse_dims d, MixCfg c, const double2* __restrict__ G
 }
 
 // ---------------------------------------------------------------------------
-// tensor-core kernel
+// tensor-core kernel (persistent, warp-specialised)
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c, const unsigned* __restrict__ gmax,
-                   double2* __restrict__ S_less, double2* __restrict__ S_greater, unsigned* __restrict__ status) {
+                   const int* __restrict__ ew_bond, double2* __restrict__ S_less, double2* __restrict__ S_greater,
+                   unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // TMA destinations need 128-byte alignment: round the dynamic base up (the launch adds 128 bytes)
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
-    __shared__ __align__(8) uint64_t bars[2];  // [0] TMA window, [1] MMA batch done
-    __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
     const sse_dims& d = p.d;
     const int N = d.Norb, nel = c.nel, TE = c.TE;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int E0 = blockIdx.x * TE;
-    const int k = blockIdx.y;
-    const int a = d.a_begin + (int)(blockIdx.z >> 1);
-    const int t = (int)(blockIdx.z & 1);
-    const int row = tid;  // tile row = TMEM lane
-    const int le = row / N, mrow = row - le * N;
-    const bool row_ok = le < TE && E0 + le < d.NE;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nA = d.a_end - d.a_begin;
+    const int nitems = c.ntiles * d.Nkz * 2 * nA;
 
-    unsigned char* sWin = smem;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + c.off_bar);
+    // barriers: win_full[2] win_empty[2] b_full[4] b_empty[4] acc_full[2] acc_empty[2] mma_done
+    const uint32_t bar0 = smem_u32(bar);
+    auto B_ = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+    const int WF = 0, WE = 2, BF = 4, BE = 8, AF = 12, AE = 14, MD = 16;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + c.off_bar + 17 * 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + c.off_bar + 17 * 8 + 4);
+
     unsigned char* sB = smem + c.off_B;
-    float2* sDw = reinterpret_cast<float2*>(smem + c.off_D);      // [2 sigma][Nw][9] (unscaled weights)
-    float2* sAh = reinterpret_cast<float2*>(smem + c.off_Ah);     // [3][l][n] = conj(dH_j[n][l])
+    float2* sD = reinterpret_cast<float2*>(smem + c.off_D);        // [2 qz parity][2 sigma][Nw][9] weights
+    float2* sAh = reinterpret_cast<float2*>(smem + c.off_Ah);      // [3][n][l] = conj(dH_j[n][l])
     double2* sA64 = reinterpret_cast<double2*>(smem + c.off_A64);  // [3][nel] dH (FP64)
-    unsigned* sRed = reinterpret_cast<unsigned*>(smem + c.off_red);
-    double* sY = reinterpret_cast<double*>(smem);                  // [128][kMaxCols] (final multiply)
-    const uint32_t bar_tma = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+    double* sY = reinterpret_cast<double*>(smem + c.off_Y);        // [128][kYStride] FP64 accumulators
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+    if (tid == 0) {
+        mbar_init(B_(WF + 0), 1);
+        mbar_init(B_(WF + 1), 1);
+        mbar_init(B_(WE + 0), 1);
+        mbar_init(B_(WE + 1), 1);
+        for (int i = 0; i < kBStages; ++i) {
+            mbar_init(B_(BF + i), kRole);
+            mbar_init(B_(BE + i), 1);
+        }
+        mbar_init(B_(AF + 0), 1);
+        mbar_init(B_(AF + 1), 1);
+        mbar_init(B_(AE + 0), kRole);
+        mbar_init(B_(AE + 1), kRole);
+        mbar_init(B_(MD), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(c.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        mbar_init(bar_tma, 1);
-        mbar_init(bar_mma, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        abort_flag = 0;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    // padding entries of every W tile must be zero; the producers never write them
+    for (int i = tid; i < kBStages * c.tg * c.btile / 16; i += kThreads)
+        reinterpret_cast<uint4*>(sB)[i] = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_slot;
-    uint32_t ph_tma = 0, ph_mma = 0;
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
 
-    const uint32_t idesc = (1u << 4) | (MODE == SSE_MODE_BF16X3 ? (1u << 7) | (1u << 10) : (2u << 7) | (2u << 10)) |
-                           ((uint32_t)(c.npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    const uint32_t win_addr = smem_u32(sWin), b_addr = smem_u32(sB);
-    const uint32_t plane = (uint32_t)c.wr * 16, bplane = (uint32_t)c.npad * 16;
-    const int ncols = 6 * N;
-
-    double2 sig[kMaxNorb];
-#pragma unroll
-    for (int n = 0; n < kMaxNorb; ++n) sig[n] = make_double2(0.0, 0.0);
-
-    for (int s = 0; s < d.NB; ++s) {
-        const int b = p.nbr[(size_t)a * d.NB + s];
-        if (b < 0 || b >= d.NA) {  // uniform per CTA
-            if (tid == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
-            continue;
-        }
-        __syncthreads();  // previous slot's final multiply is done with sY / sA64
-        // the B region is reused: padding entries of every tile must be zero
-        for (int i = tid; i < c.wb * c.btile / 16; i += kThreads)
-            reinterpret_cast<uint4*>(sB)[i] = make_uint4(0, 0, 0, 0);
-        const double2* Ag = p.dH + ((size_t)a * d.NB + s) * 3 * nel;
-        float amax = 0.f;
-        for (int i = tid; i < 3 * nel; i += kThreads) {
-            const double2 v = Ag[i];
-            sA64[i] = v;
-            const int j = i / nel, e = i - j * nel, nn = e / N, l = e - nn * N;
-            sAh[(j * N + l) * N + nn] = make_float2((float)v.x, -(float)v.y);
-            amax = fmaxf(amax, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
-        }
-        float dmax = 0.f;
-        for (int i = tid; i < 2 * d.Nqz * d.Nw * 9; i += kThreads) {
-            const int tau = i / (d.Nqz * d.Nw * 9), r = i - tau * d.Nqz * d.Nw * 9;
-            const int qw = r / 9, ij = r - qw * 9;
-            const double2 v = p.D[tau][(((size_t)qw * d.NA + a) * d.NB + s) * 9 + ij];
-            dmax = fmaxf(dmax, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
-        }
-        if (tid == 0) { sRed[0] = 0; sRed[1] = 0; }
-        __syncthreads();
-        atomicMax(&sRed[0], __float_as_uint(amax));
-        atomicMax(&sRed[1], __float_as_uint(dmax));
-        __syncthreads();
-        // |W_i[l][n]| <= sum_j |D_ij| |dH_j[n][l]| <= 2 * 3 * dmax * amax (re and im parts)
-        const float wbound = 6.f * __uint_as_float(sRed[0]) * __uint_as_float(sRed[1]);
-        const int ew = floor_log2(wbound) + 1;
-        const float sW = ldexpf(1.f, -ew);
-        const int eg = floor_log2(__uint_as_float(gmax[t * d.NA + b]));
-        const double unscale = ldexp(1.0, ew + eg);  // 1 / (sG * sW)
-
-        double Y[kMaxCols];
-#pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) Y[j] = 0.0;
-
-        for (int q = 0; q < d.Nqz; ++q) {
-            const int kp = ((k - q) % d.Nkz + d.Nkz) % d.Nkz;
-            const int slice = (t * d.Nkz + kp) * d.NA + b;
-            __syncthreads();  // all MMAs of the previous slice are complete (waited below)
-            for (int i = tid; i < 2 * d.Nw * 9; i += kThreads) {
-                const int sg = i / (d.Nw * 9), r = i - sg * d.Nw * 9;
-                const int w = r / 9, ij = r - w * 9;
-                const int tau = sg == 0 ? t : 1 - t;
-                const double2 v = p.D[tau][((((size_t)q * d.Nw + w) * d.NA + a) * d.NB + s) * 9 + ij];
-                sDw[i] = make_float2((float)v.x, (float)v.y);
-            }
-            __syncthreads();
-            uint32_t acc_flag = 0;
-            for (int sg = 0; sg < 2; ++sg) {
-                const int sigma = sg == 0 ? +1 : -1;
-                const int wend = min(d.Nw, sigma > 0 ? E0 + TE - 1 : d.NE - 1 - E0);
-                for (int w0 = 0; w0 < wend; w0 += c.wc) {
-                    const int wn = min(c.wc, wend - w0);
-                    const int r0 = E0 * N;
-                    const int start = sigma > 0 ? r0 - (w0 + wn) * N : r0 + (w0 + 1) * N;
-                    if (tid == 0) {  // the window is free: the last batch of MMAs was waited for
-                        mbar_expect_tx(bar_tma, (uint32_t)(c.nch * c.wr * 16));
-                        for (int ch = 0; ch < c.nch; ++ch)
-                            for (int bk = 0; bk < c.nblk; ++bk)
-                                tma_load_3d(win_addr + (uint32_t)(ch * c.wr + bk * c.rb) * 16, &tmap, 0,
-                                            start + bk * c.rb, slice * c.nch + ch, bar_tma);
-                    }
-                    for (int wb0 = 0; wb0 < wn; wb0 += c.wb) {
-                        const int nb = min(c.wb, wn - wb0);
-                        // W tiles (B operand, K-major: row nn = (i*N + n)*2 + re/im, column kk of the A row)
-                        for (int it = tid; it < nb * 3 * nel; it += kThreads) {
-                            const int wi = it / (3 * nel), rem = it - wi * 3 * nel;
-                            const int i = rem / nel, e = rem - i * nel, l = e / N, n = e - l * N;
-                            const float2* Dw = sDw + ((size_t)sg * d.Nw + w0 + wb0 + wi) * 9 + i * 3;
-                            float wr = 0.f, wim = 0.f;
-#pragma unroll
-                            for (int j = 0; j < 3; ++j) {
-                                const float2 dv = Dw[j];
-                                const float2 ah = sAh[(j * N + l) * N + n];
-                                wr = fmaf(dv.x, ah.x, fmaf(-dv.y, ah.y, wr));
-                                wim = fmaf(dv.x, ah.y, fmaf(dv.y, ah.x, wim));
-                            }
-                            wr *= sW;
-                            wim *= sW;
-                            unsigned char* tile = sB + (size_t)wi * c.btile;
-                            const int nre = (i * N + n) * 2, nim = nre + 1;
-                            if (MODE == SSE_MODE_BF16X3) {
-                                const __nv_bfloat16 hr = __float2bfloat16_rn(wr), hi = __float2bfloat16_rn(wim);
-                                const __nv_bfloat16 lr = __float2bfloat16_rn(wr - __bfloat162float(hr));
-                                const __nv_bfloat16 li = __float2bfloat16_rn(wim - __bfloat162float(hi));
-                                const __nv_bfloat16 nhi = __hneg(hi), nli = __hneg(li);
-                                auto put = [&](int nn, int kk, __nv_bfloat16 v) {
-                                    *reinterpret_cast<__nv_bfloat16*>(tile + (kk >> 3) * bplane + nn * 16 +
-                                                                      (kk & 7) * 2) = v;
-                                };
-#pragma unroll
-                                for (int seg = 0; seg < 3; ++seg) {
-                                    const __nv_bfloat16 vr = seg < 2 ? hr : lr, vi = seg < 2 ? hi : li;
-                                    const __nv_bfloat16 nvi = seg < 2 ? nhi : nli;
-                                    const int kr = seg * 2 * N + l, ki = kr + N;
-                                    put(nre, kr, vr);
-                                    put(nre, ki, nvi);
-                                    put(nim, kr, vi);
-                                    put(nim, ki, vr);
+    if (warp == 0) {
+        // ------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            const uint32_t win_bytes = (uint32_t)(c.nch * c.wr * 16);
+            uint32_t wcnt = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+                const Item it = decode(item, d, c);
+                if (it.wend_p + it.wend_m == 0) continue;
+                for (int s = 0; s < d.NB; ++s) {
+                    const int b = p.nbr[(size_t)it.a * d.NB + s];
+                    if (b < 0 || b >= d.NA) continue;
+                    for (int q = 0; q < d.Nqz; ++q) {
+                        const int kp = ((it.k - q) % d.Nkz + d.Nkz) % d.Nkz;
+                        const int slice = (it.t * d.Nkz + kp) * d.NA + b;
+                        for (int sg = 0; sg < 2; ++sg) {
+                            const int wend = sg ? it.wend_m : it.wend_p;
+                            for (int w0 = 0; w0 < wend; w0 += c.wc) {
+                                const int wn = min(c.wc, wend - w0);
+                                const int r0 = it.E0 * N;
+                                const int start = sg == 0 ? r0 - (w0 + wn) * N : r0 + (w0 + 1) * N;
+                                const int st = (int)(wcnt & 1);
+                                wait_or_abort(B_(WE + st), ((wcnt >> 1) & 1) ^ 1, abort_flag, status);
+                                if (!*abort_flag) {
+                                    const uint32_t dst = smem_u32(smem) + (uint32_t)st * win_bytes;
+                                    mbar_expect_tx(B_(WF + st), win_bytes);
+                                    for (int ch = 0; ch < c.nch; ++ch)
+                                        for (int bk = 0; bk < c.nblk; ++bk)
+                                            tma_load_3d(dst + (uint32_t)(ch * c.wr + bk * c.rb) * 16, &tmap, 0,
+                                                        start + bk * c.rb, slice * c.nch + ch, B_(WF + st));
                                 }
-                            } else {
-                                const float vr = to_tf32(wr), vi = to_tf32(wim);
-                                auto put = [&](int nn, int kk, float v) {
-                                    *reinterpret_cast<float*>(tile + (kk >> 2) * bplane + nn * 16 + (kk & 3) * 4) = v;
-                                };
-                                put(nre, l, vr);
-                                put(nre, N + l, -vi);
-                                put(nim, l, vi);
-                                put(nim, N + l, vr);
+                                ++wcnt;
                             }
                         }
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        __syncthreads();
-                        int bad = 0;
-                        if (tid == 0) {
-                            if (wb0 == 0) bad = !mbar_wait(bar_tma, ph_tma);
-                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                            if (!bad) {
-                                for (int wi = 0; wi < nb; ++wi) {
-                                    const int w = w0 + wb0 + wi;
-                                    const int roff = sigma > 0 ? (w0 + wn - w - 1) * N : (w - w0) * N;
-                                    for (int kc = 0; kc < c.kmma; ++kc) {
-                                        const uint64_t da =
-                                            smem_desc(win_addr + (uint32_t)(2 * kc) * plane + (uint32_t)roff * 16, plane, 128);
-                                        const uint64_t db =
-                                            smem_desc(b_addr + (uint32_t)(wi * c.btile) + (uint32_t)(2 * kc) * bplane, bplane, 128);
-                                        umma<MODE>(tmem, da, db, idesc, acc_flag);
-                                        acc_flag = 1;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) |
+                                   (MODE == SSE_MODE_BF16X3 ? (1u << 7) | (1u << 10) : (2u << 7) | (2u << 10)) |
+                                   ((uint32_t)(c.npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            const uint32_t win_bytes = (uint32_t)(c.nch * c.wr * 16);
+            const uint32_t plane = (uint32_t)c.wr * 16, bplane = (uint32_t)c.npad * 16;
+            const uint32_t win0 = smem_u32(smem), b0 = smem_u32(sB);
+            uint32_t wcnt = 0, bcnt = 0, acnt = 0;
+            for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+                const Item it = decode(item, d, c);
+                if (it.wend_p + it.wend_m == 0) continue;
+                for (int s = 0; s < d.NB; ++s) {
+                    const int b = p.nbr[(size_t)it.a * d.NB + s];
+                    if (b < 0 || b >= d.NA) continue;
+                    for (int q = 0; q < d.Nqz; ++q) {
+                        const int ab = (int)(acnt & 1);
+                        wait_or_abort(B_(AE + ab), ((acnt >> 1) & 1) ^ 1, abort_flag, status);
+                        tc_fence_after();
+                        const uint32_t dtm = tmem + (uint32_t)(ab * c.acc_stride);
+                        uint32_t acc = 0;
+                        for (int sg = 0; sg < 2; ++sg) {
+                            const int wend = sg ? it.wend_m : it.wend_p;
+                            for (int w0 = 0; w0 < wend; w0 += c.wc) {
+                                const int wn = min(c.wc, wend - w0);
+                                const int st = (int)(wcnt & 1);
+                                wait_or_abort(B_(WF + st), (wcnt >> 1) & 1, abort_flag, status);
+                                tc_fence_after();
+                                for (int g0 = 0; g0 < wn; g0 += c.tg) {
+                                    const int ng = min(c.tg, wn - g0);
+                                    const int bs = (int)(bcnt % kBStages);
+                                    wait_or_abort(B_(BF + bs), (bcnt / kBStages) & 1, abort_flag, status);
+                                    tc_fence_after();
+                                    if (!*abort_flag) {
+                                        for (int gi = 0; gi < ng; ++gi) {
+                                            const int wi = g0 + gi;
+                                            const int roff = sg == 0 ? (wn - 1 - wi) * N : wi * N;
+                                            const uint32_t bt = b0 + (uint32_t)((bs * c.tg + gi) * c.btile);
+                                            for (int kc = 0; kc < c.kmma; ++kc) {
+                                                const uint64_t da = smem_desc(win0 + (uint32_t)st * win_bytes +
+                                                                                  (uint32_t)(2 * kc) * plane + (uint32_t)roff * 16,
+                                                                              plane, 128);
+                                                const uint64_t db = smem_desc(bt + (uint32_t)(2 * kc) * bplane, bplane, 128);
+                                                umma<MODE>(dtm, da, db, idesc, acc);
+                                                acc = 1;
+                                            }
+                                        }
+                                    }
+                                    umma_commit(B_(BE + bs));  // the W stage is free once these MMAs are done
+                                    ++bcnt;
+                                }
+                                umma_commit(B_(WE + st));  // the window stage is free
+                                ++wcnt;
+                            }
+                        }
+                        umma_commit(B_(AF + ab));  // the slice is complete in TMEM
+                        ++acnt;
+                    }
+                }
+            }
+            umma_commit(B_(MD));
+            wait_or_abort(B_(MD), 0, abort_flag, status);  // nothing in flight when TMEM is released
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------------------- W-tile producers
+        const int rt = tid - kBThread0;
+        const uint32_t bplane = (uint32_t)c.npad * 16;
+        const int dq = 2 * d.Nw * 9;  // float2 per qz buffer
+        // The (tile, i, n, l) items of a full stage are the same for every stage: decode this
+        // thread's items once (packed gi | i << 4 | n << 8 | l << 12; -1 = none).
+        const int P2 = (N + 1) / 2;
+        const int per_tile = MODE == SSE_MODE_BF16X3 ? 3 * N * P2 : 3 * nel;
+        int code[kMaxItems];
+#pragma unroll
+        for (int k = 0; k < kMaxItems; ++k) {
+            const int e = rt + k * kRole;
+            code[k] = -1;
+            if (e < c.tg * per_tile) {
+                const int gi = e / per_tile, r = e - gi * per_tile;
+                int i, n, l;
+                if (MODE == SSE_MODE_BF16X3) {
+                    i = r / (N * P2);
+                    const int r2 = r - i * N * P2;
+                    n = r2 / P2;
+                    l = 2 * (r2 - n * P2);
+                } else {
+                    i = r / nel;
+                    const int r2 = r - i * nel;
+                    n = r2 / N;
+                    l = r2 - n * N;
+                }
+                code[k] = gi | (i << 4) | (n << 8) | (l << 12);
+            }
+        }
+        uint32_t bcnt = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            const Item it = decode(item, d, c);
+            if (it.wend_p + it.wend_m == 0) continue;
+            for (int s = 0; s < d.NB; ++s) {
+                const int b = p.nbr[(size_t)it.a * d.NB + s];
+                if (b < 0 || b >= d.NA) continue;
+                const float sW = ldexpf(1.f, -ew_bond[(it.a - d.a_begin) * d.NB + s]);
+                const size_t dbase = ((size_t)it.a * d.NB + s) * 9;      // + ((q*Nw + w)*NA*NB)*9 + ij
+                const size_t dstride_w = (size_t)d.NA * d.NB * 9;
+                auto d_index = [&](int q, int i, int& tau) -> size_t {   // i in [0, 2*Nw*9): (sigma, w, ij)
+                    const int sg = i / (d.Nw * 9), r = i - sg * d.Nw * 9;
+                    const int w = r / 9, ij = r - w * 9;
+                    tau = sg == 0 ? it.t : 1 - it.t;
+                    return dbase + ((size_t)q * d.Nw + w) * dstride_w + ij;
+                };
+                named_bar(1, kRole);  // the previous slot's sAh / sD are no longer read
+                const double2* Ag = p.dH + ((size_t)it.a * d.NB + s) * 3 * nel;
+                for (int i = rt; i < 3 * nel; i += kRole) {  // i = (j, n, l): conj(dH_j[n][l]) stored at [j][n][l]
+                    const double2 v = Ag[i];
+                    sAh[i] = make_float2((float)v.x, -(float)v.y);
+                }
+                for (int i = rt; i < dq; i += kRole) {
+                    int tau;
+                    const size_t o = d_index(0, i, tau);
+                    const double2 dv = p.D[tau][o];
+                    sD[i] = make_float2((float)dv.x, (float)dv.y);
+                }
+                named_bar(1, kRole);
+                for (int q = 0; q < d.Nqz; ++q) {
+                    const float2* sDq = sD + (size_t)(q & 1) * dq;
+                    // prefetch the next qz's weights into registers while this qz's tiles are made
+                    constexpr int kPre = 8;
+                    double2 pre[kPre];
+                    const bool more = q + 1 < d.Nqz;
+#pragma unroll
+                    for (int u = 0; u < kPre; ++u) {
+                        const int i = rt + u * kRole;
+                        if (more && i < dq) {
+                            int tau;
+                            const size_t o = d_index(q + 1, i, tau);
+                            pre[u] = p.D[tau][o];
+                        }
+                    }
+                    for (int sg = 0; sg < 2; ++sg) {
+                        const int wend = sg ? it.wend_m : it.wend_p;
+                        for (int w0 = 0; w0 < wend; w0 += c.wc) {
+                            const int wn = min(c.wc, wend - w0);
+                            for (int g0 = 0; g0 < wn; g0 += c.tg) {
+                                const int ng = min(c.tg, wn - g0);
+                                const int bs = (int)(bcnt % kBStages);
+                                wait_or_abort(B_(BE + bs), ((bcnt / kBStages) & 1) ^ 1, abort_flag, status);
+                                unsigned char* stage = sB + (size_t)bs * c.tg * c.btile;
+                                const float2* Dst = sDq + ((size_t)sg * d.Nw + w0 + g0) * 9;
+                                if (MODE == SSE_MODE_BF16X3) {
+#pragma unroll
+                                    for (int k = 0; k < kItemsBf16; ++k) {
+                                        const int cd = code[k];
+                                        if (cd < 0 || (cd & 15) >= ng) continue;
+                                        const int gi = cd & 15, i = (cd >> 4) & 15, n = (cd >> 8) & 15, l0 = cd >> 12;
+                                        const bool two = l0 + 1 < N;
+                                        const int l1 = two ? l0 + 1 : l0;
+                                        const float2* Dw = Dst + gi * 9 + i * 3;
+                                        float wr0 = 0.f, wi0 = 0.f, wr1 = 0.f, wi1 = 0.f;
+#pragma unroll
+                                        for (int j = 0; j < 3; ++j) {
+                                            const float2 dv = Dw[j];
+                                            float2 a0, a1;
+                                            if ((N & 1) == 0) {  // l0 even: the pair is one 16-byte load
+                                                const float4 a01 = *reinterpret_cast<const float4*>(sAh + (j * N + n) * N + l0);
+                                                a0 = make_float2(a01.x, a01.y);
+                                                a1 = make_float2(a01.z, a01.w);
+                                            } else {
+                                                a0 = sAh[(j * N + n) * N + l0];
+                                                a1 = sAh[(j * N + n) * N + l1];
+                                            }
+                                            wr0 = fmaf(dv.x, a0.x, fmaf(-dv.y, a0.y, wr0));
+                                            wi0 = fmaf(dv.x, a0.y, fmaf(dv.y, a0.x, wi0));
+                                            wr1 = fmaf(dv.x, a1.x, fmaf(-dv.y, a1.y, wr1));
+                                            wi1 = fmaf(dv.x, a1.y, fmaf(dv.y, a1.x, wi1));
+                                        }
+                                        wr0 *= sW; wi0 *= sW; wr1 *= sW; wi1 *= sW;
+                                        const __nv_bfloat16 hr0 = __float2bfloat16_rn(wr0), hi0 = __float2bfloat16_rn(wi0);
+                                        const __nv_bfloat16 hr1 = __float2bfloat16_rn(wr1), hi1 = __float2bfloat16_rn(wi1);
+                                        const __nv_bfloat16 lr0 = __float2bfloat16_rn(wr0 - __bfloat162float(hr0));
+                                        const __nv_bfloat16 li0 = __float2bfloat16_rn(wi0 - __bfloat162float(hi0));
+                                        const __nv_bfloat16 lr1 = __float2bfloat16_rn(wr1 - __bfloat162float(hr1));
+                                        const __nv_bfloat16 li1 = __float2bfloat16_rn(wi1 - __bfloat162float(hi1));
+                                        unsigned char* tile = stage + (size_t)gi * c.btile;
+                                        const int nre = (i * N + n) * 2, nim = nre + 1;
+                                        if ((N & 1) == 0) {  // (l0, l0+1) is an aligned bf16 pair inside one chunk
+                                            const uint32_t phr = pack_bf16x2(hr0, hr1), phi = pack_bf16x2(hi0, hi1);
+                                            const uint32_t plr = pack_bf16x2(lr0, lr1), pli = pack_bf16x2(li0, li1);
+#pragma unroll
+                                            for (int seg = 0; seg < 3; ++seg) {
+                                                const uint32_t pr = seg < 2 ? phr : plr, pi = seg < 2 ? phi : pli;
+                                                const int kr = seg * 2 * N + l0, ki = kr + N;
+                                                unsigned char* br = tile + (kr >> 3) * bplane + (kr & 7) * 2;
+                                                unsigned char* bi = tile + (ki >> 3) * bplane + (ki & 7) * 2;
+                                                *reinterpret_cast<uint32_t*>(br + nre * 16) = pr;
+                                                *reinterpret_cast<uint32_t*>(bi + nre * 16) = pi ^ 0x80008000u;  // -Im
+                                                *reinterpret_cast<uint32_t*>(br + nim * 16) = pi;
+                                                *reinterpret_cast<uint32_t*>(bi + nim * 16) = pr;
+                                            }
+                                        } else {
+                                            const __nv_bfloat16 vr[2][2] = {{hr0, hr1}, {lr0, lr1}};
+                                            const __nv_bfloat16 vi[2][2] = {{hi0, hi1}, {li0, li1}};
+#pragma unroll
+                                            for (int u = 0; u < 2; ++u) {
+                                                if (u == 1 && !two) break;
+#pragma unroll
+                                                for (int seg = 0; seg < 3; ++seg) {
+                                                    const int h = seg < 2 ? 0 : 1;
+                                                    const int kr = seg * 2 * N + l0 + u, ki = kr + N;
+                                                    auto at = [&](int nn, int kk) {
+                                                        return reinterpret_cast<__nv_bfloat16*>(tile + (kk >> 3) * bplane + nn * 16 + (kk & 7) * 2);
+                                                    };
+                                                    *at(nre, kr) = vr[h][u];
+                                                    *at(nre, ki) = __hneg(vi[h][u]);
+                                                    *at(nim, kr) = vi[h][u];
+                                                    *at(nim, ki) = vr[h][u];
+                                                }
+                                            }
+                                        }
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int k = 0; k < kMaxItems; ++k) {
+                                        const int cd = code[k];
+                                        if (cd < 0 || (cd & 15) >= ng) continue;
+                                        const int gi = cd & 15, i = (cd >> 4) & 15, n = (cd >> 8) & 15, l = cd >> 12;
+                                        const float2* Dw = Dst + gi * 9 + i * 3;
+                                        float wr = 0.f, wim = 0.f;
+#pragma unroll
+                                        for (int j = 0; j < 3; ++j) {
+                                            const float2 dv = Dw[j];
+                                            const float2 ah = sAh[(j * N + n) * N + l];
+                                            wr = fmaf(dv.x, ah.x, fmaf(-dv.y, ah.y, wr));
+                                            wim = fmaf(dv.x, ah.y, fmaf(dv.y, ah.x, wim));
+                                        }
+                                        const float vr = to_tf32(wr * sW), vi = to_tf32(wim * sW);
+                                        unsigned char* tile = stage + (size_t)gi * c.btile;
+                                        const int nre = (i * N + n) * 2, nim = nre + 1;
+                                        auto at = [&](int nn, int kk) {
+                                            return reinterpret_cast<float*>(tile + (kk >> 2) * bplane + nn * 16 + (kk & 3) * 4);
+                                        };
+                                        *at(nre, l) = vr;
+                                        *at(nre, N + l) = -vi;
+                                        *at(nim, l) = vi;
+                                        *at(nim, N + l) = vr;
                                     }
                                 }
-                                umma_commit(bar_mma);
+                                fence_async_smem();
+                                mbar_arrive(B_(BF + bs));
+                                ++bcnt;
                             }
                         }
-                        if (!bad) bad = !mbar_wait(bar_mma, ph_mma);
-                        ph_mma ^= 1;
-                        if (__syncthreads_or(bad)) {
-                            if (tid == 0) atomicOr(status, DEV_TIMEOUT);
-                            goto cleanup;
+                    }
+                    if (more) {
+                        float2* nxt = sD + (size_t)((q + 1) & 1) * dq;
+#pragma unroll
+                        for (int u = 0; u < kPre; ++u) {
+                            const int i = rt + u * kRole;
+                            if (i < dq) nxt[i] = make_float2((float)pre[u].x, (float)pre[u].y);
                         }
-                        acc_flag = 1;  // every later MMA of this slice accumulates
+                        for (int i = rt + kPre * kRole; i < dq; i += kRole) {  // Nw > 56: the rest directly
+                            int tau;
+                            const size_t o = d_index(q + 1, i, tau);
+                            const double2 dv = p.D[tau][o];
+                            nxt[i] = make_float2((float)dv.x, (float)dv.y);
+                        }
                     }
-                    ph_tma ^= 1;
+                    named_bar(1, kRole);  // next qz's weights are in place; this qz's buffer is free
                 }
-            }
-            // drain the slice: FP32 TMEM -> FP64 registers, undo the scales
-            if (acc_flag) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (int c0 = 0; c0 < kMaxCols; c0 += 16) {
-                    if (c0 < ncols) {
-                        float v[16];
-                        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (c0 + j < kMaxCols) Y[c0 + j] += (double)v[j] * unscale;
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             }
         }
-        // final multiply in FP64: sig[n'] += sum_i sum_l dH_i[m][l] Y_i[(le, l)][n']
-        __syncthreads();  // window / B regions are free (aliased by sY)
+    } else {
+        // ------------------------------------------------------------- epilogue
+        const int rt = tid - kEThread0;
+        const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row = quad * 32 + lane;
+        const int le = row / N, mrow = row - le * N;
+        const double sc = p.scale;
+        const bool sym = (p.flags & SSE_FLAG_SYMMETRIZE) != 0;
+        uint32_t acnt = 0;
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+            const Item it = decode(item, d, c);
+            const bool any = it.wend_p + it.wend_m > 0;
+            const bool row_ok = le < TE && it.E0 + le < d.NE;
+            double2 sig[kMaxNorb];
 #pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) sY[(size_t)row * kMaxCols + j] = Y[j];
-        __syncthreads();
-        if (row_ok) {
-            for (int i = 0; i < 3; ++i)
-                for (int l = 0; l < N; ++l) {
-                    const double2 A = sA64[i * nel + mrow * N + l];
-                    const double* Yr = sY + (size_t)(le * N + l) * kMaxCols + i * N * 2;
+            for (int n = 0; n < kMaxNorb; ++n) sig[n] = make_double2(0.0, 0.0);
+            for (int s = 0; s < d.NB; ++s) {
+                const int b = p.nbr[(size_t)it.a * d.NB + s];
+                if (b < 0 || b >= d.NA) {
+                    if (rt == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
+                    continue;
+                }
+                if (!any) continue;
+                const int ew = ew_bond[(it.a - d.a_begin) * d.NB + s];
+                named_bar(2, kRole);  // the previous slot's final multiply is done with sA64 / sY
+                const int eg = floor_log2(__uint_as_float(gmax[it.t * d.NA + b]));
+                const double unscale = ldexp(1.0, ew + eg);  // 1 / (sG * sW)
+                const double2* Ag = p.dH + ((size_t)it.a * d.NB + s) * 3 * nel;
+                for (int i = rt; i < 3 * nel; i += kRole) sA64[i] = Ag[i];
+                double* Yrow = sY + (size_t)row * kYStride;  // this thread's FP64 accumulator row
+                for (int j = 0; j < kMaxCols; ++j) Yrow[j] = 0.0;
+                for (int q = 0; q < d.Nqz; ++q) {
+                    const int ab = (int)(acnt & 1);
+                    wait_or_abort(B_(AF + ab), (acnt >> 1) & 1, abort_flag, status);
+                    tc_fence_after();
+                    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * c.acc_stride);
 #pragma unroll
-                    for (int n = 0; n < kMaxNorb; ++n)
-                        if (n < N) {
-                            const double yr = Yr[2 * n], yi = Yr[2 * n + 1];
-                            sig[n].x = fma(A.x, yr, fma(-A.y, yi, sig[n].x));
-                            sig[n].y = fma(A.x, yi, fma(A.y, yr, sig[n].y));
+                    for (int c0 = 0; c0 < kMaxCols; c0 += 16) {
+                        if (c0 < 6 * N) {
+                            float v[16];
+                            tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < kMaxCols) Yrow[c0 + j] = fma((double)v[j], unscale, Yrow[c0 + j]);
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(B_(AE + ab));  // the accumulator buffer may be overwritten
+                    ++acnt;
+                }
+                // final multiply in FP64: sig[n'] += sum_i sum_l dH_i[m][l] Y_i[(le, l)][n']
+                named_bar(2, kRole);  // all rows accumulated; sA64 written
+                if (row_ok) {
+                    for (int i = 0; i < 3; ++i)
+                        for (int l = 0; l < N; ++l) {
+                            const double2 A = sA64[i * nel + mrow * N + l];
+                            const double* Yr = sY + (size_t)(le * N + l) * kYStride + i * N * 2;
+#pragma unroll
+                            for (int n = 0; n < kMaxNorb; ++n)
+                                if (n < N) {
+                                    const double yr = Yr[2 * n], yi = Yr[2 * n + 1];
+                                    sig[n].x = fma(A.x, yr, fma(-A.y, yi, sig[n].x));
+                                    sig[n].y = fma(A.x, yi, fma(A.y, yr, sig[n].y));
+                                }
                         }
                 }
+                named_bar(2, kRole);  // sA64 / sY are free for the next slot
+            }
+            // store Sigma = i*scale*sig, optionally (S - S^H)/2 in FP64
+            double2* sS = reinterpret_cast<double2*>(sY);  // [128][kMaxNorb] (the accumulator rows are free)
+#pragma unroll
+            for (int n = 0; n < kMaxNorb; ++n) {
+                sig[n] = make_double2(-sc * sig[n].y, sc * sig[n].x);
+                sS[(size_t)row * kMaxNorb + n] = sig[n];
+            }
+            named_bar(2, kRole);
+            if (row_ok) {
+                double2* out = (it.t == 0 ? S_less : S_greater) +
+                               ((((size_t)it.k * d.NE + it.E0 + le) * d.NA + it.a) * N + mrow) * N;
+#pragma unroll
+                for (int n = 0; n < kMaxNorb; ++n)
+                    if (n < N) {
+                        double2 v = sig[n];
+                        if (sym) {
+                            const double2 u = sS[(size_t)(le * N + n) * kMaxNorb + mrow];
+                            v = make_double2(0.5 * (v.x - u.x), 0.5 * (v.y + u.y));
+                        }
+                        out[n] = v;
+                    }
+            }
+            named_bar(2, kRole);  // sS is free
         }
     }
 
-    {
-        // store Sigma = i*scale*sig, optionally (S - S^H)/2 (FP64)
-        const double sc = p.scale;
-        double2* out = t == 0 ? S_less : S_greater;
-        double2* sS = reinterpret_cast<double2*>(smem);  // [128][kMaxNorb]
-        const bool sym = (p.flags & SSE_FLAG_SYMMETRIZE) != 0;
-        __syncthreads();
-#pragma unroll
-        for (int n = 0; n < kMaxNorb; ++n) {
-            sig[n] = make_double2(-sc * sig[n].y, sc * sig[n].x);
-            sS[(size_t)row * kMaxNorb + n] = sig[n];
-        }
-        __syncthreads();
-        if (row_ok) {
-            double2* o = out + ((((size_t)k * d.NE + E0 + le) * d.NA + a) * N + mrow) * N;
-#pragma unroll
-            for (int n = 0; n < kMaxNorb; ++n)
-                if (n < N) {
-                    double2 v = sig[n];
-                    if (sym) {
-                        const double2 u = sS[(size_t)(le * N + n) * kMaxNorb + mrow];
-                        v = make_double2(0.5 * (v.x - u.x), 0.5 * (v.y + u.y));
-                    }
-                    o[n] = v;
-                }
-        }
-    }
-cleanup:
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(c.tmem_cols));
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(c.tmem_cols));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -548,13 +823,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 struct WsLayout {
-    size_t gmax_off, staged_off, total;
+    size_t gmax_off, ew_off, staged_off, total;
 };
 
 WsLayout ws_layout(const sse_dims& d, const MixCfg& c) {
     WsLayout w;
     w.gmax_off = 0;
-    w.staged_off = ((size_t)2 * d.NA * 4 + 255) / 256 * 256;
+    w.ew_off = ((size_t)2 * d.NA * 4 + 255) / 256 * 256;
+    w.staged_off = w.ew_off + ((size_t)d.NA * d.NB * 4 + 255) / 256 * 256;
     w.total = w.staged_off + (size_t)2 * d.Nkz * d.NA * c.nch * c.nrows * 16;
     return w;
 }
@@ -568,9 +844,15 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
     uint4* staged = reinterpret_cast<uint4*>(static_cast<char*>(ws) + L.staged_off);
     cudaError_t e = cudaMemsetAsync(gmax, 0, (size_t)2 * d.NA * 4, st);
     if (e != cudaSuccess) return e;
-    gmax_kernel<<<152 * 8, 256, 0, st>>>(d, p.G[0], p.G[1], gmax);
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    int* ew = reinterpret_cast<int*>(static_cast<char*>(ws) + L.ew_off);
+    gmax_kernel<<<nsm * 8, 256, 0, st>>>(d, p.G[0], p.G[1], gmax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    stage_kernel<MODE><<<152 * 16, 256, 0, st>>>(d, c, p.G[0], p.G[1], gmax, staged);
+    wexp_kernel<<<nsm * 4, 256, 0, st>>>(p, ew);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    stage_kernel<MODE><<<nsm * 16, 256, 0, st>>>(d, c, p.G[0], p.G[1], gmax, staged);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
@@ -587,8 +869,9 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
     e = cudaFuncSetAttribute(sigma_mixed_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
     if (e != cudaSuccess) return e;
     const int nA = d.a_end - d.a_begin;
-    dim3 grid((d.NE + c.TE - 1) / c.TE, d.Nkz, 2 * nA);
-    sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, gmax, Sl, Sg, status);
+    const long long nitems = (long long)c.ntiles * d.Nkz * 2 * nA;
+    const int grid = (int)(nitems < nsm ? nitems : nsm);
+    sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, gmax, ew, Sl, Sg, status);
     return cudaGetLastError();
 }
 
@@ -603,7 +886,8 @@ cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_gr
                       size_t ws_bytes, cudaStream_t st) {
     if (p.d.Norb > kMaxNorb) return cudaErrorNotSupported;
     const MixCfg c = make_cfg(p.d, mode);
-    if (c.smem > 113 * 1024 || ws_bytes < ws_layout(p.d, c).total) return cudaErrorNotSupported;
+    if (c.smem > 227 * 1024 || ws_bytes < ws_layout(p.d, c).total) return cudaErrorNotSupported;
+    if ((long long)c.ntiles * p.d.Nkz * 2 * (p.d.a_end - p.d.a_begin) > 0x7fffffffLL) return cudaErrorNotSupported;
     if (mode == SSE_MODE_BF16X3) return launch<SSE_MODE_BF16X3>(p, c, S_less, S_greater, status, ws, st);
     return launch<SSE_MODE_TF32>(p, c, S_less, S_greater, status, ws, st);
 }
