@@ -59,17 +59,21 @@ constexpr int kYStride = kMaxCols + 1;  // doubles per FP64 accumulator row (odd
 constexpr uint32_t kWaitIters = 1u << 22;  // bounded waits (well under a second of polling)
 constexpr int kThreads = 320;              // 10 warps
 constexpr int kBThread0 = 64, kEThread0 = 192, kRole = 128;
+// Energies are processed in windows of kWindowE output energies: G is staged for the window plus a
+// +-Nw halo (the halo supplies every shifted energy inside the grid; outside [0, NE) the TMA unit
+// zero-fills), which bounds the staged workspace independently of NE.
+constexpr int kWindowE = 256;
 constexpr int kBStages = 4;  // W-tile ring: stages of up to `tg` consecutive taps
 constexpr int kMaxItems = 5;   // W-tile items per producer thread and stage, TF32 (tg * 3 Norb^2 <= 5 * 128)
 constexpr int kItemsBf16 = 3;  // the same for BF16X3 (tg * 3 Norb ceil(Norb/2) <= 3 * 128)
 
 struct MixCfg {
-    int mode, Norb, nel, TE, ntiles;
+    int mode, Norb, nel, TE, wE;     // energies per 128-row tile, output energies per window
     int esz, kpad, nch, npad, kmma;  // element bytes, K per term, 16-B chunks per row, N, MMAs per term
     int wc, wr, rb, nblk;            // window: frequencies, rows (alloc), rows per TMA box, boxes per plane
     int tmem_cols, acc_stride, btile, tg;  // TMEM columns, offset of the 2nd accumulator, W tile bytes, taps per W stage
     int off_B, off_D, off_Ah, off_A64, off_Y, off_bar, smem;
-    int nrows;                       // NE * Norb
+    int nrows;                       // staged rows per slice for the largest window: min(NE, wE + 2 Nw) * Norb
 };
 
 MixCfg make_cfg(const sse_dims& d, int mode) {
@@ -78,7 +82,7 @@ MixCfg make_cfg(const sse_dims& d, int mode) {
     c.Norb = d.Norb;
     c.nel = d.Norb * d.Norb;
     c.TE = 128 / d.Norb;
-    c.ntiles = (d.NE + c.TE - 1) / c.TE;
+    c.wE = d.NE < kWindowE ? d.NE : kWindowE;
     c.esz = mode == SSE_MODE_BF16X3 ? 2 : 4;
     const int kraw = mode == SSE_MODE_BF16X3 ? 6 * d.Norb : 2 * d.Norb;
     const int kstep = mode == SSE_MODE_BF16X3 ? 16 : 8;  // K per tcgen05.mma
@@ -89,7 +93,7 @@ MixCfg make_cfg(const sse_dims& d, int mode) {
     c.tmem_cols = 2 * c.npad <= 32 ? 32 : (2 * c.npad <= 64 ? 64 : 128);
     c.acc_stride = c.tmem_cols / 2;
     c.btile = c.npad * c.kpad * c.esz;
-    c.nrows = d.NE * d.Norb;
+    c.nrows = (d.NE < c.wE + 2 * d.Nw ? d.NE : c.wE + 2 * d.Nw) * d.Norb;
     c.wc = d.Nw < 16 ? d.Nw : 16;
     const int need = 128 + (c.wc - 1) * d.Norb;
     c.nblk = (need + 255) / 256;
@@ -217,18 +221,23 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+// One energy window: outputs [E0, E1), staged energies [Es, Es + nEs), ntiles 128-row tiles.
+struct Win {
+    int E0, E1, Es, nEs, ntiles;
+};
+
 struct Item {
     int tile, k, a, t, E0, wend_p, wend_m;
 };
-__device__ __forceinline__ Item decode(int item, const sse_dims& d, const MixCfg& c) {
+__device__ __forceinline__ Item decode(int item, const sse_dims& d, const MixCfg& c, const Win& win) {
     Item it;
-    it.tile = item % c.ntiles;
-    int r = item / c.ntiles;
+    it.tile = item % win.ntiles;
+    int r = item / win.ntiles;
     it.k = r % d.Nkz;
     r /= d.Nkz;
     it.t = r & 1;
     it.a = d.a_begin + (r >> 1);
-    it.E0 = it.tile * c.TE;
+    it.E0 = win.E0 + it.tile * c.TE;  // absolute energy of the tile's first row
     // frequencies whose shifted energy is off the grid for the whole tile contribute nothing
     it.wend_p = max(0, min(d.Nw, it.E0 + c.TE - 1));
     it.wend_m = max(0, min(d.Nw, d.NE - 1 - it.E0));
@@ -287,10 +296,11 @@ __global__ void gmax_kernel(sse_dims d, const double2* __restrict__ Gl, const do
 }
 
 template <int MODE>
-__global__ void stage_kernel(sse_dims d, MixCfg c, const double2* __restrict__ Gl, const double2* __restrict__ Gg,
-                             const unsigned* __restrict__ gmax, uint4* __restrict__ staged) {
+__global__ void stage_kernel(sse_dims d, MixCfg c, Win win, const double2* __restrict__ Gl,
+                             const double2* __restrict__ Gg, const unsigned* __restrict__ gmax,
+                             uint4* __restrict__ staged) {
     const int N = d.Norb;
-    const size_t rows_per_slice = (size_t)c.nrows;
+    const size_t rows_per_slice = (size_t)win.nEs * N;
     const size_t total = 2ull * d.Nkz * d.NA * rows_per_slice;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t slice = i / rows_per_slice;  // (t*Nkz + k)*NA + b
@@ -298,7 +308,8 @@ __global__ void stage_kernel(sse_dims d, MixCfg c, const double2* __restrict__ G
         const int b = (int)(slice % d.NA);
         const size_t tk = slice / d.NA;
         const int t = (int)(tk / d.Nkz), k = (int)(tk % d.Nkz);
-        const int E = row / N, m = row - E * N;
+        const int El = row / N, m = row - El * N;
+        const int E = win.Es + El;
         const double sG = ldexp(1.0, -floor_log2(__uint_as_float(gmax[t * d.NA + b])));
         const double2* src = (t ? Gg : Gl) + ((((size_t)k * d.NE + E) * d.NA + b) * N + m) * N;
         uint32_t w[32];  // up to 128 bytes of the staged row (kpad*esz <= 128 for Norb <= 10)
@@ -339,7 +350,8 @@ __global__ void stage_kernel(sse_dims d, MixCfg c, const double2* __restrict__ G
 // ---------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c, const unsigned* __restrict__ gmax,
+sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c, Win win,
+                   const unsigned* __restrict__ gmax,
                    const int* __restrict__ ew_bond, double2* __restrict__ S_less, double2* __restrict__ S_greater,
                    unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -349,7 +361,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
     const int N = d.Norb, nel = c.nel, TE = c.TE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nA = d.a_end - d.a_begin;
-    const int nitems = c.ntiles * d.Nkz * 2 * nA;
+    const int nitems = win.ntiles * d.Nkz * 2 * nA;
 
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + c.off_bar);
     // barriers: win_full[2] win_empty[2] b_full[4] b_empty[4] acc_full[2] acc_empty[2] mma_done
@@ -402,7 +414,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
             const uint32_t win_bytes = (uint32_t)(c.nch * c.wr * 16);
             uint32_t wcnt = 0;
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-                const Item it = decode(item, d, c);
+                const Item it = decode(item, d, c, win);
                 if (it.wend_p + it.wend_m == 0) continue;
                 for (int s = 0; s < d.NB; ++s) {
                     const int b = p.nbr[(size_t)it.a * d.NB + s];
@@ -414,7 +426,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                             const int wend = sg ? it.wend_m : it.wend_p;
                             for (int w0 = 0; w0 < wend; w0 += c.wc) {
                                 const int wn = min(c.wc, wend - w0);
-                                const int r0 = it.E0 * N;
+                                const int r0 = (it.E0 - win.Es) * N;  // staged row of the tile's first row
                                 const int start = sg == 0 ? r0 - (w0 + wn) * N : r0 + (w0 + 1) * N;
                                 const int st = (int)(wcnt & 1);
                                 wait_or_abort(B_(WE + st), ((wcnt >> 1) & 1) ^ 1, abort_flag, status);
@@ -444,7 +456,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
             const uint32_t win0 = smem_u32(smem), b0 = smem_u32(sB);
             uint32_t wcnt = 0, bcnt = 0, acnt = 0;
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-                const Item it = decode(item, d, c);
+                const Item it = decode(item, d, c, win);
                 if (it.wend_p + it.wend_m == 0) continue;
                 for (int s = 0; s < d.NB; ++s) {
                     const int b = p.nbr[(size_t)it.a * d.NB + s];
@@ -530,7 +542,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
         }
         uint32_t bcnt = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-            const Item it = decode(item, d, c);
+            const Item it = decode(item, d, c, win);
             if (it.wend_p + it.wend_m == 0) continue;
             for (int s = 0; s < d.NB; ++s) {
                 const int b = p.nbr[(size_t)it.a * d.NB + s];
@@ -714,9 +726,9 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
         const bool sym = (p.flags & SSE_FLAG_SYMMETRIZE) != 0;
         uint32_t acnt = 0;
         for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-            const Item it = decode(item, d, c);
+            const Item it = decode(item, d, c, win);
             const bool any = it.wend_p + it.wend_m > 0;
-            const bool row_ok = le < TE && it.E0 + le < d.NE;
+            const bool row_ok = le < TE && it.E0 + le < win.E1;
             double2 sig[kMaxNorb];
 #pragma unroll
             for (int n = 0; n < kMaxNorb; ++n) sig[n] = make_double2(0.0, 0.0);
@@ -852,26 +864,37 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     wexp_kernel<<<nsm * 4, 256, 0, st>>>(p, ew);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    stage_kernel<MODE><<<nsm * 16, 256, 0, st>>>(d, c, p.G[0], p.G[1], gmax, staged);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    CUtensorMap map;
-    const cuuint64_t dims[3] = {16, (cuuint64_t)c.nrows, (cuuint64_t)2 * d.Nkz * d.NA * c.nch};
-    const cuuint64_t strides[2] = {16, (cuuint64_t)c.nrows * 16};
-    const cuuint32_t box[3] = {16, (cuuint32_t)c.rb, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, staged, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(sigma_mixed_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
     if (e != cudaSuccess) return e;
     const int nA = d.a_end - d.a_begin;
-    const long long nitems = (long long)c.ntiles * d.Nkz * 2 * nA;
-    const int grid = (int)(nitems < nsm ? nitems : nsm);
-    sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, gmax, ew, Sl, Sg, status);
+    for (int E0 = 0; E0 < d.NE; E0 += c.wE) {
+        Win win;
+        win.E0 = E0;
+        win.E1 = E0 + c.wE < d.NE ? E0 + c.wE : d.NE;
+        win.Es = E0 - d.Nw > 0 ? E0 - d.Nw : 0;
+        win.nEs = (win.E1 + d.Nw < d.NE ? win.E1 + d.Nw : d.NE) - win.Es;
+        win.ntiles = (win.E1 - win.E0 + c.TE - 1) / c.TE;
+        stage_kernel<MODE><<<nsm * 16, 256, 0, st>>>(d, c, win, p.G[0], p.G[1], gmax, staged);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // rows outside [0, nEs*Norb) of a slice read as zero: energies outside the grid, or never
+        // reached (the halo covers every shifted energy inside the grid)
+        CUtensorMap map;
+        const cuuint64_t rows = (cuuint64_t)win.nEs * d.Norb;
+        const cuuint64_t dims[3] = {16, rows, (cuuint64_t)2 * d.Nkz * d.NA * c.nch};
+        const cuuint64_t strides[2] = {16, rows * 16};
+        const cuuint32_t box[3] = {16, (cuuint32_t)c.rb, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, staged, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        const long long nitems = (long long)win.ntiles * d.Nkz * 2 * nA;
+        const int grid = (int)(nitems < nsm ? nitems : nsm);
+        sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, win, gmax, ew, Sl, Sg, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -887,7 +910,8 @@ cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_gr
     if (p.d.Norb > kMaxNorb) return cudaErrorNotSupported;
     const MixCfg c = make_cfg(p.d, mode);
     if (c.smem > 227 * 1024 || ws_bytes < ws_layout(p.d, c).total) return cudaErrorNotSupported;
-    if ((long long)c.ntiles * p.d.Nkz * 2 * (p.d.a_end - p.d.a_begin) > 0x7fffffffLL) return cudaErrorNotSupported;
+    if ((long long)((c.wE + c.TE - 1) / c.TE) * p.d.Nkz * 2 * (p.d.a_end - p.d.a_begin) > 0x7fffffffLL)
+        return cudaErrorNotSupported;
     if (mode == SSE_MODE_BF16X3) return launch<SSE_MODE_BF16X3>(p, c, S_less, S_greater, status, ws, st);
     return launch<SSE_MODE_TF32>(p, c, S_less, S_greater, status, ws, st);
 }

@@ -1,0 +1,95 @@
+"""Large workload (NA=4096, NB=4, Norb=10, NE=1024, Nkz=Nqz=5, Nw=64).
+
+Mixed-precision (BF16X3) forward processed in energy windows of 256 outputs
+with a 2*64 halo, checked against the FP64 oracle on sampled blocks (grid
+edges, window boundaries, interior), and the FP64 adjoint on a subset of
+atoms checked against central differences of the FP64 forward.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import normwise
+from oracle.subproblem import oracle_blocks
+from paper_1912_10024_gb300 import binding as B
+from paper_1912_10024_gb300.inputs import LARGE, make_inputs, make_upstream
+
+pytestmark = pytest.mark.gpu
+SCALE = 1.0 / (2.0 * math.pi)
+
+
+@pytest.fixture(scope="module")
+def large():
+    torch.cuda.empty_cache()
+    inp = make_inputs(LARGE, seed=5, device="cuda")
+    yield inp
+    del inp
+    torch.cuda.empty_cache()
+
+
+def test_large_bf16x3_windows_sampled(large):
+    inp = large
+    Sl, Sg = B.sigma(inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, mode="bf16x3",
+                     check=True)
+    torch.cuda.synchronize()
+    errs = []
+    # energies at the grid edges and across the window boundaries 256 and 512
+    for (a, E0, E1) in [(0, 0, 2), (4095, 1022, 1024), (2047, 255, 257), (1500, 511, 513), (77, 700, 702)]:
+        Ol, Og = oracle_blocks(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, a,
+                               E0, E1)
+        for S, O in ((Sl, Ol), (Sg, Og)):
+            errs.append(normwise(S[:, E0:E1, a].cpu().numpy(), O))
+    print("large bf16x3 sampled errors", errs)
+    assert max(errs) <= 2e-5
+    for S in (Sl, Sg):  # anti-Hermitian inputs give anti-Hermitian Sigma, up to the mode's error
+        blk = S[:, ::101, ::257]
+        assert float((blk + blk.conj().transpose(-1, -2)).abs().max()) <= 2e-5 * float(blk.abs().max())
+    del Sl, Sg
+    torch.cuda.empty_cache()
+
+
+def test_large_fp64_adjoint_atom_subset(large):
+    """FP64 gradients for atoms [0, 8) at the large sizes vs central differences (h = 1e-6)."""
+    inp = large
+    a0, a1 = 0, 8
+    W, V = make_upstream(LARGE, seed=6, device="cuda")
+    g_dH, g_Dl, g_Dg = B.sigma_grad(inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, W, V,
+                                    scale=SCALE, atoms=(a0, a1), check=True)
+    torch.cuda.synchronize()
+    grads = {"dH": g_dH, "D_less": g_Dl, "D_greater": g_Dg}
+    gscale = max(float(g_dH[a0:a1].abs().max()), float(g_Dl[:, :, a0:a1].abs().max()),
+                 float(g_Dg[:, :, a0:a1].abs().max()))
+
+    out = (torch.zeros_like(inp.G_less), torch.zeros_like(inp.G_greater))  # reused: 2 x 33.5 GB
+
+    def loss(a):
+        Sl, Sg = B.sigma(inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, scale=SCALE,
+                         atoms=(a, a + 1), out=out)
+        return float((W[:, :, a].conj() * Sl[:, :, a]).real.sum() + (V[:, :, a].conj() * Sg[:, :, a]).real.sum())
+
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for _ in range(8):
+        name = ("dH", "D_less", "D_greater")[int(rng.integers(3))]
+        base = getattr(inp, name)
+        a = int(rng.integers(a0, a1))
+        sub = base[a] if name == "dH" else base[:, :, a]
+        flat = int(rng.integers(sub.numel()))
+        part = int(rng.integers(2))
+        idx = np.unravel_index(flat, tuple(sub.shape))
+        full_idx = (a,) + idx if name == "dH" else idx[:2] + (a,) + idx[2:]
+        orig = base[full_idx].item()
+        step = h if part == 0 else 1j * h
+        base[full_idx] = orig + step
+        lp = loss(a)
+        base[full_idx] = orig - step
+        lm = loss(a)
+        base[full_idx] = orig
+        fd = (lp - lm) / (2 * h)
+        an = grads[name][full_idx].item()
+        an = an.real if part == 0 else an.imag
+        assert abs(fd - an) <= 1e-7 * gscale, (name, full_idx, part, fd, an)
+    # atoms outside the range are untouched (zero-initialised by the binding)
+    assert float(g_dH[a1:].abs().max()) == 0.0

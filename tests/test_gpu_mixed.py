@@ -44,6 +44,8 @@ def test_tiny_error_bound(mode):
     Dims(NA=5, NB=2, Norb=10, NE=90, Nkz=2, Nqz=2, Nw=40),   # two frequency chunks per window
     Dims(NA=6, NB=4, Norb=4, NE=200, Nkz=3, Nqz=3, Nw=33),
     Dims(NA=4, NB=2, Norb=7, NE=37, Nkz=3, Nqz=1, Nw=9),
+    Dims(NA=5, NB=2, Norb=4, NE=700, Nkz=2, Nqz=2, Nw=40),   # three energy windows with halos
+    Dims(NA=3, NB=2, Norb=10, NE=600, Nkz=2, Nqz=1, Nw=20),
 ], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}")
 def test_shapes(mode, dims):
     inp = make_inputs(dims, seed=dims.NE, nbr=ring_neighbours(dims.NA, dims.NB))
