@@ -123,6 +123,28 @@ SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* d
                   uint32_t flags, const double* gS_less, const double* gS_greater, double* g_dH, double* g_D_less,
                   double* g_D_greater, void* workspace, size_t ws_bytes, void* stream);
 
+/* Bond weights of Eq. (3) (Sec. 2) from the raw phonon Green's functions.
+ *   Draw^t complex128 [Nqz][Nw][NA][NB+1][3][3]: slot s < NB holds D_ab for b = nbr[a][s],
+ *                                                slot NB holds the self block D_aa.
+ *   D^t    complex128 [Nqz][Nw][NA][NB][3][3]:   D^t(a,s) = D_ba - D_bb - D_aa + D_ab,
+ * where D_ba is the block atom b stores in the slot s' with nbr[b][s'] = a: the
+ * neighbour lists must be symmetric. Rows of atoms [a_begin, a_end) are written
+ * (NE, Nkz and Norb are not used; they must still pass the checks of sse_dims).
+ * A bond without a reverse slot, or with a neighbour outside [0, NA), gets a zero
+ * weight; with SSE_FLAG_CHECK it is reported as SSE_ERR_DEVICE_CHECK. Workspace:
+ * at least 256 bytes (256-byte aligned) for the status word. Asynchronous on stream. */
+SSE_API int sse_dcomb_fwd(const sse_dims* d, const int32_t* nbr, const double* Draw_less, const double* Draw_greater,
+                          double* D_less, double* D_greater, uint32_t flags, void* workspace, size_t ws_bytes,
+                          void* stream);
+
+/* Adjoint of sse_dcomb_fwd: from the gradients gD^t w.r.t. the bond weights (read for
+ * every atom) it writes the gradients gDraw^t w.r.t. the raw blocks of atoms
+ * [a_begin, a_end): slot s < NB gets gD(a,s) + gD(b,s'), slot NB gets minus the sum of
+ * those over a's bonds. Same checks, workspace and status as sse_dcomb_fwd. */
+SSE_API int sse_dcomb_bwd(const sse_dims* d, const int32_t* nbr, const double* gD_less, const double* gD_greater,
+                          double* gDraw_less, double* gDraw_greater, uint32_t flags, void* workspace,
+                          size_t ws_bytes, void* stream);
+
 /* Size of the library's static device scratch array used by sse_sigma_bwd_static. */
 #define SSE_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 

@@ -61,6 +61,9 @@ def _open(path):
     lib.sse_oracle_bwd.argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, vp, vp, ctypes.c_double, vp, vp,
                                    vp, vp, vp, ctypes.c_int]
     lib.sse_oracle_bwd.restype = ctypes.c_int
+    for name in ("sse_oracle_dcomb", "sse_oracle_dcomb_adj"):
+        getattr(lib, name).argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, vp]
+        getattr(lib, name).restype = ctypes.c_int
     return lib
 
 
@@ -159,3 +162,44 @@ def sigma_grad(nbr, dH, D_less, D_greater, G_less, G_greater, scale, W_less, W_g
     if rc != 0:
         raise ValueError(f"sse_oracle_bwd failed with status {rc}")
     return g_dH, g_Dl, g_Dg
+
+
+def _raw_dims(raw, nbr, a_range):
+    Nqz, Nw, NA = raw.shape[0], raw.shape[1], raw.shape[2]
+    NB = nbr.shape[1]
+    a0, a1 = a_range if a_range is not None else (0, NA)
+    # the energy/kz fields are unused by the combination; any valid values pass the checks
+    return _Dims(NA, NB, 1, 1, Nqz, Nqz, Nw, a0, a1, 0, 1)
+
+
+def dcomb(nbr, raw_less, raw_greater, a_range=None):
+    """Bond weights D_ba - D_bb - D_aa + D_ab of Eq. (3) from raw [Nqz,Nw,NA,NB+1,3,3] tensors.
+
+    Returns (Dc_less, Dc_greater) [Nqz,Nw,NA,NB,3,3]; atoms outside ``a_range`` stay zero.
+    """
+    lib = _load()
+    r_l, r_g = _np(raw_less, np.complex128), _np(raw_greater, np.complex128)
+    nbr_ = _np(nbr, np.int32)
+    d = _raw_dims(r_l, nbr_, a_range)
+    shape = r_l.shape[:3] + (nbr_.shape[1], 3, 3)
+    D_l, D_g = np.zeros(shape, np.complex128), np.zeros(shape, np.complex128)
+    rc = lib.sse_oracle_dcomb(ctypes.byref(d), nbr_.ctypes.data, r_l.ctypes.data, r_g.ctypes.data,
+                              D_l.ctypes.data, D_g.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"sse_oracle_dcomb failed with status {rc}")
+    return D_l, D_g
+
+
+def dcomb_adjoint(nbr, g_less, g_greater):
+    """Gradient w.r.t. the raw tensors given the gradient w.r.t. the bond weights (all atoms)."""
+    lib = _load()
+    g_l, g_g = _np(g_less, np.complex128), _np(g_greater, np.complex128)
+    nbr_ = _np(nbr, np.int32)
+    d = _raw_dims(g_l, nbr_, None)
+    shape = g_l.shape[:3] + (nbr_.shape[1] + 1, 3, 3)
+    r_l, r_g = np.zeros(shape, np.complex128), np.zeros(shape, np.complex128)
+    rc = lib.sse_oracle_dcomb_adj(ctypes.byref(d), nbr_.ctypes.data, g_l.ctypes.data, g_g.ctypes.data,
+                                  r_l.ctypes.data, r_g.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"sse_oracle_dcomb_adj failed with status {rc}")
+    return r_l, r_g

@@ -439,3 +439,87 @@ int sse_oracle_bwd(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH,
     pthread_mutex_destroy(&J.lock);
     return J.fail ? ORACLE_NO_MEM : ORACLE_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* phonon weight combination of Eq. (3)                                 */
+/* ------------------------------------------------------------------ */
+/*
+ * The phonon Green's functions are stored as [Nqz][Nw][NA][NB+1][3][3] (Sec. 2):
+ * slot s < NB holds D_ab for b = nbr[a][s], slot NB holds the self block D_aa.
+ * The weight of the bond (a, s) in Eq. (3) is D_ba - D_bb - D_aa + D_ab, where
+ * D_ba is the block stored by atom b in the slot s' with nbr[b][s'] = a (the
+ * neighbour lists must be symmetric). Dc has the layout [Nqz][Nw][NA][NB][3][3].
+ * Atoms [a_begin, a_end) are written; returns ORACLE_BAD_ARG if a bond has no
+ * reverse slot.
+ */
+static int reverse_slot(const sse_oracle_dims* d, const int32_t* nbr, int a, int b) {
+    for (int s = 0; s < d->NB; ++s)
+        if (nbr[(size_t)b * d->NB + s] == a) return s;
+    return -1;
+}
+
+static size_t off_raw(const sse_oracle_dims* d, int q, int w, int a, int slot) {
+    return ((((size_t)q * d->Nw + w) * d->NA + a) * (d->NB + 1) + slot) * 9;
+}
+
+int sse_oracle_dcomb(const sse_oracle_dims* d, const int32_t* nbr, const cplx* raw_less, const cplx* raw_greater,
+                     cplx* Dc_less, cplx* Dc_greater) {
+    if (!check_dims(d) || !nbr || !raw_less || !raw_greater || !Dc_less || !Dc_greater) return ORACLE_BAD_ARG;
+    const cplx* raw[2] = {raw_less, raw_greater};
+    cplx* out[2] = {Dc_less, Dc_greater};
+    for (int a = d->a_begin; a < d->a_end; ++a)
+        for (int s = 0; s < d->NB; ++s) {
+            const int b = nbr[(size_t)a * d->NB + s];
+            if (b < 0 || b >= d->NA) return ORACLE_BAD_ARG;
+            const int sr = reverse_slot(d, nbr, a, b);
+            if (sr < 0) return ORACLE_BAD_ARG;
+            for (int t = 0; t < 2; ++t)
+                for (int q = 0; q < d->Nqz; ++q)
+                    for (int w = 0; w < d->Nw; ++w) {
+                        const cplx* Dba = raw[t] + off_raw(d, q, w, b, sr);
+                        const cplx* Dbb = raw[t] + off_raw(d, q, w, b, d->NB);
+                        const cplx* Daa = raw[t] + off_raw(d, q, w, a, d->NB);
+                        const cplx* Dab = raw[t] + off_raw(d, q, w, a, s);
+                        cplx* o = out[t] + off_D(d, q, w, a, s);
+                        for (int e = 0; e < 9; ++e) o[e] = Dba[e] - Dbb[e] - Daa[e] + Dab[e];
+                    }
+        }
+    return ORACLE_OK;
+}
+
+/*
+ * Adjoint of sse_oracle_dcomb: each bond (a, s) adds its weight gradient to the
+ * four raw blocks it reads (+D_ba, -D_bb, -D_aa, +D_ab). Every bond of every atom
+ * is visited; the raw gradient is written for all atoms.
+ */
+int sse_oracle_dcomb_adj(const sse_oracle_dims* d, const int32_t* nbr, const cplx* g_less, const cplx* g_greater,
+                         cplx* graw_less, cplx* graw_greater) {
+    if (!check_dims(d) || !nbr || !g_less || !g_greater || !graw_less || !graw_greater) return ORACLE_BAD_ARG;
+    const cplx* g[2] = {g_less, g_greater};
+    cplx* out[2] = {graw_less, graw_greater};
+    const size_t nraw = (size_t)d->Nqz * d->Nw * d->NA * (d->NB + 1) * 9;
+    for (int t = 0; t < 2; ++t) memset(out[t], 0, sizeof(cplx) * nraw);
+    for (int a = 0; a < d->NA; ++a)
+        for (int s = 0; s < d->NB; ++s) {
+            const int b = nbr[(size_t)a * d->NB + s];
+            if (b < 0 || b >= d->NA) return ORACLE_BAD_ARG;
+            const int sr = reverse_slot(d, nbr, a, b);
+            if (sr < 0) return ORACLE_BAD_ARG;
+            for (int t = 0; t < 2; ++t)
+                for (int q = 0; q < d->Nqz; ++q)
+                    for (int w = 0; w < d->Nw; ++w) {
+                        const cplx* gi = g[t] + off_D(d, q, w, a, s);
+                        cplx* Dba = out[t] + off_raw(d, q, w, b, sr);
+                        cplx* Dbb = out[t] + off_raw(d, q, w, b, d->NB);
+                        cplx* Daa = out[t] + off_raw(d, q, w, a, d->NB);
+                        cplx* Dab = out[t] + off_raw(d, q, w, a, s);
+                        for (int e = 0; e < 9; ++e) {
+                            Dba[e] += gi[e];
+                            Dbb[e] -= gi[e];
+                            Daa[e] -= gi[e];
+                            Dab[e] += gi[e];
+                        }
+                    }
+        }
+    return ORACLE_OK;
+}

@@ -19,7 +19,8 @@ from . import build as _build
 SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3 = 0, 1, 2
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK = 1, 2
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3}
-EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_strerror")
+EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
+            "sse_dcomb_bwd", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -58,6 +59,9 @@ def load() -> ctypes.CDLL:
             lib.sse_sigma_bwd.restype = i32
             lib.sse_sigma_bwd_static.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, vp, vp, vp]
             lib.sse_sigma_bwd_static.restype = i32
+            for name in ("sse_dcomb_fwd", "sse_dcomb_bwd"):
+                getattr(lib, name).argtypes = [pd, vp, vp, vp, vp, vp, u32, vp, ctypes.c_size_t, vp]
+                getattr(lib, name).restype = i32
             lib.sse_strerror.argtypes = [i32]
             lib.sse_strerror.restype = ctypes.c_char_p
             _lib = lib
@@ -109,6 +113,18 @@ def sse_sigma_bwd_static(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_grea
                                            _p(G_less), _p(G_greater), float(scale), int(mode), int(flags),
                                            _p(gS_less), _p(gS_greater), _p(g_dH), _p(g_D_less), _p(g_D_greater),
                                            _stream(stream)))
+
+
+def sse_dcomb_fwd(d: sse_dims, nbr, Draw_less, Draw_greater, D_less, D_greater, flags: int, workspace,
+                  ws_bytes: int, stream=None) -> int:
+    return int(load().sse_dcomb_fwd(ctypes.byref(d), _p(nbr), _p(Draw_less), _p(Draw_greater), _p(D_less),
+                                    _p(D_greater), int(flags), _p(workspace), int(ws_bytes), _stream(stream)))
+
+
+def sse_dcomb_bwd(d: sse_dims, nbr, gD_less, gD_greater, gDraw_less, gDraw_greater, flags: int, workspace,
+                  ws_bytes: int, stream=None) -> int:
+    return int(load().sse_dcomb_bwd(ctypes.byref(d), _p(nbr), _p(gD_less), _p(gD_greater), _p(gDraw_less),
+                                    _p(gDraw_greater), int(flags), _p(workspace), int(ws_bytes), _stream(stream)))
 
 
 def sse_strerror(status: int) -> str:
@@ -231,3 +247,66 @@ class SigmaFunction(torch.autograd.Function):
 def sigma_autograd(dH, D_less, D_greater, G_less, G_greater, nbr, scale=1.0 / (2.0 * math.pi), mode="fp64",
                    symmetrize=False):
     return SigmaFunction.apply(dH, D_less, D_greater, G_less, G_greater, nbr, scale, mode, symmetrize)
+
+
+# ---- bond weights from raw phonon Green's functions ---------------------
+
+def _dcomb_dims(raw_or_bond: torch.Tensor, nbr: torch.Tensor, atoms=None) -> sse_dims:
+    Nqz, Nw, NA = raw_or_bond.shape[:3]
+    a0, a1 = (0, NA) if atoms is None else atoms
+    # NE, Nkz, Norb are unused by the combination; values that pass the checks
+    return sse_dims(NA, nbr.shape[1], 1, Nw + 1, Nqz, Nqz, Nw, a0, a1)
+
+
+def dcomb(Draw_less, Draw_greater, nbr, check: bool = False, atoms=None, stream=None):
+    """D^t(a,s) = D_ba - D_bb - D_aa + D_ab of Eq. (3) from raw [Nqz,Nw,NA,NB+1,3,3] tensors."""
+    NB = nbr.shape[1]
+    _check_tensor("Draw_less", Draw_less, torch.complex128, Draw_less.shape[:3] + (NB + 1, 3, 3))
+    _check_tensor("Draw_greater", Draw_greater, torch.complex128, Draw_less.shape[:3] + (NB + 1, 3, 3))
+    _check_tensor("nbr", nbr, torch.int32, (Draw_less.shape[2], NB))
+    d = _dcomb_dims(Draw_less, nbr, atoms)
+    shape = tuple(Draw_less.shape[:3]) + (NB, 3, 3)
+    alloc = torch.empty if atoms is None else torch.zeros
+    out = (alloc(shape, dtype=torch.complex128, device=nbr.device), alloc(shape, dtype=torch.complex128, device=nbr.device))
+    ws = torch.empty(256, dtype=torch.uint8, device=nbr.device)
+    rc = sse_dcomb_fwd(d, nbr, Draw_less, Draw_greater, out[0], out[1], SSE_FLAG_CHECK if check else 0, ws, 256,
+                       stream)
+    if rc != 0:
+        raise SseError(rc, "sse_dcomb_fwd")
+    return out
+
+
+def dcomb_grad(gD_less, gD_greater, nbr, check: bool = False, stream=None):
+    """Gradients w.r.t. the raw tensors from the gradients w.r.t. the bond weights."""
+    NB = nbr.shape[1]
+    _check_tensor("gD_less", gD_less, torch.complex128, gD_less.shape[:3] + (NB, 3, 3))
+    _check_tensor("gD_greater", gD_greater, torch.complex128, gD_less.shape[:3] + (NB, 3, 3))
+    d = _dcomb_dims(gD_less, nbr)
+    shape = tuple(gD_less.shape[:3]) + (NB + 1, 3, 3)
+    out = (torch.empty(shape, dtype=torch.complex128, device=nbr.device),
+           torch.empty(shape, dtype=torch.complex128, device=nbr.device))
+    ws = torch.empty(256, dtype=torch.uint8, device=nbr.device)
+    rc = sse_dcomb_bwd(d, nbr, gD_less.contiguous(), gD_greater.contiguous(), out[0], out[1],
+                       SSE_FLAG_CHECK if check else 0, ws, 256, stream)
+    if rc != 0:
+        raise SseError(rc, "sse_dcomb_bwd")
+    return out
+
+
+class DcombFunction(torch.autograd.Function):
+    """(Draw^<, Draw^>) -> (D^<, D^>) bond weights, with the gather adjoint."""
+
+    @staticmethod
+    def forward(ctx, Draw_less, Draw_greater, nbr):
+        ctx.save_for_backward(nbr)
+        return dcomb(Draw_less, Draw_greater, nbr)
+
+    @staticmethod
+    def backward(ctx, gl, gg):
+        (nbr,) = ctx.saved_tensors
+        if gl is None:
+            gl = torch.zeros_like(gg)
+        if gg is None:
+            gg = torch.zeros_like(gl)
+        r = dcomb_grad(gl, gg, nbr)
+        return r[0], r[1], None

@@ -149,3 +149,44 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }
+
+namespace {
+int dcomb_common(const sse_dims* d, const int32_t* nbr, const double* in_l, const double* in_g, double* out_l,
+                 double* out_g, uint32_t flags, void* workspace, size_t ws_bytes) {
+    if (!valid_dims(d) || !valid_flags(flags)) return SSE_ERR_INVALID_ARG;
+    if (!nbr || !in_l || !in_g || !out_l || !out_g) return SSE_ERR_INVALID_ARG;
+    if (!aligned(nbr, 4) || !aligned(in_l, 16) || !aligned(in_g, 16) || !aligned(out_l, 16) || !aligned(out_g, 16))
+        return SSE_ERR_INVALID_ARG;
+    if (!supported_dims(d)) return SSE_ERR_UNSUPPORTED;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes) return SSE_ERR_WORKSPACE;
+    return SSE_OK;
+}
+}  // namespace
+
+extern "C" int sse_dcomb_fwd(const sse_dims* d, const int32_t* nbr, const double* Draw_less,
+                             const double* Draw_greater, double* D_less, double* D_greater, uint32_t flags,
+                             void* workspace, size_t ws_bytes, void* stream) {
+    int rc = dcomb_common(d, nbr, Draw_less, Draw_greater, D_less, D_greater, flags, workspace, ws_bytes);
+    if (rc != SSE_OK || d->a_begin == d->a_end) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(workspace);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
+    cudaError_t e = sse::dcomb_fwd(*d, nbr, reinterpret_cast<const double2*>(Draw_less),
+                                   reinterpret_cast<const double2*>(Draw_greater), reinterpret_cast<double2*>(D_less),
+                                   reinterpret_cast<double2*>(D_greater), status, st);
+    return finish(e, status, flags, st);
+}
+
+extern "C" int sse_dcomb_bwd(const sse_dims* d, const int32_t* nbr, const double* gD_less, const double* gD_greater,
+                             double* gDraw_less, double* gDraw_greater, uint32_t flags, void* workspace,
+                             size_t ws_bytes, void* stream) {
+    int rc = dcomb_common(d, nbr, gD_less, gD_greater, gDraw_less, gDraw_greater, flags, workspace, ws_bytes);
+    if (rc != SSE_OK || d->a_begin == d->a_end) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(workspace);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
+    cudaError_t e = sse::dcomb_bwd(*d, nbr, reinterpret_cast<const double2*>(gD_less),
+                                   reinterpret_cast<const double2*>(gD_greater), reinterpret_cast<double2*>(gDraw_less),
+                                   reinterpret_cast<double2*>(gDraw_greater), status, st);
+    return finish(e, status, flags, st);
+}

@@ -44,6 +44,25 @@ BWD = [
     ("grad dH left term misses G^H", "mm_bh(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */",
      "mm(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */"),
 ]
+DCOMB = [
+    ("own slot instead of the reverse slot", "const cplx* Dba = raw[t] + off_raw(d, q, w, b, sr);",
+     "const cplx* Dba = raw[t] + off_raw(d, q, w, b, s);"),
+    ("self block of the wrong atom", "const cplx* Daa = raw[t] + off_raw(d, q, w, a, d->NB);",
+     "const cplx* Daa = raw[t] + off_raw(d, q, w, b, d->NB);"),
+    ("sign of D_aa", "for (int e = 0; e < 9; ++e) o[e] = Dba[e] - Dbb[e] - Daa[e] + Dab[e];",
+     "for (int e = 0; e < 9; ++e) o[e] = Dba[e] - Dbb[e] + Daa[e] + Dab[e];"),
+    ("adjoint misses the D_bb term", "                            Dbb[e] -= gi[e];\n", "\n"),
+]
+
+
+def _dcomb_pins():
+    import test_oracle_dcomb as dc
+    yield dc.test_worked_example
+    yield lambda: dc.test_exchange_symmetry("diamond")
+    yield lambda: dc.test_exchange_symmetry("two_way_ring")
+    yield dc.test_uniform_blocks_cancel
+    yield dc.test_adjoint_dot_product
+
 
 def _fwd_pins():
     yield pins.test_scalar_worked_example
@@ -93,6 +112,11 @@ def test_adjoint_mutation_is_caught(tmp_path, name, old, new):
     assert _caught(_build(tmp_path, old, new), _bwd_pins()), f"no pin caught: {name}"
 
 
+@pytest.mark.parametrize("name,old,new", DCOMB, ids=[m[0] for m in DCOMB])
+def test_dcomb_mutation_is_caught(tmp_path, name, old, new):
+    assert _caught(_build(tmp_path, old, new), _dcomb_pins()), f"no pin caught: {name}"
+
+
 def test_unmutated_source_passes(tmp_path):
     so = _build(tmp_path, "#include <complex.h>", "#include <complex.h>")
-    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()))
+    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()) + list(_dcomb_pins()))
