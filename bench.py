@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=sorted(B.MODES))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the BF16X3/TF32 comparison in an FP64 run")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
 
@@ -289,6 +290,44 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
         del host, hSl, hSg
 
+    # ---- FP64 vs mixed precision on the same inputs (the metric's comparison) ----
+    mixed = None
+    if args.mode == "fp64" and not args.no_mixed and rank == 0:
+        mixed = {}
+        ref = (Sl.clone(), Sg.clone())
+        for mname, bound in (("bf16x3", 2e-5), ("tf32", 2e-3)):
+            m = B.MODES[mname]
+            wsm = B.workspace(dims, m, 0, dev)
+            Ml, Mg = torch.empty_like(Sl), torch.empty_like(Sg)
+
+            def mstep():
+                rc = B.sse_sigma_fwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater,
+                                     SCALE, m, 0, Ml, Mg, wsm, wsm.numel(), stream)
+                if rc != 0:
+                    raise B.SseError(rc, "sse_sigma_fwd")
+
+            for _ in range(max(3, args.warmup)):
+                mstep()
+            torch.cuda.synchronize(dev)
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(stream)
+            for _ in range(args.steps):
+                mstep()
+            m1.record(stream)
+            torch.cuda.synchronize(dev)
+            mms = m0.elapsed_time(m1) / args.steps
+            # normwise error of the mixed result against this run's FP64 result (which matches the oracle to 1e-12)
+            err = max(float((Ml - ref[0]).abs().max() / ref[0].abs().max()),
+                      float((Mg - ref[1]).abs().max() / ref[1].abs().max()))
+            mixed[mname] = {"value": uf / (mms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": mms,
+                            "speedup_vs_fp64": ms_per_step / mms, "max_normwise_err_vs_fp64": err,
+                            "stated_bound": bound,
+                            "tensor_frac": mixed_tensor_flops(d, mname) / (mms * 1e-3) / 1e12 /
+                            (load_peaks()[0]["bf16_tflops_sustained"] * (1.0 if mname == "bf16x3" else 1.1 / 2.25))}
+            del wsm, Ml, Mg
+        del ref
+        torch.cuda.empty_cache()
+
     out = None
     if rank == 0:
         avg_launch_s = statistics.mean(launch_ms) * 1e-3
@@ -315,6 +354,8 @@ def main():
                           "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (2 * inp.G_less.numel() * 16 / 1e9)},
                "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
                "gpu_launches": args.steps * (1 if args.mode == "fp64" else 3)}
+        if mixed:
+            out["mixed"] = mixed
         if world == 1 and not args.no_cpu:
             del Sl, Sg
             torch.cuda.empty_cache()
