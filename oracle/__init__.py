@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the electron scattering self-energy of Eq. (3).
+"""FP64 CPU oracle for the electron and phonon scattering self-energies, Eqs. (3) and (4).
 
 TEST INFRASTRUCTURE ONLY: the plain, slow reference that the CUDA path is
 checked against. Only the test suite, ``__graft_entry__.smoke()`` and the
@@ -64,6 +64,8 @@ def _open(path):
     for name in ("sse_oracle_dcomb", "sse_oracle_dcomb_adj"):
         getattr(lib, name).argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, vp]
         getattr(lib, name).restype = ctypes.c_int
+    lib.sse_oracle_pi.argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, ctypes.c_double, vp, vp, ctypes.c_int]
+    lib.sse_oracle_pi.restype = ctypes.c_int
     return lib
 
 
@@ -203,3 +205,27 @@ def dcomb_adjoint(nbr, g_less, g_greater):
     if rc != 0:
         raise ValueError(f"sse_oracle_dcomb_adj failed with status {rc}")
     return r_l, r_g
+
+
+def pi(nbr, dH, G_less, G_greater, scale, Nqz, Nw, a_range=None, nthreads=None):
+    """Pi^<, Pi^> of Eq. (4) in FP64 on the host.
+
+    G [Nkz,NE,NA,Norb,Norb], dH [NA,NB,3,Norb,Norb], nbr [NA,NB] int32.
+    Returns (P_less, P_greater) [Nqz,Nw,NA,NB+1,3,3] complex128: slot s < NB is
+    the block Pi_ab for b = nbr[a][s], slot NB the diagonal block Pi_aa.
+    Atoms outside ``a_range`` stay zero.
+    """
+    lib = _load()
+    G_l, G_g = _np(G_less, np.complex128), _np(G_greater, np.complex128)
+    dH_, nbr_ = _np(dH, np.complex128), _np(nbr, np.int32)
+    Nkz, NE, NA, Norb, _ = G_l.shape
+    NB = dH_.shape[1]
+    a0, a1 = a_range if a_range is not None else (0, NA)
+    d = _Dims(NA, NB, Norb, NE, Nkz, int(Nqz), int(Nw), a0, a1, 0, NE)
+    shape = (int(Nqz), int(Nw), NA, NB + 1, 3, 3)
+    P_l, P_g = np.zeros(shape, np.complex128), np.zeros(shape, np.complex128)
+    rc = lib.sse_oracle_pi(ctypes.byref(d), nbr_.ctypes.data, dH_.ctypes.data, G_l.ctypes.data, G_g.ctypes.data,
+                           float(scale), P_l.ctypes.data, P_g.ctypes.data, int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError(f"sse_oracle_pi failed with status {rc}")
+    return P_l, P_g

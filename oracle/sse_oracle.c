@@ -1,7 +1,8 @@
 /*
- * FP64 CPU oracle for the electron scattering self-energy (SSE) of
- * Ziogas et al., "A Data-Centric Approach to Extreme-Scale Ab initio
- * Dissipative Quantum Transport Simulations" (SC'19), Eq. (3).
+ * FP64 CPU oracle for the electron and phonon scattering self-energies (SSE)
+ * of Ziogas et al., "A Data-Centric Approach to Extreme-Scale Ab initio
+ * Dissipative Quantum Transport Simulations" (SC'19), Eqs. (3) and (4), and
+ * for the bond-weight combination D_ba - D_bb - D_aa + D_ab of Eq. (3).
  *
  * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference that the
  * CUDA path is checked against. Only the test suite, the package smoke check
@@ -521,5 +522,157 @@ int sse_oracle_dcomb_adj(const sse_oracle_dims* d, const int32_t* nbr, const cpl
                         }
                     }
         }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* phonon self-energy, Eq. (4)                                          */
+/* ------------------------------------------------------------------ */
+/*
+ * Pi^t_ab(w, q)_ij = -i*scale * sum_k sum_l sum_E
+ *        tr{ dH_i(l,a) . G^t_aa(E + (w+1), (k + q) mod Nkz) . dH_j(a,l) . G^{t'}_ll(E, k) }
+ * with the readings used throughout this project:
+ *   - t' is the other type (G^< pairs with G^>, Eq. 4's lesser/greater order);
+ *   - dH_i(l,a) = dH_i(a,l)^H, dH_j(a,l) = dH[a][slot of l][j];
+ *   - off-diagonal block b = nbr[a][s] (slot s < NB): the sum over l has the
+ *     single term l = b; diagonal block (slot NB): l runs over the NB
+ *     neighbours of a;
+ *   - energies with E or E + (w+1) outside [0, NE) contribute zero; kz wraps;
+ *   - the integral dE/2pi over the uniform energy grid is the sum over E times
+ *     `scale` (= grid step / 2pi).
+ * Output Pi^t [Nqz][Nw][NA][NB+1][3][3]. Each trace is evaluated as
+ * tr{ (dH_i^H G^t_aa)(dH_j G^{t'}_ll) }, the two half products formed once per
+ * (E, k) of the bond (associativity of the matrix product).
+ */
+typedef struct {
+    const sse_oracle_dims* d;
+    const int32_t* nbr;
+    const cplx* dH;
+    const cplx* G[2];
+    cplx* acc; /* [2][nA][NB][Nqz][Nw][9] unscaled bond sums */
+    long long n_jobs, next;
+    pthread_mutex_t lock;
+    int fail;
+} pi_job;
+
+static size_t off_pi(const sse_oracle_dims* d, int q, int w, int a, int slot) {
+    return ((((size_t)q * d->Nw + w) * d->NA + a) * (d->NB + 1) + slot) * 9;
+}
+
+/* One bond (t, a, s): acc[q][w][i*3+j] = sum_k sum_E tr{ dH_i^H G^t_a(E+w+1, k+q) dH_j G^{t'}_b(E, k) }. */
+static void pi_bond(pi_job* J, int t, int a, int s, cplx* P, cplx* R, cplx* acc) {
+    const sse_oracle_dims* d = J->d;
+    const int n = d->Norb, nn = n * n;
+    const int b = J->nbr[(size_t)a * d->NB + s];
+    const cplx* A = J->dH + off_dH(d, a, s, 0);
+    /* P[k][E][i] = dH_i^H G^t_a(E, k);  R[k][E][j] = dH_j G^{t'}_b(E, k) */
+    for (int k = 0; k < d->Nkz; ++k)
+        for (int E = 0; E < d->NE; ++E)
+            for (int i = 0; i < 3; ++i) {
+                const size_t o = (((size_t)k * d->NE + E) * 3 + i) * nn;
+                mm_ah(n, A + (size_t)i * nn, J->G[t] + off_G(d, k, E, a), P + o);
+                mm(n, A + (size_t)i * nn, J->G[1 - t] + off_G(d, k, E, b), R + o);
+            }
+    for (int q = 0; q < d->Nqz; ++q)
+        for (int w = 0; w < d->Nw; ++w) {
+            cplx* o = acc + ((size_t)q * d->Nw + w) * 9;
+            for (int e = 0; e < 9; ++e) o[e] = 0;
+            for (int k = 0; k < d->Nkz; ++k) {
+                const int kp = (k + q) % d->Nkz; /* kz + qz, periodic */
+                for (int E = 0; E < d->NE; ++E) {
+                    const int Ep = E + (w + 1);
+                    if (Ep >= d->NE) continue; /* out of range: zero */
+                    for (int i = 0; i < 3; ++i) {
+                        const cplx* Pi = P + (((size_t)kp * d->NE + Ep) * 3 + i) * nn;
+                        for (int j = 0; j < 3; ++j) {
+                            const cplx* Rj = R + (((size_t)k * d->NE + E) * 3 + j) * nn;
+                            cplx tr = 0; /* tr(Pi Rj) */
+                            for (int m = 0; m < n; ++m)
+                                for (int l = 0; l < n; ++l) tr += Pi[m * n + l] * Rj[l * n + m];
+                            o[i * 3 + j] += tr;
+                        }
+                    }
+                }
+            }
+        }
+}
+
+static void* pi_worker(void* arg) {
+    pi_job* J = (pi_job*)arg;
+    const sse_oracle_dims* d = J->d;
+    const size_t half = (size_t)d->Nkz * d->NE * 3 * d->Norb * d->Norb;
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * 2 * half);
+    if (!buf) {
+        pthread_mutex_lock(&J->lock);
+        J->fail = 1;
+        pthread_mutex_unlock(&J->lock);
+        return NULL;
+    }
+    const int nA = d->a_end - d->a_begin;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        long long o = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (o >= J->n_jobs) break;
+        const int s = (int)(o % d->NB);
+        const int la = (int)((o / d->NB) % nA);
+        const int t = (int)(o / ((long long)d->NB * nA));
+        pi_bond(J, t, d->a_begin + la, s, buf, buf + half,
+                J->acc + (((size_t)t * nA + la) * d->NB + s) * d->Nqz * d->Nw * 9);
+    }
+    free(buf);
+    return NULL;
+}
+
+/*
+ * Pi^<, Pi^> of Eq. (4) for atoms [a_begin, a_end): all NB+1 slots, all (qz, w).
+ * Blocks of other atoms are untouched. Nqz and Nw are the phonon grid sizes of
+ * the output. Host pointers, complex128 interleaved. Returns 0 on success.
+ */
+int sse_oracle_pi(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH, const cplx* G_less,
+                  const cplx* G_greater, double scale, cplx* P_less, cplx* P_greater, int nthreads) {
+    if (!check_dims(d) || !nbr || !dH || !G_less || !G_greater || !P_less || !P_greater) return ORACLE_BAD_ARG;
+    for (size_t e = 0; e < (size_t)d->NA * d->NB; ++e)
+        if (nbr[e] < 0 || nbr[e] >= d->NA) return ORACLE_BAD_ARG;
+    const int nA = d->a_end - d->a_begin;
+    const size_t per_bond = (size_t)d->Nqz * d->Nw * 9;
+    pi_job J;
+    memset(&J, 0, sizeof J);
+    J.d = d;
+    J.nbr = nbr;
+    J.dH = dH;
+    J.G[0] = G_less;
+    J.G[1] = G_greater;
+    J.acc = (cplx*)calloc((size_t)2 * nA * d->NB * per_bond + 1, sizeof(cplx));
+    if (!J.acc) return ORACLE_NO_MEM;
+    J.n_jobs = 2LL * nA * d->NB;
+    pthread_mutex_init(&J.lock, NULL);
+    run_threads(pi_worker, &J, nthreads);
+    pthread_mutex_destroy(&J.lock);
+    if (J.fail) {
+        free(J.acc);
+        return ORACLE_NO_MEM;
+    }
+    const cplx c = -I * scale;
+    cplx* out[2] = {P_less, P_greater};
+    for (int t = 0; t < 2; ++t)
+        for (int la = 0; la < nA; ++la)
+            for (int q = 0; q < d->Nqz; ++q)
+                for (int w = 0; w < d->Nw; ++w) {
+                    const int a = d->a_begin + la;
+                    cplx self[9] = {0};
+                    for (int s = 0; s < d->NB; ++s) {
+                        const cplx* v = J.acc + ((((size_t)t * nA + la) * d->NB + s) * per_bond) +
+                                        ((size_t)q * d->Nw + w) * 9;
+                        cplx* o = out[t] + off_pi(d, q, w, a, s);
+                        for (int e = 0; e < 9; ++e) {
+                            o[e] = c * v[e];  /* l = b */
+                            self[e] += v[e];  /* diagonal block: sum over all neighbours l */
+                        }
+                    }
+                    cplx* o = out[t] + off_pi(d, q, w, a, d->NB);
+                    for (int e = 0; e < 9; ++e) o[e] = c * self[e];
+                }
+    free(J.acc);
     return ORACLE_OK;
 }

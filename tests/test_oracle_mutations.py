@@ -1,8 +1,9 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case plants one mistake in a copy of oracle/sse_oracle.c (on the CPU),
-builds it, and checks that at least one pin of tests/test_oracle_pins.py or
-tests/test_oracle_adjoint.py fails against the mutated build.
+builds it, and checks that at least one pin (tests/test_oracle_pins.py,
+tests/test_oracle_adjoint.py, tests/test_oracle_dcomb.py, tests/test_oracle_pi.py)
+fails against the mutated build.
 """
 import os
 
@@ -53,6 +54,36 @@ DCOMB = [
      "for (int e = 0; e < 9; ++e) o[e] = Dba[e] - Dbb[e] + Daa[e] + Dab[e];"),
     ("adjoint misses the D_bb term", "                            Dbb[e] -= gi[e];\n", "\n"),
 ]
+PI = [
+    ("G_ll of the same type", "mm(n, A + (size_t)i * nn, J->G[1 - t] + off_G(d, k, E, b), R + o);",
+     "mm(n, A + (size_t)i * nn, J->G[t] + off_G(d, k, E, b), R + o);"),
+    ("energy shift sign", "const int Ep = E + (w + 1);\n                    if (Ep >= d->NE) continue;",
+     "const int Ep = E - (w + 1);\n                    if (Ep < 0) continue;"),
+    ("frequency offset off by one", "const int Ep = E + (w + 1);\n                    if (Ep >= d->NE) continue;",
+     "const int Ep = E + (w + 0);\n                    if (Ep >= d->NE) continue;"),
+    ("edge energies wrapped", "const int Ep = E + (w + 1);\n                    if (Ep >= d->NE) continue;",
+     "const int Ep = (E + (w + 1)) % d->NE;\n                    if (Ep >= d->NE) continue;"),
+    ("kz shift sign", "const int kp = (k + q) % d->Nkz; /* kz + qz, periodic */",
+     "const int kp = ((k - q) % d->Nkz + d->Nkz) % d->Nkz; /* kz + qz, periodic */"),
+    ("left coupling not conjugate-transposed", "mm_ah(n, A + (size_t)i * nn, J->G[t] + off_G(d, k, E, a), P + o);",
+     "mm(n, A + (size_t)i * nn, J->G[t] + off_G(d, k, E, a), P + o);"),
+    ("neighbour G replaced by own atom", "mm(n, A + (size_t)i * nn, J->G[1 - t] + off_G(d, k, E, b), R + o);",
+     "mm(n, A + (size_t)i * nn, J->G[1 - t] + off_G(d, k, E, a), R + o);"),
+    ("(i, j) transposed", "o[i * 3 + j] += tr;", "o[j * 3 + i] += tr;"),
+    ("prefactor sign", "const cplx c = -I * scale;", "const cplx c = I * scale;"),
+    ("diagonal block misses a neighbour", "self[e] += v[e];  /* diagonal", "if (s > 0) self[e] += v[e];  /* diagonal"),
+]
+
+
+def _pi_pins():
+    import test_oracle_pi as pp
+    yield pp.test_closed_form_constant_G
+    for args in [(2, 6, 0, 3), (0, 4, 1, 0), (1, 8, 1, 7)]:
+        yield lambda a=args: pp.test_delta_response(*a)
+    yield pp.test_anti_hermitian_blocks
+    yield pp.test_quadratic_in_coupling
+    yield lambda: pp.test_equals_sigma_adjoint_weight_gradient("ring")
+    yield lambda: pp.test_equals_sigma_adjoint_weight_gradient("two_way_ring")
 
 
 def _dcomb_pins():
@@ -117,6 +148,11 @@ def test_dcomb_mutation_is_caught(tmp_path, name, old, new):
     assert _caught(_build(tmp_path, old, new), _dcomb_pins()), f"no pin caught: {name}"
 
 
+@pytest.mark.parametrize("name,old,new", PI, ids=[m[0] for m in PI])
+def test_pi_mutation_is_caught(tmp_path, name, old, new):
+    assert _caught(_build(tmp_path, old, new), _pi_pins()), f"no pin caught: {name}"
+
+
 def test_unmutated_source_passes(tmp_path):
     so = _build(tmp_path, "#include <complex.h>", "#include <complex.h>")
-    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()) + list(_dcomb_pins()))
+    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()) + list(_dcomb_pins()) + list(_pi_pins()))
