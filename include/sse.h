@@ -68,8 +68,17 @@ typedef struct sse_dims {
  *            one qz slice, FP64 sums over qz, neighbours and the final
  *            multiply by dH (Sec. 4.4 adapted to TF32).
  *   BF16X3 : like TF32 but each operand split into bf16 hi + lo parts and the
- *            three products hi*hi + hi*lo + lo*hi accumulated in FP32. */
-typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 2 } sse_mode;
+ *            three products hi*hi + hi*lo + lo*hi accumulated in FP32.
+ *   FP64_FFT : IEEE double throughout, evaluated with the convolution theorem:
+ *            Eq. (3) is, per bond, a convolution of G^t_b with the phonon
+ *            weights over (E, kz) -- cyclic in kz, linear in E -- so G is
+ *            transformed (zero-padded in E to L >= NE + Nw, L = 2^a 3^b 5^c),
+ *            each frequency needs 6 Norb x Norb block products per bond, and
+ *            the result is transformed back. Same values as FP64 up to the
+ *            rounding of the transforms (normwise ~1e-15), far fewer flops;
+ *            workspace Nkz*L*(NA + 2*nA)*Norb^2*16 + Nkz*L*nA*NB*9*16 bytes
+ *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~6000. */
+typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 2, SSE_MODE_FP64_FFT = 3 } sse_mode;
 
 /* SYMMETRIZE: replace each output block S by (S - S^H)/2 in FP64 before the
  *             store (exact Sigma is anti-Hermitian when G and D are; this
@@ -107,7 +116,8 @@ SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* d
                   uint32_t flags, double* S_less, double* S_greater, void* workspace, size_t ws_bytes,
                   void* stream);
 
-/* Adjoint of sse_sigma_fwd (FP64 mode only). For the loss
+/* Adjoint of sse_sigma_fwd (modes FP64 and FP64_FFT, both run the FP64 adjoint
+ * kernels). For the loss
  *   L = sum_t sum_{a in range, E, k} Re tr( gS^t_a(E,k)^H Sigma^t_a(E,k) )
  * it writes the gradients w.r.t. dH, D^< and D^> in the PyTorch convention
  * for complex tensors (grad z = dL/dRe z + i dL/dIm z):

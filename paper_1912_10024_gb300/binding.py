@@ -16,9 +16,9 @@ import torch
 
 from . import build as _build
 
-SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3 = 0, 1, 2
+SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT = 0, 1, 2, 3
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK = 1, 2
-MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3}
+MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
             "sse_dcomb_bwd", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20

@@ -29,11 +29,15 @@ bool supported_dims(const sse_dims* d) {
     return g < 4e18 && dd < 4e18;
 }
 
-bool valid_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3; }
+bool valid_mode(int mode) {
+    return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3 || mode == SSE_MODE_FP64_FFT;
+}
+bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
 bool valid_flags(uint32_t f) { return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK)) == 0; }
 
 size_t fwd_ws(const sse_dims& d, int mode) {
     if (mode == SSE_MODE_FP64) return sse::fp64_fwd_workspace(d);
+    if (mode == SSE_MODE_FP64_FFT) return sse::spectral_fwd_workspace(d);
     return sse::mixed_fwd_workspace(d, mode);
 }
 
@@ -93,7 +97,7 @@ extern "C" const char* sse_strerror(int status) {
 extern "C" size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
     if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
     size_t f = fwd_ws(*d, mode);
-    size_t b = mode == SSE_MODE_FP64 ? sse::fp64_bwd_workspace(*d) : 0;
+    size_t b = fp64_mode(mode) ? sse::fp64_bwd_workspace(*d) : 0;
     return sse::kStatusBytes + (f > b ? f : b);
 }
 
@@ -115,8 +119,9 @@ extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double
     const sse::Problem p = make_problem(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, flags);
     double2* Sl = reinterpret_cast<double2*>(S_less);
     double2* Sg = reinterpret_cast<double2*>(S_greater);
-    cudaError_t e = mode == SSE_MODE_FP64 ? sse::fp64_fwd(p, Sl, Sg, status, ws, wsb, st)
-                                          : sse::mixed_fwd(p, mode, Sl, Sg, status, ws, wsb, st);
+    cudaError_t e = mode == SSE_MODE_FP64       ? sse::fp64_fwd(p, Sl, Sg, status, ws, wsb, st)
+                    : mode == SSE_MODE_FP64_FFT ? sse::spectral_fwd(p, Sl, Sg, status, ws, wsb, st)
+                                                : sse::mixed_fwd(p, mode, Sl, Sg, status, ws, wsb, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }
@@ -132,7 +137,7 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
     if (!aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_dH, 16) || !aligned(g_D_less, 16) ||
         !aligned(g_D_greater, 16))
         return SSE_ERR_INVALID_ARG;
-    if (mode != SSE_MODE_FP64) return SSE_ERR_UNSUPPORTED;
+    if (!fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
     if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::fp64_bwd_workspace(*d))
         return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;

@@ -44,6 +44,13 @@ size_t mixed_fwd_workspace(const sse_dims& d, int mode);
 cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status,
                       void* ws, size_t ws_bytes, cudaStream_t st);
 
+// Transform-based FP64 forward (sse_spectral.cu): FFT length along E, size limits, workspace.
+int spectral_length(const sse_dims& d);
+bool spectral_supported(const sse_dims& d);
+size_t spectral_fwd_workspace(const sse_dims& d);
+cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                         size_t ws_bytes, cudaStream_t st);
+
 // Bond weights D_ba - D_bb - D_aa + D_ab from raw phonon Green's functions (sse_dcomb.cu).
 cudaError_t dcomb_fwd(const sse_dims& d, const int32_t* nbr, const double2* raw_l, const double2* raw_g,
                       double2* Dl, double2* Dg, unsigned* status, cudaStream_t st);

@@ -1,0 +1,533 @@
+// Transform-based FP64 forward of Eq. (3) (the convolution theorem along kz and E).
+//
+// For one bond (a, s), b = nbr[a][s], Eq. (3) is a 2-D convolution of G^t_b
+// with a lag kernel K:
+//
+//   Sigma^t_a(E,k) = i*scale * sum_s sum_ij sum_{q,l} K^{t,(a,s)}_ij(q,l) dH_i G^t_b(E-l, k-q) dH_j^H,
+//   K(q, l = +(w+1)) = D^t(q,w,a,s),  K(q, l = -(w+1)) = D^{t'}(q,w,a,s)   (t' = other type),
+//
+// cyclic in kz (period Nkz) and linear in E (G is zero outside [0, NE)). With
+// G zero-padded to a length L >= NE + Nw the linear convolution equals the
+// cyclic one of period L on [0, NE), so with DFTs over (kz, E) -> (kappa, eps)
+//
+//   Sigma^^t_a(kappa,eps) = i*scale * sum_s sum_i dH_i G^^t_b(kappa,eps) W_i(kappa,eps),
+//   W_i = sum_j K^^_ij(kappa,eps) dH_j^H,
+//
+// i.e. per frequency and bond 6 products of Norb x Norb blocks instead of the
+// 2*Nqz*Nw*3 of the direct form. Steps, per type t (FP64 throughout):
+//   1. G^t -> E-FFT (length L, zero-padded) -> kz-DFT (length Nkz)   -> G^^   [Nkz][L][NA][Norb^2]
+//   2. D^t, D^t' placed at lags +-(w+1) -> E-FFT -> qz->kappa DFT      -> K^^   [Nkz][L][nA][NB][9]
+//   3. per (a, frequency): the block products above (Gauss 3-multiply
+//      complex MACs on pre-formed (re, im, re+im) planes)             -> S^^   [Nkz][L][nA][Norb^2]
+//   4. inverse kz-DFT, inverse E-FFT, scale 1/(Nkz L), keep E < NE     -> Sigma^t
+// The E-FFT is a Stockham radix-4/2/3/5 transform of C columns at once in
+// shared memory (L = smallest 2^a 3^b 5^c >= NE + Nw); twiddles come from one
+// table of exp(-2 pi i m / L) built with sincospi. The results equal Eq. (3)
+// up to the rounding of the transforms (normwise ~1e-15).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sse_internal.h"
+
+namespace sse {
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kFftSmemBudget = 200 * 1024;
+constexpr int kMaxStages = 24;
+constexpr int kMaxNk = 16;  // kz grid sizes handled by the small DFT pass
+
+struct FftPlan {
+    int L, C, nst;
+    int radix[kMaxStages];
+    int smem;  // two L x C buffers + the twiddle table
+};
+
+FftPlan make_plan(int L) {
+    FftPlan p{};
+    p.L = L;
+    int m = L;
+    while (m % 4 == 0) p.radix[p.nst++] = 4, m /= 4;
+    while (m % 2 == 0) p.radix[p.nst++] = 2, m /= 2;
+    while (m % 3 == 0) p.radix[p.nst++] = 3, m /= 3;
+    while (m % 5 == 0) p.radix[p.nst++] = 5, m /= 5;
+    p.C = 16;
+    while (p.C > 1 && (2 * (size_t)L * p.C + L) * 16 > (size_t)kFftSmemBudget) p.C /= 2;
+    p.smem = (int)((2 * (size_t)L * p.C + L) * 16);
+    return p;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// tw[m] = exp(-2 pi i m / L)
+__global__ void twiddle_kernel(int L, double2* __restrict__ tw) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < L; m += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)m / (double)L, &s, &c);
+        tw[m] = make_double2(c, -s);
+    }
+}
+
+// In-place forward DFT of R values (R in {2, 3, 4, 5}); tw is the length-L table.
+__device__ __forceinline__ void dft_small(int R, double2* v, const double2* tw, int L) {
+    if (R == 2) {
+        const double2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        const double2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const double2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        const double2 md13 = make_double2(d13.y, -d13.x);  // -i * d13
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, md13);
+        v[3] = csub(d02, md13);
+    } else if (R == 3) {
+        const double2 w1 = tw[L / 3];  // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
+        const double2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        const double2 m = make_double2(v[0].x + w1.x * t.x, v[0].y + w1.x * t.y);
+        const double2 r = make_double2(-w1.y * d.y, w1.y * d.x);  // i * Im(w1) * d
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    } else {  // R == 5: plain 5-point DFT with table twiddles
+        double2 w[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) w[e] = tw[(e * (L / 5))];
+        double2 y[5];
+#pragma unroll
+        for (int p = 0; p < 5; ++p) {
+            double2 acc = v[0];
+#pragma unroll
+            for (int r = 1; r < 5; ++r) acc = cadd(acc, cmul(v[r], w[(r * p) % 5]));
+            y[p] = acc;
+        }
+#pragma unroll
+        for (int p = 0; p < 5; ++p) v[p] = y[p];
+    }
+}
+
+// Stockham autosort FFT of C columns stored [L][C] in `src`; returns the buffer holding the result.
+__device__ double2* fft_columns(const FftPlan& p, double2* src, double2* dst, const double2* tw) {
+    int Ns = 1;
+    for (int st = 0; st < p.nst; ++st) {
+        const int R = p.radix[st];
+        const int nb = p.L / R;
+        const int span = p.L / (Ns * R);
+        for (int it = threadIdx.x; it < nb * p.C; it += blockDim.x) {
+            const int j = it / p.C, c = it - j * p.C;
+            const int k = j % Ns;
+            double2 v[5];
+            for (int r = 0; r < R; ++r) {
+                v[r] = src[(size_t)(j + r * nb) * p.C + c];
+                if (r > 0 && k > 0) v[r] = cmul(v[r], tw[r * k * span]);
+            }
+            dft_small(R, v, tw, p.L);
+            const int d0 = (j / Ns) * Ns * R + k;
+            for (int r = 0; r < R; ++r) dst[(size_t)(d0 + r * Ns) * p.C + c] = v[r];
+        }
+        __syncthreads();
+        double2* t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+// ---------------------------------------------------------------------------
+// E-direction transforms. Each CTA transforms C consecutive columns of one
+// batch (kz slice or qz slice); the loader yields row r (r < L) of column col.
+// ---------------------------------------------------------------------------
+
+// G^t[k][E][col] (col over NA*Norb^2), rows E >= NE are zero  ->  out[k][eps][col]
+struct LoadG {
+    const double2* G;
+    int NE;
+    size_t ncols;
+    __device__ double2 operator()(int k, int r, size_t col) const {
+        return r < NE ? G[((size_t)k * NE + r) * ncols + col] : make_double2(0.0, 0.0);
+    }
+};
+// lag kernel of one qz slice: row w+1 <- D^t(q,w), row L-(w+1) <- D^t'(q,w), else zero.
+// col over (a - a_begin, s, ij); D rows have NA*NB*9 entries, the range starts at a_begin*NB*9.
+struct LoadLag {
+    const double2* Dt;
+    const double2* Dtb;
+    int Nw, L;
+    size_t rowlen, col0;
+    __device__ double2 operator()(int q, int r, size_t col) const {
+        if (r >= 1 && r <= Nw) return Dt[((size_t)q * Nw + (r - 1)) * rowlen + col0 + col];
+        if (r >= L - Nw) return Dtb[((size_t)q * Nw + (L - 1 - r)) * rowlen + col0 + col];
+        return make_double2(0.0, 0.0);
+    }
+};
+// spectrum [k][eps][col], conjugated (inverse transform = conj(FFT(conj(x))))
+struct LoadSpecConj {
+    const double2* X;
+    int L;
+    size_t ncols;
+    __device__ double2 operator()(int k, int r, size_t col) const {
+        return cconj(X[((size_t)k * L + r) * ncols + col]);
+    }
+};
+
+struct StoreSpec {  // out[batch][r][col]
+    double2* X;
+    int L;
+    size_t ncols;
+    int rows;
+    __device__ void operator()(int b, int r, size_t col, double2 v) const { X[((size_t)b * L + r) * ncols + col] = v; }
+};
+struct StoreSigma {  // S[k][E][a_begin*nel + col] = conj(v) * inv, E < NE
+    double2* S;
+    int NE;
+    size_t rowlen, col0;
+    double inv;
+    int rows;
+    __device__ void operator()(int k, int r, size_t col, double2 v) const {
+        S[((size_t)k * NE + r) * rowlen + col0 + col] = make_double2(v.x * inv, -v.y * inv);
+    }
+};
+
+template <class Load, class Store>
+__global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const double2* __restrict__ tw_g, Load ld,
+                                                            Store sv, size_t ncols) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* b0 = reinterpret_cast<double2*>(smem_raw);
+    double2* b1 = b0 + (size_t)p.L * p.C;
+    double2* tw = b1 + (size_t)p.L * p.C;
+    const size_t col0 = (size_t)blockIdx.x * p.C;
+    const int batch = blockIdx.y;
+    for (int m = threadIdx.x; m < p.L; m += blockDim.x) tw[m] = tw_g[m];
+    for (int it = threadIdx.x; it < p.L * p.C; it += blockDim.x) {
+        const int r = it / p.C, c = it - r * p.C;
+        b0[it] = (col0 + c < ncols) ? ld(batch, r, col0 + c) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const double2* res = fft_columns(p, b0, b1, tw);
+    for (int it = threadIdx.x; it < sv.rows * p.C; it += blockDim.x) {
+        const int r = it / p.C, c = it - r * p.C;
+        if (col0 + c < ncols) sv(batch, r, col0 + c, res[it]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kz-direction DFT, in place on X[Nk][M]: out[kappa] = sum_{k < n_in} in[k] exp(-+2 pi i k kappa / Nk)
+// ---------------------------------------------------------------------------
+__global__ void dft_k_kernel(double2* __restrict__ X, int Nk, int n_in, size_t M, int inverse) {
+    __shared__ double2 w[kMaxNk];
+    if (threadIdx.x < Nk) {
+        double s, c;
+        sincospi(2.0 * (double)threadIdx.x / (double)Nk, &s, &c);
+        w[threadIdx.x] = make_double2(c, inverse ? s : -s);
+    }
+    __syncthreads();
+    for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
+        double2 in[kMaxNk];
+        for (int k = 0; k < n_in; ++k) in[k] = X[(size_t)k * M + m];
+        for (int kap = 0; kap < Nk; ++kap) {
+            double2 acc = in[0];
+            for (int k = 1; k < n_in; ++k) acc = cadd(acc, cmul(in[k], w[(k * kap) % Nk]));
+            X[(size_t)kap * M + m] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-frequency block products
+// ---------------------------------------------------------------------------
+constexpr int kProdMaxThreads = 384;
+
+struct ProdCfg {
+    int nel, F, threads, fchunk;
+    int off_A, off_G, off_K, off_W, off_U, smem;
+};
+
+ProdCfg make_prod_cfg(const sse_dims& d, size_t nfreq) {
+    ProdCfg c{};
+    c.nel = d.Norb * d.Norb;
+    c.F = kProdMaxThreads / c.nel;
+    if (c.F < 1) c.F = 1;
+    c.threads = ((c.F * c.nel + 31) / 32) * 32;
+    const int pl = c.nel * 24;  // one (re, im, re+im) plane triple
+    auto a16 = [](int x) { return (x + 15) & ~15; };  // every region starts on a 16-byte boundary
+    c.off_A = 0;                                   // [NB][3][planes]
+    c.off_G = a16(c.off_A + d.NB * 3 * pl);        // [F][planes]
+    c.off_K = a16(c.off_G + c.F * pl);             // [F][9] complex
+    c.off_W = a16(c.off_K + c.F * 9 * 16);         // [F][3][planes]
+    c.off_U = a16(c.off_W + c.F * 3 * pl);         // [F][3][planes]
+    c.smem = a16(c.off_U + c.F * 3 * pl);
+    // frequencies per CTA: enough CTAs for ~8 waves of 2 CTAs per SM over all atoms
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    size_t want = (size_t)152 * 2 * 8;
+    size_t chunks = (want + nA - 1) / (nA ? nA : 1);
+    if (chunks < 1) chunks = 1;
+    size_t fc = (nfreq + chunks - 1) / chunks;
+    fc = ((fc + c.F - 1) / c.F) * c.F;
+    c.fchunk = (int)(fc < 1 ? 1 : fc);
+    return c;
+}
+
+// Planes of a complex block: re, im, re+im (Gauss 3-multiply MACs).
+__device__ __forceinline__ void put3(double* P, int nel, int e, double2 v) {
+    P[e] = v.x;
+    P[nel + e] = v.y;
+    P[2 * nel + e] = v.x + v.y;
+}
+
+__global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restrict__ nbr,
+                                 const double2* __restrict__ dH, const double2* __restrict__ Ghat,
+                                 const double2* __restrict__ Khat, double2* __restrict__ Shat, int L, double scale,
+                                 unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Norb = d.Norb, nel = c.nel;
+    const int la = blockIdx.x;
+    const int a = d.a_begin + la;
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const size_t nfreq = (size_t)d.Nkz * L;
+    const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
+    const size_t f_end = min(nfreq, f_begin + c.fchunk);
+    double* sA = reinterpret_cast<double*>(smem + c.off_A);
+    double* sG = reinterpret_cast<double*>(smem + c.off_G);
+    double2* sK = reinterpret_cast<double2*>(smem + c.off_K);
+    double* sW = reinterpret_cast<double*>(smem + c.off_W);
+    double* sU = reinterpret_cast<double*>(smem + c.off_U);
+    const int tid = threadIdx.x;
+    const int fl = tid / nel, e = tid - fl * nel;
+    const int m = e / Norb, n = e - m * Norb;
+    const bool lane = fl < c.F;
+
+    for (int i = tid; i < d.NB * 3 * nel; i += blockDim.x) {
+        const int si = i / nel, ee = i - si * nel;
+        put3(sA + (size_t)si * 3 * nel, nel, ee, dH[((size_t)a * d.NB) * 3 * nel + i]);
+    }
+    int bnb[16];
+    for (int s = 0; s < d.NB && s < 16; ++s) {
+        const int b = nbr[(size_t)a * d.NB + s];
+        bnb[s] = (b >= 0 && b < d.NA) ? b : -1;
+        if (bnb[s] < 0 && tid == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
+    }
+    __syncthreads();
+
+    for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
+        const size_t f = f0 + fl;
+        const bool act = lane && f < f_end;
+        double T1 = 0.0, T2 = 0.0, T3 = 0.0;
+        for (int s = 0; s < d.NB; ++s) {
+            const int b = s < 16 ? bnb[s] : -1;
+            // stage G^_b(f) and K^_(a,s)(f)
+            if (lane) {
+                double2 g = make_double2(0.0, 0.0);
+                if (act && b >= 0) g = Ghat[(f * d.NA + b) * nel + e];
+                put3(sG + (size_t)fl * 3 * nel, nel, e, g);
+            }
+            for (int i = tid; i < c.F * 9; i += blockDim.x) {
+                const int fk = i / 9, ij = i - fk * 9;
+                const size_t ff = f0 + fk;
+                double2 k = make_double2(0.0, 0.0);
+                if (ff < f_end && b >= 0) k = Khat[((ff * nA + la) * d.NB + s) * 9 + ij];
+                sK[i] = k;
+            }
+            __syncthreads();
+            // W_i[m][n] = sum_j K_ij conj(dH_j[n][m])
+            if (lane) {
+                const double* A = sA + (size_t)s * 9 * nel;
+                const int et = n * Norb + m;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const double2 k = sK[fl * 9 + i * 3 + j];
+                        const double ar = A[(size_t)j * 3 * nel + et], ai = -A[(size_t)j * 3 * nel + nel + et];
+                        acc.x += k.x * ar - k.y * ai;
+                        acc.y += k.x * ai + k.y * ar;
+                    }
+                    put3(sW + ((size_t)fl * 3 + i) * 3 * nel, nel, e, acc);
+                }
+            }
+            __syncthreads();
+            // U_i = G^ W_i
+            if (lane) {
+                const double* Gp = sG + (size_t)fl * 3 * nel;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double* Wp = sW + ((size_t)fl * 3 + i) * 3 * nel;
+                    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+                    for (int l = 0; l < Norb; ++l) {
+                        const int ga = m * Norb + l, wb = l * Norb + n;
+                        t1 = fma(Gp[ga], Wp[wb], t1);
+                        t2 = fma(Gp[nel + ga], Wp[nel + wb], t2);
+                        t3 = fma(Gp[2 * nel + ga], Wp[2 * nel + wb], t3);
+                    }
+                    put3(sU + ((size_t)fl * 3 + i) * 3 * nel, nel, e, make_double2(t1 - t2, t3 - t1 - t2));
+                }
+            }
+            __syncthreads();
+            // acc += sum_i dH_i U_i
+            if (lane) {
+                const double* A = sA + (size_t)s * 9 * nel;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double* Ap = A + (size_t)i * 3 * nel;
+                    const double* Up = sU + ((size_t)fl * 3 + i) * 3 * nel;
+                    for (int l = 0; l < Norb; ++l) {
+                        const int aa = m * Norb + l, ub = l * Norb + n;
+                        T1 = fma(Ap[aa], Up[ub], T1);
+                        T2 = fma(Ap[nel + aa], Up[nel + ub], T2);
+                        T3 = fma(Ap[2 * nel + aa], Up[2 * nel + ub], T3);
+                    }
+                }
+            }
+        }
+        if (act) {
+            const double re = T1 - T2, im = T3 - T1 - T2;
+            Shat[(f * nA + la) * nel + e] = make_double2(-scale * im, scale * re);  // i*scale*(re + i im)
+        }
+    }
+}
+
+// (S - S^H)/2 on the blocks of atoms in range
+__global__ void symmetrize_kernel(sse_dims d, double2* __restrict__ S) {
+    const int Norb = d.Norb, nel = Norb * Norb;
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const size_t nblk = (size_t)d.Nkz * d.NE * nA;
+    const size_t total = nblk * nel;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % nel);
+        const size_t blk = i / nel;
+        const int m = e / Norb, n = e - m * Norb;
+        if (n < m) continue;
+        const size_t ke = blk / nA, la = blk - ke * nA;
+        double2* B = S + (ke * d.NA + d.a_begin + la) * nel;
+        const double2 x = B[m * Norb + n], y = B[n * Norb + m];
+        B[m * Norb + n] = make_double2(0.5 * (x.x - y.x), 0.5 * (x.y + y.y));
+        if (m != n) B[n * Norb + m] = make_double2(0.5 * (y.x - x.x), 0.5 * (y.y + x.y));
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct SpecLayout {
+    int L;
+    size_t off_tw, off_G, off_K, off_S, total;
+};
+
+SpecLayout spec_layout(const sse_dims& d) {
+    SpecLayout l{};
+    l.L = spectral_length(d);
+    const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
+    const size_t spec = (size_t)d.Nkz * l.L;
+    l.off_tw = 0;
+    l.off_G = align256(l.off_tw + (size_t)l.L * 16);
+    l.off_K = align256(l.off_G + spec * d.NA * nel * 16);
+    l.off_S = align256(l.off_K + spec * nA * d.NB * 9 * 16);
+    l.total = align256(l.off_S + spec * nA * nel * 16);
+    return l;
+}
+
+unsigned grid_for(size_t work, int threads) {
+    size_t g = (work + threads - 1) / threads;
+    const size_t cap = (size_t)152 * 16;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+template <class Load, class Store>
+cudaError_t launch_fft(const FftPlan& p, const double2* tw, Load ld, Store sv, size_t ncols, int batches,
+                       cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(fft_e_kernel<Load, Store>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    if (e != cudaSuccess) return e;
+    const size_t gx = (ncols + p.C - 1) / p.C;
+    if (gx > 0x7fffffffu || batches > 65535) return cudaErrorInvalidValue;
+    fft_e_kernel<Load, Store><<<dim3((unsigned)gx, (unsigned)batches), kFftThreads, p.smem, st>>>(p, tw, ld, sv, ncols);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int spectral_length(const sse_dims& d) {
+    for (int L = d.NE + d.Nw;; ++L) {
+        int m = L;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        while (m % 5 == 0) m /= 5;
+        if (m == 1) return L;
+    }
+}
+
+bool spectral_supported(const sse_dims& d) {
+    const int L = spectral_length(d);
+    return d.Nkz <= kMaxNk && make_plan(L).smem <= kFftSmemBudget && d.NB <= 16 &&
+           make_prod_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
+}
+
+size_t spectral_fwd_workspace(const sse_dims& d) { return spec_layout(d).total; }
+
+cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                         size_t ws_bytes, cudaStream_t st) {
+    const sse_dims& d = p.d;
+    if (!spectral_supported(d)) return cudaErrorNotSupported;
+    const SpecLayout lay = spec_layout(d);
+    if (ws_bytes < lay.total) return cudaErrorInvalidValue;
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    double2* tw = reinterpret_cast<double2*>(base + lay.off_tw);
+    double2* Gh = reinterpret_cast<double2*>(base + lay.off_G);
+    double2* Kh = reinterpret_cast<double2*>(base + lay.off_K);
+    double2* Sh = reinterpret_cast<double2*>(base + lay.off_S);
+    const int L = lay.L;
+    const FftPlan plan = make_plan(L);
+    const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
+    const size_t gcols = (size_t)d.NA * nel, kcols = nA * d.NB * 9, scols = nA * nel;
+    const size_t nfreq = (size_t)d.Nkz * L;
+    cudaError_t e;
+    if (nA == 0) return cudaSuccess;
+
+    twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const ProdCfg pc = make_prod_cfg(d, nfreq);
+    if ((e = cudaFuncSetAttribute(spec_prod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
+        cudaSuccess)
+        return e;
+    double2* S[2] = {S_less, S_greater};
+    for (int t = 0; t < 2; ++t) {
+        // 1. G^t -> G^
+        e = launch_fft(plan, tw, LoadG{p.G[t], d.NE, gcols}, StoreSpec{Gh, L, gcols, L}, gcols, d.Nkz, st);
+        if (e != cudaSuccess) return e;
+        dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 2. lag kernel -> K^
+        LoadLag ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
+        e = launch_fft(plan, tw, ll, StoreSpec{Kh, L, kcols, L}, kcols, d.Nqz, st);
+        if (e != cudaSuccess) return e;
+        dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 3. block products
+        const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
+        spec_prod_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
+            pc, d, p.nbr, p.dH, Gh, Kh, Sh, L, p.scale, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 4. inverse transforms into Sigma^t
+        dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const double inv = 1.0 / ((double)d.Nkz * (double)L);
+        e = launch_fft(plan, tw, LoadSpecConj{Sh, L, scols},
+                       StoreSigma{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols, d.Nkz,
+                       st);
+        if (e != cudaSuccess) return e;
+        if (p.flags & SSE_FLAG_SYMMETRIZE) {
+            symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sse
