@@ -3,10 +3,13 @@
 
 One step = one sse_sigma_fwd call: Sigma^< and Sigma^> for every atom,
 energy and kz of the workload (default: the Si-FinFET-shaped problem,
-NA=1024, NB=4, Norb=10, NE=512, Nkz=Nqz=7, Nw=32, FP64), inputs resident in
-HBM. Prints one JSON line (rank 0).
+NA=1024, NB=4, Norb=10, NE=512, Nkz=Nqz=7, Nw=32), inputs resident in HBM.
+Default mode: FP64 through the convolution theorem (fp64_fft); the other
+modes (direct FP64, BF16X3, TF32) are timed on the same inputs in the
+"compare" object, with their error against this run's result. Prints one
+JSON line (rank 0).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--mode fp64|tf32|bf16x3]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--mode fp64_fft|fp64|tf32|bf16x3]
 
 Metric: useful TFLOP/s of the paper-equivalent (regrouped, Sec. 5.1) flop
 count, plus (E,kz) points/s. Multi-GPU (torchrun): every rank solves its own
@@ -62,6 +65,28 @@ def fp64_kernel_flops(d) -> float:
     nv = n_valid(d.NE, d.Nw)
     per = sum(54 * d.Norb ** 2 * d.Nqz * nv[E] + 96 * d.Norb ** 3 for E in range(d.NE))
     return 2.0 * d.NA * d.NB * d.Nkz * per
+
+
+def fft_length(NE: int, Nw: int) -> int:
+    """FFT length along E of the fp64_fft mode: the smallest 2^a 3^b 5^c >= NE + Nw."""
+    L = NE + Nw
+    while True:
+        m = L
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return L
+        L += 1
+
+
+def spectral_prod_flops(d) -> float:
+    """FP64 flops one spec_prod_kernel launch (one type) executes: per (atom, slot, frequency) and block
+    element, the weight block W_i (9 complex MACs at 4 FMA) and two block products (3 Norb complex
+    MACs each at 3 FMA, Gauss form); 2 flops per FMA."""
+    L = fft_length(d.NE, d.Nw)
+    nel = d.Norb * d.Norb
+    return 2.0 * d.NA * d.NB * d.Nkz * L * nel * (36 + 18 * d.Norb)
 
 
 def mixed_tensor_flops(d, mode: str) -> float:
@@ -165,6 +190,13 @@ def cpu_baseline(d, seconds: float, inp=None, seed: int = 0):
                       f"all kz, Sigma^< and Sigma^>; FP64 C loops (pthreads)"}
 
 
+def bench_config(args, d):
+    """The workload description shared by both arms."""
+    g_bytes = 2 * d.Nkz * d.NE * d.NA * d.Norb * d.Norb * 16
+    return {"workload": args.workload, **d.__dict__, "mode": args.mode,
+            "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (g_bytes / 1e9)}
+
+
 def run_reference(args, d, rank, world):
     if rank != 0:
         return 0
@@ -178,7 +210,7 @@ def run_reference(args, d, rank, world):
     out = {"impl": "reference", "metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": v,
            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, **d.__dict__, "mode": "fp64"},
+           "config": bench_config(args, d),
            "cpu_baseline": {**cb, "value": v},
            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -192,10 +224,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="finfet", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="fp64", choices=sorted(B.MODES))
+    ap.add_argument("--mode", default="fp64_fft", choices=sorted(B.MODES))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the BF16X3/TF32 comparison in an FP64 run")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other modes on the same inputs")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
 
@@ -224,9 +256,9 @@ def main():
     Sg = torch.empty_like(inp.G_greater)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def step(flags=0):
         rc = B.sse_sigma_fwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
-                             mode, 0, Sl, Sg, ws, ws.numel(), stream)
+                             mode, flags, Sl, Sg, ws, ws.numel(), stream)
         if rc != 0:
             raise B.SseError(rc, "sse_sigma_fwd")
 
@@ -235,20 +267,18 @@ def main():
     torch.cuda.synchronize(dev)
     barrier()
     torch.cuda.synchronize(dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    B.sse_profile_read()  # drop anything recorded before the timed region
     with ClockSampler(local) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for i in range(args.steps):
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
+            step(B.SSE_FLAG_PROFILE)  # CUDA events around each kernel, on this stream
         t1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
     total_ms = t0.elapsed_time(t1)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    kernels = {name: (ms, n) for name, ms, n in B.sse_profile_read()}
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -290,12 +320,15 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
         del host, hSl, hSg
 
-    # ---- FP64 vs mixed precision on the same inputs (the metric's comparison) ----
-    mixed = None
-    if args.mode == "fp64" and not args.no_mixed and rank == 0:
-        mixed = {}
+    # ---- the other modes on the same inputs (the metric's FP64-versus-mixed comparison) ----
+    compare = None
+    if not args.no_compare and rank == 0:
+        compare = {}
         ref = (Sl.clone(), Sg.clone())
-        for mname, bound in (("bf16x3", 2e-5), ("tf32", 2e-3)):
+        bounds = {"fp64": 1e-12, "fp64_fft": 1e-12, "bf16x3": 2e-5, "tf32": 2e-3}
+        for mname in ("fp64", "bf16x3", "tf32", "fp64_fft"):
+            if mname == args.mode:
+                continue
             m = B.MODES[mname]
             wsm = B.workspace(dims, m, 0, dev)
             Ml, Mg = torch.empty_like(Sl), torch.empty_like(Sg)
@@ -306,7 +339,8 @@ def main():
                 if rc != 0:
                     raise B.SseError(rc, "sse_sigma_fwd")
 
-            for _ in range(max(3, args.warmup)):
+            mw = 1 if mname == "fp64" else max(3, args.warmup)  # the direct FP64 kernel runs about a minute
+            for _ in range(mw):
                 mstep()
             torch.cuda.synchronize(dev)
             m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -316,46 +350,56 @@ def main():
             m1.record(stream)
             torch.cuda.synchronize(dev)
             mms = m0.elapsed_time(m1) / args.steps
-            # normwise error of the mixed result against this run's FP64 result (which matches the oracle to 1e-12)
             err = max(float((Ml - ref[0]).abs().max() / ref[0].abs().max()),
                       float((Mg - ref[1]).abs().max() / ref[1].abs().max()))
-            mixed[mname] = {"value": uf / (mms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": mms,
-                            "speedup_vs_fp64": ms_per_step / mms, "max_normwise_err_vs_fp64": err,
-                            "stated_bound": bound,
-                            "tensor_frac": mixed_tensor_flops(d, mname) / (mms * 1e-3) / 1e12 /
-                            (load_peaks()[0]["bf16_tflops_sustained"] * (1.0 if mname == "bf16x3" else 1.1 / 2.25))}
+            compare[mname] = {"value": uf / (mms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": mms,
+                              "warmup": mw, "speedup_of_this_run": mms / ms_per_step,
+                              "max_normwise_diff_vs_this_run": err, "stated_bound_vs_oracle": bounds[mname]}
             del wsm, Ml, Mg
         del ref
         torch.cuda.empty_cache()
 
     out = None
     if rank == 0:
-        avg_launch_s = statistics.mean(launch_ms) * 1e-3
+        def kernel_s(name):
+            ms, n = kernels[name]
+            return ms * 1e-3 / n, n
+
         if args.mode == "fp64":
-            achieved = fp64_kernel_flops(d) / avg_launch_s / 1e12
+            ks, n = kernel_s("sigma_fp64_fwd_kernel")
+            achieved = fp64_kernel_flops(d) / (n / args.steps) / ks / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sigma_fp64_fwd_kernel",
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
+        elif args.mode == "fp64_fft":
+            ks, n = kernel_s("spec_prod_kernel")
+            achieved = spectral_prod_flops(d) / ks / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "spec_prod_kernel",
+                    "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
         else:
             peaks, src = load_peaks()
-            key = "bf16_tflops_sustained" if avg_launch_s > 1.0 else "bf16_tflops"
+            ks, n = kernel_s("sigma_mixed_kernel")
+            key = "bf16_tflops_sustained" if ks > 1.0 else "bf16_tflops"
             peak = peaks[key] * (1.0 if args.mode == "bf16x3" else 1.1 / 2.25)
-            achieved = mixed_tensor_flops(d, args.mode) / avg_launch_s / 1e12
+            achieved = mixed_tensor_flops(d, args.mode) / (n / args.steps) / ks / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "sigma_mixed_kernel (timed with its staging kernels)",
+                    "frac": achieved / peak, "traffic": None, "kernel": "sigma_mixed_kernel",
                     "peak_source": f"{src} {key}" + ("" if args.mode == "bf16x3" else " x 1.1/2.25 (tf32/bf16 nominal)")}
+        roof["launch_ms"] = ks * 1e3
+        roof["kernel_share_of_step"] = kernels[roof["kernel"]][0] / total_ms
+        roof["kernels"] = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                           for k, v in kernels.items()}
         out = {"metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": value, "unit": "TFLOP/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": {"fp64": "f64", "tf32": "tf32+f64", "bf16x3": "bf16x3+f64"}[args.mode],
+               "dtype": {"fp64": "f64", "fp64_fft": "f64", "tf32": "tf32+f64", "bf16x3": "bf16x3+f64"}[args.mode],
                "data": "synthetic (seeded; Si-FinFET-shaped)",
-               "config": {"workload": args.workload, **d.__dict__, "mode": args.mode,
-                          "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (2 * inp.G_less.numel() * 16 / 1e9)},
+               "config": bench_config(args, d),
                "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
-               "gpu_launches": args.steps * (1 if args.mode == "fp64" else 3)}
-        if mixed:
-            out["mixed"] = mixed
+               "gpu_launches": sum(v[1] for v in kernels.values())}
+        if compare:
+            out["compare"] = compare
         if world == 1 and not args.no_cpu:
             del Sl, Sg
             torch.cuda.empty_cache()

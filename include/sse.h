@@ -87,8 +87,11 @@ typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 
  * CHECK     : after the launches, synchronise `stream` and report device-side
  *             input checks (neighbour indices outside [0, NA)) as
  *             SSE_ERR_DEVICE_CHECK. Without CHECK such entries contribute zero
- *             and the call stays asynchronous. */
-enum { SSE_FLAG_SYMMETRIZE = 1u << 0, SSE_FLAG_CHECK = 1u << 1 };
+ *             and the call stays asynchronous.
+ * PROFILE   : record a pair of CUDA events on `stream` around every kernel the
+ *             call launches (no synchronisation, no effect on the results);
+ *             sse_profile_read reports the device time per kernel. */
+enum { SSE_FLAG_SYMMETRIZE = 1u << 0, SSE_FLAG_CHECK = 1u << 1, SSE_FLAG_PROFILE = 1u << 2 };
 
 typedef enum sse_status {
     SSE_OK = 0,
@@ -182,6 +185,21 @@ SSE_API int sse_sigma_bwd_static(const sse_dims* d, const int32_t* nbr, const do
                                  double scale, int mode, uint32_t flags, const double* gS_less,
                                  const double* gS_greater, double* g_dH, double* g_D_less, double* g_D_greater,
                                  void* stream);
+
+/* Device time of one kernel over the calls recorded with SSE_FLAG_PROFILE. */
+typedef struct sse_profile_entry {
+    const char* name; /* static string, e.g. "sigma_fp64_fwd_kernel"      */
+    double ms;        /* summed device time of its launches, milliseconds  */
+    int32_t launches; /* number of launches recorded                       */
+} sse_profile_entry;
+
+/* Kernel times recorded (by any host thread of this process) since the previous
+ * call: waits for the recorded events, writes up to `max` entries to `out` (one per
+ * kernel name, in first-launch order; `out` may be NULL with max = 0), clears the
+ * records and returns the number of kernel names, or -1 if a CUDA event query
+ * failed (the records are cleared all the same). At most 65536 launches are kept
+ * between reads; later ones are not recorded. Host memory only. */
+SSE_API int sse_profile_read(sse_profile_entry* out, int max);
 
 /* Static, NUL-terminated description of a status code (never NULL). */
 SSE_API const char* sse_strerror(int status);

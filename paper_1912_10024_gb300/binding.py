@@ -17,11 +17,15 @@ import torch
 from . import build as _build
 
 SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT = 0, 1, 2, 3
-SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK = 1, 2
+SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE = 1, 2, 4
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
-            "sse_dcomb_bwd", "sse_strerror")
+            "sse_dcomb_bwd", "sse_profile_read", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20
+
+
+class sse_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("ms", ctypes.c_double), ("launches", ctypes.c_int32)]
 
 
 class sse_dims(ctypes.Structure):
@@ -64,6 +68,8 @@ def load() -> ctypes.CDLL:
                 getattr(lib, name).restype = i32
             lib.sse_strerror.argtypes = [i32]
             lib.sse_strerror.restype = ctypes.c_char_p
+            lib.sse_profile_read.argtypes = [ctypes.POINTER(sse_profile_entry), i32]
+            lib.sse_profile_read.restype = i32
             _lib = lib
     return _lib
 
@@ -127,6 +133,16 @@ def sse_dcomb_bwd(d: sse_dims, nbr, gD_less, gD_greater, gDraw_less, gDraw_great
                                     _p(gDraw_greater), int(flags), _p(workspace), int(ws_bytes), _stream(stream)))
 
 
+def sse_profile_read(max_entries: int = 64):
+    """Kernel device times recorded by calls made with SSE_FLAG_PROFILE since the last read:
+    a list of (name, total ms, launches); clears the records."""
+    buf = (sse_profile_entry * max_entries)()
+    n = int(load().sse_profile_read(buf, max_entries))
+    if n < 0:
+        raise RuntimeError("sse_profile_read: a CUDA event query failed")
+    return [(buf[i].name.decode(), float(buf[i].ms), int(buf[i].launches)) for i in range(min(n, max_entries))]
+
+
 def sse_strerror(status: int) -> str:
     return load().sse_strerror(int(status)).decode()
 
@@ -173,7 +189,7 @@ def workspace(d: sse_dims, mode: int, flags: int, device) -> torch.Tensor:
 
 def sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2.0 * math.pi), mode: str = "fp64",
           symmetrize: bool = False, check: bool = False, atoms=None, out=None, ws: Optional[torch.Tensor] = None,
-          stream=None):
+          stream=None, profile: bool = False):
     """Sigma^<, Sigma^> of Eq. (3) on the current CUDA device via sse_sigma_fwd.
 
     Returns (S_less, S_greater), complex128 tensors shaped like G. With
@@ -184,6 +200,7 @@ def sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2
     d = dims_of(G_less, D_less, dH, atoms)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    flags |= SSE_FLAG_PROFILE if profile else 0
     if out is None:
         alloc = torch.empty if atoms is None else torch.zeros
         out = (alloc(G_less.shape, dtype=torch.complex128, device=G_less.device),

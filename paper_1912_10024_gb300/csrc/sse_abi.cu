@@ -33,7 +33,9 @@ bool valid_mode(int mode) {
     return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3 || mode == SSE_MODE_FP64_FFT;
 }
 bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
-bool valid_flags(uint32_t f) { return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK)) == 0; }
+bool valid_flags(uint32_t f) {
+    return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK | SSE_FLAG_PROFILE)) == 0;
+}
 
 size_t fwd_ws(const sse_dims& d, int mode) {
     if (mode == SSE_MODE_FP64) return sse::fp64_fwd_workspace(d);
@@ -105,6 +107,7 @@ extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double
                              const double* D_greater, const double* G_less, const double* G_greater, double scale,
                              int mode, uint32_t flags, double* S_less, double* S_greater, void* workspace,
                              size_t ws_bytes, void* stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
     int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
@@ -131,6 +134,7 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
                              int mode, uint32_t flags, const double* gS_less, const double* gS_greater,
                              double* g_dH, double* g_D_less, double* g_D_greater, void* workspace, size_t ws_bytes,
                              void* stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
     int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!gS_less || !gS_greater || !g_dH || !g_D_less || !g_D_greater) return SSE_ERR_INVALID_ARG;
@@ -171,6 +175,7 @@ int dcomb_common(const sse_dims* d, const int32_t* nbr, const double* in_l, cons
 extern "C" int sse_dcomb_fwd(const sse_dims* d, const int32_t* nbr, const double* Draw_less,
                              const double* Draw_greater, double* D_less, double* D_greater, uint32_t flags,
                              void* workspace, size_t ws_bytes, void* stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
     int rc = dcomb_common(d, nbr, Draw_less, Draw_greater, D_less, D_greater, flags, workspace, ws_bytes);
     if (rc != SSE_OK || d->a_begin == d->a_end) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -185,6 +190,7 @@ extern "C" int sse_dcomb_fwd(const sse_dims* d, const int32_t* nbr, const double
 extern "C" int sse_dcomb_bwd(const sse_dims* d, const int32_t* nbr, const double* gD_less, const double* gD_greater,
                              double* gDraw_less, double* gDraw_greater, uint32_t flags, void* workspace,
                              size_t ws_bytes, void* stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
     int rc = dcomb_common(d, nbr, gD_less, gD_greater, gDraw_less, gDraw_greater, flags, workspace, ws_bytes);
     if (rc != SSE_OK || d->a_begin == d->a_end) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

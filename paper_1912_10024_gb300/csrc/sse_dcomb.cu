@@ -110,13 +110,13 @@ __global__ void dcomb_bwd_kernel(sse_dims d, const int32_t* __restrict__ nbr, co
 
 cudaError_t dcomb_fwd(const sse_dims& d, const int32_t* nbr, const double2* raw_l, const double2* raw_g,
                       double2* Dl, double2* Dg, unsigned* status, cudaStream_t st) {
-    dcomb_fwd_kernel<<<152 * 8, 256, 0, st>>>(d, nbr, raw_l, raw_g, Dl, Dg, status);
+    SSE_TIMED("dcomb_fwd_kernel", st, dcomb_fwd_kernel<<<152 * 8, 256, 0, st>>>(d, nbr, raw_l, raw_g, Dl, Dg, status));
     return cudaGetLastError();
 }
 
 cudaError_t dcomb_bwd(const sse_dims& d, const int32_t* nbr, const double2* g_l, const double2* g_g, double2* r_l,
                       double2* r_g, unsigned* status, cudaStream_t st) {
-    dcomb_bwd_kernel<<<152 * 8, 256, 0, st>>>(d, nbr, g_l, g_g, r_l, r_g, status);
+    SSE_TIMED("dcomb_bwd_kernel", st, dcomb_bwd_kernel<<<152 * 8, 256, 0, st>>>(d, nbr, g_l, g_g, r_l, r_g, status));
     return cudaGetLastError();
 }
 

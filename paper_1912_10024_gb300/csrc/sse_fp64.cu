@@ -126,7 +126,7 @@ cudaError_t fp64_fwd(const Problem& p, double2* S_less, double2* S_greater, unsi
     if (e != cudaSuccess) return e;
     const int nA = p.d.a_end - p.d.a_begin;
     dim3 grid((p.d.NE + c.TE - 1) / c.TE, p.d.Nkz, 2 * nA);
-    sigma_fp64_fwd_kernel<<<grid, c.nthreads, c.smem, st>>>(p, c, S_less, S_greater, status);
+    SSE_TIMED("sigma_fp64_fwd_kernel", st, sigma_fp64_fwd_kernel<<<grid, c.nthreads, c.smem, st>>>(p, c, S_less, S_greater, status));
     return cudaGetLastError();
 }
 

@@ -340,16 +340,16 @@ cudaError_t fp64_bwd(const Problem& p, const double2* gS_less, const double2* gS
     if (c.smem > 227 * 1024) return cudaErrorNotSupported;
     cudaError_t e = cudaFuncSetAttribute(grad_dh_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
     if (e != cudaSuccess) return e;
-    grad_dh_partial_kernel<<<dim3(d.Nkz, 2 * nA), c.nthreads, c.smem, st>>>(p, c, gS_less, gS_greater, part, status);
+    SSE_TIMED("grad_dh_partial_kernel", st, grad_dh_partial_kernel<<<dim3(d.Nkz, 2 * nA), c.nthreads, c.smem, st>>>(p, c, gS_less, gS_greater, part, status));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    grad_dh_reduce_kernel<<<1024, 256, 0, st>>>(d, part, g_dH);
+    SSE_TIMED("grad_dh_reduce_kernel", st, grad_dh_reduce_kernel<<<1024, 256, 0, st>>>(d, part, g_dH));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     const DCfg dc = make_dcfg(d);
     if (dc.smem > 227 * 1024) return cudaErrorNotSupported;
     e = cudaFuncSetAttribute(grad_d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dc.smem);
     if (e != cudaSuccess) return e;
-    grad_d_kernel<<<nA * d.NB, kThreadsD, dc.smem, st>>>(p, dc, gS_less, gS_greater, g_D_less, g_D_greater, status);
+    SSE_TIMED("grad_d_kernel", st, grad_d_kernel<<<nA * d.NB, kThreadsD, dc.smem, st>>>(p, dc, gS_less, gS_greater, g_D_less, g_D_greater, status));
     return cudaGetLastError();
 }
 

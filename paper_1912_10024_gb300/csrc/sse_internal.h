@@ -25,6 +25,25 @@ struct Problem {
     uint32_t flags;
 };
 
+// Kernel timing (SSE_FLAG_PROFILE, sse_profile.cu): while a ProfScope(true) is alive on this
+// thread, prof_begin/prof_end record a CUDA event pair on the launching stream around a kernel.
+class ProfScope {
+  public:
+    explicit ProfScope(bool on);
+    ~ProfScope();
+
+  private:
+    bool prev_;
+};
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+#define SSE_TIMED(name, st, ...)     \
+    do {                              \
+        ::sse::prof_begin(name, st);  \
+        __VA_ARGS__;                  \
+        ::sse::prof_end(st);          \
+    } while (0)
+
 // Workspace layout: [0, 256) status word + padding; the rest per mode.
 constexpr size_t kStatusBytes = 256;
 

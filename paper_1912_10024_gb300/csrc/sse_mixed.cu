@@ -860,9 +860,9 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     int* ew = reinterpret_cast<int*>(static_cast<char*>(ws) + L.ew_off);
-    gmax_kernel<<<nsm * 8, 256, 0, st>>>(d, p.G[0], p.G[1], gmax);
+    SSE_TIMED("gmax_kernel", st, gmax_kernel<<<nsm * 8, 256, 0, st>>>(d, p.G[0], p.G[1], gmax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    wexp_kernel<<<nsm * 4, 256, 0, st>>>(p, ew);
+    SSE_TIMED("wexp_kernel", st, wexp_kernel<<<nsm * 4, 256, 0, st>>>(p, ew));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -876,7 +876,7 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
         win.Es = E0 - d.Nw > 0 ? E0 - d.Nw : 0;
         win.nEs = (win.E1 + d.Nw < d.NE ? win.E1 + d.Nw : d.NE) - win.Es;
         win.ntiles = (win.E1 - win.E0 + c.TE - 1) / c.TE;
-        stage_kernel<MODE><<<nsm * 16, 256, 0, st>>>(d, c, win, p.G[0], p.G[1], gmax, staged);
+        SSE_TIMED("stage_kernel", st, stage_kernel<MODE><<<nsm * 16, 256, 0, st>>>(d, c, win, p.G[0], p.G[1], gmax, staged));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // rows outside [0, nEs*Norb) of a slice read as zero: energies outside the grid, or never
         // reached (the halo covers every shifted energy inside the grid)
@@ -892,7 +892,7 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
             return cudaErrorInvalidValue;
         const long long nitems = (long long)win.ntiles * d.Nkz * 2 * nA;
         const int grid = (int)(nitems < nsm ? nitems : nsm);
-        sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, win, gmax, ew, Sl, Sg, status);
+        SSE_TIMED("sigma_mixed_kernel", st, sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, win, gmax, ew, Sl, Sg, status));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaGetLastError();

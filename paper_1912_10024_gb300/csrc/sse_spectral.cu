@@ -441,13 +441,15 @@ unsigned grid_for(size_t work, int threads) {
 }
 
 template <class Load, class Store>
-cudaError_t launch_fft(const FftPlan& p, const double2* tw, Load ld, Store sv, size_t ncols, int batches,
-                       cudaStream_t st) {
+cudaError_t launch_fft(const char* name, const FftPlan& p, const double2* tw, Load ld, Store sv, size_t ncols,
+                       int batches, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(fft_e_kernel<Load, Store>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
     if (e != cudaSuccess) return e;
     const size_t gx = (ncols + p.C - 1) / p.C;
     if (gx > 0x7fffffffu || batches > 65535) return cudaErrorInvalidValue;
-    fft_e_kernel<Load, Store><<<dim3((unsigned)gx, (unsigned)batches), kFftThreads, p.smem, st>>>(p, tw, ld, sv, ncols);
+    SSE_TIMED(name, st,
+              fft_e_kernel<Load, Store><<<dim3((unsigned)gx, (unsigned)batches), kFftThreads, p.smem, st>>>(
+                  p, tw, ld, sv, ncols));
     return cudaGetLastError();
 }
 
@@ -490,7 +492,7 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
     cudaError_t e;
     if (nA == 0) return cudaSuccess;
 
-    twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw);
+    SSE_TIMED("twiddle_kernel", st, twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const ProdCfg pc = make_prod_cfg(d, nfreq);
     if ((e = cudaFuncSetAttribute(spec_prod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
@@ -499,31 +501,36 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
     double2* S[2] = {S_less, S_greater};
     for (int t = 0; t < 2; ++t) {
         // 1. G^t -> G^
-        e = launch_fft(plan, tw, LoadG{p.G[t], d.NE, gcols}, StoreSpec{Gh, L, gcols, L}, gcols, d.Nkz, st);
+        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadG{p.G[t], d.NE, gcols}, StoreSpec{Gh, L, gcols, L}, gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
-        dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0);
+        SSE_TIMED("dft_k_kernel(G)", st,
+                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 2. lag kernel -> K^
         LoadLag ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-        e = launch_fft(plan, tw, ll, StoreSpec{Kh, L, kcols, L}, kcols, d.Nqz, st);
+        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpec{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
-        dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0);
+        SSE_TIMED("dft_k_kernel(K)", st,
+                  dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 3. block products
         const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
-        spec_prod_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
-            pc, d, p.nbr, p.dH, Gh, Kh, Sh, L, p.scale, status);
+        SSE_TIMED("spec_prod_kernel", st,
+                  spec_prod_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
+                      pc, d, p.nbr, p.dH, Gh, Kh, Sh, L, p.scale, status));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 4. inverse transforms into Sigma^t
-        dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1);
+        SSE_TIMED("dft_k_kernel(S)", st,
+                  dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
-        e = launch_fft(plan, tw, LoadSpecConj{Sh, L, scols},
+        e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConj{Sh, L, scols},
                        StoreSigma{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols, d.Nkz,
                        st);
         if (e != cudaSuccess) return e;
         if (p.flags & SSE_FLAG_SYMMETRIZE) {
-            symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]);
+            SSE_TIMED("symmetrize_kernel", st,
+                      symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }

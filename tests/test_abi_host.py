@@ -101,3 +101,7 @@ def test_bwd_rejects_non_fp64_and_nulls():
     args = [FAKE] * 6
     assert B.sse_sigma_bwd(d, *args, 0.1, 1, 0, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 20, 0) == 2
     assert B.sse_sigma_bwd(d, *args, 0.1, 0, 0, 0, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 20, 0) == 1
+
+
+def test_profile_read_without_records():
+    assert B.sse_profile_read() == []
