@@ -89,6 +89,15 @@ def spectral_prod_flops(d) -> float:
     return 2.0 * d.NA * d.NB * d.Nkz * L * nel * (36 + 18 * d.Norb)
 
 
+def spectral_pi_flops(d) -> float:
+    """FP64 flops one spec_pi_kernel launch (both types) executes: per (type, atom, slot, frequency) and block
+    element, the half products dH_i^H G^ and dH_j G^ (3 Norb complex MACs each at 3 FMA) and the 9 trace
+    terms (2 FMA each); 2 flops per FMA."""
+    L = fft_length(d.NE, d.Nw)
+    nel = d.Norb * d.Norb
+    return 2.0 * 2 * d.NA * d.NB * d.Nkz * L * nel * (18 * d.Norb + 18)
+
+
 def mixed_tensor_flops(d, mode: str) -> float:
     """Tensor-pipe flops one sse_sigma_fwd launch issues in a mixed mode (padding included):
     per (atom, slot, type, kz, 128-row tile) and in-range (q, w, sigma) tap, kpad/kstep MMAs of
@@ -229,6 +238,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other modes on the same inputs")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-pi", action="store_true", help="skip timing the phonon self-energy (Eq. 4)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -359,6 +369,44 @@ def main():
         del ref
         torch.cuda.empty_cache()
 
+    # ---- the phonon self-energy Pi of Eq. (4) on the same inputs ----
+    pi_line = None
+    if not args.no_pi and rank == 0:
+        del Sl, Sg
+        torch.cuda.empty_cache()
+        pd = B.sse_dims(d.NA, d.NB, d.Norb, d.NE, d.Nkz, d.Nqz, d.Nw, 0, d.NA)
+        wsp = torch.empty(B.sse_pi_workspace_bytes(pd, B.SSE_MODE_FP64, 0), dtype=torch.uint8, device=dev)
+        shape = (d.Nqz, d.Nw, d.NA, d.NB + 1, 3, 3)
+        Pout = (torch.empty(shape, dtype=torch.complex128, device=dev),
+                torch.empty(shape, dtype=torch.complex128, device=dev))
+
+        def pstep(flags=0):
+            B.pi(inp.G_less, inp.G_greater, inp.dH, inp.nbr, d.Nqz, d.Nw, scale=SCALE, out=Pout, ws=wsp,
+                 stream=stream, profile=bool(flags))
+
+        for _ in range(max(3, args.warmup)):
+            pstep()
+        torch.cuda.synchronize(dev)
+        B.sse_profile_read()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            pstep(1)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = p0.elapsed_time(p1) / args.steps
+        pk = {name: (ms, n) for name, ms, n in B.sse_profile_read()}
+        ks = pk["spec_pi_kernel"][0] * 1e-3 / pk["spec_pi_kernel"][1]
+        ach = spectral_pi_flops(d) / ks / 1e12
+        pi_line = {"op": "Pi^<, Pi^> of Eq. 4 (sse_pi_fwd, FP64 via the convolution theorem)",
+                   "ms_per_step": pms, "warmup": max(3, args.warmup),
+                   "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": ach / FP64_PEAK_TFLOPS, "kernel": "spec_pi_kernel", "launch_ms": ks * 1e3,
+                                "kernels": {k: {"ms_per_step": v[0] / args.steps,
+                                                "launches_per_step": v[1] / args.steps} for k, v in pk.items()}}}
+        del wsp, Pout
+        torch.cuda.empty_cache()
+
     out = None
     if rank == 0:
         def kernel_s(name):
@@ -400,8 +448,10 @@ def main():
                "gpu_launches": sum(v[1] for v in kernels.values())}
         if compare:
             out["compare"] = compare
+        if pi_line:
+            out["pi"] = pi_line
         if world == 1 and not args.no_cpu:
-            del Sl, Sg
+            Sl = Sg = None
             torch.cuda.empty_cache()
             out["cpu_baseline"] = cpu_baseline(d, args.cpu_seconds, inp)
         print(json.dumps(out))

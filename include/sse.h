@@ -1,8 +1,9 @@
 /*
- * sse.h -- C ABI of the GB300 (sm_103a) electron scattering self-energy library.
+ * sse.h -- C ABI of the GB300 (sm_103a) scattering self-energy library.
  *
  * The library evaluates the electron-phonon scattering self-energies
- * Sigma^<, Sigma^> of Eq. (3) of Ziogas et al., "A Data-Centric Approach to
+ * Sigma^<, Sigma^> of Eq. (3) and Pi^<, Pi^> of Eq. (4) of Ziogas et al.,
+ * "A Data-Centric Approach to
  * Extreme-Scale Ab initio Dissipative Quantum Transport Simulations"
  * (SC'19, Sec. 2), and the adjoint of that map.
  *
@@ -135,6 +136,25 @@ SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* d
                   const double* D_greater, const double* G_less, const double* G_greater, double scale, int mode,
                   uint32_t flags, const double* gS_less, const double* gS_greater, double* g_dH, double* g_D_less,
                   double* g_D_greater, void* workspace, size_t ws_bytes, void* stream);
+
+/* Phonon scattering self-energy Pi^<, Pi^> of Eq. (4) (Sec. 2) for atoms [a_begin, a_end):
+ *   P^t complex128 [Nqz][Nw][NA][NB+1][3][3]: slot s < NB is the block Pi^t_ab for
+ *        b = nbr[a][s], slot NB the diagonal block Pi^t_aa; indices (i, j) of the
+ *        3x3 block are the displacement directions.
+ *   Pi^t_{a,s}(q, w)_ij = -i*scale * sum_{k<Nkz} sum_E
+ *        tr( dH_i(a,s)^H G^t_aa(E+(w+1), (k+q) mod Nkz) dH_j(a,s) G^t'_bb(E, k) ),
+ *   t' the other type; energies with E or E+(w+1) outside [0, NE) contribute zero;
+ *   the diagonal block sums the NB bond terms (the sum over l of Eq. (4); an
+ *   off-diagonal block keeps l = b). `scale` is the energy-integration weight.
+ * Modes FP64 and FP64_FFT (both evaluate it with the convolution theorem in FP64:
+ * per frequency 6 block products and 9 traces per bond, then one inverse
+ * transform per (bond, i, j)); other modes return SSE_ERR_UNSUPPORTED.
+ * Flags: SYMMETRIZE replaces each 3x3 block B by (B - B^H)/2; CHECK, PROFILE as above.
+ * Rows of other atoms are untouched. Workspace: sse_pi_workspace_bytes(). */
+SSE_API size_t sse_pi_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
+SSE_API int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* G_less,
+                       const double* G_greater, double scale, int mode, uint32_t flags, double* P_less,
+                       double* P_greater, void* workspace, size_t ws_bytes, void* stream);
 
 /* Bond weights of Eq. (3) (Sec. 2) from the raw phonon Green's functions.
  *   Draw^t complex128 [Nqz][Nw][NA][NB+1][3][3]: slot s < NB holds D_ab for b = nbr[a][s],

@@ -20,7 +20,7 @@ SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT = 0, 1, 2, 3
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE = 1, 2, 4
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
-            "sse_dcomb_bwd", "sse_profile_read", "sse_strerror")
+            "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_profile_read", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -68,6 +68,10 @@ def load() -> ctypes.CDLL:
                 getattr(lib, name).restype = i32
             lib.sse_strerror.argtypes = [i32]
             lib.sse_strerror.restype = ctypes.c_char_p
+            lib.sse_pi_workspace_bytes.argtypes = [pd, i32, u32]
+            lib.sse_pi_workspace_bytes.restype = ctypes.c_size_t
+            lib.sse_pi_fwd.argtypes = [pd, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, ctypes.c_size_t, vp]
+            lib.sse_pi_fwd.restype = i32
             lib.sse_profile_read.argtypes = [ctypes.POINTER(sse_profile_entry), i32]
             lib.sse_profile_read.restype = i32
             _lib = lib
@@ -101,6 +105,17 @@ def sse_sigma_fwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, sc
     return int(load().sse_sigma_fwd(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater), _p(G_less),
                                     _p(G_greater), float(scale), int(mode), int(flags), _p(S_less), _p(S_greater),
                                     _p(workspace), int(ws_bytes), _stream(stream)))
+
+
+def sse_pi_workspace_bytes(d: sse_dims, mode: int, flags: int) -> int:
+    return int(load().sse_pi_workspace_bytes(ctypes.byref(d), int(mode), int(flags)))
+
+
+def sse_pi_fwd(d: sse_dims, nbr, dH, G_less, G_greater, scale: float, mode: int, flags: int, P_less, P_greater,
+               workspace, ws_bytes: int, stream=None) -> int:
+    return int(load().sse_pi_fwd(ctypes.byref(d), _p(nbr), _p(dH), _p(G_less), _p(G_greater), float(scale),
+                                 int(mode), int(flags), _p(P_less), _p(P_greater), _p(workspace), int(ws_bytes),
+                                 _stream(stream)))
 
 
 def sse_sigma_bwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int, flags: int,
@@ -234,6 +249,41 @@ def sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greate
     if rc != 0:
         raise SseError(rc, "sse_sigma_bwd")
     return g_dH, g_Dl, g_Dg
+
+
+def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 * math.pi),
+       symmetrize: bool = False, check: bool = False, atoms=None, out=None, ws: Optional[torch.Tensor] = None,
+       stream=None, profile: bool = False):
+    """Pi^<, Pi^> of Eq. (4) on the current CUDA device via sse_pi_fwd (FP64).
+
+    Returns (P_less, P_greater), complex128 [Nqz, Nw, NA, NB+1, 3, 3]: slot s < NB is the block for
+    b = nbr[a][s], slot NB the diagonal block.
+    """
+    c128 = torch.complex128
+    Nkz, NE, NA, Norb, _ = G_less.shape
+    NB = dH.shape[1]
+    _check_tensor("G_less", G_less, c128, (Nkz, NE, NA, Norb, Norb))
+    _check_tensor("G_greater", G_greater, c128, (Nkz, NE, NA, Norb, Norb))
+    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb))
+    _check_tensor("nbr", nbr, torch.int32, (NA, NB))
+    a0, a1 = (0, NA) if atoms is None else atoms
+    d = sse_dims(NA, NB, Norb, NE, Nkz, int(Nqz), int(Nw), a0, a1)
+    flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    flags |= SSE_FLAG_PROFILE if profile else 0
+    shape = (int(Nqz), int(Nw), NA, NB + 1, 3, 3)
+    if out is None:
+        alloc = torch.empty if atoms is None else torch.zeros
+        out = (alloc(shape, dtype=c128, device=G_less.device), alloc(shape, dtype=c128, device=G_less.device))
+    if ws is None:
+        n = sse_pi_workspace_bytes(d, SSE_MODE_FP64, flags)
+        if n == 0:
+            raise ValueError("invalid or unsupported problem sizes for libsse")
+        ws = torch.empty(n, dtype=torch.uint8, device=G_less.device)
+    rc = sse_pi_fwd(d, nbr, dH, G_less, G_greater, scale, SSE_MODE_FP64, flags, out[0], out[1], ws, ws.numel(),
+                    stream)
+    if rc != 0:
+        raise SseError(rc, "sse_pi_fwd")
+    return out
 
 
 class SigmaFunction(torch.autograd.Function):

@@ -201,3 +201,34 @@ extern "C" int sse_dcomb_bwd(const sse_dims* d, const int32_t* nbr, const double
                                    reinterpret_cast<double2*>(gDraw_greater), status, st);
     return finish(e, status, flags, st);
 }
+
+extern "C" size_t sse_pi_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
+    return sse::kStatusBytes + sse::spectral_pi_workspace(*d);
+}
+
+extern "C" int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* G_less,
+                          const double* G_greater, double scale, int mode, uint32_t flags, double* P_less,
+                          double* P_greater, void* workspace, size_t ws_bytes, void* stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !isfinite(scale)) return SSE_ERR_INVALID_ARG;
+    if (!nbr || !dH || !G_less || !G_greater || !P_less || !P_greater) return SSE_ERR_INVALID_ARG;
+    if (!aligned(nbr, 4) || !aligned(dH, 16) || !aligned(G_less, 16) || !aligned(G_greater, 16) ||
+        !aligned(P_less, 16) || !aligned(P_greater, 16))
+        return SSE_ERR_INVALID_ARG;
+    if (!supported_dims(d) || !fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::spectral_pi_workspace(*d))
+        return SSE_ERR_WORKSPACE;
+    if (d->a_begin == d->a_end) return SSE_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(workspace);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
+    cudaError_t e = sse::spectral_pi(*d, nbr, reinterpret_cast<const double2*>(dH),
+                                     reinterpret_cast<const double2*>(G_less),
+                                     reinterpret_cast<const double2*>(G_greater), scale, flags,
+                                     reinterpret_cast<double2*>(P_less), reinterpret_cast<double2*>(P_greater), status,
+                                     static_cast<char*>(workspace) + sse::kStatusBytes,
+                                     ws_bytes - sse::kStatusBytes, st);
+    if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
+    return finish(e, status, flags, st);
+}

@@ -70,6 +70,13 @@ size_t spectral_fwd_workspace(const sse_dims& d);
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                          size_t ws_bytes, cudaStream_t st);
 
+// Phonon self-energy of Eq. (4), transform-based FP64 (sse_spectral.cu).
+size_t spectral_pi_workspace(const sse_dims& d);
+bool spectral_pi_supported(const sse_dims& d);
+cudaError_t spectral_pi(const sse_dims& d, const int32_t* nbr, const double2* dH, const double2* G_less,
+                        const double2* G_greater, double scale, uint32_t flags, double2* P_less, double2* P_greater,
+                        unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st);
+
 // Bond weights D_ba - D_bb - D_aa + D_ab from raw phonon Green's functions (sse_dcomb.cu).
 cudaError_t dcomb_fwd(const sse_dims& d, const int32_t* nbr, const double2* raw_l, const double2* raw_g,
                       double2* Dl, double2* Dg, unsigned* status, cudaStream_t st);

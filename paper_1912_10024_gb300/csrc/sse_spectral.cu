@@ -34,7 +34,8 @@ namespace sse {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kFftSmemBudget = 200 * 1024;
+constexpr int kFftSmemBudget = 100 * 1024;  // two CTAs per SM
+constexpr int kFftLoadBatch = 8;             // global loads in flight per thread
 constexpr int kMaxStages = 24;
 constexpr int kMaxNk = 16;  // kz grid sizes handled by the small DFT pass
 
@@ -207,9 +208,20 @@ __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const dou
     const size_t col0 = (size_t)blockIdx.x * p.C;
     const int batch = blockIdx.y;
     for (int m = threadIdx.x; m < p.L; m += blockDim.x) tw[m] = tw_g[m];
-    for (int it = threadIdx.x; it < p.L * p.C; it += blockDim.x) {
-        const int r = it / p.C, c = it - r * p.C;
-        b0[it] = (col0 + c < ncols) ? ld(batch, r, col0 + c) : make_double2(0.0, 0.0);
+    const int n = p.L * p.C;
+    for (int base = threadIdx.x; base < n; base += kFftLoadBatch * blockDim.x) {
+        double2 v[kFftLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kFftLoadBatch; ++u) {
+            const int it = base + u * blockDim.x;
+            const int r = it / p.C, c = it - r * p.C;
+            v[u] = (it < n && col0 + c < ncols) ? ld(batch, r, col0 + c) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < kFftLoadBatch; ++u) {
+            const int it = base + u * blockDim.x;
+            if (it < n) b0[it] = v[u];
+        }
     }
     __syncthreads();
     const double2* res = fft_columns(p, b0, b1, tw);
@@ -220,23 +232,62 @@ __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const dou
 }
 
 // ---------------------------------------------------------------------------
-// kz-direction DFT, in place on X[Nk][M]: out[kappa] = sum_{k < n_in} in[k] exp(-+2 pi i k kappa / Nk)
+// kz-direction DFT, in place on X[Nk][M]: out[kappa] = sum_{k < n_in} in[k] exp(-+2 pi i k kappa / Nk).
+// Inputs k and Nk-k are paired (p = x_k + x_{Nk-k}, m = x_k - x_{Nk-k}) and so are outputs kappa and
+// Nk-kappa: out[kappa] = C -+ i S, out[Nk-kappa] = C +- i S with C = x_0 (+ (-1)^kappa x_{Nk/2}) +
+// sum_k p_k cos(2 pi k kappa / Nk), S = sum_k m_k sin(2 pi k kappa / Nk).
 // ---------------------------------------------------------------------------
 __global__ void dft_k_kernel(double2* __restrict__ X, int Nk, int n_in, size_t M, int inverse) {
-    __shared__ double2 w[kMaxNk];
+    __shared__ double cs[kMaxNk], sn[kMaxNk];
     if (threadIdx.x < Nk) {
         double s, c;
         sincospi(2.0 * (double)threadIdx.x / (double)Nk, &s, &c);
-        w[threadIdx.x] = make_double2(c, inverse ? s : -s);
+        cs[threadIdx.x] = c;
+        sn[threadIdx.x] = s;
     }
     __syncthreads();
+    const int half = (Nk - 1) / 2;  // number of (k, Nk-k) pairs
+    const bool even = (Nk % 2) == 0;
+    const double sgn = inverse ? 1.0 : -1.0;  // out = C + sgn * i * S for kappa <= half
     for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
-        double2 in[kMaxNk];
-        for (int k = 0; k < n_in; ++k) in[k] = X[(size_t)k * M + m];
-        for (int kap = 0; kap < Nk; ++kap) {
-            double2 acc = in[0];
-            for (int k = 1; k < n_in; ++k) acc = cadd(acc, cmul(in[k], w[(k * kap) % Nk]));
-            X[(size_t)kap * M + m] = acc;
+        double2 x[kMaxNk];
+        for (int k = 0; k < Nk; ++k) x[k] = k < n_in ? X[(size_t)k * M + m] : make_double2(0.0, 0.0);
+        double2 p[kMaxNk / 2 + 1], q[kMaxNk / 2 + 1];
+        double2 c0 = x[0];
+        for (int k = 1; k <= half; ++k) {
+            p[k] = cadd(x[k], x[Nk - k]);
+            q[k] = csub(x[k], x[Nk - k]);
+            c0 = cadd(c0, p[k]);
+        }
+        const double2 xh = even ? x[Nk / 2] : make_double2(0.0, 0.0);
+        X[m] = cadd(c0, xh);  // kappa = 0
+        for (int kap = 1; kap <= half; ++kap) {
+            double2 C = x[0], S = make_double2(0.0, 0.0);
+            for (int k = 1; k <= half; ++k) {
+                const int r = (k * kap) % Nk;
+                C.x = fma(p[k].x, cs[r], C.x);
+                C.y = fma(p[k].y, cs[r], C.y);
+                S.x = fma(q[k].x, sn[r], S.x);
+                S.y = fma(q[k].y, sn[r], S.y);
+            }
+            if (even) {
+                const double e = (kap & 1) ? -1.0 : 1.0;
+                C.x = fma(e, xh.x, C.x);
+                C.y = fma(e, xh.y, C.y);
+            }
+            // i*S = (-S.y, S.x)
+            X[(size_t)kap * M + m] = make_double2(C.x - sgn * S.y, C.y + sgn * S.x);
+            X[(size_t)(Nk - kap) * M + m] = make_double2(C.x + sgn * S.y, C.y - sgn * S.x);
+        }
+        if (even && Nk > 1) {  // kappa = Nk/2: cos(pi k) = (-1)^k, sin = 0
+            double2 C = x[0];
+            for (int k = 1; k <= half; ++k) {
+                const double e = (k & 1) ? -1.0 : 1.0;
+                C.x = fma(e, p[k].x, C.x);
+                C.y = fma(e, p[k].y, C.y);
+            }
+            const double e = ((Nk / 2) & 1) ? -1.0 : 1.0;
+            X[(size_t)(Nk / 2) * M + m] = make_double2(fma(e, xh.x, C.x), fma(e, xh.y, C.y));
         }
     }
 }
@@ -341,15 +392,22 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restric
             if (lane) {
                 const double* A = sA + (size_t)s * 9 * nel;
                 const int et = n * Norb + m;
+                double ar[3], ai[3];  // conj(dH_j[n][m]) = (ar, -ai)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    ar[j] = A[(size_t)j * 3 * nel + et];
+                    ai[j] = A[(size_t)j * 3 * nel + nel + et];
+                }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    double2 acc = make_double2(0.0, 0.0);
+                    double2 acc = make_double2(0.0, 0.0);  // plain FMA chains: no separate multiplies or adds
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
                         const double2 k = sK[fl * 9 + i * 3 + j];
-                        const double ar = A[(size_t)j * 3 * nel + et], ai = -A[(size_t)j * 3 * nel + nel + et];
-                        acc.x += k.x * ar - k.y * ai;
-                        acc.y += k.x * ai + k.y * ar;
+                        acc.x = fma(k.x, ar[j], acc.x);
+                        acc.x = fma(k.y, ai[j], acc.x);
+                        acc.y = fma(k.y, ar[j], acc.y);
+                        acc.y = fma(-k.x, ai[j], acc.y);
                     }
                     put3(sW + ((size_t)fl * 3 + i) * 3 * nel, nel, e, acc);
                 }
@@ -392,6 +450,208 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restric
             const double re = T1 - T2, im = T3 - T1 - T2;
             Shat[(f * nA + la) * nel + e] = make_double2(-scale * im, scale * re);  // i*scale*(re + i im)
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phonon self-energy, Eq. (4): per (a, slot s, frequency)
+//   C^_ij(kappa,eps) = tr( dH_i^H G^t_a(kappa,eps) dH_j G^t'_b(-kappa,-eps) ),
+// the transform of the correlation sum_{k,E} tr(dH_i^H G^t_a(E+l, k+q) dH_j G^t'_b(E, k)) over the lags
+// (q, l); slot NB (the diagonal block) is the sum over the bonds.
+// ---------------------------------------------------------------------------
+struct PiCfg {
+    int nel, F, threads, fchunk;
+    int off_A, off_X, off_Y, off_R, off_red, off_self, smem;
+};
+
+PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
+    PiCfg c{};
+    c.nel = d.Norb * d.Norb;
+    c.F = kProdMaxThreads / c.nel;
+    if (c.F < 1) c.F = 1;
+    c.threads = ((c.F * c.nel + 31) / 32) * 32;
+    const int pl = c.nel * 8;
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    c.off_A = 0;                                    // [NB][3][4 planes: re, im, re+im, re-im]
+    c.off_X = a16(c.off_A + d.NB * 3 * 4 * pl);     // [F][3 planes]
+    c.off_Y = a16(c.off_X + c.F * 3 * pl);          // [F][3 planes]
+    c.off_R = a16(c.off_Y + c.F * 3 * pl);          // [F][3 j][2 planes]
+    c.off_red = a16(c.off_R + c.F * 6 * pl);        // [F][9][nel] complex
+    c.off_self = a16(c.off_red + c.F * 9 * c.nel * 16);  // [F][9] complex: diagonal-block sums
+    c.smem = a16(c.off_self + c.F * 9 * 16);
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    size_t want = (size_t)152 * 2 * 8;
+    size_t chunks = (want + 2 * nA - 1) / (2 * nA ? 2 * nA : 1);
+    if (chunks < 1) chunks = 1;
+    size_t fc = (nfreq + chunks - 1) / chunks;
+    fc = ((fc + c.F - 1) / c.F) * c.F;
+    c.fchunk = (int)(fc < 1 ? 1 : fc);
+    return c;
+}
+
+__global__ void spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr,
+                               const double2* __restrict__ dH, const double2* __restrict__ Gl_hat,
+                               const double2* __restrict__ Gg_hat, double2* __restrict__ Cl_hat,
+                               double2* __restrict__ Cg_hat, int L, unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Norb = d.Norb, nel = c.nel;
+    const int la = blockIdx.x;
+    const int a = d.a_begin + la;
+    const int t = blockIdx.z;
+    const double2* X_hat = t == 0 ? Gl_hat : Gg_hat;  // G^t of atom a
+    const double2* Y_hat = t == 0 ? Gg_hat : Gl_hat;  // G^t' of the neighbour
+    double2* C_hat = t == 0 ? Cl_hat : Cg_hat;
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const int Nk = d.Nkz;
+    const size_t nfreq = (size_t)Nk * L;
+    const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
+    const size_t f_end = min(nfreq, f_begin + c.fchunk);
+    double* sA = reinterpret_cast<double*>(smem + c.off_A);
+    double* sX = reinterpret_cast<double*>(smem + c.off_X);
+    double* sY = reinterpret_cast<double*>(smem + c.off_Y);
+    double* sR = reinterpret_cast<double*>(smem + c.off_R);
+    double2* sRed = reinterpret_cast<double2*>(smem + c.off_red);
+    double2* sSelf = reinterpret_cast<double2*>(smem + c.off_self);
+    const int tid = threadIdx.x;
+    const int fl = tid / nel, e = tid - fl * nel;
+    const int m = e / Norb, n = e - m * Norb;
+    const bool lane = fl < c.F;
+    const int slots = d.NB + 1;
+
+    for (int i = tid; i < d.NB * 3 * nel; i += blockDim.x) {
+        const int si = i / nel, ee = i - si * nel;
+        const double2 v = dH[((size_t)a * d.NB) * 3 * nel + i];
+        double* P = sA + (size_t)si * 4 * nel;
+        P[ee] = v.x;
+        P[nel + ee] = v.y;
+        P[2 * nel + ee] = v.x + v.y;
+        P[3 * nel + ee] = v.x - v.y;
+    }
+    int bnb[16];
+    for (int s = 0; s < d.NB && s < 16; ++s) {
+        const int b = nbr[(size_t)a * d.NB + s];
+        bnb[s] = (b >= 0 && b < d.NA) ? b : -1;
+        if (bnb[s] < 0 && tid == 0 && t == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
+    }
+    __syncthreads();
+
+    for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
+        const size_t f = f0 + fl;
+        const bool act = lane && f < f_end;
+        // -f: (-kappa mod Nk, -eps mod L)
+        size_t fneg = 0;
+        if (act) {
+            const int kap = (int)(f / L), eps = (int)(f - (size_t)kap * L);
+            fneg = (size_t)((Nk - kap) % Nk) * L + (size_t)((L - eps) % L);
+        }
+        if (lane) {
+            double2 x = make_double2(0.0, 0.0);
+            if (act) x = X_hat[(f * d.NA + a) * nel + e];
+            put3(sX + (size_t)fl * 3 * nel, nel, e, x);
+        }
+        // diagonal-block sums: entry g = (frequency, ij) belongs to thread g mod blockDim for the whole batch
+        for (int g = tid; g < c.F * 9; g += blockDim.x) sSelf[g] = make_double2(0.0, 0.0);
+        for (int s = 0; s < d.NB; ++s) {
+            const int b = s < 16 ? bnb[s] : -1;
+            if (lane) {
+                double2 y = make_double2(0.0, 0.0);
+                if (act && b >= 0) y = Y_hat[(fneg * d.NA + b) * nel + e];
+                put3(sY + (size_t)fl * 3 * nel, nel, e, y);
+            }
+            __syncthreads();
+            double2 P[3];
+            if (lane) {
+                const double* A = sA + (size_t)s * 12 * nel;
+                const double* Xp = sX + (size_t)fl * 3 * nel;
+                const double* Yp = sY + (size_t)fl * 3 * nel;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double* Ai = A + (size_t)i * 4 * nel;
+                    // P_i[m][n] = sum_l conj(A_i[l][m]) X[l][n]  (Gauss with conj(A) = (re, -im))
+                    double t1 = 0.0, u2 = 0.0, t3 = 0.0;
+                    // R_i[m][n] = sum_l A_i[m][l] Y[l][n]
+                    double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+                    for (int l = 0; l < Norb; ++l) {
+                        const int lm = l * Norb + m, ml = m * Norb + l, ln = l * Norb + n;
+                        t1 = fma(Ai[lm], Xp[ln], t1);
+                        u2 = fma(Ai[nel + lm], Xp[nel + ln], u2);
+                        t3 = fma(Ai[3 * nel + lm], Xp[2 * nel + ln], t3);
+                        r1 = fma(Ai[ml], Yp[ln], r1);
+                        r2 = fma(Ai[nel + ml], Yp[nel + ln], r2);
+                        r3 = fma(Ai[2 * nel + ml], Yp[2 * nel + ln], r3);
+                    }
+                    P[i] = make_double2(t1 + u2, t3 - t1 + u2);
+                    double* R = sR + ((size_t)fl * 3 + i) * 2 * nel;
+                    R[e] = r1 - r2;
+                    R[nel + e] = r3 - r1 - r2;
+                }
+            }
+            __syncthreads();
+            // per-element trace terms P_i[m][n] R_j[n][m]
+            if (lane) {
+                const int et = n * Norb + m;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const double* R = sR + ((size_t)fl * 3 + j) * 2 * nel;
+                    const double rr = R[et], ri = R[nel + et];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        double2 v;
+                        v.x = fma(P[i].x, rr, -P[i].y * ri);
+                        v.y = fma(P[i].x, ri, P[i].y * rr);
+                        sRed[((size_t)fl * 9 + i * 3 + j) * nel + e] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int g = tid; g < c.F * 9; g += blockDim.x) {  // fixed-order sums over the block elements
+                const int rf = g / 9, ij = g - rf * 9;
+                const size_t ff = f0 + rf;
+                const double2* v = sRed + (size_t)g * nel;
+                double2 acc[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                                  make_double2(0.0, 0.0)};
+                for (int ee = 0; ee < nel; ++ee) acc[ee & 3] = cadd(acc[ee & 3], v[ee]);
+                const double2 sum = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+                const double2 self = cadd(sSelf[g], sum);
+                sSelf[g] = self;
+                if (ff < f_end) C_hat[((ff * nA + la) * slots + s) * 9 + ij] = sum;
+                if (s == d.NB - 1 && ff < f_end) C_hat[((ff * nA + la) * slots + d.NB) * 9 + ij] = self;
+            }
+            // the next bond rewrites sY after its own barrier; sR and sRed are rewritten only after two more
+        }
+        __syncthreads();  // sX of the next frequency batch
+    }
+}
+
+// Pi^t[q][w][a][slot][ij] = -i*scale * conj(v) * inv for rows l = w+1 in [1, Nw]
+struct StorePi {
+    double2* P;
+    int Nw, NA, slots;
+    size_t col0;
+    double inv_scale;  // scale / (Nkz L)
+    int rows;
+    __device__ void operator()(int q, int r, size_t col, double2 v) const {
+        if (r < 1 || r > Nw) return;
+        const size_t rowlen = (size_t)NA * slots * 9;
+        // C = conj(v) * inv; Pi = -i * scale * C
+        P[((size_t)q * Nw + (r - 1)) * rowlen + col0 + col] = make_double2(-v.y * inv_scale, -v.x * inv_scale);
+    }
+};
+
+// (P - P^H)/2 on every 3x3 block of the atoms in range
+__global__ void symmetrize3_kernel(sse_dims d, double2* __restrict__ P) {
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const int slots = d.NB + 1;
+    const size_t nblk = (size_t)d.Nqz * d.Nw * nA * slots;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nblk; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t qw = i / (nA * slots), rem = i - qw * nA * slots;
+        double2* B = P + ((qw * d.NA + d.a_begin) * slots + rem) * 9;
+        for (int r = 0; r < 3; ++r)
+            for (int c2 = r; c2 < 3; ++c2) {
+                const double2 x = B[r * 3 + c2], y = B[c2 * 3 + r];
+                B[r * 3 + c2] = make_double2(0.5 * (x.x - y.x), 0.5 * (x.y + y.y));
+                if (r != c2) B[c2 * 3 + r] = make_double2(0.5 * (y.x - x.x), 0.5 * (y.y + x.y));
+            }
     }
 }
 
@@ -467,7 +727,7 @@ int spectral_length(const sse_dims& d) {
 
 bool spectral_supported(const sse_dims& d) {
     const int L = spectral_length(d);
-    return d.Nkz <= kMaxNk && make_plan(L).smem <= kFftSmemBudget && d.NB <= 16 &&
+    return d.Nkz <= kMaxNk && make_plan(L).smem <= 227 * 1024 && d.NB <= 16 &&
            make_prod_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
 }
 
@@ -531,6 +791,92 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
         if (p.flags & SSE_FLAG_SYMMETRIZE) {
             SSE_TIMED("symmetrize_kernel", st,
                       symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+struct PiLayout {
+    int L;
+    size_t off_tw, off_G[2], off_C[2], total;
+};
+
+PiLayout pi_layout(const sse_dims& d) {
+    PiLayout l{};
+    l.L = spectral_length(d);
+    const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
+    const size_t spec = (size_t)d.Nkz * l.L;
+    l.off_tw = 0;
+    l.off_G[0] = align256((size_t)l.L * 16);
+    l.off_G[1] = align256(l.off_G[0] + spec * d.NA * nel * 16);
+    l.off_C[0] = align256(l.off_G[1] + spec * d.NA * nel * 16);
+    l.off_C[1] = align256(l.off_C[0] + spec * nA * (d.NB + 1) * 9 * 16);
+    l.total = align256(l.off_C[1] + spec * nA * (d.NB + 1) * 9 * 16);
+    return l;
+}
+
+size_t spectral_pi_workspace(const sse_dims& d) { return pi_layout(d).total; }
+
+bool spectral_pi_supported(const sse_dims& d) {
+    const int L = spectral_length(d);
+    return d.Nkz <= kMaxNk && make_plan(L).smem <= 227 * 1024 && d.NB <= 16 &&
+           make_pi_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
+}
+
+cudaError_t spectral_pi(const sse_dims& d, const int32_t* nbr, const double2* dH, const double2* G_less,
+                        const double2* G_greater, double scale, uint32_t flags, double2* P_less, double2* P_greater,
+                        unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+    if (!spectral_pi_supported(d)) return cudaErrorNotSupported;
+    const PiLayout lay = pi_layout(d);
+    if (ws_bytes < lay.total) return cudaErrorInvalidValue;
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    double2* tw = reinterpret_cast<double2*>(base + lay.off_tw);
+    double2* Gh[2] = {reinterpret_cast<double2*>(base + lay.off_G[0]), reinterpret_cast<double2*>(base + lay.off_G[1])};
+    double2* Ch[2] = {reinterpret_cast<double2*>(base + lay.off_C[0]), reinterpret_cast<double2*>(base + lay.off_C[1])};
+    const int L = lay.L;
+    const FftPlan plan = make_plan(L);
+    const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
+    const size_t gcols = (size_t)d.NA * nel, ccols = nA * (d.NB + 1) * 9;
+    const size_t nfreq = (size_t)d.Nkz * L;
+    if (nA == 0) return cudaSuccess;
+    cudaError_t e;
+    SSE_TIMED("twiddle_kernel", st, twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const double2* G[2] = {G_less, G_greater};
+    for (int t = 0; t < 2; ++t) {
+        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadG{G[t], d.NE, gcols}, StoreSpec{Gh[t], L, gcols, L}, gcols,
+                       d.Nkz, st);
+        if (e != cudaSuccess) return e;
+        SSE_TIMED("dft_k_kernel(G)", st,
+                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh[t], d.Nkz, d.Nkz,
+                                                                                 (size_t)L * gcols, 0));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const PiCfg pc = make_pi_cfg(d, nfreq);
+    if ((e = cudaFuncSetAttribute(spec_pi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
+        cudaSuccess)
+        return e;
+    const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
+    SSE_TIMED("spec_pi_kernel", st,
+              spec_pi_kernel<<<dim3((unsigned)nA, (unsigned)gy, 2), pc.threads, pc.smem, st>>>(
+                  pc, d, nbr, dH, Gh[0], Gh[1], Ch[0], Ch[1], L, status));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    double2* P[2] = {P_less, P_greater};
+    const double inv_scale = scale / ((double)d.Nkz * (double)L);
+    for (int t = 0; t < 2; ++t) {
+        SSE_TIMED("dft_k_kernel(C)", st,
+                  dft_k_kernel<<<grid_for((size_t)L * ccols, 256), 256, 0, st>>>(Ch[t], d.Nkz, d.Nkz,
+                                                                                 (size_t)L * ccols, 1));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = launch_fft("fft_e_kernel(C)", plan, tw, LoadSpecConj{Ch[t], L, ccols},
+                       StorePi{P[t], d.Nw, d.NA, d.NB + 1, (size_t)d.a_begin * (d.NB + 1) * 9, inv_scale, d.Nw + 1},
+                       ccols, d.Nqz, st);
+        if (e != cudaSuccess) return e;
+        if (flags & SSE_FLAG_SYMMETRIZE) {
+            SSE_TIMED("symmetrize3_kernel", st,
+                      symmetrize3_kernel<<<grid_for((size_t)d.Nqz * d.Nw * nA * (d.NB + 1), 256), 256, 0, st>>>(
+                          d, P[t]));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }

@@ -105,3 +105,27 @@ def test_bwd_rejects_non_fp64_and_nulls():
 
 def test_profile_read_without_records():
     assert B.sse_profile_read() == []
+
+
+def call_pi(d, **over):
+    args = dict(nbr=FAKE, dH=FAKE, G_less=FAKE, G_greater=FAKE, scale=0.1, mode=0, flags=0, P_less=FAKE,
+                P_greater=FAKE, workspace=FAKE, ws_bytes=1 << 20)
+    args.update(over)
+    return B.sse_pi_fwd(d, stream=0, **args)
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(G_less=0), 1), (dict(P_greater=0), 1), (dict(dH=FAKE + 8), 1), (dict(nbr=FAKE + 2), 1),
+    (dict(scale=float("inf")), 1), (dict(mode=9), 1), (dict(flags=1 << 5), 1), (dict(mode=1), 2),
+    (dict(mode=2), 2), (dict(workspace=0), 6), (dict(workspace=FAKE + 16), 6), (dict(ws_bytes=16), 6),
+])
+def test_pi_rejects_bad_arguments_on_host(over, status):
+    assert call_pi(good_dims(), **over) == status
+
+
+def test_pi_workspace_bytes():
+    d = good_dims()
+    assert B.sse_pi_workspace_bytes(d, B.SSE_MODE_FP64, 0) > 256
+    bad = good_dims()
+    bad.Nw = bad.NE
+    assert B.sse_pi_workspace_bytes(bad, B.SSE_MODE_FP64, 0) == 0
