@@ -461,7 +461,7 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restric
 // ---------------------------------------------------------------------------
 struct PiCfg {
     int nel, F, threads, fchunk;
-    int off_A, off_X, off_Y, off_R, off_red, off_self, smem;
+    int off_A, off_X, off_Y, off_P, off_R, off_D, off_self, smem;
 };
 
 PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
@@ -472,12 +472,13 @@ PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
     c.threads = ((c.F * c.nel + 31) / 32) * 32;
     const int pl = c.nel * 8;
     auto a16 = [](int x) { return (x + 15) & ~15; };
-    c.off_A = 0;                                    // [NB][3][4 planes: re, im, re+im, re-im]
-    c.off_X = a16(c.off_A + d.NB * 3 * 4 * pl);     // [F][3 planes]
-    c.off_Y = a16(c.off_X + c.F * 3 * pl);          // [F][3 planes]
-    c.off_R = a16(c.off_Y + c.F * 3 * pl);          // [F][3 j][2 planes]
-    c.off_red = a16(c.off_R + c.F * 6 * pl);        // [F][9][nel] complex
-    c.off_self = a16(c.off_red + c.F * 9 * c.nel * 16);  // [F][9] complex: diagonal-block sums
+    c.off_A = 0;                                     // [NB][3][4 planes: re, im, re+im, re-im]
+    c.off_X = a16(c.off_A + d.NB * 3 * 4 * pl);      // [F][3 planes]
+    c.off_Y = a16(c.off_X + c.F * 3 * pl);           // [F][3 planes]
+    c.off_P = a16(c.off_Y + c.F * 3 * pl);           // [F][3 i][2 planes]
+    c.off_R = a16(c.off_P + c.F * 6 * pl);           // [F][3 j][2 planes]
+    c.off_D = a16(c.off_R + c.F * 6 * pl);           // [F][9][Norb] complex: diagonal terms
+    c.off_self = a16(c.off_D + c.F * 9 * d.Norb * 16);  // [F][9] complex: diagonal-block sums
     c.smem = a16(c.off_self + c.F * 9 * 16);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
@@ -489,10 +490,10 @@ PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
     return c;
 }
 
-__global__ void spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr,
-                               const double2* __restrict__ dH, const double2* __restrict__ Gl_hat,
-                               const double2* __restrict__ Gg_hat, double2* __restrict__ Cl_hat,
-                               double2* __restrict__ Cg_hat, int L, unsigned* __restrict__ status) {
+__global__ void __launch_bounds__(kProdMaxThreads, 2)
+spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr, const double2* __restrict__ dH,
+               const double2* __restrict__ Gl_hat, const double2* __restrict__ Gg_hat, double2* __restrict__ Cl_hat,
+               double2* __restrict__ Cg_hat, int L, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int Norb = d.Norb, nel = c.nel;
     const int la = blockIdx.x;
@@ -509,14 +510,16 @@ __global__ void spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ 
     double* sA = reinterpret_cast<double*>(smem + c.off_A);
     double* sX = reinterpret_cast<double*>(smem + c.off_X);
     double* sY = reinterpret_cast<double*>(smem + c.off_Y);
+    double* sP = reinterpret_cast<double*>(smem + c.off_P);
     double* sR = reinterpret_cast<double*>(smem + c.off_R);
-    double2* sRed = reinterpret_cast<double2*>(smem + c.off_red);
+    double2* sD = reinterpret_cast<double2*>(smem + c.off_D);
     double2* sSelf = reinterpret_cast<double2*>(smem + c.off_self);
     const int tid = threadIdx.x;
     const int fl = tid / nel, e = tid - fl * nel;
     const int m = e / Norb, n = e - m * Norb;
     const bool lane = fl < c.F;
     const int slots = d.NB + 1;
+    const int ndiag = c.F * 9 * Norb;
 
     for (int i = tid; i < d.NB * 3 * nel; i += blockDim.x) {
         const int si = i / nel, ee = i - si * nel;
@@ -527,19 +530,17 @@ __global__ void spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ 
         P[2 * nel + ee] = v.x + v.y;
         P[3 * nel + ee] = v.x - v.y;
     }
-    int bnb[16];
-    for (int s = 0; s < d.NB && s < 16; ++s) {
-        const int b = nbr[(size_t)a * d.NB + s];
-        bnb[s] = (b >= 0 && b < d.NA) ? b : -1;
-        if (bnb[s] < 0 && tid == 0 && t == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
-    }
+    if (tid == 0 && t == 0)
+        for (int s = 0; s < d.NB; ++s) {
+            const int b = nbr[(size_t)a * d.NB + s];
+            if (b < 0 || b >= d.NA) atomicOr(status, DEV_BAD_NEIGHBOUR);
+        }
     __syncthreads();
 
     for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
         const size_t f = f0 + fl;
         const bool act = lane && f < f_end;
-        // -f: (-kappa mod Nk, -eps mod L)
-        size_t fneg = 0;
+        size_t fneg = 0;  // -f = (-kappa mod Nk, -eps mod L)
         if (act) {
             const int kap = (int)(f / L), eps = (int)(f - (size_t)kap * L);
             fneg = (size_t)((Nk - kap) % Nk) * L + (size_t)((L - eps) % L);
@@ -552,72 +553,72 @@ __global__ void spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ 
         // diagonal-block sums: entry g = (frequency, ij) belongs to thread g mod blockDim for the whole batch
         for (int g = tid; g < c.F * 9; g += blockDim.x) sSelf[g] = make_double2(0.0, 0.0);
         for (int s = 0; s < d.NB; ++s) {
-            const int b = s < 16 ? bnb[s] : -1;
+            const int b = nbr[(size_t)a * d.NB + s];
+            const bool bok = b >= 0 && b < d.NA;
             if (lane) {
                 double2 y = make_double2(0.0, 0.0);
-                if (act && b >= 0) y = Y_hat[(fneg * d.NA + b) * nel + e];
+                if (act && bok) y = Y_hat[(fneg * d.NA + b) * nel + e];
                 put3(sY + (size_t)fl * 3 * nel, nel, e, y);
             }
             __syncthreads();
-            double2 P[3];
+            // half products P_i = dH_i^H X, R_j = dH_j Y (Gauss 3-multiply MACs)
             if (lane) {
                 const double* A = sA + (size_t)s * 12 * nel;
                 const double* Xp = sX + (size_t)fl * 3 * nel;
                 const double* Yp = sY + (size_t)fl * 3 * nel;
-#pragma unroll
+#pragma unroll 1
                 for (int i = 0; i < 3; ++i) {
                     const double* Ai = A + (size_t)i * 4 * nel;
-                    // P_i[m][n] = sum_l conj(A_i[l][m]) X[l][n]  (Gauss with conj(A) = (re, -im))
-                    double t1 = 0.0, u2 = 0.0, t3 = 0.0;
-                    // R_i[m][n] = sum_l A_i[m][l] Y[l][n]
-                    double r1 = 0.0, r2 = 0.0, r3 = 0.0;
+                    double t1 = 0.0, u2 = 0.0, t3 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
                     for (int l = 0; l < Norb; ++l) {
                         const int lm = l * Norb + m, ml = m * Norb + l, ln = l * Norb + n;
-                        t1 = fma(Ai[lm], Xp[ln], t1);
+                        t1 = fma(Ai[lm], Xp[ln], t1);                  // conj(A_i[l][m]) X[l][n]
                         u2 = fma(Ai[nel + lm], Xp[nel + ln], u2);
                         t3 = fma(Ai[3 * nel + lm], Xp[2 * nel + ln], t3);
-                        r1 = fma(Ai[ml], Yp[ln], r1);
+                        r1 = fma(Ai[ml], Yp[ln], r1);                  // A_i[m][l] Y[l][n]
                         r2 = fma(Ai[nel + ml], Yp[nel + ln], r2);
                         r3 = fma(Ai[2 * nel + ml], Yp[2 * nel + ln], r3);
                     }
-                    P[i] = make_double2(t1 + u2, t3 - t1 + u2);
+                    double* P = sP + ((size_t)fl * 3 + i) * 2 * nel;
+                    P[e] = t1 + u2;
+                    P[nel + e] = t3 - t1 + u2;
                     double* R = sR + ((size_t)fl * 3 + i) * 2 * nel;
                     R[e] = r1 - r2;
                     R[nel + e] = r3 - r1 - r2;
                 }
             }
             __syncthreads();
-            // per-element trace terms P_i[m][n] R_j[n][m]
-            if (lane) {
-                const int et = n * Norb + m;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const double* R = sR + ((size_t)fl * 3 + j) * 2 * nel;
-                    const double rr = R[et], ri = R[nel + et];
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        double2 v;
-                        v.x = fma(P[i].x, rr, -P[i].y * ri);
-                        v.y = fma(P[i].x, ri, P[i].y * rr);
-                        sRed[((size_t)fl * 9 + i * 3 + j) * nel + e] = v;
-                    }
+            // diagonal terms D_ij[m] = sum_n P_i[m][n] R_j[n][m]
+            for (int g = tid; g < ndiag; g += blockDim.x) {
+                const int fi = g / (9 * Norb), rem = g - fi * 9 * Norb;
+                const int ij = rem / Norb, mm = rem - ij * Norb;
+                const int i = ij / 3, j = ij - 3 * i;
+                const double* P = sP + ((size_t)fi * 3 + i) * 2 * nel;
+                const double* R = sR + ((size_t)fi * 3 + j) * 2 * nel;
+                double re = 0.0, im = 0.0;
+                for (int nn = 0; nn < Norb; ++nn) {
+                    const double pr = P[mm * Norb + nn], pi = P[nel + mm * Norb + nn];
+                    const double rr = R[nn * Norb + mm], ri = R[nel + nn * Norb + mm];
+                    re = fma(pr, rr, re);
+                    re = fma(-pi, ri, re);
+                    im = fma(pr, ri, im);
+                    im = fma(pi, rr, im);
                 }
+                sD[g] = make_double2(re, im);
             }
             __syncthreads();
-            for (int g = tid; g < c.F * 9; g += blockDim.x) {  // fixed-order sums over the block elements
+            for (int g = tid; g < c.F * 9; g += blockDim.x) {  // fixed-order sums over the rows m
                 const int rf = g / 9, ij = g - rf * 9;
                 const size_t ff = f0 + rf;
-                const double2* v = sRed + (size_t)g * nel;
-                double2 acc[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
-                                  make_double2(0.0, 0.0)};
-                for (int ee = 0; ee < nel; ++ee) acc[ee & 3] = cadd(acc[ee & 3], v[ee]);
-                const double2 sum = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+                const double2* v = sD + (size_t)g * Norb;
+                double2 sum = v[0];
+                for (int mm = 1; mm < Norb; ++mm) sum = cadd(sum, v[mm]);
                 const double2 self = cadd(sSelf[g], sum);
                 sSelf[g] = self;
                 if (ff < f_end) C_hat[((ff * nA + la) * slots + s) * 9 + ij] = sum;
                 if (s == d.NB - 1 && ff < f_end) C_hat[((ff * nA + la) * slots + d.NB) * 9 + ij] = self;
             }
-            // the next bond rewrites sY after its own barrier; sR and sRed are rewritten only after two more
+            // the next bond rewrites sY before its first barrier; sP, sR and sD only after it
         }
         __syncthreads();  // sX of the next frequency batch
     }
