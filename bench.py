@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1912_10024_gb300 import binding as B  # noqa: E402
-from paper_1912_10024_gb300.inputs import WORKLOADS, make_inputs  # noqa: E402
+from paper_1912_10024_gb300.inputs import WORKLOADS, make_inputs, make_upstream  # noqa: E402
 
 SCALE = 1.0 / (2.0 * math.pi)
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2070 MHz (derivation in the design doc).
@@ -96,6 +96,16 @@ def spectral_pi_flops(d) -> float:
     L = fft_length(d.NE, d.Nw)
     nel = d.Norb * d.Norb
     return 2.0 * 2 * d.NA * d.NB * d.Nkz * L * nel * (18 * d.Norb + 18)
+
+
+def spectral_adj_flops(d) -> float:
+    """FP64 flops one spec_adj_kernel launch (one type) executes: per (atom, slot, frequency) and block
+    element, 12 block products (3 Norb complex MACs each at 3 FMA), the coupling-gradient weights
+    (6 complex MACs at 4 FMA per direction) and the weight-gradient traces (9 Norb^2 complex MACs at 4 FMA
+    per frequency); 2 flops per FMA."""
+    L = fft_length(d.NE, d.Nw)
+    nel = d.Norb * d.Norb
+    return 2.0 * d.NA * d.NB * d.Nkz * L * nel * (36 * d.Norb + 108)
 
 
 def mixed_tensor_flops(d, mode: str) -> float:
@@ -239,6 +249,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other modes on the same inputs")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pi", action="store_true", help="skip timing the phonon self-energy (Eq. 4)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip timing the FP64 adjoint")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -407,6 +418,46 @@ def main():
         del wsp, Pout
         torch.cuda.empty_cache()
 
+    # ---- the FP64 adjoint (transform-based) on the same inputs ----
+    adj_line = None
+    if not args.no_adjoint and rank == 0:
+        Sl = Sg = None
+        torch.cuda.empty_cache()
+        W, V = make_upstream(d, seed=1000 + rank, device=dev)
+        mfft = B.MODES["fp64_fft"]
+        wsa = B.workspace(dims, mfft, 0, dev)
+        gout = (torch.empty_like(inp.dH), torch.empty_like(inp.D_less), torch.empty_like(inp.D_greater))
+
+        def astep(flags=0):
+            rc = B.sse_sigma_bwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                                 mfft, flags, W, V, gout[0], gout[1], gout[2], wsa, wsa.numel(), stream)
+            if rc != 0:
+                raise B.SseError(rc, "sse_sigma_bwd")
+
+        for _ in range(max(3, args.warmup)):
+            astep()
+        torch.cuda.synchronize(dev)
+        B.sse_profile_read()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            astep(B.SSE_FLAG_PROFILE)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ams = a0.elapsed_time(a1) / args.steps
+        ak = {name: (ms, n) for name, ms, n in B.sse_profile_read()}
+        ks = ak["spec_adj_kernel"][0] * 1e-3 / ak["spec_adj_kernel"][1]
+        ach = spectral_adj_flops(d) / ks / 1e12
+        adj_line = {"op": "adjoint of Eq. 3 (sse_sigma_bwd, FP64 via the transforms): grad dH, D^<, D^>",
+                    "ms_per_step": ams, "warmup": max(3, args.warmup),
+                    "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": ach / FP64_PEAK_TFLOPS, "kernel": "spec_adj_kernel",
+                                 "launch_ms": ks * 1e3,
+                                 "kernels": {k: {"ms_per_step": v[0] / args.steps,
+                                                 "launches_per_step": v[1] / args.steps} for k, v in ak.items()}}}
+        del W, V, wsa, gout
+        torch.cuda.empty_cache()
+
     out = None
     if rank == 0:
         def kernel_s(name):
@@ -450,6 +501,8 @@ def main():
             out["compare"] = compare
         if pi_line:
             out["pi"] = pi_line
+        if adj_line:
+            out["adjoint"] = adj_line
         if world == 1 and not args.no_cpu:
             Sl = Sg = None
             torch.cuda.empty_cache()

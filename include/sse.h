@@ -120,8 +120,12 @@ SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* d
                   uint32_t flags, double* S_less, double* S_greater, void* workspace, size_t ws_bytes,
                   void* stream);
 
-/* Adjoint of sse_sigma_fwd (modes FP64 and FP64_FFT, both run the FP64 adjoint
- * kernels). For the loss
+/* Adjoint of sse_sigma_fwd, in FP64: mode FP64 runs direct kernels (correlations
+ * recomputed from the gathered G windows), mode FP64_FFT the transform-based adjoint
+ * (per bond and frequency Q_j = W^ dH_j G^^H and R_i = W^^H dH_i G^, the weight
+ * gradient from the inverse transform of tr(dH_i^H Q_j), the coupling gradient
+ * summed over frequencies in a fixed order); other modes return SSE_ERR_UNSUPPORTED.
+ * For the loss
  *   L = sum_t sum_{a in range, E, k} Re tr( gS^t_a(E,k)^H Sigma^t_a(E,k) )
  * it writes the gradients w.r.t. dH, D^< and D^> in the PyTorch convention
  * for complex tensors (grad z = dL/dRe z + i dL/dIm z):

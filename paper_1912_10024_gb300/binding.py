@@ -297,6 +297,8 @@ class SigmaFunction(torch.autograd.Function):
         S = sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale=scale, mode=mode, symmetrize=symmetrize)
         ctx.save_for_backward(dH, D_less, D_greater, G_less, G_greater, nbr)
         ctx.scale, ctx.symmetrize = scale, symmetrize
+        # the adjoint runs in FP64: transform-based after a transform-based forward, direct otherwise
+        ctx.bwd_mode = "fp64_fft" if mode in ("fp64_fft", SSE_MODE_FP64_FFT) else "fp64"
         return S
 
     @staticmethod
@@ -307,7 +309,7 @@ class SigmaFunction(torch.autograd.Function):
         if gSg is None:
             gSg = torch.zeros_like(G_greater)
         g = sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gSl, gSg, scale=ctx.scale,
-                       symmetrize=ctx.symmetrize)
+                       symmetrize=ctx.symmetrize, mode=ctx.bwd_mode)
         return g[0], g[1], g[2], None, None, None, None, None, None
 
 

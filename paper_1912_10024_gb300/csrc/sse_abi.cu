@@ -99,7 +99,9 @@ extern "C" const char* sse_strerror(int status) {
 extern "C" size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
     if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
     size_t f = fwd_ws(*d, mode);
-    size_t b = fp64_mode(mode) ? sse::fp64_bwd_workspace(*d) : 0;
+    size_t b = mode == SSE_MODE_FP64 ? sse::fp64_bwd_workspace(*d)
+               : mode == SSE_MODE_FP64_FFT ? sse::spectral_bwd_workspace(*d)
+                                           : 0;
     return sse::kStatusBytes + (f > b ? f : b);
 }
 
@@ -142,8 +144,8 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
         !aligned(g_D_greater, 16))
         return SSE_ERR_INVALID_ARG;
     if (!fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
-    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::fp64_bwd_workspace(*d))
-        return SSE_ERR_WORKSPACE;
+    const size_t need = mode == SSE_MODE_FP64 ? sse::fp64_bwd_workspace(*d) : sse::spectral_bwd_workspace(*d);
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + need) return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned* status = static_cast<unsigned*>(workspace);
@@ -151,10 +153,13 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
     void* ws = static_cast<char*>(workspace) + sse::kStatusBytes;
     const size_t wsb = ws_bytes - sse::kStatusBytes;
     const sse::Problem p = make_problem(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, flags);
-    cudaError_t e = sse::fp64_bwd(p, reinterpret_cast<const double2*>(gS_less),
-                                  reinterpret_cast<const double2*>(gS_greater), reinterpret_cast<double2*>(g_dH),
-                                  reinterpret_cast<double2*>(g_D_less), reinterpret_cast<double2*>(g_D_greater),
-                                  status, ws, wsb, st);
+    const double2* gl = reinterpret_cast<const double2*>(gS_less);
+    const double2* gg = reinterpret_cast<const double2*>(gS_greater);
+    double2* gh = reinterpret_cast<double2*>(g_dH);
+    double2* gdl = reinterpret_cast<double2*>(g_D_less);
+    double2* gdg = reinterpret_cast<double2*>(g_D_greater);
+    cudaError_t e = mode == SSE_MODE_FP64 ? sse::fp64_bwd(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st)
+                                          : sse::spectral_bwd(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }

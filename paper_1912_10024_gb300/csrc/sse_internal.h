@@ -70,6 +70,13 @@ size_t spectral_fwd_workspace(const sse_dims& d);
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                          size_t ws_bytes, cudaStream_t st);
 
+// Transform-based FP64 adjoint of Eq. (3) (sse_spectral.cu).
+size_t spectral_bwd_workspace(const sse_dims& d);
+bool spectral_bwd_supported(const sse_dims& d);
+cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
+                         double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
+                         cudaStream_t st);
+
 // Phonon self-energy of Eq. (4), transform-based FP64 (sse_spectral.cu).
 size_t spectral_pi_workspace(const sse_dims& d);
 bool spectral_pi_supported(const sse_dims& d);

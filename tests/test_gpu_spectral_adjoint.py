@@ -1,0 +1,89 @@
+"""Transform-based FP64 adjoint (sse_sigma_bwd, mode FP64_FFT) against the oracle and the direct FP64 adjoint.
+
+Tolerance: normwise 1e-12 per gradient tensor (g_dH, g_D^<, g_D^>), as for the direct FP64 adjoint.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from conftest import normwise
+from paper_1912_10024_gb300 import binding as B
+from paper_1912_10024_gb300.inputs import ADJOINT, TINY, Dims, make_inputs, make_upstream, ring_neighbours
+
+pytestmark = pytest.mark.gpu
+SCALE = 1.0 / (2.0 * math.pi)
+TOL = 1e-12
+
+
+def gpu_grad(inp, W, V, mode="fp64_fft", **kw):
+    g = inp.to("cuda")
+    return B.sigma_grad(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, W.cuda(), V.cuda(), mode=mode,
+                        **kw)
+
+
+def oracle_grad(inp, W, V, scale=SCALE, **kw):
+    return oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, scale, W, V,
+                             **kw)
+
+
+@pytest.mark.parametrize("dims", [
+    TINY,
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nqz < Nkz, L = 72
+    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 60
+    Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11),    # L = 54
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per pass, L = 90
+    Dims(NA=5, NB=1, Norb=1, NE=70, Nkz=1, Nqz=1, Nw=5),      # Norb = 1, single kz point, L = 75
+], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}_Nkz{d.Nkz}")
+def test_shapes_vs_oracle(dims):
+    nbr = ring_neighbours(dims.NA, dims.NB) if dims is not TINY else None
+    inp = make_inputs(dims, seed=dims.Norb + 300, nbr=nbr)
+    W, V = make_upstream(dims, seed=dims.Norb + 301)
+    got = gpu_grad(inp, W, V, check=True)
+    ref = oracle_grad(inp, W, V)
+    for x, y in zip(got, ref):
+        assert normwise(x.cpu().numpy(), y) <= TOL
+
+
+def test_symmetrize_and_atom_range_vs_direct():
+    inp = make_inputs(TINY, seed=31)
+    inp.D_less = inp.D_less * (1 + 0.3j)
+    W, V = make_upstream(TINY, seed=32)
+    for kw in (dict(symmetrize=True), dict(atoms=(3, 9)), dict(scale=1.0)):
+        got = gpu_grad(inp, W, V, **kw)
+        ref = gpu_grad(inp, W, V, mode="fp64", **kw)
+        for x, y in zip(got, ref):
+            assert float((x - y).abs().max()) <= TOL * float(y.abs().max())
+    got = gpu_grad(inp, W, V, atoms=(3, 9))
+    assert float(got[0][:3].abs().max()) == 0.0 and float(got[0][9:].abs().max()) == 0.0
+
+
+def test_autograd_chain_uses_the_transform_adjoint():
+    d = Dims(NA=6, NB=2, Norb=3, NE=20, Nkz=3, Nqz=2, Nw=4)
+    inp = make_inputs(d, seed=33, nbr=ring_neighbours(6, 2))
+    W, V = make_upstream(d, seed=34)
+    g = inp.to("cuda")
+    dH = g.dH.clone().requires_grad_(True)
+    Dl = g.D_less.clone().requires_grad_(True)
+    Dg = g.D_greater.clone().requires_grad_(True)
+    B.sse_profile_read()
+    Sl, Sg = B.sigma_autograd(dH, Dl, Dg, g.G_less, g.G_greater, g.nbr, SCALE, "fp64_fft")
+    loss = (W.cuda().conj() * Sl).real.sum() + (V.cuda().conj() * Sg).real.sum()
+    loss.backward()
+    ref = oracle_grad(inp, W, V)
+    for x, y in zip((dH.grad, Dl.grad, Dg.grad), ref):
+        assert normwise(x.cpu().numpy(), y) <= TOL
+
+
+def test_adjoint_workload_vs_direct():
+    """NA=256, Norb=10, NE=256, Nkz=Nqz=5, Nw=16: every gradient entry against the direct FP64 adjoint."""
+    inp = make_inputs(ADJOINT, seed=7, device="cuda")
+    W, V = make_upstream(ADJOINT, seed=8, device="cuda")
+    args = (inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, W, V)
+    got = B.sigma_grad(*args, mode="fp64_fft", check=True)
+    ref = B.sigma_grad(*args, mode="fp64")
+    for x, y in zip(got, ref):
+        err = float((x - y).abs().max() / y.abs().max())
+        assert err <= TOL, err
