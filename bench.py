@@ -68,11 +68,11 @@ def fp64_kernel_flops(d) -> float:
 
 
 def fft_length(NE: int, Nw: int) -> int:
-    """FFT length along E of the fp64_fft mode: the smallest 2^a 3^b 5^c >= NE + Nw."""
+    """FFT length along E of the fp64_fft mode: the smallest 2^a 3^b >= NE + Nw."""
     L = NE + Nw
     while True:
         m = L
-        for p in (2, 3, 5):
+        for p in (2, 3):
             while m % p == 0:
                 m //= p
         if m == 1:

@@ -73,12 +73,12 @@ typedef struct sse_dims {
  *   FP64_FFT : IEEE double throughout, evaluated with the convolution theorem:
  *            Eq. (3) is, per bond, a convolution of G^t_b with the phonon
  *            weights over (E, kz) -- cyclic in kz, linear in E -- so G is
- *            transformed (zero-padded in E to L >= NE + Nw, L = 2^a 3^b 5^c),
+ *            transformed (zero-padded in E to L >= NE + Nw, L = 2^a 3^b),
  *            each frequency needs 6 Norb x Norb block products per bond, and
  *            the result is transformed back. Same values as FP64 up to the
  *            rounding of the transforms (normwise ~1e-15), far fewer flops;
  *            workspace Nkz*L*(NA + 2*nA)*Norb^2*16 + Nkz*L*nA*NB*9*16 bytes
- *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~6000. */
+ *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~4800. */
 typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 2, SSE_MODE_FP64_FFT = 3 } sse_mode;
 
 /* SYMMETRIZE: replace each output block S by (S - S^H)/2 in FP64 before the

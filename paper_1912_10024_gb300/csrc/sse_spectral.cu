@@ -20,8 +20,8 @@
 //   3. per (a, frequency): the block products above (Gauss 3-multiply
 //      complex MACs on pre-formed (re, im, re+im) planes)             -> S^^   [Nkz][L][nA][Norb^2]
 //   4. inverse kz-DFT, inverse E-FFT, scale 1/(Nkz L), keep E < NE     -> Sigma^t
-// The E-FFT is a Stockham radix-4/2/3/5 transform of C columns at once in
-// shared memory (L = smallest 2^a 3^b 5^c >= NE + Nw); twiddles come from one
+// The E-FFT is a Stockham radix-4/2/3 transform of C columns at once in
+// shared memory (L = smallest 2^a 3^b >= NE + Nw); twiddles come from one
 // table of exp(-2 pi i m / L) built with sincospi. The results equal Eq. (3)
 // up to the rounding of the transforms (normwise ~1e-15).
 #include <cuda_runtime.h>
@@ -52,7 +52,6 @@ FftPlan make_plan(int L) {
     while (m % 4 == 0) p.radix[p.nst++] = 4, m /= 4;
     while (m % 2 == 0) p.radix[p.nst++] = 2, m /= 2;
     while (m % 3 == 0) p.radix[p.nst++] = 3, m /= 3;
-    while (m % 5 == 0) p.radix[p.nst++] = 5, m /= 5;
     p.C = 16;
     while (p.C > 1 && (2 * (size_t)L * p.C + L) * 16 > (size_t)kFftSmemBudget) p.C /= 2;
     p.smem = (int)((2 * (size_t)L * p.C + L) * 16);
@@ -76,7 +75,7 @@ __global__ void twiddle_kernel(int L, double2* __restrict__ tw) {
     }
 }
 
-// In-place forward DFT of R values (R in {2, 3, 4, 5}); tw is the length-L table.
+// In-place forward DFT of R values (R in {2, 3, 4}); tw is the length-L table.
 __device__ __forceinline__ void dft_small(int R, double2* v, const double2* tw, int L) {
     if (R == 2) {
         const double2 a = v[0], b = v[1];
@@ -98,20 +97,6 @@ __device__ __forceinline__ void dft_small(int R, double2* v, const double2* tw, 
         v[0] = cadd(v[0], t);
         v[1] = cadd(m, r);
         v[2] = csub(m, r);
-    } else {  // R == 5: plain 5-point DFT with table twiddles
-        double2 w[5];
-#pragma unroll
-        for (int e = 0; e < 5; ++e) w[e] = tw[(e * (L / 5))];
-        double2 y[5];
-#pragma unroll
-        for (int p = 0; p < 5; ++p) {
-            double2 acc = v[0];
-#pragma unroll
-            for (int r = 1; r < 5; ++r) acc = cadd(acc, cmul(v[r], w[(r * p) % 5]));
-            y[p] = acc;
-        }
-#pragma unroll
-        for (int p = 0; p < 5; ++p) v[p] = y[p];
     }
 }
 
@@ -125,7 +110,7 @@ __device__ double2* fft_columns(const FftPlan& p, double2* src, double2* dst, co
         for (int it = threadIdx.x; it < nb * p.C; it += blockDim.x) {
             const int j = it / p.C, c = it - j * p.C;
             const int k = j % Ns;
-            double2 v[5];
+            double2 v[4];
             for (int r = 0; r < R; ++r) {
                 v[r] = src[(size_t)(j + r * nb) * p.C + c];
                 if (r > 0 && k > 0) v[r] = cmul(v[r], tw[r * k * span]);
@@ -1002,11 +987,10 @@ cudaError_t launch_fft(const char* name, const FftPlan& p, const double2* tw, Lo
 }  // namespace
 
 int spectral_length(const sse_dims& d) {
-    for (int L = d.NE + d.Nw;; ++L) {
+    for (int L = d.NE + d.Nw;; ++L) {  // smallest 2^a 3^b: radix-4/2/3 stages only
         int m = L;
         while (m % 2 == 0) m /= 2;
         while (m % 3 == 0) m /= 3;
-        while (m % 5 == 0) m /= 5;
         if (m == 1) return L;
     }
 }

@@ -1,9 +1,11 @@
 """Large workload (NA=4096, NB=4, Norb=10, NE=1024, Nkz=Nqz=5, Nw=64).
 
 Mixed-precision (BF16X3) forward processed in energy windows of 256 outputs
-with a 2*64 halo, checked against the FP64 oracle on sampled blocks (grid
-edges, window boundaries, interior), and the FP64 adjoint on a subset of
-atoms checked against central differences of the FP64 forward.
+with a 2*64 halo and the transform-based FP64 forward (FFT length 1152),
+checked against the FP64 oracle on sampled blocks (grid edges, window
+boundaries, interior); the phonon self-energy Pi on a sampled atom; and the
+FP64 adjoint on a subset of atoms checked against central differences of the
+FP64 forward.
 """
 import math
 
@@ -47,6 +49,42 @@ def test_large_bf16x3_windows_sampled(large):
         blk = S[:, ::101, ::257]
         assert float((blk + blk.conj().transpose(-1, -2)).abs().max()) <= 2e-5 * float(blk.abs().max())
     del Sl, Sg
+    torch.cuda.empty_cache()
+
+
+def test_large_fp64_fft_sampled(large):
+    inp = large
+    Sl, Sg = B.sigma(inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, mode="fp64_fft",
+                     check=True)
+    torch.cuda.synchronize()
+    errs = []
+    for (a, E0, E1) in [(0, 0, 2), (4095, 1022, 1024), (2047, 511, 513), (77, 700, 702)]:
+        Ol, Og = oracle_blocks(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, a,
+                               E0, E1)
+        for S, O in ((Sl, Ol), (Sg, Og)):
+            errs.append(normwise(S[:, E0:E1, a].cpu().numpy(), O))
+    print("large fp64_fft sampled errors", errs)
+    assert max(errs) <= 1e-12
+    del Sl, Sg
+    torch.cuda.empty_cache()
+
+
+def test_large_pi_sampled(large):
+    """Pi of Eq. (4) at the large sizes; the oracle on the exact sub-problem of one atom and its neighbours."""
+    import oracle
+    inp = large
+    Pl, Pg = B.pi(inp.G_less, inp.G_greater, inp.dH, inp.nbr, LARGE.Nqz, LARGE.Nw, check=True)
+    torch.cuda.synchronize()
+    a = 3001
+    nb = [int(x) for x in inp.nbr[a].cpu()]
+    idx = torch.tensor([a] + nb, device="cuda")
+    nbr = torch.zeros((len(nb) + 1, len(nb)), dtype=torch.int32)
+    nbr[0] = torch.arange(1, len(nb) + 1, dtype=torch.int32)
+    Ol, Og = oracle.pi(nbr, inp.dH.index_select(0, idx).cpu(), inp.G_less.index_select(2, idx).cpu(),
+                       inp.G_greater.index_select(2, idx).cpu(), SCALE, LARGE.Nqz, LARGE.Nw, a_range=(0, 1))
+    for P, O in ((Pl, Ol), (Pg, Og)):
+        assert normwise(P[:, :, a].cpu().numpy(), O[:, :, 0]) <= 1e-12
+    del Pl, Pg
     torch.cuda.empty_cache()
 
 

@@ -1,7 +1,7 @@
 """Phonon self-energy Pi of Eq. (4) (sse_pi_fwd, FP64 through the convolution theorem) against the oracle.
 
 Tolerance: normwise max|gpu - oracle| / max|oracle| <= 1e-12 per output tensor.
-Cases: every FFT radix, Nqz < Nkz, a single kz point, Norb from 1 to 16,
+Cases: every FFT radix (2, 3, 4), Nqz < Nkz, a single kz point, Norb from 1 to 16,
 atom ranges, the symmetrisation flag, a bad neighbour index, and the
 adjoint and FinFET workloads on sampled atoms (exact sub-problems: the atom
 and its neighbours).
@@ -42,11 +42,11 @@ def test_tiny_full(scale):
 
 @pytest.mark.parametrize("dims", [
     Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nqz < Nkz, L = 72
-    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 60 (radix 4, 3, 5)
+    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 64
     Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11),    # L = 54
-    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per pass, L = 90
-    Dims(NA=5, NB=1, Norb=4, NE=70, Nkz=1, Nqz=1, Nw=5),      # single kz point, one neighbour, L = 75
-    Dims(NA=6, NB=3, Norb=1, NE=100, Nkz=9, Nqz=4, Nw=25),    # Norb = 1, L = 125, Nkz = 9
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per pass, L = 96
+    Dims(NA=5, NB=1, Norb=4, NE=70, Nkz=1, Nqz=1, Nw=5),      # single kz point, one neighbour, L = 81
+    Dims(NA=6, NB=3, Norb=1, NE=100, Nkz=9, Nqz=4, Nw=25),    # Norb = 1, L = 128, Nkz = 9
 ], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}_Nkz{d.Nkz}")
 def test_shapes_full(dims):
     inp = make_inputs(dims, seed=dims.Norb + 200, nbr=ring_neighbours(dims.NA, dims.NB))

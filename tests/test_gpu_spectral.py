@@ -2,7 +2,7 @@
 
 Same contract as the direct FP64 path: normwise max|gpu - oracle| / max|oracle|
 <= 1e-12 per output tensor. The cases cover FFT lengths with every radix
-(2, 3, 4, 5), NE + Nw just above and at a 2^a 3^b 5^c length, Nqz < Nkz, a
+(2, 3, 4), NE + Nw just above and at a 2^a 3^b length, Nqz < Nkz, a
 single kz point, every Norb class of the product kernel, atom ranges, the
 symmetrisation flag, bad neighbours, and the adjoint and FinFET workloads
 (full comparison with the direct FP64 kernel, oracle on sampled blocks).
@@ -43,14 +43,14 @@ def test_tiny_full(scale):
 
 
 @pytest.mark.parametrize("dims", [
-    Dims(NA=9, NB=3, Norb=1, NE=1000, Nkz=2, Nqz=2, Nw=7),    # L = 1024 (radix 4 only), 4 columns per FFT CTA
-    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nqz < Nkz, L = 72
-    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 60 (radix 4, 3, 5)
+    Dims(NA=9, NB=3, Norb=1, NE=1000, Nkz=2, Nqz=2, Nw=7),    # L = 1024 (radix 4 only), 2 columns per FFT CTA
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nqz < Nkz, L = 72 (4, 2, 3, 3)
+    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 64 (4, 4, 4)
     Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11),    # Norb of the workloads, L = 54 (2, 3, 3, 3)
-    Dims(NA=4, NB=2, Norb=12, NE=23, Nkz=2, Nqz=1, Nw=6),     # L = 30 (2, 3, 5)
-    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per product pass, L = 90
-    Dims(NA=5, NB=2, Norb=4, NE=70, Nkz=1, Nqz=1, Nw=5),      # single kz point, L = 75 (3, 5, 5)
-    Dims(NA=6, NB=3, Norb=2, NE=100, Nkz=9, Nqz=4, Nw=25),    # L = 125 (5, 5, 5), Nkz = 9
+    Dims(NA=4, NB=2, Norb=12, NE=23, Nkz=2, Nqz=1, Nw=6),     # L = 32 (4, 4, 2)
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per product pass, L = 96
+    Dims(NA=5, NB=2, Norb=4, NE=70, Nkz=1, Nqz=1, Nw=5),      # single kz point, L = 81 (3, 3, 3, 3)
+    Dims(NA=6, NB=3, Norb=2, NE=100, Nkz=9, Nqz=4, Nw=25),    # L = 128 (4, 4, 4, 2), Nkz = 9
 ], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}_Nkz{d.Nkz}")
 def test_shapes_full(dims):
     inp = make_inputs(dims, seed=dims.Norb + 100, nbr=ring_neighbours(dims.NA, dims.NB))

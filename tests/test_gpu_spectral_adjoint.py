@@ -32,10 +32,10 @@ def oracle_grad(inp, W, V, scale=SCALE, **kw):
 @pytest.mark.parametrize("dims", [
     TINY,
     Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nqz < Nkz, L = 72
-    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 60
+    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # L = 64
     Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11),    # L = 54
-    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per pass, L = 90
-    Dims(NA=5, NB=1, Norb=1, NE=70, Nkz=1, Nqz=1, Nw=5),      # Norb = 1, single kz point, L = 75
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # one frequency per pass, L = 96
+    Dims(NA=5, NB=1, Norb=1, NE=70, Nkz=1, Nqz=1, Nw=5),      # Norb = 1, single kz point, L = 81
 ], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}_Nkz{d.Nkz}")
 def test_shapes_vs_oracle(dims):
     nbr = ring_neighbours(dims.NA, dims.NB) if dims is not TINY else None
