@@ -123,6 +123,28 @@ def mixed_tensor_flops(d, mode: str) -> float:
     return 2.0 * 128 * npad * kpad * taps * d.Nqz * d.NB * d.Nkz * 2 * d.NA
 
 
+# DRAM bytes (read + write) per unit of work measured by ncu for the transform-path kernels
+# (profiles/spec_*_adjoint_ncu_full.md), valid for the kernel source they were taken on.
+NCU_TRAFFIC = {
+    "spec_prod_kernel": (4429.3, "c8a6f75cb574210d", "atom-frequency of one type"),
+    "spec_pi_kernel": (4872.6, "c8a6f75cb574210d", "type-atom-frequency"),
+    "spec_adj_kernel": (14302.1, "c8a6f75cb574210d", "atom-frequency of one type"),
+}
+
+
+def ncu_traffic(kernel: str, units: float):
+    """Per-launch DRAM traffic scaled from the ncu capture by the units one launch processes, or None
+    when the kernel source changed since the capture."""
+    import hashlib
+    if kernel not in NCU_TRAFFIC:
+        return None
+    per, sha, _ = NCU_TRAFFIC[kernel]
+    with open(os.path.join(ROOT, "paper_1912_10024_gb300", "csrc", "sse_spectral.cu"), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != sha:
+            return None
+    return per * units
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -413,6 +435,8 @@ def main():
                    "ms_per_step": pms, "warmup": max(3, args.warmup),
                    "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": ach / FP64_PEAK_TFLOPS, "kernel": "spec_pi_kernel", "launch_ms": ks * 1e3,
+                                "traffic": ncu_traffic("spec_pi_kernel",
+                                                       2 * d.NA * d.Nkz * fft_length(d.NE, d.Nw)),
                                 "kernels": {k: {"ms_per_step": v[0] / args.steps,
                                                 "launches_per_step": v[1] / args.steps} for k, v in pk.items()}}}
         del wsp, Pout
@@ -453,6 +477,7 @@ def main():
                     "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                  "frac": ach / FP64_PEAK_TFLOPS, "kernel": "spec_adj_kernel",
                                  "launch_ms": ks * 1e3,
+                                 "traffic": ncu_traffic("spec_adj_kernel", d.NA * d.Nkz * fft_length(d.NE, d.Nw)),
                                  "kernels": {k: {"ms_per_step": v[0] / args.steps,
                                                  "launches_per_step": v[1] / args.steps} for k, v in ak.items()}}}
         del W, V, wsa, gout
@@ -473,8 +498,11 @@ def main():
         elif args.mode == "fp64_fft":
             ks, n = kernel_s("spec_prod_kernel")
             achieved = spectral_prod_flops(d) / ks / 1e12
+            units = d.NA * d.Nkz * fft_length(d.NE, d.Nw)
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "spec_prod_kernel",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic("spec_prod_kernel", units),
+                    "traffic_source": "ncu capture at the adjoint workload, bytes per atom-frequency x units",
+                    "kernel": "spec_prod_kernel",
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
         else:
             peaks, src = load_peaks()
