@@ -64,6 +64,9 @@ def _open(path):
     for name in ("sse_oracle_dcomb", "sse_oracle_dcomb_adj"):
         getattr(lib, name).argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, vp]
         getattr(lib, name).restype = ctypes.c_int
+    lib.sse_oracle_bwd_g.argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, ctypes.c_double, vp, vp, vp, vp,
+                                     ctypes.c_int]
+    lib.sse_oracle_bwd_g.restype = ctypes.c_int
     lib.sse_oracle_pi.argtypes = [ctypes.POINTER(_Dims), vp, vp, vp, vp, ctypes.c_double, vp, vp, ctypes.c_int]
     lib.sse_oracle_pi.restype = ctypes.c_int
     return lib
@@ -229,3 +232,22 @@ def pi(nbr, dH, G_less, G_greater, scale, Nqz, Nw, a_range=None, nthreads=None):
     if rc != 0:
         raise ValueError(f"sse_oracle_pi failed with status {rc}")
     return P_l, P_g
+
+
+def sigma_grad_G(nbr, dH, D_less, D_greater, scale, W_less, W_greater, a_range=None, nthreads=None):
+    """Gradients w.r.t. G^<, G^> of L = sum_t Re tr(W^t^H Sigma^t) over atoms in ``a_range``.
+
+    PyTorch convention for complex tensors. Returns (gG_less, gG_greater) shaped like G (every atom).
+    """
+    lib = _load()
+    D_l, D_g = _np(D_less, np.complex128), _np(D_greater, np.complex128)
+    dH_, nbr_ = _np(dH, np.complex128), _np(nbr, np.int32)
+    W_l, W_g = _np(W_less, np.complex128), _np(W_greater, np.complex128)
+    d = _dims(W_l, D_l, dH_, a_range, None)
+    gG_l, gG_g = np.zeros_like(W_l), np.zeros_like(W_g)
+    rc = lib.sse_oracle_bwd_g(ctypes.byref(d), nbr_.ctypes.data, dH_.ctypes.data, D_l.ctypes.data, D_g.ctypes.data,
+                              float(scale), W_l.ctypes.data, W_g.ctypes.data, gG_l.ctypes.data, gG_g.ctypes.data,
+                              int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError(f"sse_oracle_bwd_g failed with status {rc}")
+    return gG_l, gG_g

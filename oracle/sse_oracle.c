@@ -676,3 +676,114 @@ int sse_oracle_pi(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH, 
     free(J.acc);
     return ORACLE_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* gradient with respect to G (adjoint of Eq. 3 in its G argument)      */
+/* ------------------------------------------------------------------ */
+/*
+ * For L = sum_t sum_{a in range, E, k} Re tr( W^t_a(E,k)^H Sigma^t_a(E,k) ) each term
+ * c * Dc_ij * dH_i G dH_j^H of Eq. (3) gives grad G = conj(c * Dc_ij) dH_i^H W dH_j, so
+ *   grad G^t_b(E', k') = sum over bonds (a, s) with nbr[a][s] = b, a in range, and over (q, w, sigma)
+ *                        with E = E' + sigma*(w+1) in [0, NE), k = (k' + q) mod Nkz:
+ *                        sum_ij conj(c * Dc^{tau(t,sigma)}_ij(q,w,a,s)) dH_i(a,s)^H W^t_a(E,k) dH_j(a,s).
+ * Written for every atom b (atoms that no bond in range reaches get zero).
+ */
+typedef struct {
+    const sse_oracle_dims* d;
+    const int32_t* nbr;
+    const cplx* dH;
+    const cplx* D[2];
+    const cplx* W[2];
+    cplx* gG[2];
+    cplx c;
+    long long n_out, next;
+    pthread_mutex_t lock;
+    int fail;
+} bwdg_job;
+
+static void bwdg_one(bwdg_job* J, int t, int b, int Ep, int kp, cplx* P, cplx* Q, cplx* acc) {
+    const sse_oracle_dims* d = J->d;
+    const int n = d->Norb, nn = n * n;
+    memset(acc, 0, sizeof(cplx) * nn);
+    for (int a = d->a_begin; a < d->a_end; ++a)
+        for (int s = 0; s < d->NB; ++s) {
+            if (J->nbr[(size_t)a * d->NB + s] != b) continue;
+            for (int q = 0; q < d->Nqz; ++q) {
+                const int k = (kp + q) % d->Nkz; /* kz - qz = k' */
+                for (int w = 0; w < d->Nw; ++w)
+                    for (int sg = 0; sg < 2; ++sg) {
+                        const int sigma = sg == 0 ? +1 : -1;
+                        const int E = Ep + sigma * (w + 1);
+                        if (E < 0 || E >= d->NE) continue;
+                        const int tau = sigma == +1 ? t : 1 - t;
+                        const cplx* Wa = J->W[t] + off_G(d, k, E, a);
+                        const cplx* Dc = J->D[tau] + off_D(d, q, w, a, s);
+                        for (int i = 0; i < 3; ++i) {
+                            mm_ah(n, J->dH + off_dH(d, a, s, i), Wa, P); /* dH_i^H W */
+                            for (int j = 0; j < 3; ++j) {
+                                mm(n, P, J->dH + off_dH(d, a, s, j), Q); /* ... dH_j */
+                                const cplx f = conj(J->c * Dc[i * 3 + j]);
+                                for (int e = 0; e < nn; ++e) acc[e] += f * Q[e];
+                            }
+                        }
+                    }
+            }
+        }
+    cplx* out = J->gG[t] + off_G(d, kp, Ep, b);
+    for (int e = 0; e < nn; ++e) out[e] = acc[e];
+}
+
+static void* bwdg_worker(void* arg) {
+    bwdg_job* J = (bwdg_job*)arg;
+    const sse_oracle_dims* d = J->d;
+    const int nn = d->Norb * d->Norb;
+    cplx* buf = (cplx*)malloc(sizeof(cplx) * nn * 3);
+    if (!buf) {
+        pthread_mutex_lock(&J->lock);
+        J->fail = 1;
+        pthread_mutex_unlock(&J->lock);
+        return NULL;
+    }
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        long long o = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (o >= J->n_out) break;
+        const int kp = (int)(o % d->Nkz);
+        long long r = o / d->Nkz;
+        const int Ep = (int)(r % d->NE);
+        r /= d->NE;
+        const int b = (int)(r % d->NA);
+        const int t = (int)(r / d->NA);
+        bwdg_one(J, t, b, Ep, kp, buf, buf + nn, buf + 2 * nn);
+    }
+    free(buf);
+    return NULL;
+}
+
+/* grad G^<, grad G^> (layout of G, every atom overwritten) of the loss above. */
+int sse_oracle_bwd_g(const sse_oracle_dims* d, const int32_t* nbr, const cplx* dH, const cplx* D_less,
+                     const cplx* D_greater, double scale, const cplx* W_less, const cplx* W_greater, cplx* gG_less,
+                     cplx* gG_greater, int nthreads) {
+    if (!check_dims(d) || !nbr || !dH || !D_less || !D_greater || !W_less || !W_greater || !gG_less || !gG_greater)
+        return ORACLE_BAD_ARG;
+    for (size_t e = 0; e < (size_t)d->NA * d->NB; ++e)
+        if (nbr[e] < 0 || nbr[e] >= d->NA) return ORACLE_BAD_ARG;
+    bwdg_job J;
+    memset(&J, 0, sizeof J);
+    J.d = d;
+    J.nbr = nbr;
+    J.dH = dH;
+    J.D[0] = D_less;
+    J.D[1] = D_greater;
+    J.W[0] = W_less;
+    J.W[1] = W_greater;
+    J.gG[0] = gG_less;
+    J.gG[1] = gG_greater;
+    J.c = I * scale;
+    J.n_out = 2LL * d->NA * d->NE * d->Nkz;
+    pthread_mutex_init(&J.lock, NULL);
+    run_threads(bwdg_worker, &J, nthreads);
+    pthread_mutex_destroy(&J.lock);
+    return J.fail ? ORACLE_NO_MEM : ORACLE_OK;
+}

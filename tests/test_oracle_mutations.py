@@ -2,8 +2,8 @@
 
 Each case plants one mistake in a copy of oracle/sse_oracle.c (on the CPU),
 builds it, and checks that at least one pin (tests/test_oracle_pins.py,
-tests/test_oracle_adjoint.py, tests/test_oracle_dcomb.py, tests/test_oracle_pi.py)
-fails against the mutated build.
+tests/test_oracle_adjoint.py, tests/test_oracle_dcomb.py, tests/test_oracle_pi.py,
+tests/test_oracle_grad_g.py) fails against the mutated build.
 """
 import os
 
@@ -73,6 +73,31 @@ PI = [
     ("prefactor sign", "const cplx c = -I * scale;", "const cplx c = I * scale;"),
     ("diagonal block misses a neighbour", "self[e] += v[e];  /* diagonal", "if (s > 0) self[e] += v[e];  /* diagonal"),
 ]
+GRADG = [
+    ("grad G energy shift sign", "const int E = Ep + sigma * (w + 1);", "const int E = Ep - sigma * (w + 1);"),
+    ("grad G kz shift sign", "const int k = (kp + q) % d->Nkz; /* kz - qz = k' */",
+     "const int k = ((kp - q) % d->Nkz + d->Nkz) % d->Nkz; /* kz - qz = k' */"),
+    ("grad G weight not conjugated", "const cplx f = conj(J->c * Dc[i * 3 + j]);", "const cplx f = J->c * Dc[i * 3 + j];"),
+    ("grad G types swapped", "const int tau = sigma == +1 ? t : 1 - t;\n                        const cplx* Wa",
+     "const int tau = sigma == +1 ? 1 - t : t;\n                        const cplx* Wa"),
+    ("grad G left coupling not conjugate-transposed", "mm_ah(n, J->dH + off_dH(d, a, s, i), Wa, P); /* dH_i^H W */",
+     "mm(n, J->dH + off_dH(d, a, s, i), Wa, P); /* dH_i^H W */"),
+]
+
+
+def _gradg_pins():
+    import test_oracle_grad_g as gg
+
+    class _Req:
+        def __init__(self, p):
+            self.param = p
+
+    def run(kind):
+        prob = gg.problem.__wrapped__(_Req(kind))
+        gg.test_dot_product(prob)
+        gg.test_central_differences(prob)
+    yield lambda: run("ring")
+    yield lambda: run("two_way_ring")
 
 
 def _pi_pins():
@@ -153,6 +178,12 @@ def test_pi_mutation_is_caught(tmp_path, name, old, new):
     assert _caught(_build(tmp_path, old, new), _pi_pins()), f"no pin caught: {name}"
 
 
+@pytest.mark.parametrize("name,old,new", GRADG, ids=[m[0] for m in GRADG])
+def test_gradg_mutation_is_caught(tmp_path, name, old, new):
+    assert _caught(_build(tmp_path, old, new), _gradg_pins()), f"no pin caught: {name}"
+
+
 def test_unmutated_source_passes(tmp_path):
     so = _build(tmp_path, "#include <complex.h>", "#include <complex.h>")
-    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()) + list(_dcomb_pins()) + list(_pi_pins()))
+    assert not _caught(so, list(_fwd_pins()) + list(_bwd_pins()) + list(_dcomb_pins()) + list(_pi_pins()) +
+                       list(_gradg_pins()))
