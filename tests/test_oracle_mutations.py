@@ -31,7 +31,8 @@ FWD = [
      "mm(n, P, J->dH + off_dH(d, a, s, j), Q);"),
     ("factor order G dH_i", "mm(n, J->dH + off_dH(d, a, s, i), Gp, P);", "mm(n, Gp, J->dH + off_dH(d, a, s, i), P);"),
     ("weight indices transposed", "const cplx dij = Dc[i * 3 + j];", "const cplx dij = Dc[j * 3 + i];"),
-    ("prefactor i dropped", "J.c = I * scale;\n    J.n_out", "J.c = scale;\n    J.n_out"),
+    ("prefactor i dropped", "J.c = I * scale;\n    J.n_out = 2LL * (d->a_end",
+     "J.c = scale;\n    J.n_out = 2LL * (d->a_end"),
     ("neighbour G replaced by own atom", "const cplx* Gp = J->G[t] + off_G(d, kp, Ep, b);\n                    const cplx* Dc = J->D[tau]",
      "const cplx* Gp = J->G[t] + off_G(d, kp, Ep, a);\n                    const cplx* Dc = J->D[tau]"),
     ("edge terms wrapped instead of dropped",
