@@ -480,7 +480,33 @@ def main():
                                  "traffic": ncu_traffic("spec_adj_kernel", d.NA * d.Nkz * fft_length(d.NE, d.Nw)),
                                  "kernels": {k: {"ms_per_step": v[0] / args.steps,
                                                  "launches_per_step": v[1] / args.steps} for k, v in ak.items()}}}
-        del W, V, wsa, gout
+        # gradient w.r.t. G^<, G^> (sse_sigma_bwd_g), same upstream
+        del wsa
+        torch.cuda.empty_cache()
+        wsg = torch.empty(B.sse_sigma_bwd_g_workspace_bytes(dims, mfft, 0), dtype=torch.uint8, device=dev)
+        gG = (torch.empty_like(inp.G_less), torch.empty_like(inp.G_greater))
+
+        def gstep(flags=0):
+            rc = B.sse_sigma_bwd_g(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, SCALE, mfft, flags, W, V,
+                                   gG[0], gG[1], wsg, wsg.numel(), stream)
+            if rc != 0:
+                raise B.SseError(rc, "sse_sigma_bwd_g")
+
+        for _ in range(max(3, args.warmup)):
+            gstep()
+        torch.cuda.synchronize(dev)
+        B.sse_profile_read()
+        a0.record(stream)
+        for _ in range(args.steps):
+            gstep(B.SSE_FLAG_PROFILE)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        gk = {name: (ms, n) for name, ms, n in B.sse_profile_read()}
+        adj_line["grad_G"] = {"op": "gradient w.r.t. G^<, G^> (sse_sigma_bwd_g, FP64 via the transforms)",
+                              "ms_per_step": a0.elapsed_time(a1) / args.steps,
+                              "kernels": {k: {"ms_per_step": v[0] / args.steps,
+                                              "launches_per_step": v[1] / args.steps} for k, v in gk.items()}}
+        del W, V, wsg, gout, gG
         torch.cuda.empty_cache()
 
     out = None

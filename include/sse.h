@@ -141,6 +141,21 @@ SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* d
                   uint32_t flags, const double* gS_less, const double* gS_greater, double* g_dH, double* g_D_less,
                   double* g_D_greater, void* workspace, size_t ws_bytes, void* stream);
 
+/* Gradient of the same loss as sse_sigma_bwd with respect to G^<, G^> (Sigma is linear in
+ * G, so G itself is not an argument):
+ *   g_G^t_b(E', k') = sum over bonds (a, s) with nbr[a][s] = b and a in [a_begin, a_end),
+ *                     over (q, w, sigma) with E = E' + sigma*(w+1) in [0, NE), k = (k'+q) mod Nkz:
+ *                     sum_ij conj(i*scale * D^tau_ij(q,w,a,s)) dH_i(a,s)^H gS^t_a(E,k) dH_j(a,s).
+ * g_G_less / g_G_greater have the layout of G and are fully overwritten for every atom (zero where
+ * no bond in range reaches). FP64 through the transforms (modes FP64 and FP64_FFT): per atom and
+ * frequency, the bonds into it in (a, s) order from a list built on the device (deterministic sums).
+ * SYMMETRIZE projects gS as in sse_sigma_bwd. Workspace: sse_sigma_bwd_g_workspace_bytes(). */
+SSE_API size_t sse_sigma_bwd_g_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
+SSE_API int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                            const double* D_greater, double scale, int mode, uint32_t flags, const double* gS_less,
+                            const double* gS_greater, double* g_G_less, double* g_G_greater, void* workspace,
+                            size_t ws_bytes, void* stream);
+
 /* Phonon scattering self-energy Pi^<, Pi^> of Eq. (4) (Sec. 2) for atoms [a_begin, a_end):
  *   P^t complex128 [Nqz][Nw][NA][NB+1][3][3]: slot s < NB is the block Pi^t_ab for
  *        b = nbr[a][s], slot NB the diagonal block Pi^t_aa; indices (i, j) of the

@@ -20,7 +20,8 @@ SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT = 0, 1, 2, 3
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE = 1, 2, 4
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
-            "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_profile_read", "sse_strerror")
+            "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes", "sse_sigma_bwd_g",
+            "sse_profile_read", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -72,6 +73,10 @@ def load() -> ctypes.CDLL:
             lib.sse_pi_workspace_bytes.restype = ctypes.c_size_t
             lib.sse_pi_fwd.argtypes = [pd, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, ctypes.c_size_t, vp]
             lib.sse_pi_fwd.restype = i32
+            lib.sse_sigma_bwd_g_workspace_bytes.argtypes = [pd, i32, u32]
+            lib.sse_sigma_bwd_g_workspace_bytes.restype = ctypes.c_size_t
+            lib.sse_sigma_bwd_g.argtypes = [pd, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+            lib.sse_sigma_bwd_g.restype = i32
             lib.sse_profile_read.argtypes = [ctypes.POINTER(sse_profile_entry), i32]
             lib.sse_profile_read.restype = i32
             _lib = lib
@@ -116,6 +121,17 @@ def sse_pi_fwd(d: sse_dims, nbr, dH, G_less, G_greater, scale: float, mode: int,
     return int(load().sse_pi_fwd(ctypes.byref(d), _p(nbr), _p(dH), _p(G_less), _p(G_greater), float(scale),
                                  int(mode), int(flags), _p(P_less), _p(P_greater), _p(workspace), int(ws_bytes),
                                  _stream(stream)))
+
+
+def sse_sigma_bwd_g_workspace_bytes(d: sse_dims, mode: int, flags: int) -> int:
+    return int(load().sse_sigma_bwd_g_workspace_bytes(ctypes.byref(d), int(mode), int(flags)))
+
+
+def sse_sigma_bwd_g(d: sse_dims, nbr, dH, D_less, D_greater, scale: float, mode: int, flags: int, gS_less,
+                    gS_greater, g_G_less, g_G_greater, workspace, ws_bytes: int, stream=None) -> int:
+    return int(load().sse_sigma_bwd_g(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater), float(scale),
+                                      int(mode), int(flags), _p(gS_less), _p(gS_greater), _p(g_G_less),
+                                      _p(g_G_greater), _p(workspace), int(ws_bytes), _stream(stream)))
 
 
 def sse_sigma_bwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int, flags: int,
@@ -286,10 +302,32 @@ def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 
     return out
 
 
-class SigmaFunction(torch.autograd.Function):
-    """(dH, D^<, D^>) -> (Sigma^<, Sigma^>) with the hand-written adjoint.
+def sigma_grad_G(dH, D_less, D_greater, nbr, gS_less, gS_greater, scale: float = 1.0 / (2.0 * math.pi),
+                 symmetrize: bool = False, check: bool = False, atoms=None, ws: Optional[torch.Tensor] = None,
+                 stream=None, profile: bool = False):
+    """Gradients (g_G_less, g_G_greater) of sum_t Re tr(gS^t^H Sigma^t) with respect to G via sse_sigma_bwd_g."""
+    d = dims_of(gS_less, D_less, dH, atoms)
+    flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    flags |= SSE_FLAG_PROFILE if profile else 0
+    gSl, gSg = gS_less.contiguous(), gS_greater.contiguous()
+    g_Gl, g_Gg = torch.empty_like(gSl), torch.empty_like(gSg)
+    if ws is None:
+        n = sse_sigma_bwd_g_workspace_bytes(d, SSE_MODE_FP64_FFT, flags)
+        if n == 0:
+            raise ValueError("invalid or unsupported problem sizes for libsse")
+        ws = torch.empty(n, dtype=torch.uint8, device=dH.device)
+    rc = sse_sigma_bwd_g(d, nbr, dH, D_less, D_greater, scale, SSE_MODE_FP64_FFT, flags, gSl, gSg, g_Gl, g_Gg, ws,
+                         ws.numel(), stream)
+    if rc != 0:
+        raise SseError(rc, "sse_sigma_bwd_g")
+    return g_Gl, g_Gg
 
-    G^<, G^>, nbr and the scalar options are not differentiated.
+
+class SigmaFunction(torch.autograd.Function):
+    """(dH, D^<, D^>, G^<, G^>) -> (Sigma^<, Sigma^>) with the hand-written adjoints.
+
+    Gradients for G^<, G^> are computed only when requested (sse_sigma_bwd_g); nbr and the
+    scalar options are not differentiated.
     """
 
     @staticmethod
@@ -310,7 +348,10 @@ class SigmaFunction(torch.autograd.Function):
             gSg = torch.zeros_like(G_greater)
         g = sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gSl, gSg, scale=ctx.scale,
                        symmetrize=ctx.symmetrize, mode=ctx.bwd_mode)
-        return g[0], g[1], g[2], None, None, None, None, None, None
+        gG = (None, None)
+        if ctx.needs_input_grad[3] or ctx.needs_input_grad[4]:
+            gG = sigma_grad_G(dH, D_less, D_greater, nbr, gSl, gSg, scale=ctx.scale, symmetrize=ctx.symmetrize)
+        return g[0], g[1], g[2], gG[0], gG[1], None, None, None, None
 
 
 def sigma_autograd(dH, D_less, D_greater, G_less, G_greater, nbr, scale=1.0 / (2.0 * math.pi), mode="fp64",

@@ -237,3 +237,36 @@ extern "C" int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* d
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }
+
+extern "C" size_t sse_sigma_bwd_g_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
+    return sse::kStatusBytes + sse::spectral_bwd_g_workspace(*d);
+}
+
+extern "C" int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                               const double* D_greater, double scale, int mode, uint32_t flags, const double* gS_less,
+                               const double* gS_greater, double* g_G_less, double* g_G_greater, void* workspace,
+                               size_t ws_bytes, void* stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !isfinite(scale)) return SSE_ERR_INVALID_ARG;
+    if (!nbr || !dH || !D_less || !D_greater || !gS_less || !gS_greater || !g_G_less || !g_G_greater)
+        return SSE_ERR_INVALID_ARG;
+    if (!aligned(nbr, 4) || !aligned(dH, 16) || !aligned(D_less, 16) || !aligned(D_greater, 16) ||
+        !aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_G_less, 16) || !aligned(g_G_greater, 16))
+        return SSE_ERR_INVALID_ARG;
+    if (!supported_dims(d) || !fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::spectral_bwd_g_workspace(*d))
+        return SSE_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned* status = static_cast<unsigned*>(workspace);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
+    // G does not enter the gradient (Sigma is linear in G); the Problem's G pointers stay null
+    const sse::Problem p = make_problem(d, nbr, dH, D_less, D_greater, nullptr, nullptr, scale, flags);
+    cudaError_t e = sse::spectral_bwd_g(p, reinterpret_cast<const double2*>(gS_less),
+                                        reinterpret_cast<const double2*>(gS_greater),
+                                        reinterpret_cast<double2*>(g_G_less), reinterpret_cast<double2*>(g_G_greater),
+                                        status, static_cast<char*>(workspace) + sse::kStatusBytes,
+                                        ws_bytes - sse::kStatusBytes, st);
+    if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
+    return finish(e, status, flags, st);
+}

@@ -129,3 +129,15 @@ def test_pi_workspace_bytes():
     bad = good_dims()
     bad.Nw = bad.NE
     assert B.sse_pi_workspace_bytes(bad, B.SSE_MODE_FP64, 0) == 0
+
+
+def test_bwd_g_rejects_bad_arguments_on_host():
+    d = good_dims()
+    base = dict(nbr=FAKE, dH=FAKE, D_less=FAKE, D_greater=FAKE, scale=0.1, mode=3, flags=0, gS_less=FAKE,
+                gS_greater=FAKE, g_G_less=FAKE, g_G_greater=FAKE, workspace=FAKE, ws_bytes=1 << 20)
+    for over, status in ((dict(dH=0), 1), (dict(g_G_less=FAKE + 8), 1), (dict(mode=2), 2), (dict(flags=1 << 5), 1),
+                         (dict(workspace=0), 6), (dict(ws_bytes=8), 6)):
+        args = dict(base)
+        args.update(over)
+        assert B.sse_sigma_bwd_g(d, stream=0, **args) == status, over
+    assert B.sse_sigma_bwd_g_workspace_bytes(d, 3, 0) > 256
