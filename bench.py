@@ -80,22 +80,29 @@ def fft_length(NE: int, Nw: int) -> int:
         L += 1
 
 
-def spectral_prod_flops(d) -> float:
+def freq_count(d, half: bool) -> int:
+    """Frequencies the product kernels evaluate: Nkz * L, or one of each (f, -f) pair with
+    SSE_FLAG_ANTIHERMITIAN (the library's frequency map)."""
+    L = fft_length(d.NE, d.Nw)
+    if not half:
+        return d.Nkz * L
+    return d.Nkz * ((L - 1) // 2) + (d.Nkz // 2 + 1) * (2 if L % 2 == 0 else 1)
+
+
+def spectral_prod_flops(d, half: bool = False) -> float:
     """FP64 flops one spec_prod_kernel launch (one type) executes: per (atom, slot, frequency) and block
     element, the weight block W_i (9 complex MACs at 4 FMA) and two block products (3 Norb complex
     MACs each at 3 FMA, Gauss form); 2 flops per FMA."""
-    L = fft_length(d.NE, d.Nw)
     nel = d.Norb * d.Norb
-    return 2.0 * d.NA * d.NB * d.Nkz * L * nel * (36 + 18 * d.Norb)
+    return 2.0 * d.NA * d.NB * freq_count(d, half) * nel * (36 + 18 * d.Norb)
 
 
-def spectral_pi_flops(d) -> float:
+def spectral_pi_flops(d, half: bool = False) -> float:
     """FP64 flops one spec_pi_kernel launch (both types) executes: per (type, atom, slot, frequency) and block
     element, the half products dH_i^H G^ and dH_j G^ (3 Norb complex MACs each at 3 FMA) and the 9 trace
     terms (2 FMA each); 2 flops per FMA."""
-    L = fft_length(d.NE, d.Nw)
     nel = d.Norb * d.Norb
-    return 2.0 * 2 * d.NA * d.NB * d.Nkz * L * nel * (18 * d.Norb + 18)
+    return 2.0 * 2 * d.NA * d.NB * freq_count(d, half) * nel * (18 * d.Norb + 18)
 
 
 def spectral_adj_flops(d) -> float:
@@ -235,6 +242,7 @@ def bench_config(args, d):
     """The workload description shared by both arms."""
     g_bytes = 2 * d.Nkz * d.NE * d.NA * d.Norb * d.Norb * 16
     return {"workload": args.workload, **d.__dict__, "mode": args.mode,
+            "antihermitian_inputs_flag": bool(getattr(args, "antihermitian", False)),
             "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (g_bytes / 1e9)}
 
 
@@ -270,6 +278,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other modes on the same inputs")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--antihermitian", action="store_true",
+                    help="pass SSE_FLAG_ANTIHERMITIAN (the synthetic G and D blocks are exactly anti-Hermitian)")
     ap.add_argument("--no-pi", action="store_true", help="skip timing the phonon self-energy (Eq. 4)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip timing the FP64 adjoint")
     args = ap.parse_args()
@@ -293,6 +303,7 @@ def main():
 
     inp = make_inputs(d, seed=rank, device=dev)
     mode = B.MODES[args.mode]
+    run_flags = B.SSE_FLAG_ANTIHERMITIAN if args.antihermitian else 0
     dims = B.dims_of(inp.G_less, inp.D_less, inp.dH)
     ws = B.workspace(dims, mode, 0, dev)
     Sl = torch.empty_like(inp.G_less)
@@ -301,7 +312,7 @@ def main():
 
     def step(flags=0):
         rc = B.sse_sigma_fwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
-                             mode, flags, Sl, Sg, ws, ws.numel(), stream)
+                             mode, flags | run_flags, Sl, Sg, ws, ws.numel(), stream)
         if rc != 0:
             raise B.SseError(rc, "sse_sigma_fwd")
 
@@ -368,17 +379,19 @@ def main():
     if not args.no_compare and rank == 0:
         compare = {}
         ref = (Sl.clone(), Sg.clone())
-        bounds = {"fp64": 1e-12, "fp64_fft": 1e-12, "bf16x3": 2e-5, "tf32": 2e-3}
-        for mname in ("fp64", "bf16x3", "tf32", "fp64_fft"):
-            if mname == args.mode:
+        bounds = {"fp64": 1e-12, "fp64_fft": 1e-12, "bf16x3": 2e-5, "tf32": 2e-3, "fp64_fft_antihermitian": 1e-12}
+        variants = [("fp64", 0), ("bf16x3", 0), ("tf32", 0), ("fp64_fft", 0),
+                    ("fp64_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN)]
+        for mname, mflags in variants:
+            if mname == args.mode and mflags == run_flags:
                 continue
-            m = B.MODES[mname]
+            m = B.MODES[mname.replace("_antihermitian", "")]
             wsm = B.workspace(dims, m, 0, dev)
             Ml, Mg = torch.empty_like(Sl), torch.empty_like(Sg)
 
             def mstep():
                 rc = B.sse_sigma_fwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater,
-                                     SCALE, m, 0, Ml, Mg, wsm, wsm.numel(), stream)
+                                     SCALE, m, mflags, Ml, Mg, wsm, wsm.numel(), stream)
                 if rc != 0:
                     raise B.SseError(rc, "sse_sigma_fwd")
 
@@ -415,7 +428,7 @@ def main():
 
         def pstep(flags=0):
             B.pi(inp.G_less, inp.G_greater, inp.dH, inp.nbr, d.Nqz, d.Nw, scale=SCALE, out=Pout, ws=wsp,
-                 stream=stream, profile=bool(flags))
+                 stream=stream, profile=bool(flags), antihermitian=args.antihermitian)
 
         for _ in range(max(3, args.warmup)):
             pstep()
@@ -430,13 +443,12 @@ def main():
         pms = p0.elapsed_time(p1) / args.steps
         pk = {name: (ms, n) for name, ms, n in B.sse_profile_read()}
         ks = pk["spec_pi_kernel"][0] * 1e-3 / pk["spec_pi_kernel"][1]
-        ach = spectral_pi_flops(d) / ks / 1e12
+        ach = spectral_pi_flops(d, args.antihermitian) / ks / 1e12
         pi_line = {"op": "Pi^<, Pi^> of Eq. 4 (sse_pi_fwd, FP64 via the convolution theorem)",
                    "ms_per_step": pms, "warmup": max(3, args.warmup),
                    "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": ach / FP64_PEAK_TFLOPS, "kernel": "spec_pi_kernel", "launch_ms": ks * 1e3,
-                                "traffic": ncu_traffic("spec_pi_kernel",
-                                                       2 * d.NA * d.Nkz * fft_length(d.NE, d.Nw)),
+                                "traffic": ncu_traffic("spec_pi_kernel", 2 * d.NA * freq_count(d, args.antihermitian)),
                                 "kernels": {k: {"ms_per_step": v[0] / args.steps,
                                                 "launches_per_step": v[1] / args.steps} for k, v in pk.items()}}}
         del wsp, Pout
@@ -523,8 +535,8 @@ def main():
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
         elif args.mode == "fp64_fft":
             ks, n = kernel_s("spec_prod_kernel")
-            achieved = spectral_prod_flops(d) / ks / 1e12
-            units = d.NA * d.Nkz * fft_length(d.NE, d.Nw)
+            achieved = spectral_prod_flops(d, args.antihermitian) / ks / 1e12
+            units = d.NA * freq_count(d, args.antihermitian)
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": ncu_traffic("spec_prod_kernel", units),
                     "traffic_source": "ncu capture at the adjoint workload, bytes per atom-frequency x units",

@@ -88,11 +88,26 @@ typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 
  * CHECK     : after the launches, synchronise `stream` and report device-side
  *             input checks (neighbour indices outside [0, NA)) as
  *             SSE_ERR_DEVICE_CHECK. Without CHECK such entries contribute zero
- *             and the call stays asynchronous.
+ *             and the call stays asynchronous. With ANTIHERMITIAN it also reports
+ *             input blocks that are not anti-Hermitian.
  * PROFILE   : record a pair of CUDA events on `stream` around every kernel the
  *             call launches (no synchronisation, no effect on the results);
- *             sse_profile_read reports the device time per kernel. */
-enum { SSE_FLAG_SYMMETRIZE = 1u << 0, SSE_FLAG_CHECK = 1u << 1, SSE_FLAG_PROFILE = 1u << 2 };
+ *             sse_profile_read reports the device time per kernel.
+ * ANTIHERMITIAN : the caller states that every Norb x Norb block of G^< and G^>
+ *             (and, for sse_sigma_fwd, every 3x3 block of D^< and D^>) is exactly
+ *             anti-Hermitian, as lesser and greater Green's functions are. The
+ *             FP64_FFT forward and sse_pi_fwd then compute one frequency of each
+ *             pair (f, -f) and obtain the other from Sigma^(-f) = -Sigma^(f)^H,
+ *             C^(-f) = C^(f)^H (half the block products). With CHECK the inputs are
+ *             verified bit for bit and a violation is reported as
+ *             SSE_ERR_DEVICE_CHECK; without it the results for inputs that are not
+ *             anti-Hermitian are unspecified. Ignored by the other modes and entries. */
+enum {
+    SSE_FLAG_SYMMETRIZE = 1u << 0,
+    SSE_FLAG_CHECK = 1u << 1,
+    SSE_FLAG_PROFILE = 1u << 2,
+    SSE_FLAG_ANTIHERMITIAN = 1u << 3
+};
 
 typedef enum sse_status {
     SSE_OK = 0,

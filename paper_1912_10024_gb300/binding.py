@@ -17,7 +17,7 @@ import torch
 from . import build as _build
 
 SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT = 0, 1, 2, 3
-SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE = 1, 2, 4
+SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE, SSE_FLAG_ANTIHERMITIAN = 1, 2, 4, 8
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
             "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes", "sse_sigma_bwd_g",
@@ -220,7 +220,7 @@ def workspace(d: sse_dims, mode: int, flags: int, device) -> torch.Tensor:
 
 def sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2.0 * math.pi), mode: str = "fp64",
           symmetrize: bool = False, check: bool = False, atoms=None, out=None, ws: Optional[torch.Tensor] = None,
-          stream=None, profile: bool = False):
+          stream=None, profile: bool = False, antihermitian: bool = False):
     """Sigma^<, Sigma^> of Eq. (3) on the current CUDA device via sse_sigma_fwd.
 
     Returns (S_less, S_greater), complex128 tensors shaped like G. With
@@ -231,7 +231,7 @@ def sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2
     d = dims_of(G_less, D_less, dH, atoms)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
-    flags |= SSE_FLAG_PROFILE if profile else 0
+    flags |= (SSE_FLAG_PROFILE if profile else 0) | (SSE_FLAG_ANTIHERMITIAN if antihermitian else 0)
     if out is None:
         alloc = torch.empty if atoms is None else torch.zeros
         out = (alloc(G_less.shape, dtype=torch.complex128, device=G_less.device),
@@ -269,7 +269,7 @@ def sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greate
 
 def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 * math.pi),
        symmetrize: bool = False, check: bool = False, atoms=None, out=None, ws: Optional[torch.Tensor] = None,
-       stream=None, profile: bool = False):
+       stream=None, profile: bool = False, antihermitian: bool = False):
     """Pi^<, Pi^> of Eq. (4) on the current CUDA device via sse_pi_fwd (FP64).
 
     Returns (P_less, P_greater), complex128 [Nqz, Nw, NA, NB+1, 3, 3]: slot s < NB is the block for
@@ -285,7 +285,7 @@ def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 
     a0, a1 = (0, NA) if atoms is None else atoms
     d = sse_dims(NA, NB, Norb, NE, Nkz, int(Nqz), int(Nw), a0, a1)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
-    flags |= SSE_FLAG_PROFILE if profile else 0
+    flags |= (SSE_FLAG_PROFILE if profile else 0) | (SSE_FLAG_ANTIHERMITIAN if antihermitian else 0)
     shape = (int(Nqz), int(Nw), NA, NB + 1, 3, 3)
     if out is None:
         alloc = torch.empty if atoms is None else torch.zeros

@@ -34,7 +34,7 @@ bool valid_mode(int mode) {
 }
 bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
 bool valid_flags(uint32_t f) {
-    return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK | SSE_FLAG_PROFILE)) == 0;
+    return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK | SSE_FLAG_PROFILE | SSE_FLAG_ANTIHERMITIAN)) == 0;
 }
 
 size_t fwd_ws(const sse_dims& d, int mode) {
@@ -50,7 +50,7 @@ int finish(cudaError_t launch, unsigned* status, uint32_t flags, cudaStream_t st
     if (cudaMemcpyAsync(&h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess) return SSE_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return SSE_ERR_CUDA;
     if (h & sse::DEV_TIMEOUT) return SSE_ERR_TIMEOUT;
-    if (h & sse::DEV_BAD_NEIGHBOUR) return SSE_ERR_DEVICE_CHECK;
+    if (h & (sse::DEV_BAD_NEIGHBOUR | sse::DEV_NOT_ANTIHERMITIAN)) return SSE_ERR_DEVICE_CHECK;
     return SSE_OK;
 }
 

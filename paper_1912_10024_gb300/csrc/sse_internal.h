@@ -12,6 +12,7 @@ namespace sse {
 enum : unsigned {
     DEV_BAD_NEIGHBOUR = 1u,  // nbr[a][s] outside [0, NA): that bond contributed zero
     DEV_TIMEOUT = 2u,        // a bounded mbarrier / flag wait gave up
+    DEV_NOT_ANTIHERMITIAN = 4u,  // SSE_FLAG_ANTIHERMITIAN with CHECK: an input block is not anti-Hermitian
 };
 
 // Device views of the inputs of Eq. (3). Complex tensors are double2 (re, im).

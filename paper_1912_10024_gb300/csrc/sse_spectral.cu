@@ -278,6 +278,86 @@ __global__ void dft_k_kernel(double2* __restrict__ X, int Nk, int n_in, size_t M
 }
 
 // ---------------------------------------------------------------------------
+// frequency index maps. With anti-Hermitian inputs (SSE_FLAG_ANTIHERMITIAN) the spectra obey
+// S^(-f) = -S^(f)^H (Sigma) and C^(-f) = C^(f)^H (Pi), so only one frequency of each pair (f, -f)
+// is computed: eps in [1, (L-1)/2] for every kappa, and on the rows eps = 0 and eps = L/2 (L even)
+// kappa in [0, Nk/2]; a mirror kernel fills the partners.
+// ---------------------------------------------------------------------------
+struct FreqMap {
+    int Nk, L, half, Lh, nK0;
+    size_t count;
+};
+
+FreqMap make_freq_map(int Nk, int L, bool half) {
+    FreqMap m{};
+    m.Nk = Nk;
+    m.L = L;
+    m.half = half ? 1 : 0;
+    m.Lh = (L - 1) / 2;
+    m.nK0 = Nk / 2 + 1;
+    m.count = half ? (size_t)Nk * m.Lh + (size_t)m.nK0 * ((L % 2 == 0) ? 2 : 1) : (size_t)Nk * L;
+    return m;
+}
+
+__device__ __forceinline__ size_t freq_of(const FreqMap& m, size_t i) {
+    if (!m.half) return i;
+    const size_t body = (size_t)m.Nk * m.Lh;
+    if (i < body) return (i / m.Lh) * (size_t)m.L + 1 + (i % m.Lh);
+    const size_t r = i - body;
+    const size_t row = r / m.nK0, kap = r - row * m.nK0;
+    return kap * (size_t)m.L + (row == 0 ? 0 : (size_t)(m.L / 2));
+}
+
+__device__ __forceinline__ size_t freq_neg(const FreqMap& m, size_t f) {
+    const int kap = (int)(f / m.L), eps = (int)(f - (size_t)kap * m.L);
+    return (size_t)((m.Nk - kap) % m.Nk) * m.L + (size_t)((m.L - eps) % m.L);
+}
+
+// Sigma^(-f) = -Sigma^(f)^H per atom block, for the computed half
+__global__ void mirror_sigma_kernel(FreqMap fm, size_t nA, int Norb, double2* __restrict__ Sh) {
+    const int nel = Norb * Norb;
+    const size_t total = fm.count * nA * nel;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % nel);
+        const size_t r = i / nel;
+        const size_t la = r % nA, ix = r / nA;
+        const size_t f = freq_of(fm, ix), fn = freq_neg(fm, f);
+        if (fn == f) continue;
+        const int m = e / Norb, n = e - m * Norb;
+        const double2 v = Sh[(f * nA + la) * nel + e];
+        Sh[(fn * nA + la) * nel + n * Norb + m] = make_double2(-v.x, v.y);
+    }
+}
+
+// C^(-f) = C^(f)^H per 3x3 block (Pi), for the computed half
+__global__ void mirror_pi_kernel(FreqMap fm, size_t nblk, double2* __restrict__ Ch) {
+    const size_t total = fm.count * nblk * 9;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int ij = (int)(i % 9);
+        const size_t r = i / 9;
+        const size_t blk = r % nblk, ix = r / nblk;
+        const size_t f = freq_of(fm, ix), fn = freq_neg(fm, f);
+        if (fn == f) continue;
+        const int ii = ij / 3, jj = ij - 3 * ii;
+        const double2 v = Ch[(f * nblk + blk) * 9 + ij];
+        Ch[(fn * nblk + blk) * 9 + jj * 3 + ii] = make_double2(v.x, -v.y);
+    }
+}
+
+// With CHECK: every n x n block must be exactly anti-Hermitian, B[r][c] = -conj(B[c][r]).
+__global__ void check_antiherm_kernel(const double2* __restrict__ X, size_t nblk, int n,
+                                      unsigned* __restrict__ status) {
+    const size_t total = nblk * n * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % (n * n));
+        const size_t b = i / (n * n);
+        const int r = e / n, c2 = e - r * n;
+        const double2 x = X[b * n * n + e], y = X[b * n * n + c2 * n + r];
+        if (x.x != -y.x || x.y != y.y) atomicOr(status, DEV_NOT_ANTIHERMITIAN);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // per-frequency block products
 // ---------------------------------------------------------------------------
 constexpr int kProdMaxThreads = 384;
@@ -319,18 +399,17 @@ __device__ __forceinline__ void put3(double* P, int nel, int e, double2 v) {
     P[2 * nel + e] = v.x + v.y;
 }
 
-__global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restrict__ nbr,
+__global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ nbr,
                                  const double2* __restrict__ dH, const double2* __restrict__ Ghat,
-                                 const double2* __restrict__ Khat, double2* __restrict__ Shat, int L, double scale,
+                                 const double2* __restrict__ Khat, double2* __restrict__ Shat, double scale,
                                  unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int Norb = d.Norb, nel = c.nel;
     const int la = blockIdx.x;
     const int a = d.a_begin + la;
     const size_t nA = (size_t)(d.a_end - d.a_begin);
-    const size_t nfreq = (size_t)d.Nkz * L;
-    const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
-    const size_t f_end = min(nfreq, f_begin + c.fchunk);
+    const size_t i_begin = (size_t)blockIdx.y * c.fchunk;  // frequency indices of the map
+    const size_t i_end = min(fm.count, i_begin + c.fchunk);
     double* sA = reinterpret_cast<double*>(smem + c.off_A);
     double* sG = reinterpret_cast<double*>(smem + c.off_G);
     double2* sK = reinterpret_cast<double2*>(smem + c.off_K);
@@ -353,9 +432,9 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restric
     }
     __syncthreads();
 
-    for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
-        const size_t f = f0 + fl;
-        const bool act = lane && f < f_end;
+    for (size_t i0 = i_begin; i0 < i_end; i0 += c.F) {
+        const bool act = lane && i0 + fl < i_end;
+        const size_t f = act ? freq_of(fm, i0 + fl) : 0;
         double T1 = 0.0, T2 = 0.0, T3 = 0.0;
         for (int s = 0; s < d.NB; ++s) {
             const int b = s < 16 ? bnb[s] : -1;
@@ -367,9 +446,8 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, const int32_t* __restric
             }
             for (int i = tid; i < c.F * 9; i += blockDim.x) {
                 const int fk = i / 9, ij = i - fk * 9;
-                const size_t ff = f0 + fk;
                 double2 k = make_double2(0.0, 0.0);
-                if (ff < f_end && b >= 0) k = Khat[((ff * nA + la) * d.NB + s) * 9 + ij];
+                if (i0 + fk < i_end && b >= 0) k = Khat[((freq_of(fm, i0 + fk) * nA + la) * d.NB + s) * 9 + ij];
                 sK[i] = k;
             }
             __syncthreads();
@@ -476,9 +554,9 @@ PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
 }
 
 __global__ void __launch_bounds__(kProdMaxThreads, 2)
-spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr, const double2* __restrict__ dH,
+spec_pi_kernel(PiCfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ nbr, const double2* __restrict__ dH,
                const double2* __restrict__ Gl_hat, const double2* __restrict__ Gg_hat, double2* __restrict__ Cl_hat,
-               double2* __restrict__ Cg_hat, int L, unsigned* __restrict__ status) {
+               double2* __restrict__ Cg_hat, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int Norb = d.Norb, nel = c.nel;
     const int la = blockIdx.x;
@@ -488,10 +566,8 @@ spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr, const doubl
     const double2* Y_hat = t == 0 ? Gg_hat : Gl_hat;  // G^t' of the neighbour
     double2* C_hat = t == 0 ? Cl_hat : Cg_hat;
     const size_t nA = (size_t)(d.a_end - d.a_begin);
-    const int Nk = d.Nkz;
-    const size_t nfreq = (size_t)Nk * L;
-    const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
-    const size_t f_end = min(nfreq, f_begin + c.fchunk);
+    const size_t i_begin = (size_t)blockIdx.y * c.fchunk;  // frequency indices of the map
+    const size_t i_end = min(fm.count, i_begin + c.fchunk);
     double* sA = reinterpret_cast<double*>(smem + c.off_A);
     double* sX = reinterpret_cast<double*>(smem + c.off_X);
     double* sY = reinterpret_cast<double*>(smem + c.off_Y);
@@ -522,14 +598,10 @@ spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr, const doubl
         }
     __syncthreads();
 
-    for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
-        const size_t f = f0 + fl;
-        const bool act = lane && f < f_end;
-        size_t fneg = 0;  // -f = (-kappa mod Nk, -eps mod L)
-        if (act) {
-            const int kap = (int)(f / L), eps = (int)(f - (size_t)kap * L);
-            fneg = (size_t)((Nk - kap) % Nk) * L + (size_t)((L - eps) % L);
-        }
+    for (size_t i0 = i_begin; i0 < i_end; i0 += c.F) {
+        const bool act = lane && i0 + fl < i_end;
+        const size_t f = act ? freq_of(fm, i0 + fl) : 0;
+        const size_t fneg = act ? freq_neg(fm, f) : 0;
         if (lane) {
             double2 x = make_double2(0.0, 0.0);
             if (act) x = X_hat[(f * d.NA + a) * nel + e];
@@ -594,14 +666,16 @@ spec_pi_kernel(PiCfg c, sse_dims d, const int32_t* __restrict__ nbr, const doubl
             __syncthreads();
             for (int g = tid; g < c.F * 9; g += blockDim.x) {  // fixed-order sums over the rows m
                 const int rf = g / 9, ij = g - rf * 9;
-                const size_t ff = f0 + rf;
                 const double2* v = sD + (size_t)g * Norb;
                 double2 sum = v[0];
                 for (int mm = 1; mm < Norb; ++mm) sum = cadd(sum, v[mm]);
                 const double2 self = cadd(sSelf[g], sum);
                 sSelf[g] = self;
-                if (ff < f_end) C_hat[((ff * nA + la) * slots + s) * 9 + ij] = sum;
-                if (s == d.NB - 1 && ff < f_end) C_hat[((ff * nA + la) * slots + d.NB) * 9 + ij] = self;
+                if (i0 + rf < i_end) {
+                    const size_t ff = freq_of(fm, i0 + rf);
+                    C_hat[((ff * nA + la) * slots + s) * 9 + ij] = sum;
+                    if (s == d.NB - 1) C_hat[((ff * nA + la) * slots + d.NB) * 9 + ij] = self;
+                }
             }
             // the next bond rewrites sY before its first barrier; sP, sR and sD only after it
         }
@@ -1178,7 +1252,21 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
 
     SSE_TIMED("twiddle_kernel", st, twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const ProdCfg pc = make_prod_cfg(d, nfreq);
+    const bool half = (p.flags & SSE_FLAG_ANTIHERMITIAN) != 0;
+    const FreqMap fm = make_freq_map(d.Nkz, L, half);
+    if (half && (p.flags & SSE_FLAG_CHECK)) {
+        for (int t = 0; t < 2; ++t) {
+            SSE_TIMED("check_antiherm_kernel", st,
+                      check_antiherm_kernel<<<grid_for((size_t)d.Nkz * d.NE * d.NA * nel, 256), 256, 0, st>>>(
+                          p.G[t], (size_t)d.Nkz * d.NE * d.NA, d.Norb, status));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            SSE_TIMED("check_antiherm_kernel", st,
+                      check_antiherm_kernel<<<grid_for((size_t)d.Nqz * d.Nw * d.NA * d.NB * 9, 256), 256, 0, st>>>(
+                          p.D[t], (size_t)d.Nqz * d.Nw * d.NA * d.NB, 3, status));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    const ProdCfg pc = make_prod_cfg(d, fm.count);
     if ((e = cudaFuncSetAttribute(spec_prod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
         cudaSuccess)
         return e;
@@ -1197,12 +1285,17 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
         SSE_TIMED("dft_k_kernel(K)", st,
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // 3. block products
-        const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
+        // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
+        const size_t gy = (fm.count + pc.fchunk - 1) / pc.fchunk;
         SSE_TIMED("spec_prod_kernel", st,
                   spec_prod_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
-                      pc, d, p.nbr, p.dH, Gh, Kh, Sh, L, p.scale, status));
+                      pc, d, fm, p.nbr, p.dH, Gh, Kh, Sh, p.scale, status));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (half) {
+            SSE_TIMED("mirror_sigma_kernel", st,
+                      mirror_sigma_kernel<<<grid_for(fm.count * nA * nel, 256), 256, 0, st>>>(fm, nA, d.Norb, Sh));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         // 4. inverse transforms into Sigma^t
         SSE_TIMED("dft_k_kernel(S)", st,
                   dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1));
@@ -1277,15 +1370,31 @@ cudaError_t spectral_pi(const sse_dims& d, const int32_t* nbr, const double2* dH
                                                                                  (size_t)L * gcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const PiCfg pc = make_pi_cfg(d, nfreq);
+    const bool half = (flags & SSE_FLAG_ANTIHERMITIAN) != 0;
+    const FreqMap fm = make_freq_map(d.Nkz, L, half);
+    if (half && (flags & SSE_FLAG_CHECK))
+        for (int t = 0; t < 2; ++t) {
+            SSE_TIMED("check_antiherm_kernel", st,
+                      check_antiherm_kernel<<<grid_for((size_t)d.Nkz * d.NE * d.NA * nel, 256), 256, 0, st>>>(
+                          G[t], (size_t)d.Nkz * d.NE * d.NA, d.Norb, status));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    const PiCfg pc = make_pi_cfg(d, fm.count);
     if ((e = cudaFuncSetAttribute(spec_pi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
         cudaSuccess)
         return e;
-    const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
+    const size_t gy = (fm.count + pc.fchunk - 1) / pc.fchunk;
     SSE_TIMED("spec_pi_kernel", st,
               spec_pi_kernel<<<dim3((unsigned)nA, (unsigned)gy, 2), pc.threads, pc.smem, st>>>(
-                  pc, d, nbr, dH, Gh[0], Gh[1], Ch[0], Ch[1], L, status));
+                  pc, d, fm, nbr, dH, Gh[0], Gh[1], Ch[0], Ch[1], status));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (half)
+        for (int t = 0; t < 2; ++t) {
+            SSE_TIMED("mirror_pi_kernel", st,
+                      mirror_pi_kernel<<<grid_for(fm.count * nA * (d.NB + 1) * 9, 256), 256, 0, st>>>(
+                          fm, nA * (d.NB + 1), Ch[t]));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     double2* P[2] = {P_less, P_greater};
     const double inv_scale = scale / ((double)d.Nkz * (double)L);
     for (int t = 0; t < 2; ++t) {

@@ -135,3 +135,22 @@ def test_finfet_workload_sampled():
     for P in (Pl, Pg):
         blk = P[:, ::5, ::97]
         assert float((blk + blk.conj().transpose(-1, -2)).abs().max()) <= 1e-12 * float(P.abs().max())
+
+
+@pytest.mark.parametrize("dims", [
+    TINY,
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nkz even, L = 72
+    Dims(NA=5, NB=1, Norb=4, NE=70, Nkz=1, Nqz=1, Nw=5),      # L = 81 (odd)
+], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nkz{d.Nkz}")
+def test_antihermitian_half_spectrum(dims):
+    """SSE_FLAG_ANTIHERMITIAN: half the frequencies plus the mirror C^(-f) = C^(f)^H."""
+    nbr = None if dims is TINY else ring_neighbours(dims.NA, dims.NB)
+    inp = make_inputs(dims, seed=dims.Norb + 700, nbr=nbr)
+    Pl, Pg = gpu_pi(inp, dims, antihermitian=True, check=True)
+    Ol, Og = oracle_pi(inp, dims)
+    assert normwise(Pl.cpu().numpy(), Ol) <= TOL
+    assert normwise(Pg.cpu().numpy(), Og) <= TOL
+    inp.G_less[0, 3, 2, 1, 1] += 1e-3  # a diagonal element with a real part breaks anti-Hermiticity
+    with pytest.raises(B.SseError) as e:
+        gpu_pi(inp, dims, antihermitian=True, check=True)
+    assert e.value.status == 5

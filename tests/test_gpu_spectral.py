@@ -151,3 +151,33 @@ def test_finfet_workload_sampled():
     for S in (Fl, Fg):
         blk = S[:, ::37, ::61]
         assert float((blk + blk.conj().transpose(-1, -2)).abs().max()) <= 1e-12 * float(S.abs().max())
+
+
+@pytest.mark.parametrize("dims", [
+    TINY,                                                     # L = 36, Nkz = 3
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nkz even, L = 72
+    Dims(NA=5, NB=2, Norb=4, NE=70, Nkz=1, Nqz=1, Nw=5),      # L = 81 (odd), one kz point
+    Dims(NA=6, NB=3, Norb=2, NE=100, Nkz=9, Nqz=4, Nw=25),    # L = 128
+], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nkz{d.Nkz}")
+def test_antihermitian_half_spectrum(dims):
+    """SSE_FLAG_ANTIHERMITIAN (inputs are exactly anti-Hermitian by construction): half the frequencies plus the
+    mirror S^(-f) = -S^(f)^H give Eq. (3) to the FP64 tolerance; CHECK passes."""
+    nbr = None if dims is TINY else ring_neighbours(dims.NA, dims.NB)
+    inp = make_inputs(dims, seed=dims.Norb + 600, nbr=nbr)
+    Sl, Sg = gpu_sigma(inp, antihermitian=True, check=True)
+    Ol, Og = oracle_sigma(inp)
+    assert normwise(Sl.cpu().numpy(), Ol) <= TOL
+    assert normwise(Sg.cpu().numpy(), Og) <= TOL
+
+
+def test_antihermitian_check_reports_violations():
+    inp = make_inputs(TINY, seed=7)
+    inp.G_greater[1, 5, 3, 0, 1] += 1e-3  # one element breaks G^> = -G^>^H
+    with pytest.raises(B.SseError) as e:
+        gpu_sigma(inp, antihermitian=True, check=True)
+    assert e.value.status == 5
+    inp = make_inputs(TINY, seed=7)
+    inp.D_less[0, 2, 4, 1, 0, 2] += 1e-3j  # one weight block breaks D^< = -D^<^H
+    with pytest.raises(B.SseError) as e:
+        gpu_sigma(inp, antihermitian=True, check=True)
+    assert e.value.status == 5
