@@ -3,9 +3,10 @@
 Mixed-precision (BF16X3) forward processed in energy windows of 256 outputs
 with a 2*64 halo and the transform-based FP64 forward (FFT length 1152),
 checked against the FP64 oracle on sampled blocks (grid edges, window
-boundaries, interior); the phonon self-energy Pi on a sampled atom; and the
+boundaries, interior); the phonon self-energy Pi on a sampled atom; the
 FP64 adjoint on a subset of atoms checked against central differences of the
-FP64 forward.
+FP64 forward; and the transform-based adjoint on a subset of atoms against
+the direct one.
 """
 import math
 
@@ -131,3 +132,17 @@ def test_large_fp64_adjoint_atom_subset(large):
         assert abs(fd - an) <= 1e-7 * gscale, (name, full_idx, part, fd, an)
     # atoms outside the range are untouched (zero-initialised by the binding)
     assert float(g_dH[a1:].abs().max()) == 0.0
+
+
+def test_large_fp64_fft_adjoint_atom_subset(large):
+    """Transform-based adjoint at the large sizes for atoms [100, 108) against the direct FP64 adjoint."""
+    inp = large
+    W, V = make_upstream(LARGE, seed=9, device="cuda")
+    args = (inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, W, V)
+    got = B.sigma_grad(*args, mode="fp64_fft", atoms=(100, 108), check=True)
+    ref = B.sigma_grad(*args, mode="fp64", atoms=(100, 108))
+    for x, y, sl in zip(got, ref, (np.s_[100:108], np.s_[:, :, 100:108], np.s_[:, :, 100:108])):
+        err = float((x[sl] - y[sl]).abs().max() / y[sl].abs().max())
+        assert err <= 1e-12, err
+    del W, V
+    torch.cuda.empty_cache()

@@ -2,8 +2,9 @@
 
 Each rank owns a contiguous atom range and only its own G blocks, fetches
 the halo blocks with paper_1912_10024_gb300.parallel.exchange_halo, and
-evaluates its shard with the CPU oracle. The gathered shards must equal the
-unsharded oracle result bit for bit (same arithmetic, same order).
+evaluates its shard of Sigma (Eq. 3) and of Pi (Eq. 4: the same atom halo)
+with the CPU oracle. The gathered shards must equal the unsharded oracle
+results bit for bit (same arithmetic, same order).
 """
 import os
 import socket
@@ -41,15 +42,19 @@ def _worker(rank, world, port, dims, seed, nbr, q):
         local = P.local_problem(inp.nbr, a0, a1, G_owned, halo, inp.dH[a0:a1],
                                 (inp.D_less[:, :, a0:a1], inp.D_greater[:, :, a0:a1]))
         Sl, Sg = oracle.sigma(*local, SCALE, a_range=(0, a1 - a0), nthreads=2)
-        shard = [torch.from_numpy(Sl[:, :, : a1 - a0]).contiguous(), torch.from_numpy(Sg[:, :, : a1 - a0]).contiguous()]
+        Pl, Pg = oracle.pi(local[0], local[1], local[4], local[5], SCALE, dims.Nqz, dims.Nw, a_range=(0, a1 - a0),
+                           nthreads=2)
+        shard = [torch.from_numpy(X[:, :, : a1 - a0]).contiguous() for X in (Sl, Sg, Pl, Pg)]
         gathered = [None] * world
         dist.all_gather_object(gathered, (a0, a1, shard))
         if rank == 0:
             full = oracle.sigma(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
                                 nthreads=2)
+            full = tuple(full) + tuple(oracle.pi(inp.nbr, inp.dH, inp.G_less, inp.G_greater, SCALE, dims.Nqz,
+                                                 dims.Nw, nthreads=2))
             ok = True
             for (b0, b1, sh) in gathered:
-                for t in range(2):
+                for t in range(4):
                     ok &= np.array_equal(sh[t].numpy(), full[t][:, :, b0:b1])
             q.put(ok)
     finally:
