@@ -360,7 +360,31 @@ __global__ void check_antiherm_kernel(const double2* __restrict__ X, size_t nblk
 // ---------------------------------------------------------------------------
 // per-frequency block products
 // ---------------------------------------------------------------------------
-constexpr int kProdMaxThreads = 384;
+constexpr int kProdMaxThreads = 512;
+
+// Frequencies per CTA for the product kernels: the F that keeps the most block-element lanes busy per SM
+// (whole warps issue on the FP64 pipe, so lanes past F*Norb^2 are lost), given the shared memory per CTA,
+// 64 warps per SM and about 64 registers per thread.
+template <class SmemOf>
+int pick_frequencies(int nel, SmemOf smem_of) {
+    int best = 1;
+    long best_useful = -1, best_smem = 0;
+    for (int F = 1; F * nel <= kProdMaxThreads; ++F) {
+        const int threads = ((F * nel + 31) / 32) * 32;
+        const long sm = smem_of(F);
+        if (sm > 227 * 1024) break;
+        long ctas = (228L * 1024) / (sm + 1024);
+        ctas = ctas < 2048 / threads ? ctas : 2048 / threads;
+        ctas = ctas < 65536 / (threads * 64) ? ctas : 65536 / (threads * 64);
+        const long useful = ctas * F * nel;
+        if (useful > best_useful || (useful == best_useful && sm < best_smem)) {
+            best = F;
+            best_useful = useful;
+            best_smem = sm;
+        }
+    }
+    return best;
+}
 
 struct ProdCfg {
     int nel, F, threads, fchunk;
@@ -370,11 +394,12 @@ struct ProdCfg {
 ProdCfg make_prod_cfg(const sse_dims& d, size_t nfreq) {
     ProdCfg c{};
     c.nel = d.Norb * d.Norb;
-    c.F = kProdMaxThreads / c.nel;
-    if (c.F < 1) c.F = 1;
-    c.threads = ((c.F * c.nel + 31) / 32) * 32;
     const int pl = c.nel * 24;  // one (re, im, re+im) plane triple
     auto a16 = [](int x) { return (x + 15) & ~15; };  // every region starts on a 16-byte boundary
+    c.F = pick_frequencies(c.nel, [&](int F) {
+        return (long)a16(a16(a16(a16(d.NB * 3 * pl) + F * pl) + F * 9 * 16) + F * 3 * pl) + F * 3 * pl;
+    });
+    c.threads = ((c.F * c.nel + 31) / 32) * 32;
     c.off_A = 0;                                   // [NB][3][planes]
     c.off_G = a16(c.off_A + d.NB * 3 * pl);        // [F][planes]
     c.off_K = a16(c.off_G + c.F * pl);             // [F][9] complex
@@ -530,11 +555,12 @@ struct PiCfg {
 PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
     PiCfg c{};
     c.nel = d.Norb * d.Norb;
-    c.F = kProdMaxThreads / c.nel;
-    if (c.F < 1) c.F = 1;
-    c.threads = ((c.F * c.nel + 31) / 32) * 32;
     const int pl = c.nel * 8;
     auto a16 = [](int x) { return (x + 15) & ~15; };
+    c.F = pick_frequencies(c.nel, [&](int F) {
+        return (long)d.NB * 3 * 4 * pl + F * 3 * pl * 2 + F * 6 * pl * 2 + F * 9 * d.Norb * 16 + F * 9 * 16 + 96;
+    });
+    c.threads = ((c.F * c.nel + 31) / 32) * 32;
     c.off_A = 0;                                     // [NB][3][4 planes: re, im, re+im, re-im]
     c.off_X = a16(c.off_A + d.NB * 3 * 4 * pl);      // [F][3 planes]
     c.off_Y = a16(c.off_X + c.F * 3 * pl);           // [F][3 planes]
