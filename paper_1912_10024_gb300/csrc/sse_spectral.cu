@@ -755,16 +755,32 @@ struct AdjCfg {
     int off_A, off_W, off_G, off_K, off_T, off_V, off_Q, off_D, smem;
 };
 
+constexpr int kAdjMaxThreads = 320;
+
 AdjCfg make_adj_cfg(const sse_dims& d, size_t nfreq) {
     AdjCfg c{};
     c.nel = d.Norb * d.Norb;
-    c.F = 256 / c.nel;
-    if (c.F < 1) c.F = 1;
-    c.threads = ((c.F * c.nel + 31) / 32) * 32;
     const int pl = c.nel * 8;
     auto a16 = [](int x) { return (x + 15) & ~15; };
-    c.off_A = 0;                                   // [NB][3][4 planes: re, im, re+im, re-im]
-    c.off_W = a16(c.off_A + d.NB * 3 * 4 * pl);    // [F][4 planes]
+    // per CTA: the current bond's dH planes, then per frequency 27 plane-sized buffers and the traces
+    auto smem_of = [&](int F) {
+        return (long)3 * 4 * pl + F * (8 * pl + 9 * 16 + 9 * pl * 2 + 6 * pl + 9 * d.Norb * 16) + 128;
+    };
+    c.F = 1;
+    long best = -1;
+    for (int F = 1; F * c.nel <= kAdjMaxThreads; ++F) {  // most busy lanes per SM (see pick_frequencies)
+        const int threads = ((F * c.nel + 31) / 32) * 32;
+        const long sm = smem_of(F);
+        if (sm > 227 * 1024) break;
+        long ctas = (228L * 1024) / (sm + 1024);
+        ctas = ctas < 2 ? ctas : 2;  // registers: up to ~100 per thread at 2 x 320 threads
+        const long useful = ctas * F * c.nel;
+        if (useful > best) best = useful, c.F = F;
+        (void)threads;
+    }
+    c.threads = ((c.F * c.nel + 31) / 32) * 32;
+    c.off_A = 0;                                   // [3][4 planes: re, im, re+im, re-im] of the current bond
+    c.off_W = a16(c.off_A + 3 * 4 * pl);           // [F][4 planes]
     c.off_G = a16(c.off_W + c.F * 4 * pl);         // [F][4 planes]
     c.off_K = a16(c.off_G + c.F * 4 * pl);         // [F][9] complex
     c.off_T = a16(c.off_K + c.F * 9 * 16);         // [F][3 j][3 planes]  W^ dH_j
@@ -790,7 +806,7 @@ __device__ __forceinline__ void put4(double* P, int nel, int e, double2 v) {
     P[3 * nel + e] = v.x - v.y;
 }
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(kAdjMaxThreads, 2)
 spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const double2* __restrict__ dH,
                 const double2* __restrict__ What, const double2* __restrict__ Ghat, const double2* __restrict__ Khat,
                 double2* __restrict__ Hhat, double2* __restrict__ gdh_part, int L, double scale,
@@ -817,17 +833,17 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
     const bool lane = fl < c.F;
     const int ndiag = c.F * 9 * Norb;
 
-    for (int i = tid; i < d.NB * 3 * nel; i += blockDim.x) {
-        const int si = i / nel, ee = i - si * nel;
-        put4(sA + (size_t)si * 4 * nel, nel, ee, dH[((size_t)a * d.NB) * 3 * nel + i]);
-    }
-    __syncthreads();
-
     for (int s = 0; s < d.NB; ++s) {
         const int b = nbr[(size_t)a * d.NB + s];
         const bool bok = b >= 0 && b < d.NA;
         if (!bok && tid == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
-        const double* A = sA + (size_t)s * 12 * nel;
+        // this bond's dH planes (the previous bond's last barrier has passed)
+        for (int i = tid; i < 3 * nel; i += blockDim.x) {
+            const int di = i / nel, ee = i - di * nel;
+            put4(sA + (size_t)di * 4 * nel, nel, ee, dH[((size_t)a * d.NB + s) * 3 * nel + i]);
+        }
+        __syncthreads();
+        const double* A = sA;
         double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
         for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
             const size_t f = f0 + fl;
