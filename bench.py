@@ -40,6 +40,8 @@ from paper_1912_10024_gb300.inputs import WORKLOADS, make_inputs, make_upstream 
 SCALE = 1.0 / (2.0 * math.pi)
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2070 MHz (derivation in the design doc).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP32 pipe: 152 SMs x 128 FP32 FMA/clock x 2 flop x 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 def n_valid(NE: int, Nw: int):
@@ -379,9 +381,11 @@ def main():
     if not args.no_compare and rank == 0:
         compare = {}
         ref = (Sl.clone(), Sg.clone())
-        bounds = {"fp64": 1e-12, "fp64_fft": 1e-12, "bf16x3": 2e-5, "tf32": 2e-3, "fp64_fft_antihermitian": 1e-12}
+        bounds = {"fp64": 1e-12, "fp64_fft": 1e-12, "bf16x3": 2e-5, "tf32": 2e-3, "fp64_fft_antihermitian": 1e-12,
+                  "fp32_fft": 2e-6, "fp32_fft_antihermitian": 2e-6}
         variants = [("fp64", 0), ("bf16x3", 0), ("tf32", 0), ("fp64_fft", 0),
-                    ("fp64_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN)]
+                    ("fp64_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN), ("fp32_fft", 0),
+                    ("fp32_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN)]
         for mname, mflags in variants:
             if mname == args.mode and mflags == run_flags:
                 continue
@@ -533,6 +537,12 @@ def main():
             roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sigma_fp64_fwd_kernel",
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
+        elif args.mode == "fp32_fft":
+            ks, n = kernel_s("spec_prod_kernel")
+            achieved = spectral_prod_flops(d, args.antihermitian) / ks / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "spec_prod_kernel",
+                    "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2070 MHz (FFMA probe: 73)"}
         elif args.mode == "fp64_fft":
             ks, n = kernel_s("spec_prod_kernel")
             achieved = spectral_prod_flops(d, args.antihermitian) / ks / 1e12
@@ -558,7 +568,8 @@ def main():
         out = {"metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": value, "unit": "TFLOP/s",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": {"fp64": "f64", "fp64_fft": "f64", "tf32": "tf32+f64", "bf16x3": "bf16x3+f64"}[args.mode],
+               "dtype": {"fp64": "f64", "fp64_fft": "f64", "fp32_fft": "f32", "tf32": "tf32+f64",
+                         "bf16x3": "bf16x3+f64"}[args.mode],
                "data": "synthetic (seeded; Si-FinFET-shaped)",
                "config": bench_config(args, d),
                "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,

@@ -78,8 +78,18 @@ typedef struct sse_dims {
  *            the result is transformed back. Same values as FP64 up to the
  *            rounding of the transforms (normwise ~1e-15), far fewer flops;
  *            workspace Nkz*L*(NA + 2*nA)*Norb^2*16 + Nkz*L*nA*NB*9*16 bytes
- *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~4800. */
-typedef enum sse_mode { SSE_MODE_FP64 = 0, SSE_MODE_TF32 = 1, SSE_MODE_BF16X3 = 2, SSE_MODE_FP64_FFT = 3 } sse_mode;
+ *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~4800.
+ *   FP32_FFT : the same transforms and per-frequency block products in FP32 on the
+ *            CUDA cores' FP32 pipe (about 60x the FP64 pipe on GB300), FP64 inputs
+ *            and outputs; forward only (the adjoint runs in FP64). Workspace half
+ *            of FP64_FFT's. Error (normwise) a few 1e-7; tested to 2e-6. */
+typedef enum sse_mode {
+    SSE_MODE_FP64 = 0,
+    SSE_MODE_TF32 = 1,
+    SSE_MODE_BF16X3 = 2,
+    SSE_MODE_FP64_FFT = 3,
+    SSE_MODE_FP32_FFT = 4
+} sse_mode;
 
 /* SYMMETRIZE: replace each output block S by (S - S^H)/2 in FP64 before the
  *             store (exact Sigma is anti-Hermitian when G and D are; this

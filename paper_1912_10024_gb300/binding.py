@@ -16,9 +16,10 @@ import torch
 
 from . import build as _build
 
-SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT = 0, 1, 2, 3
+SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT, SSE_MODE_FP32_FFT = 0, 1, 2, 3, 4
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE, SSE_FLAG_ANTIHERMITIAN = 1, 2, 4, 8
-MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT}
+MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT,
+         "fp32_fft": SSE_MODE_FP32_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
             "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes", "sse_sigma_bwd_g",
             "sse_profile_read", "sse_strerror")
@@ -336,7 +337,7 @@ class SigmaFunction(torch.autograd.Function):
         ctx.save_for_backward(dH, D_less, D_greater, G_less, G_greater, nbr)
         ctx.scale, ctx.symmetrize = scale, symmetrize
         # the adjoint runs in FP64: transform-based after a transform-based forward, direct otherwise
-        ctx.bwd_mode = "fp64_fft" if mode in ("fp64_fft", SSE_MODE_FP64_FFT) else "fp64"
+        ctx.bwd_mode = "fp64_fft" if mode in ("fp64_fft", SSE_MODE_FP64_FFT, "fp32_fft", SSE_MODE_FP32_FFT) else "fp64"
         return S
 
     @staticmethod

@@ -30,7 +30,8 @@ bool supported_dims(const sse_dims* d) {
 }
 
 bool valid_mode(int mode) {
-    return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3 || mode == SSE_MODE_FP64_FFT;
+    return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3 || mode == SSE_MODE_FP64_FFT ||
+           mode == SSE_MODE_FP32_FFT;
 }
 bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
 bool valid_flags(uint32_t f) {
@@ -40,6 +41,7 @@ bool valid_flags(uint32_t f) {
 size_t fwd_ws(const sse_dims& d, int mode) {
     if (mode == SSE_MODE_FP64) return sse::fp64_fwd_workspace(d);
     if (mode == SSE_MODE_FP64_FFT) return sse::spectral_fwd_workspace(d);
+    if (mode == SSE_MODE_FP32_FFT) return sse::spectral_fwd32_workspace(d);
     return sse::mixed_fwd_workspace(d, mode);
 }
 
@@ -126,6 +128,7 @@ extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double
     double2* Sg = reinterpret_cast<double2*>(S_greater);
     cudaError_t e = mode == SSE_MODE_FP64       ? sse::fp64_fwd(p, Sl, Sg, status, ws, wsb, st)
                     : mode == SSE_MODE_FP64_FFT ? sse::spectral_fwd(p, Sl, Sg, status, ws, wsb, st)
+                    : mode == SSE_MODE_FP32_FFT ? sse::spectral_fwd32(p, Sl, Sg, status, ws, wsb, st)
                                                 : sse::mixed_fwd(p, mode, Sl, Sg, status, ws, wsb, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);

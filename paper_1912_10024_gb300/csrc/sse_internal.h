@@ -70,6 +70,10 @@ bool spectral_supported(const sse_dims& d);
 size_t spectral_fwd_workspace(const sse_dims& d);
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                          size_t ws_bytes, cudaStream_t st);
+// FP32 transforms and block products (mode FP32_FFT), FP64 inputs and outputs.
+size_t spectral_fwd32_workspace(const sse_dims& d);
+cudaError_t spectral_fwd32(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                           size_t ws_bytes, cudaStream_t st);
 
 // Transform-based FP64 adjoint of Eq. (3) (sse_spectral.cu).
 size_t spectral_bwd_workspace(const sse_dims& d);

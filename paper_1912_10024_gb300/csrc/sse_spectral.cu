@@ -45,7 +45,7 @@ struct FftPlan {
     int smem;  // two L x C buffers + the twiddle table
 };
 
-FftPlan make_plan(int L) {
+FftPlan make_plan(int L, int esz = 16) {
     FftPlan p{};
     p.L = L;
     int m = L;
@@ -53,8 +53,8 @@ FftPlan make_plan(int L) {
     while (m % 2 == 0) p.radix[p.nst++] = 2, m /= 2;
     while (m % 3 == 0) p.radix[p.nst++] = 3, m /= 3;
     p.C = 16;
-    while (p.C > 1 && (2 * (size_t)L * p.C + L) * 16 > (size_t)kFftSmemBudget) p.C /= 2;
-    p.smem = (int)((2 * (size_t)L * p.C + L) * 16);
+    while (p.C > 1 && (2 * (size_t)L * p.C + L) * esz > (size_t)kFftSmemBudget) p.C /= 2;
+    p.smem = (int)((2 * (size_t)L * p.C + L) * esz);
     return p;
 }
 
@@ -65,6 +65,36 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// complex element type of the transforms: double2 (FP64 modes) or float2 (FP32_FFT)
+template <class C>
+struct CT;
+template <>
+struct CT<double2> {
+    using R = double;
+    static __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+};
+template <>
+struct CT<float2> {
+    using R = float;
+    static __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+};
+template <class T>
+struct CX;
+template <>
+struct CX<double> {
+    using C = double2;
+};
+template <>
+struct CX<float> {
+    using C = float2;
+};
 
 // tw[m] = exp(-2 pi i m / L)
 __global__ void twiddle_kernel(int L, double2* __restrict__ tw) {
@@ -76,24 +106,25 @@ __global__ void twiddle_kernel(int L, double2* __restrict__ tw) {
 }
 
 // In-place forward DFT of R values (R in {2, 3, 4}); tw is the length-L table.
-__device__ __forceinline__ void dft_small(int R, double2* v, const double2* tw, int L) {
+template <class C>
+__device__ __forceinline__ void dft_small(int R, C* v, const C* tw, int L) {
     if (R == 2) {
-        const double2 a = v[0], b = v[1];
+        const C a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     } else if (R == 4) {
-        const double2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-        const double2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
-        const double2 md13 = make_double2(d13.y, -d13.x);  // -i * d13
+        const C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+        const C md13 = CT<C>::mk(d13.y, -d13.x);  // -i * d13
         v[0] = cadd(s02, s13);
         v[2] = csub(s02, s13);
         v[1] = cadd(d02, md13);
         v[3] = csub(d02, md13);
     } else if (R == 3) {
-        const double2 w1 = tw[L / 3];  // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
-        const double2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-        const double2 m = make_double2(v[0].x + w1.x * t.x, v[0].y + w1.x * t.y);
-        const double2 r = make_double2(-w1.y * d.y, w1.y * d.x);  // i * Im(w1) * d
+        const C w1 = tw[L / 3];  // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
+        const C t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        const C m = CT<C>::mk(v[0].x + w1.x * t.x, v[0].y + w1.x * t.y);
+        const C r = CT<C>::mk(-w1.y * d.y, w1.y * d.x);  // i * Im(w1) * d
         v[0] = cadd(v[0], t);
         v[1] = cadd(m, r);
         v[2] = csub(m, r);
@@ -101,7 +132,8 @@ __device__ __forceinline__ void dft_small(int R, double2* v, const double2* tw, 
 }
 
 // Stockham autosort FFT of C columns stored [L][C] in `src`; returns the buffer holding the result.
-__device__ double2* fft_columns(const FftPlan& p, double2* src, double2* dst, const double2* tw) {
+template <class C>
+__device__ C* fft_columns(const FftPlan& p, C* src, C* dst, const C* tw) {
     int Ns = 1;
     for (int st = 0; st < p.nst; ++st) {
         const int R = p.radix[st];
@@ -110,7 +142,7 @@ __device__ double2* fft_columns(const FftPlan& p, double2* src, double2* dst, co
         for (int it = threadIdx.x; it < nb * p.C; it += blockDim.x) {
             const int j = it / p.C, c = it - j * p.C;
             const int k = j % Ns;
-            double2 v[4];
+            C v[4];
             for (int r = 0; r < R; ++r) {
                 v[r] = src[(size_t)(j + r * nb) * p.C + c];
                 if (r > 0 && k > 0) v[r] = cmul(v[r], tw[r * k * span]);
@@ -120,7 +152,7 @@ __device__ double2* fft_columns(const FftPlan& p, double2* src, double2* dst, co
             for (int r = 0; r < R; ++r) dst[(size_t)(d0 + r * Ns) * p.C + c] = v[r];
         }
         __syncthreads();
-        double2* t = src;
+        C* t = src;
         src = dst;
         dst = t;
         Ns *= R;
@@ -134,73 +166,88 @@ __device__ double2* fft_columns(const FftPlan& p, double2* src, double2* dst, co
 // ---------------------------------------------------------------------------
 
 // G^t[k][E][col] (col over NA*Norb^2), rows E >= NE are zero  ->  out[k][eps][col]
-struct LoadG {
+template <class CC>
+struct LoadGT {
+    using C = CC;
     const double2* G;
     int NE;
     size_t ncols;
-    __device__ double2 operator()(int k, int r, size_t col) const {
-        return r < NE ? G[((size_t)k * NE + r) * ncols + col] : make_double2(0.0, 0.0);
+    __device__ C operator()(int k, int r, size_t col) const {
+        if (r >= NE) return CT<C>::mk(0, 0);
+        const double2 v = G[((size_t)k * NE + r) * ncols + col];
+        return CT<C>::mk(v.x, v.y);
     }
 };
+using LoadG = LoadGT<double2>;
 // lag kernel of one qz slice: row w+1 <- D^t(q,w), row L-(w+1) <- D^t'(q,w), else zero.
 // col over (a - a_begin, s, ij); D rows have NA*NB*9 entries, the range starts at a_begin*NB*9.
-struct LoadLag {
+template <class CC>
+struct LoadLagT {
+    using C = CC;
     const double2* Dt;
     const double2* Dtb;
     int Nw, L;
     size_t rowlen, col0;
-    __device__ double2 operator()(int q, int r, size_t col) const {
-        if (r >= 1 && r <= Nw) return Dt[((size_t)q * Nw + (r - 1)) * rowlen + col0 + col];
-        if (r >= L - Nw) return Dtb[((size_t)q * Nw + (L - 1 - r)) * rowlen + col0 + col];
-        return make_double2(0.0, 0.0);
+    __device__ C operator()(int q, int r, size_t col) const {
+        double2 v = make_double2(0.0, 0.0);
+        if (r >= 1 && r <= Nw) v = Dt[((size_t)q * Nw + (r - 1)) * rowlen + col0 + col];
+        else if (r >= L - Nw) v = Dtb[((size_t)q * Nw + (L - 1 - r)) * rowlen + col0 + col];
+        return CT<C>::mk(v.x, v.y);
     }
 };
+using LoadLag = LoadLagT<double2>;
 // spectrum [k][eps][col], conjugated (inverse transform = conj(FFT(conj(x))))
-struct LoadSpecConj {
-    const double2* X;
+template <class CC>
+struct LoadSpecConjT {
+    using C = CC;
+    const C* X;
     int L;
     size_t ncols;
-    __device__ double2 operator()(int k, int r, size_t col) const {
-        return cconj(X[((size_t)k * L + r) * ncols + col]);
-    }
+    __device__ C operator()(int k, int r, size_t col) const { return cconj(X[((size_t)k * L + r) * ncols + col]); }
 };
+using LoadSpecConj = LoadSpecConjT<double2>;
 
-struct StoreSpec {  // out[batch][r][col]
-    double2* X;
+template <class C>
+struct StoreSpecT {  // out[batch][r][col]
+    C* X;
     int L;
     size_t ncols;
     int rows;
-    __device__ void operator()(int b, int r, size_t col, double2 v) const { X[((size_t)b * L + r) * ncols + col] = v; }
+    __device__ void operator()(int b, int r, size_t col, C v) const { X[((size_t)b * L + r) * ncols + col] = v; }
 };
-struct StoreSigma {  // S[k][E][a_begin*nel + col] = conj(v) * inv, E < NE
+using StoreSpec = StoreSpecT<double2>;
+template <class C>
+struct StoreSigmaT {  // S[k][E][a_begin*nel + col] = conj(v) * inv in FP64, E < NE
     double2* S;
     int NE;
     size_t rowlen, col0;
     double inv;
     int rows;
-    __device__ void operator()(int k, int r, size_t col, double2 v) const {
-        S[((size_t)k * NE + r) * rowlen + col0 + col] = make_double2(v.x * inv, -v.y * inv);
+    __device__ void operator()(int k, int r, size_t col, C v) const {
+        S[((size_t)k * NE + r) * rowlen + col0 + col] = make_double2((double)v.x * inv, -(double)v.y * inv);
     }
 };
+using StoreSigma = StoreSigmaT<double2>;
 
 template <class Load, class Store>
 __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const double2* __restrict__ tw_g, Load ld,
                                                             Store sv, size_t ncols) {
+    using C = typename Load::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* b0 = reinterpret_cast<double2*>(smem_raw);
-    double2* b1 = b0 + (size_t)p.L * p.C;
-    double2* tw = b1 + (size_t)p.L * p.C;
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + (size_t)p.L * p.C;
+    C* tw = b1 + (size_t)p.L * p.C;
     const size_t col0 = (size_t)blockIdx.x * p.C;
     const int batch = blockIdx.y;
-    for (int m = threadIdx.x; m < p.L; m += blockDim.x) tw[m] = tw_g[m];
+    for (int m = threadIdx.x; m < p.L; m += blockDim.x) tw[m] = CT<C>::mk(tw_g[m].x, tw_g[m].y);
     const int n = p.L * p.C;
     for (int base = threadIdx.x; base < n; base += kFftLoadBatch * blockDim.x) {
-        double2 v[kFftLoadBatch];
+        C v[kFftLoadBatch];
 #pragma unroll
         for (int u = 0; u < kFftLoadBatch; ++u) {
             const int it = base + u * blockDim.x;
             const int r = it / p.C, c = it - r * p.C;
-            v[u] = (it < n && col0 + c < ncols) ? ld(batch, r, col0 + c) : make_double2(0.0, 0.0);
+            v[u] = (it < n && col0 + c < ncols) ? ld(batch, r, col0 + c) : CT<C>::mk(0, 0);
         }
 #pragma unroll
         for (int u = 0; u < kFftLoadBatch; ++u) {
@@ -209,7 +256,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const dou
         }
     }
     __syncthreads();
-    const double2* res = fft_columns(p, b0, b1, tw);
+    const C* res = fft_columns<C>(p, b0, b1, tw);
     for (int it = threadIdx.x; it < sv.rows * p.C; it += blockDim.x) {
         const int r = it / p.C, c = it - r * p.C;
         if (col0 + c < ncols) sv(batch, r, col0 + c, res[it]);
@@ -222,57 +269,59 @@ __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const dou
 // Nk-kappa: out[kappa] = C -+ i S, out[Nk-kappa] = C +- i S with C = x_0 (+ (-1)^kappa x_{Nk/2}) +
 // sum_k p_k cos(2 pi k kappa / Nk), S = sum_k m_k sin(2 pi k kappa / Nk).
 // ---------------------------------------------------------------------------
-__global__ void dft_k_kernel(double2* __restrict__ X, int Nk, int n_in, size_t M, int inverse) {
-    __shared__ double cs[kMaxNk], sn[kMaxNk];
+template <class C>
+__global__ void dft_k_kernel(C* __restrict__ X, int Nk, int n_in, size_t M, int inverse) {
+    using R = typename CT<C>::R;
+    __shared__ R cs[kMaxNk], sn[kMaxNk];
     if (threadIdx.x < Nk) {
         double s, c;
         sincospi(2.0 * (double)threadIdx.x / (double)Nk, &s, &c);
-        cs[threadIdx.x] = c;
-        sn[threadIdx.x] = s;
+        cs[threadIdx.x] = (R)c;
+        sn[threadIdx.x] = (R)s;
     }
     __syncthreads();
     const int half = (Nk - 1) / 2;  // number of (k, Nk-k) pairs
     const bool even = (Nk % 2) == 0;
-    const double sgn = inverse ? 1.0 : -1.0;  // out = C + sgn * i * S for kappa <= half
+    const R sgn = inverse ? (R)1 : (R)-1;  // out = C + sgn * i * S for kappa <= half
     for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
-        double2 x[kMaxNk];
-        for (int k = 0; k < Nk; ++k) x[k] = k < n_in ? X[(size_t)k * M + m] : make_double2(0.0, 0.0);
-        double2 p[kMaxNk / 2 + 1], q[kMaxNk / 2 + 1];
-        double2 c0 = x[0];
+        C x[kMaxNk];
+        for (int k = 0; k < Nk; ++k) x[k] = k < n_in ? X[(size_t)k * M + m] : CT<C>::mk(0, 0);
+        C p[kMaxNk / 2 + 1], q[kMaxNk / 2 + 1];
+        C c0 = x[0];
         for (int k = 1; k <= half; ++k) {
             p[k] = cadd(x[k], x[Nk - k]);
             q[k] = csub(x[k], x[Nk - k]);
             c0 = cadd(c0, p[k]);
         }
-        const double2 xh = even ? x[Nk / 2] : make_double2(0.0, 0.0);
+        const C xh = even ? x[Nk / 2] : CT<C>::mk(0, 0);
         X[m] = cadd(c0, xh);  // kappa = 0
         for (int kap = 1; kap <= half; ++kap) {
-            double2 C = x[0], S = make_double2(0.0, 0.0);
+            C Cs = x[0], S = CT<C>::mk(0, 0);
             for (int k = 1; k <= half; ++k) {
                 const int r = (k * kap) % Nk;
-                C.x = fma(p[k].x, cs[r], C.x);
-                C.y = fma(p[k].y, cs[r], C.y);
+                Cs.x = fma(p[k].x, cs[r], Cs.x);
+                Cs.y = fma(p[k].y, cs[r], Cs.y);
                 S.x = fma(q[k].x, sn[r], S.x);
                 S.y = fma(q[k].y, sn[r], S.y);
             }
             if (even) {
-                const double e = (kap & 1) ? -1.0 : 1.0;
-                C.x = fma(e, xh.x, C.x);
-                C.y = fma(e, xh.y, C.y);
+                const R e = (kap & 1) ? (R)-1 : (R)1;
+                Cs.x = fma(e, xh.x, Cs.x);
+                Cs.y = fma(e, xh.y, Cs.y);
             }
             // i*S = (-S.y, S.x)
-            X[(size_t)kap * M + m] = make_double2(C.x - sgn * S.y, C.y + sgn * S.x);
-            X[(size_t)(Nk - kap) * M + m] = make_double2(C.x + sgn * S.y, C.y - sgn * S.x);
+            X[(size_t)kap * M + m] = CT<C>::mk(Cs.x - sgn * S.y, Cs.y + sgn * S.x);
+            X[(size_t)(Nk - kap) * M + m] = CT<C>::mk(Cs.x + sgn * S.y, Cs.y - sgn * S.x);
         }
         if (even && Nk > 1) {  // kappa = Nk/2: cos(pi k) = (-1)^k, sin = 0
-            double2 C = x[0];
+            C Cs = x[0];
             for (int k = 1; k <= half; ++k) {
-                const double e = (k & 1) ? -1.0 : 1.0;
-                C.x = fma(e, p[k].x, C.x);
-                C.y = fma(e, p[k].y, C.y);
+                const R e = (k & 1) ? (R)-1 : (R)1;
+                Cs.x = fma(e, p[k].x, Cs.x);
+                Cs.y = fma(e, p[k].y, Cs.y);
             }
-            const double e = ((Nk / 2) & 1) ? -1.0 : 1.0;
-            X[(size_t)(Nk / 2) * M + m] = make_double2(fma(e, xh.x, C.x), fma(e, xh.y, C.y));
+            const R e = ((Nk / 2) & 1) ? (R)-1 : (R)1;
+            X[(size_t)(Nk / 2) * M + m] = CT<C>::mk(fma(e, xh.x, Cs.x), fma(e, xh.y, Cs.y));
         }
     }
 }
@@ -314,7 +363,8 @@ __device__ __forceinline__ size_t freq_neg(const FreqMap& m, size_t f) {
 }
 
 // Sigma^(-f) = -Sigma^(f)^H per atom block, for the computed half
-__global__ void mirror_sigma_kernel(FreqMap fm, size_t nA, int Norb, double2* __restrict__ Sh) {
+template <class C>
+__global__ void mirror_sigma_kernel(FreqMap fm, size_t nA, int Norb, C* __restrict__ Sh) {
     const int nel = Norb * Norb;
     const size_t total = fm.count * nA * nel;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -324,8 +374,8 @@ __global__ void mirror_sigma_kernel(FreqMap fm, size_t nA, int Norb, double2* __
         const size_t f = freq_of(fm, ix), fn = freq_neg(fm, f);
         if (fn == f) continue;
         const int m = e / Norb, n = e - m * Norb;
-        const double2 v = Sh[(f * nA + la) * nel + e];
-        Sh[(fn * nA + la) * nel + n * Norb + m] = make_double2(-v.x, v.y);
+        const C v = Sh[(f * nA + la) * nel + e];
+        Sh[(fn * nA + la) * nel + n * Norb + m] = CT<C>::mk(-v.x, v.y);
     }
 }
 
@@ -391,19 +441,19 @@ struct ProdCfg {
     int off_A, off_G, off_K, off_W, off_U, smem;
 };
 
-ProdCfg make_prod_cfg(const sse_dims& d, size_t nfreq) {
+ProdCfg make_prod_cfg(const sse_dims& d, size_t nfreq, int tsz = 8) {
     ProdCfg c{};
     c.nel = d.Norb * d.Norb;
-    const int pl = c.nel * 24;  // one (re, im, re+im) plane triple
+    const int pl = c.nel * 3 * tsz;  // one (re, im, re+im) plane triple
     auto a16 = [](int x) { return (x + 15) & ~15; };  // every region starts on a 16-byte boundary
     c.F = pick_frequencies(c.nel, [&](int F) {
-        return (long)a16(a16(a16(a16(d.NB * 3 * pl) + F * pl) + F * 9 * 16) + F * 3 * pl) + F * 3 * pl;
+        return (long)a16(a16(a16(a16(d.NB * 3 * pl) + F * pl) + F * 9 * 2 * tsz) + F * 3 * pl) + F * 3 * pl;
     });
     c.threads = ((c.F * c.nel + 31) / 32) * 32;
     c.off_A = 0;                                   // [NB][3][planes]
     c.off_G = a16(c.off_A + d.NB * 3 * pl);        // [F][planes]
     c.off_K = a16(c.off_G + c.F * pl);             // [F][9] complex
-    c.off_W = a16(c.off_K + c.F * 9 * 16);         // [F][3][planes]
+    c.off_W = a16(c.off_K + c.F * 9 * 2 * tsz);    // [F][3][planes]
     c.off_U = a16(c.off_W + c.F * 3 * pl);         // [F][3][planes]
     c.smem = a16(c.off_U + c.F * 3 * pl);
     // frequencies per CTA: enough CTAs for ~8 waves of 2 CTAs per SM over all atoms
@@ -418,16 +468,19 @@ ProdCfg make_prod_cfg(const sse_dims& d, size_t nfreq) {
 }
 
 // Planes of a complex block: re, im, re+im (Gauss 3-multiply MACs).
-__device__ __forceinline__ void put3(double* P, int nel, int e, double2 v) {
+template <class T, class C>
+__device__ __forceinline__ void put3(T* P, int nel, int e, C v) {
     P[e] = v.x;
     P[nel + e] = v.y;
     P[2 * nel + e] = v.x + v.y;
 }
 
+template <class T>
 __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ nbr,
-                                 const double2* __restrict__ dH, const double2* __restrict__ Ghat,
-                                 const double2* __restrict__ Khat, double2* __restrict__ Shat, double scale,
-                                 unsigned* __restrict__ status) {
+                                 const double2* __restrict__ dH, const typename CX<T>::C* __restrict__ Ghat,
+                                 const typename CX<T>::C* __restrict__ Khat, typename CX<T>::C* __restrict__ Shat,
+                                 double scale, unsigned* __restrict__ status) {
+    using C = typename CX<T>::C;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Norb = d.Norb, nel = c.nel;
     const int la = blockIdx.x;
@@ -435,11 +488,11 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     const size_t i_begin = (size_t)blockIdx.y * c.fchunk;  // frequency indices of the map
     const size_t i_end = min(fm.count, i_begin + c.fchunk);
-    double* sA = reinterpret_cast<double*>(smem + c.off_A);
-    double* sG = reinterpret_cast<double*>(smem + c.off_G);
-    double2* sK = reinterpret_cast<double2*>(smem + c.off_K);
-    double* sW = reinterpret_cast<double*>(smem + c.off_W);
-    double* sU = reinterpret_cast<double*>(smem + c.off_U);
+    T* sA = reinterpret_cast<T*>(smem + c.off_A);
+    T* sG = reinterpret_cast<T*>(smem + c.off_G);
+    C* sK = reinterpret_cast<C*>(smem + c.off_K);
+    T* sW = reinterpret_cast<T*>(smem + c.off_W);
+    T* sU = reinterpret_cast<T*>(smem + c.off_U);
     const int tid = threadIdx.x;
     const int fl = tid / nel, e = tid - fl * nel;
     const int m = e / Norb, n = e - m * Norb;
@@ -447,7 +500,8 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_
 
     for (int i = tid; i < d.NB * 3 * nel; i += blockDim.x) {
         const int si = i / nel, ee = i - si * nel;
-        put3(sA + (size_t)si * 3 * nel, nel, ee, dH[((size_t)a * d.NB) * 3 * nel + i]);
+        const double2 v = dH[((size_t)a * d.NB) * 3 * nel + i];
+        put3(sA + (size_t)si * 3 * nel, nel, ee, CT<C>::mk((T)v.x, (T)v.y));
     }
     int bnb[16];
     for (int s = 0; s < d.NB && s < 16; ++s) {
@@ -460,27 +514,27 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_
     for (size_t i0 = i_begin; i0 < i_end; i0 += c.F) {
         const bool act = lane && i0 + fl < i_end;
         const size_t f = act ? freq_of(fm, i0 + fl) : 0;
-        double T1 = 0.0, T2 = 0.0, T3 = 0.0;
+        T T1 = 0, T2 = 0, T3 = 0;
         for (int s = 0; s < d.NB; ++s) {
             const int b = s < 16 ? bnb[s] : -1;
             // stage G^_b(f) and K^_(a,s)(f)
             if (lane) {
-                double2 g = make_double2(0.0, 0.0);
+                C g = CT<C>::mk(0, 0);
                 if (act && b >= 0) g = Ghat[(f * d.NA + b) * nel + e];
                 put3(sG + (size_t)fl * 3 * nel, nel, e, g);
             }
             for (int i = tid; i < c.F * 9; i += blockDim.x) {
                 const int fk = i / 9, ij = i - fk * 9;
-                double2 k = make_double2(0.0, 0.0);
+                C k = CT<C>::mk(0, 0);
                 if (i0 + fk < i_end && b >= 0) k = Khat[((freq_of(fm, i0 + fk) * nA + la) * d.NB + s) * 9 + ij];
                 sK[i] = k;
             }
             __syncthreads();
             // W_i[m][n] = sum_j K_ij conj(dH_j[n][m])
             if (lane) {
-                const double* A = sA + (size_t)s * 9 * nel;
+                const T* A = sA + (size_t)s * 9 * nel;
                 const int et = n * Norb + m;
-                double ar[3], ai[3];  // conj(dH_j[n][m]) = (ar, -ai)
+                T ar[3], ai[3];  // conj(dH_j[n][m]) = (ar, -ai)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     ar[j] = A[(size_t)j * 3 * nel + et];
@@ -488,10 +542,10 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_
                 }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    double2 acc = make_double2(0.0, 0.0);  // plain FMA chains: no separate multiplies or adds
+                    C acc = CT<C>::mk(0, 0);  // plain FMA chains: no separate multiplies or adds
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        const double2 k = sK[fl * 9 + i * 3 + j];
+                        const C k = sK[fl * 9 + i * 3 + j];
                         acc.x = fma(k.x, ar[j], acc.x);
                         acc.x = fma(k.y, ai[j], acc.x);
                         acc.y = fma(k.y, ar[j], acc.y);
@@ -503,28 +557,28 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_
             __syncthreads();
             // U_i = G^ W_i
             if (lane) {
-                const double* Gp = sG + (size_t)fl * 3 * nel;
+                const T* Gp = sG + (size_t)fl * 3 * nel;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    const double* Wp = sW + ((size_t)fl * 3 + i) * 3 * nel;
-                    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+                    const T* Wp = sW + ((size_t)fl * 3 + i) * 3 * nel;
+                    T t1 = 0, t2 = 0, t3 = 0;
                     for (int l = 0; l < Norb; ++l) {
                         const int ga = m * Norb + l, wb = l * Norb + n;
                         t1 = fma(Gp[ga], Wp[wb], t1);
                         t2 = fma(Gp[nel + ga], Wp[nel + wb], t2);
                         t3 = fma(Gp[2 * nel + ga], Wp[2 * nel + wb], t3);
                     }
-                    put3(sU + ((size_t)fl * 3 + i) * 3 * nel, nel, e, make_double2(t1 - t2, t3 - t1 - t2));
+                    put3(sU + ((size_t)fl * 3 + i) * 3 * nel, nel, e, CT<C>::mk(t1 - t2, t3 - t1 - t2));
                 }
             }
             __syncthreads();
             // acc += sum_i dH_i U_i
             if (lane) {
-                const double* A = sA + (size_t)s * 9 * nel;
+                const T* A = sA + (size_t)s * 9 * nel;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    const double* Ap = A + (size_t)i * 3 * nel;
-                    const double* Up = sU + ((size_t)fl * 3 + i) * 3 * nel;
+                    const T* Ap = A + (size_t)i * 3 * nel;
+                    const T* Up = sU + ((size_t)fl * 3 + i) * 3 * nel;
                     for (int l = 0; l < Norb; ++l) {
                         const int aa = m * Norb + l, ub = l * Norb + n;
                         T1 = fma(Ap[aa], Up[ub], T1);
@@ -535,8 +589,8 @@ __global__ void spec_prod_kernel(ProdCfg c, sse_dims d, FreqMap fm, const int32_
             }
         }
         if (act) {
-            const double re = T1 - T2, im = T3 - T1 - T2;
-            Shat[(f * nA + la) * nel + e] = make_double2(-scale * im, scale * re);  // i*scale*(re + i im)
+            const T re = T1 - T2, im = T3 - T1 - T2;
+            Shat[(f * nA + la) * nel + e] = CT<C>::mk((T)(-scale * (double)im), (T)(scale * (double)re));  // i*scale*(re+i im)
         }
     }
 }
@@ -992,6 +1046,7 @@ __global__ void spec_gdh_reduce_kernel(sse_dims d, int nchunks, const double2* _
 
 // upstream gradient gS^t[k][E][a][mn] of atoms in range, optionally projected to (W - W^H)/2
 struct LoadW {
+    using C = double2;
     const double2* W;
     int NE, Norb;
     size_t rowlen, col0;
@@ -1222,16 +1277,16 @@ struct SpecLayout {
     size_t off_tw, off_G, off_K, off_S, total;
 };
 
-SpecLayout spec_layout(const sse_dims& d) {
+SpecLayout spec_layout(const sse_dims& d, size_t csz = 16) {  // csz: bytes per complex spectrum entry
     SpecLayout l{};
     l.L = spectral_length(d);
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t spec = (size_t)d.Nkz * l.L;
     l.off_tw = 0;
     l.off_G = align256(l.off_tw + (size_t)l.L * 16);
-    l.off_K = align256(l.off_G + spec * d.NA * nel * 16);
-    l.off_S = align256(l.off_K + spec * nA * d.NB * 9 * 16);
-    l.total = align256(l.off_S + spec * nA * nel * 16);
+    l.off_K = align256(l.off_G + spec * d.NA * nel * csz);
+    l.off_S = align256(l.off_K + spec * nA * d.NB * 9 * csz);
+    l.total = align256(l.off_S + spec * nA * nel * csz);
     return l;
 }
 
@@ -1272,20 +1327,26 @@ bool spectral_supported(const sse_dims& d) {
 }
 
 size_t spectral_fwd_workspace(const sse_dims& d) { return spec_layout(d).total; }
+size_t spectral_fwd32_workspace(const sse_dims& d) { return spec_layout(d, 8).total; }
 
-cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
-                         size_t ws_bytes, cudaStream_t st) {
+namespace {
+// The forward in the real type T: double (FP64_FFT) or float (FP32_FFT: FP32 transforms and block
+// products on the FP32 pipe, FP64 inputs and outputs).
+template <class T>
+cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                           size_t ws_bytes, cudaStream_t st) {
+    using C = typename CX<T>::C;
     const sse_dims& d = p.d;
     if (!spectral_supported(d)) return cudaErrorNotSupported;
-    const SpecLayout lay = spec_layout(d);
+    const SpecLayout lay = spec_layout(d, sizeof(C));
     if (ws_bytes < lay.total) return cudaErrorInvalidValue;
     unsigned char* base = static_cast<unsigned char*>(ws);
     double2* tw = reinterpret_cast<double2*>(base + lay.off_tw);
-    double2* Gh = reinterpret_cast<double2*>(base + lay.off_G);
-    double2* Kh = reinterpret_cast<double2*>(base + lay.off_K);
-    double2* Sh = reinterpret_cast<double2*>(base + lay.off_S);
+    C* Gh = reinterpret_cast<C*>(base + lay.off_G);
+    C* Kh = reinterpret_cast<C*>(base + lay.off_K);
+    C* Sh = reinterpret_cast<C*>(base + lay.off_S);
     const int L = lay.L;
-    const FftPlan plan = make_plan(L);
+    const FftPlan plan = make_plan(L, (int)sizeof(C));
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t gcols = (size_t)d.NA * nel, kcols = nA * d.NB * 9, scols = nA * nel;
     const size_t nfreq = (size_t)d.Nkz * L;
@@ -1308,21 +1369,22 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
-    const ProdCfg pc = make_prod_cfg(d, fm.count);
-    if ((e = cudaFuncSetAttribute(spec_prod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
+    const ProdCfg pc = make_prod_cfg(d, fm.count, (int)sizeof(T));
+    if ((e = cudaFuncSetAttribute(spec_prod_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
         cudaSuccess)
         return e;
     double2* S[2] = {S_less, S_greater};
     for (int t = 0; t < 2; ++t) {
         // 1. G^t -> G^
-        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadG{p.G[t], d.NE, gcols}, StoreSpec{Gh, L, gcols, L}, gcols, d.Nkz, st);
+        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
+                       gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(G)", st,
                   dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 2. lag kernel -> K^
-        LoadLag ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpec{Kh, L, kcols, L}, kcols, d.Nqz, st);
+        LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
+        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(K)", st,
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
@@ -1330,7 +1392,7 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
         // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
         const size_t gy = (fm.count + pc.fchunk - 1) / pc.fchunk;
         SSE_TIMED("spec_prod_kernel", st,
-                  spec_prod_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
+                  spec_prod_kernel<T><<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
                       pc, d, fm, p.nbr, p.dH, Gh, Kh, Sh, p.scale, status));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (half) {
@@ -1343,9 +1405,9 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
                   dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
-        e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConj{Sh, L, scols},
-                       StoreSigma{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols, d.Nkz,
-                       st);
+        e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh, L, scols},
+                       StoreSigmaT<C>{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols,
+                       d.Nkz, st);
         if (e != cudaSuccess) return e;
         if (p.flags & SSE_FLAG_SYMMETRIZE) {
             SSE_TIMED("symmetrize_kernel", st,
@@ -1354,6 +1416,17 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
         }
     }
     return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                         size_t ws_bytes, cudaStream_t st) {
+    return spectral_fwd_t<double>(p, S_less, S_greater, status, ws, ws_bytes, st);
+}
+
+cudaError_t spectral_fwd32(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                           size_t ws_bytes, cudaStream_t st) {
+    return spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st);
 }
 
 struct PiLayout {

@@ -72,7 +72,7 @@ def call_fwd(d, **over):
 
 @pytest.mark.parametrize("over,status", [
     (dict(G_less=0), 1), (dict(S_greater=0), 1), (dict(dH=FAKE + 8), 1), (dict(nbr=FAKE + 2), 1),
-    (dict(scale=float("nan")), 1), (dict(mode=4), 1), (dict(flags=1 << 5), 1),
+    (dict(scale=float("nan")), 1), (dict(mode=9), 1), (dict(flags=1 << 5), 1),
     (dict(workspace=0), 6), (dict(workspace=FAKE + 16), 6), (dict(ws_bytes=16), 6),
 ])
 def test_fwd_rejects_bad_arguments_on_host(over, status):
