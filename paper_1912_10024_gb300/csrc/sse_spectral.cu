@@ -1251,6 +1251,222 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 block products with register tiles. The FP32 pipe issues 64x the FP64 rate, so the scalar
+// kernel above becomes bound by shared-memory bandwidth (two scalar loads per FMA). Here each
+// thread computes a 2 x 2 tile of the (zero-padded, Np = Norb rounded up to even) block for one
+// frequency, with G^ and dH stored transposed so that every operand pair is one 8-byte load:
+// per reduction step 12 FMA for 6 loads. Same arithmetic as spec_prod_kernel (Gauss MACs).
+// ---------------------------------------------------------------------------
+struct Prod32Cfg {
+    int Np, TN, T, F, threads, fchunk;
+    int pl;  // floats per Np x Np plane
+    int off_A, off_G, off_K, off_W, off_U, smem;
+};
+
+Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
+    Prod32Cfg c{};
+    c.Np = d.Norb + (d.Norb & 1);
+    c.TN = c.Np / 2;
+    c.T = c.TN * c.TN;
+    c.pl = c.Np * c.Np;
+    const int pb = c.pl * 4;  // bytes per plane
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 9 * pb + F * (21 * pb + 9 * 8) + 64; });
+    c.threads = ((c.F * c.T + 31) / 32) * 32;
+    c.off_A = 0;                                  // [NB][3 dir][3 planes] dH transposed: AT[l][m] = dH[m][l]
+    c.off_G = a16(c.off_A + d.NB * 9 * pb);       // [F][3 planes] G^ transposed: GT[l][m] = G^[m][l]
+    c.off_K = a16(c.off_G + c.F * 3 * pb);        // [F][9] float2
+    c.off_W = a16(c.off_K + c.F * 9 * 8);         // [F][3 i][3 planes] W_i row-major
+    c.off_U = a16(c.off_W + c.F * 9 * pb);        // [F][3 i][3 planes] U_i row-major
+    c.smem = a16(c.off_U + c.F * 9 * pb);
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    size_t want = (size_t)152 * 2 * 8;
+    size_t chunks = (want + nA - 1) / (nA ? nA : 1);
+    if (chunks < 1) chunks = 1;
+    size_t fc = (nfreq + chunks - 1) / chunks;
+    fc = ((fc + c.F - 1) / c.F) * c.F;
+    c.fchunk = (int)(fc < 1 ? 1 : fc);
+    return c;
+}
+
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+
+__global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ nbr,
+                                   const double2* __restrict__ dH, const float2* __restrict__ Ghat,
+                                   const float2* __restrict__ Khat, float2* __restrict__ Shat, double scale,
+                                   unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Norb = d.Norb, Np = c.Np, pl = c.pl, nel = Norb * Norb;
+    const int la = blockIdx.x;
+    const int a = d.a_begin + la;
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const size_t i_begin = (size_t)blockIdx.y * c.fchunk;
+    const size_t i_end = min(fm.count, i_begin + c.fchunk);
+    float* sA = reinterpret_cast<float*>(smem + c.off_A);
+    float* sG = reinterpret_cast<float*>(smem + c.off_G);
+    float2* sK = reinterpret_cast<float2*>(smem + c.off_K);
+    float* sW = reinterpret_cast<float*>(smem + c.off_W);
+    float* sU = reinterpret_cast<float*>(smem + c.off_U);
+    const int tid = threadIdx.x;
+    const int fl = tid / c.T, tt = tid - fl * c.T;
+    const int m0 = 2 * (tt / c.TN), n0 = 2 * (tt % c.TN);
+    const bool lane = fl < c.F;
+
+    // dH planes, transposed and zero-padded: AT[s][dir][plane][l][m] = dH(a,s,dir)[m][l]
+    for (int i = tid; i < d.NB * 3 * pl; i += blockDim.x) {
+        const int sd = i / pl, e = i - sd * pl;
+        const int l = e / Np, m = e - l * Np;
+        double2 v = make_double2(0.0, 0.0);
+        if (l < Norb && m < Norb) v = dH[((size_t)a * d.NB * 3 + sd) * nel + m * Norb + l];
+        float* P = sA + (size_t)sd * 3 * pl;
+        P[e] = (float)v.x;
+        P[pl + e] = (float)v.y;
+        P[2 * pl + e] = (float)(v.x + v.y);
+    }
+    for (int s = 0; s < d.NB; ++s) {
+        const int b = nbr[(size_t)a * d.NB + s];
+        if ((b < 0 || b >= d.NA) && tid == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
+    }
+    __syncthreads();
+
+    for (size_t i0 = i_begin; i0 < i_end; i0 += c.F) {
+        const bool act = lane && i0 + fl < i_end;
+        const size_t f = act ? freq_of(fm, i0 + fl) : 0;
+        // accumulators of the 2 x 2 tile, Gauss components (re*re, im*im, (re+im)(re+im))
+        float T1[4] = {0, 0, 0, 0}, T2[4] = {0, 0, 0, 0}, T3[4] = {0, 0, 0, 0};
+        for (int s = 0; s < d.NB; ++s) {
+            const int b = nbr[(size_t)a * d.NB + s];
+            const bool bok = b >= 0 && b < d.NA;
+            // G^_b(f) -> GT planes: element (m, n) goes to GT[n][m]
+            if (lane) {
+                float* Gp = sG + (size_t)fl * 3 * pl;
+#pragma unroll
+                for (int dm = 0; dm < 2; ++dm)
+#pragma unroll
+                    for (int dn = 0; dn < 2; ++dn) {
+                        const int m = m0 + dm, n = n0 + dn;
+                        float2 g = make_float2(0.f, 0.f);
+                        if (act && bok && m < Norb && n < Norb) g = Ghat[(f * d.NA + b) * nel + m * Norb + n];
+                        const int o = n * Np + m;
+                        Gp[o] = g.x;
+                        Gp[pl + o] = g.y;
+                        Gp[2 * pl + o] = g.x + g.y;
+                    }
+            }
+            for (int i = tid; i < c.F * 9; i += blockDim.x) {
+                const int fk = i / 9, ij = i - fk * 9;
+                float2 k = make_float2(0.f, 0.f);
+                if (i0 + fk < i_end && bok) k = Khat[((freq_of(fm, i0 + fk) * nA + la) * d.NB + s) * 9 + ij];
+                sK[i] = k;
+            }
+            __syncthreads();
+            const float* A = sA + (size_t)s * 9 * pl;
+            // W_i[m][n] = sum_j K_ij conj(dH_j[n][m]) = sum_j K_ij conj(AT_j[m][n])
+            if (lane) {
+                const float2* K = sK + fl * 9;
+#pragma unroll
+                for (int dm = 0; dm < 2; ++dm) {
+                    const int m = m0 + dm;
+                    float2 ar[3], ai[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        ar[j] = ld2(A + (size_t)j * 3 * pl + m * Np + n0);
+                        ai[j] = ld2(A + (size_t)j * 3 * pl + pl + m * Np + n0);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        float wr0 = 0.f, wi0 = 0.f, wr1 = 0.f, wi1 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            const float2 k = K[i * 3 + j];
+                            wr0 = fmaf(k.x, ar[j].x, wr0);
+                            wr0 = fmaf(k.y, ai[j].x, wr0);
+                            wi0 = fmaf(k.y, ar[j].x, wi0);
+                            wi0 = fmaf(-k.x, ai[j].x, wi0);
+                            wr1 = fmaf(k.x, ar[j].y, wr1);
+                            wr1 = fmaf(k.y, ai[j].y, wr1);
+                            wi1 = fmaf(k.y, ar[j].y, wi1);
+                            wi1 = fmaf(-k.x, ai[j].y, wi1);
+                        }
+                        float* Wp = sW + ((size_t)fl * 3 + i) * 3 * pl + m * Np + n0;
+                        st2(Wp, wr0, wr1);
+                        st2(Wp + pl, wi0, wi1);
+                        st2(Wp + 2 * pl, wr0 + wi0, wr1 + wi1);
+                    }
+                }
+            }
+            __syncthreads();
+            // U_i = G^ W_i on the tile: U[m][n] = sum_l GT[l][m] W_i[l][n]
+            if (lane) {
+                const float* Gp = sG + (size_t)fl * 3 * pl;
+#pragma unroll 1
+                for (int i = 0; i < 3; ++i) {
+                    const float* Wp = sW + ((size_t)fl * 3 + i) * 3 * pl;
+                    float u1[4] = {0, 0, 0, 0}, u2[4] = {0, 0, 0, 0}, u3[4] = {0, 0, 0, 0};
+                    for (int l = 0; l < Norb; ++l) {
+                        const float2 gr = ld2(Gp + l * Np + m0), gi = ld2(Gp + pl + l * Np + m0),
+                                     gs = ld2(Gp + 2 * pl + l * Np + m0);
+                        const float2 wr = ld2(Wp + l * Np + n0), wi = ld2(Wp + pl + l * Np + n0),
+                                     ws = ld2(Wp + 2 * pl + l * Np + n0);
+                        u1[0] = fmaf(gr.x, wr.x, u1[0]); u1[1] = fmaf(gr.x, wr.y, u1[1]);
+                        u1[2] = fmaf(gr.y, wr.x, u1[2]); u1[3] = fmaf(gr.y, wr.y, u1[3]);
+                        u2[0] = fmaf(gi.x, wi.x, u2[0]); u2[1] = fmaf(gi.x, wi.y, u2[1]);
+                        u2[2] = fmaf(gi.y, wi.x, u2[2]); u2[3] = fmaf(gi.y, wi.y, u2[3]);
+                        u3[0] = fmaf(gs.x, ws.x, u3[0]); u3[1] = fmaf(gs.x, ws.y, u3[1]);
+                        u3[2] = fmaf(gs.y, ws.x, u3[2]); u3[3] = fmaf(gs.y, ws.y, u3[3]);
+                    }
+                    float* Up = sU + ((size_t)fl * 3 + i) * 3 * pl;
+#pragma unroll
+                    for (int dm = 0; dm < 2; ++dm) {
+                        const int q0 = dm * 2, q1 = dm * 2 + 1;
+                        const float r0 = u1[q0] - u2[q0], i0v = u3[q0] - u1[q0] - u2[q0];
+                        const float r1 = u1[q1] - u2[q1], i1v = u3[q1] - u1[q1] - u2[q1];
+                        float* o = Up + (m0 + dm) * Np + n0;
+                        st2(o, r0, r1);
+                        st2(o + pl, i0v, i1v);
+                        st2(o + 2 * pl, r0 + i0v, r1 + i1v);
+                    }
+                }
+            }
+            __syncthreads();
+            // acc += sum_i dH_i U_i: acc[m][n] += sum_l AT_i[l][m] U_i[l][n]
+            if (lane) {
+#pragma unroll 1
+                for (int i = 0; i < 3; ++i) {
+                    const float* Ap = A + (size_t)i * 3 * pl;
+                    const float* Up = sU + ((size_t)fl * 3 + i) * 3 * pl;
+                    for (int l = 0; l < Norb; ++l) {
+                        const float2 ar = ld2(Ap + l * Np + m0), ai = ld2(Ap + pl + l * Np + m0),
+                                     as = ld2(Ap + 2 * pl + l * Np + m0);
+                        const float2 ur = ld2(Up + l * Np + n0), ui = ld2(Up + pl + l * Np + n0),
+                                     us = ld2(Up + 2 * pl + l * Np + n0);
+                        T1[0] = fmaf(ar.x, ur.x, T1[0]); T1[1] = fmaf(ar.x, ur.y, T1[1]);
+                        T1[2] = fmaf(ar.y, ur.x, T1[2]); T1[3] = fmaf(ar.y, ur.y, T1[3]);
+                        T2[0] = fmaf(ai.x, ui.x, T2[0]); T2[1] = fmaf(ai.x, ui.y, T2[1]);
+                        T2[2] = fmaf(ai.y, ui.x, T2[2]); T2[3] = fmaf(ai.y, ui.y, T2[3]);
+                        T3[0] = fmaf(as.x, us.x, T3[0]); T3[1] = fmaf(as.x, us.y, T3[1]);
+                        T3[2] = fmaf(as.y, us.x, T3[2]); T3[3] = fmaf(as.y, us.y, T3[3]);
+                    }
+                }
+            }
+            __syncthreads();  // sG, sK, sW, sU are rewritten for the next bond
+        }
+        if (act) {
+            const float sc = (float)scale;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + q / 2, n = n0 + (q & 1);
+                if (m < Norb && n < Norb) {
+                    const float re = T1[q] - T2[q], im = T3[q] - T1[q] - T2[q];
+                    Shat[(f * nA + la) * nel + m * Norb + n] = make_float2(-sc * im, sc * re);
+                }
+            }
+        }
+    }
+}
+
 // (S - S^H)/2 on the blocks of atoms in range
 __global__ void symmetrize_kernel(sse_dims d, double2* __restrict__ S) {
     const int Norb = d.Norb, nel = Norb * Norb;
@@ -1370,8 +1586,11 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
         }
     }
     const ProdCfg pc = make_prod_cfg(d, fm.count, (int)sizeof(T));
-    if ((e = cudaFuncSetAttribute(spec_prod_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
-        cudaSuccess)
+    const Prod32Cfg pc32 = make_prod32_cfg(d, fm.count);
+    const bool tiled = sizeof(T) == 4;  // FP32: register-tiled kernel
+    if ((e = tiled ? cudaFuncSetAttribute(spec_prod32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc32.smem)
+                   : cudaFuncSetAttribute(spec_prod_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          pc.smem)) != cudaSuccess)
         return e;
     double2* S[2] = {S_less, S_greater};
     for (int t = 0; t < 2; ++t) {
@@ -1390,10 +1609,18 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
-        const size_t gy = (fm.count + pc.fchunk - 1) / pc.fchunk;
-        SSE_TIMED("spec_prod_kernel", st,
-                  spec_prod_kernel<T><<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
-                      pc, d, fm, p.nbr, p.dH, Gh, Kh, Sh, p.scale, status));
+        if (tiled) {
+            const size_t gy = (fm.count + pc32.fchunk - 1) / pc32.fchunk;
+            SSE_TIMED("spec_prod_kernel", st,
+                      spec_prod32_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc32.threads, pc32.smem, st>>>(
+                          pc32, d, fm, p.nbr, p.dH, reinterpret_cast<const float2*>(Gh),
+                          reinterpret_cast<const float2*>(Kh), reinterpret_cast<float2*>(Sh), p.scale, status));
+        } else {
+            const size_t gy = (fm.count + pc.fchunk - 1) / pc.fchunk;
+            SSE_TIMED("spec_prod_kernel", st,
+                      spec_prod_kernel<T><<<dim3((unsigned)nA, (unsigned)gy), pc.threads, pc.smem, st>>>(
+                          pc, d, fm, p.nbr, p.dH, Gh, Kh, Sh, p.scale, status));
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (half) {
             SSE_TIMED("mirror_sigma_kernel", st,
