@@ -135,9 +135,10 @@ def mixed_tensor_flops(d, mode: str) -> float:
 # DRAM bytes (read + write) per unit of work measured by ncu for the transform-path kernels
 # (profiles/spec_*_adjoint_ncu_full.md), valid for the kernel source they were taken on.
 NCU_TRAFFIC = {
-    "spec_prod_kernel": (4429.3, "c8a6f75cb574210d", "atom-frequency of one type"),
-    "spec_pi_kernel": (4872.6, "c8a6f75cb574210d", "type-atom-frequency"),
-    "spec_adj_kernel": (14302.1, "c8a6f75cb574210d", "atom-frequency of one type"),
+    "spec_prod_kernel": (4815.4, "2ba2b18d9ccb2e47", "atom-frequency of one type"),
+    "spec_pi_kernel": (5033.6, "2ba2b18d9ccb2e47", "type-atom-frequency"),
+    "spec_adj_kernel": (13877.8, "2ba2b18d9ccb2e47", "atom-frequency of one type"),
+    "spec_prod32_kernel": (1949.4, "2ba2b18d9ccb2e47", "atom-frequency of one type"),
 }
 
 
@@ -541,7 +542,9 @@ def main():
             ks, n = kernel_s("spec_prod_kernel")
             achieved = spectral_prod_flops(d, args.antihermitian) / ks / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "spec_prod_kernel",
+                    "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": ncu_traffic("spec_prod32_kernel", d.NA * freq_count(d, args.antihermitian)),
+                    "kernel": "spec_prod_kernel",
                     "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2070 MHz (FFMA probe: 73)"}
         elif args.mode == "fp64_fft":
             ks, n = kernel_s("spec_prod_kernel")
