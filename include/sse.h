@@ -145,6 +145,22 @@ SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* d
                   uint32_t flags, double* S_less, double* S_greater, void* workspace, size_t ws_bytes,
                   void* stream);
 
+/* sse_sigma_fwd with every array in HOST memory (page-locked for asynchronous copies):
+ * the call copies nbr, dH, D^<, D^>, G^< and G^> into `device_buf` on `copy_stream`,
+ * computes on `stream` and copies S^<, S^> (rows of atoms [a_begin, a_end) only) back on
+ * `copy_stream`. With modes FP64_FFT and FP32_FFT the upload of G^> overlaps the
+ * computation of Sigma^< and the download of Sigma^< the computation of Sigma^>; other modes
+ * start after the last upload. `device_buf`: caller-owned device memory of
+ * sse_sigma_fwd_host_bytes() (256-byte aligned; inputs, outputs and workspace). `stream` and
+ * `copy_stream` must differ; all work is ordered after earlier work on `stream`, and `stream`
+ * observes the completion of the copies (synchronise it before reading S_less / S_greater).
+ * Same checks, flags and status codes as sse_sigma_fwd. */
+SSE_API size_t sse_sigma_fwd_host_bytes(const sse_dims* d, int mode, uint32_t flags);
+SSE_API int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                               const double* D_greater, const double* G_less, const double* G_greater, double scale,
+                               int mode, uint32_t flags, double* S_less, double* S_greater, void* device_buf,
+                               size_t buf_bytes, void* stream, void* copy_stream);
+
 /* Adjoint of sse_sigma_fwd, in FP64: mode FP64 runs direct kernels (correlations
  * recomputed from the gathered G windows), mode FP64_FFT the transform-based adjoint
  * (per bond and frequency Q_j = W^ dH_j G^^H and R_i = W^^H dH_i G^, the weight

@@ -22,7 +22,7 @@ MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3
          "fp32_fft": SSE_MODE_FP32_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
             "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes", "sse_sigma_bwd_g",
-            "sse_profile_read", "sse_strerror")
+            "sse_sigma_fwd_host_bytes", "sse_sigma_fwd_host", "sse_profile_read", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -78,6 +78,11 @@ def load() -> ctypes.CDLL:
             lib.sse_sigma_bwd_g_workspace_bytes.restype = ctypes.c_size_t
             lib.sse_sigma_bwd_g.argtypes = [pd, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
             lib.sse_sigma_bwd_g.restype = i32
+            lib.sse_sigma_fwd_host_bytes.argtypes = [pd, i32, u32]
+            lib.sse_sigma_fwd_host_bytes.restype = ctypes.c_size_t
+            lib.sse_sigma_fwd_host.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, ctypes.c_size_t,
+                                               vp, vp]
+            lib.sse_sigma_fwd_host.restype = i32
             lib.sse_profile_read.argtypes = [ctypes.POINTER(sse_profile_entry), i32]
             lib.sse_profile_read.restype = i32
             _lib = lib
@@ -133,6 +138,17 @@ def sse_sigma_bwd_g(d: sse_dims, nbr, dH, D_less, D_greater, scale: float, mode:
     return int(load().sse_sigma_bwd_g(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater), float(scale),
                                       int(mode), int(flags), _p(gS_less), _p(gS_greater), _p(g_G_less),
                                       _p(g_G_greater), _p(workspace), int(ws_bytes), _stream(stream)))
+
+
+def sse_sigma_fwd_host_bytes(d: sse_dims, mode: int, flags: int) -> int:
+    return int(load().sse_sigma_fwd_host_bytes(ctypes.byref(d), int(mode), int(flags)))
+
+
+def sse_sigma_fwd_host(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int,
+                       flags: int, S_less, S_greater, device_buf, buf_bytes: int, stream=None, copy_stream=None) -> int:
+    return int(load().sse_sigma_fwd_host(ctypes.byref(d), _p(nbr), _p(dH), _p(D_less), _p(D_greater), _p(G_less),
+                                         _p(G_greater), float(scale), int(mode), int(flags), _p(S_less), _p(S_greater),
+                                         _p(device_buf), int(buf_bytes), _stream(stream), _stream(copy_stream)))
 
 
 def sse_sigma_bwd(d: sse_dims, nbr, dH, D_less, D_greater, G_less, G_greater, scale: float, mode: int, flags: int,
@@ -266,6 +282,38 @@ def sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greate
     if rc != 0:
         raise SseError(rc, "sse_sigma_bwd")
     return g_dH, g_Dl, g_Dg
+
+
+def sigma_host(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2.0 * math.pi),
+               mode: str = "fp64_fft", symmetrize: bool = False, check: bool = False, atoms=None, out=None,
+               device_buf: Optional[torch.Tensor] = None, stream=None, copy_stream=None, device=None):
+    """Sigma^<, Sigma^> from HOST (CPU, ideally pinned) tensors via sse_sigma_fwd_host: uploads, compute and
+    downloads overlap on two streams. Returns host tensors (S_less, S_greater); synchronises the stream."""
+    c128 = torch.complex128
+    Nkz, NE, NA, Norb, _ = G_less.shape
+    for name, x in (("G_less", G_less), ("G_greater", G_greater), ("dH", dH), ("D_less", D_less),
+                    ("D_greater", D_greater), ("nbr", nbr)):
+        if x.is_cuda or not x.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous host tensor")
+    d = dims_of(G_less, D_less, dH, atoms)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if out is None:
+        out = (torch.zeros(G_less.shape, dtype=c128).pin_memory(), torch.zeros(G_less.shape, dtype=c128).pin_memory())
+    if device_buf is None:
+        n = sse_sigma_fwd_host_bytes(d, m, flags)
+        if n == 0:
+            raise ValueError("invalid or unsupported problem sizes for libsse")
+        device_buf = torch.empty(n, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev) if stream is None else stream
+    cp = torch.cuda.Stream(device=dev) if copy_stream is None else copy_stream
+    rc = sse_sigma_fwd_host(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, out[0], out[1],
+                            device_buf, device_buf.numel(), st, cp)
+    if rc != 0:
+        raise SseError(rc, "sse_sigma_fwd_host")
+    st.synchronize()
+    return out
 
 
 def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 * math.pi),

@@ -273,3 +273,118 @@ extern "C" int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const doub
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }
+
+// ---------------------------------------------------------------------------
+// Host-buffer forward: copies in, computes, copies back, overlapping the copies with the compute.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HostLayout {
+    size_t nbr, dH, D[2], G[2], S[2], status, ws, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+HostLayout host_layout(const sse_dims& d, int mode) {
+    HostLayout l{};
+    const size_t nel = (size_t)d.Norb * d.Norb;
+    const size_t g = (size_t)d.Nkz * d.NE * d.NA * nel * 16;
+    const size_t dd = (size_t)d.Nqz * d.Nw * d.NA * d.NB * 9 * 16;
+    size_t o = 0;
+    l.nbr = o;
+    o = a256(o + (size_t)d.NA * d.NB * 4);
+    l.dH = o;
+    o = a256(o + (size_t)d.NA * d.NB * 3 * nel * 16);
+    for (int t = 0; t < 2; ++t) l.D[t] = o, o = a256(o + dd);
+    for (int t = 0; t < 2; ++t) l.G[t] = o, o = a256(o + g);
+    for (int t = 0; t < 2; ++t) l.S[t] = o, o = a256(o + g);
+    l.status = o;
+    l.ws = o + sse::kStatusBytes;
+    l.total = a256(l.ws + fwd_ws(d, mode));
+    return l;
+}
+
+}  // namespace
+
+extern "C" size_t sse_sigma_fwd_host_bytes(const sse_dims* d, int mode, uint32_t flags) {
+    if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
+    return host_layout(*d, mode).total;
+}
+
+extern "C" int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
+                                  const double* D_greater, const double* G_less, const double* G_greater,
+                                  double scale, int mode, uint32_t flags, double* S_less, double* S_greater,
+                                  void* device_buf, size_t buf_bytes, void* stream, void* copy_stream) {
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
+    int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    if (rc != SSE_OK) return rc;
+    if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
+    const HostLayout L = host_layout(*d, mode);
+    if (!device_buf || !aligned(device_buf, 256) || buf_bytes < L.total) return SSE_ERR_WORKSPACE;
+    if (d->a_begin == d->a_end) return SSE_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream), cp = static_cast<cudaStream_t>(copy_stream);
+    if (cp == st) return SSE_ERR_INVALID_ARG;  // the overlap needs a second stream
+    char* base = static_cast<char*>(device_buf);
+    const sse_dims& dd = *d;
+    const size_t nel = (size_t)dd.Norb * dd.Norb;
+    const size_t gb = (size_t)dd.Nkz * dd.NE * dd.NA * nel * 16;
+    const size_t db = (size_t)dd.Nqz * dd.Nw * dd.NA * dd.NB * 9 * 16;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // G^< in, G^> in, S^< done, S^> done, out
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SSE_ERR_CUDA;
+    auto cleanup = [&](int code) {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);  // released once the recorded work completes
+        return code;
+    };
+    unsigned* status = reinterpret_cast<unsigned*>(base + L.status);
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
+    // inputs on the copy stream: the small tensors and G^<, then G^>
+    if (cudaEventRecord(ev[4], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev[4], 0) != cudaSuccess)
+        return cleanup(SSE_ERR_CUDA);  // the device buffer is free once earlier work on `stream` is done
+    const bool ok_in = cudaMemcpyAsync(base + L.nbr, nbr, (size_t)dd.NA * dd.NB * 4, cudaMemcpyHostToDevice, cp) ==
+                           cudaSuccess &&
+                       cudaMemcpyAsync(base + L.dH, dH, (size_t)dd.NA * dd.NB * 3 * nel * 16, cudaMemcpyHostToDevice,
+                                       cp) == cudaSuccess &&
+                       cudaMemcpyAsync(base + L.D[0], D_less, db, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                       cudaMemcpyAsync(base + L.D[1], D_greater, db, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                       cudaMemcpyAsync(base + L.G[0], G_less, gb, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                       cudaEventRecord(ev[0], cp) == cudaSuccess &&
+                       cudaMemcpyAsync(base + L.G[1], G_greater, gb, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                       cudaEventRecord(ev[1], cp) == cudaSuccess;
+    if (!ok_in) return cleanup(SSE_ERR_CUDA);
+    const sse::Problem p = make_problem(d, reinterpret_cast<const int32_t*>(base + L.nbr),
+                                        reinterpret_cast<const double*>(base + L.dH),
+                                        reinterpret_cast<const double*>(base + L.D[0]),
+                                        reinterpret_cast<const double*>(base + L.D[1]),
+                                        reinterpret_cast<const double*>(base + L.G[0]),
+                                        reinterpret_cast<const double*>(base + L.G[1]), scale, flags);
+    double2* Sd[2] = {reinterpret_cast<double2*>(base + L.S[0]), reinterpret_cast<double2*>(base + L.S[1])};
+    void* ws = base + L.ws;
+    const size_t wsb = L.total - L.ws;
+    cudaError_t e;
+    if (mode == SSE_MODE_FP64_FFT || mode == SSE_MODE_FP32_FFT) {
+        e = sse::spectral_fwd_pipelined(p, mode == SSE_MODE_FP32_FFT, Sd[0], Sd[1], status, ws, wsb, st, ev, ev + 2);
+    } else {  // one kernel sequence for both types: wait for every input, one hand-off at the end
+        if (cudaStreamWaitEvent(st, ev[1], 0) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
+        e = mode == SSE_MODE_FP64 ? sse::fp64_fwd(p, Sd[0], Sd[1], status, ws, wsb, st)
+                                  : sse::mixed_fwd(p, mode, Sd[0], Sd[1], status, ws, wsb, st);
+        if (e == cudaSuccess && (cudaEventRecord(ev[2], st) != cudaSuccess || cudaEventRecord(ev[3], st) != cudaSuccess))
+            e = cudaErrorUnknown;
+    }
+    if (e == cudaErrorNotSupported) return cleanup(SSE_ERR_UNSUPPORTED);
+    if (e != cudaSuccess) return cleanup(SSE_ERR_CUDA);
+    // results back on the copy stream, rows of the atom range only (pitched copies)
+    const size_t pitch = (size_t)dd.NA * nel * 16, off = (size_t)dd.a_begin * nel * 16;
+    const size_t width = (size_t)(dd.a_end - dd.a_begin) * nel * 16, rows = (size_t)dd.Nkz * dd.NE;
+    double* Sh[2] = {S_less, S_greater};
+    for (int t = 0; t < 2; ++t)
+        if (cudaStreamWaitEvent(cp, ev[2 + t], 0) != cudaSuccess ||
+            cudaMemcpy2DAsync(reinterpret_cast<char*>(Sh[t]) + off, pitch, base + L.S[t] + off, pitch, width, rows,
+                              cudaMemcpyDeviceToHost, cp) != cudaSuccess)
+            return cleanup(SSE_ERR_CUDA);
+    // `stream` observes the completion of the copies
+    if (cudaEventRecord(ev[4], cp) != cudaSuccess || cudaStreamWaitEvent(st, ev[4], 0) != cudaSuccess)
+        return cleanup(SSE_ERR_CUDA);
+    return cleanup(finish(cudaSuccess, status, flags, st));
+}

@@ -1550,7 +1550,9 @@ namespace {
 // products on the FP32 pipe, FP64 inputs and outputs).
 template <class T>
 cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
-                           size_t ws_bytes, cudaStream_t st) {
+                           size_t ws_bytes, cudaStream_t st, const cudaEvent_t* g_ready = nullptr,
+                           const cudaEvent_t* s_done = nullptr) {
+    // g_ready[t]: G^t (and, for t = 0, every other input) is on the device; s_done[t]: Sigma^t is written.
     using C = typename CX<T>::C;
     const sse_dims& d = p.d;
     if (!spectral_supported(d)) return cudaErrorNotSupported;
@@ -1574,6 +1576,9 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
     const bool half = (p.flags & SSE_FLAG_ANTIHERMITIAN) != 0;
     const FreqMap fm = make_freq_map(d.Nkz, L, half);
     if (half && (p.flags & SSE_FLAG_CHECK)) {
+        if (g_ready)
+            for (int t = 0; t < 2; ++t)
+                if ((e = cudaStreamWaitEvent(st, g_ready[t], 0)) != cudaSuccess) return e;
         for (int t = 0; t < 2; ++t) {
             SSE_TIMED("check_antiherm_kernel", st,
                       check_antiherm_kernel<<<grid_for((size_t)d.Nkz * d.NE * d.NA * nel, 256), 256, 0, st>>>(
@@ -1594,6 +1599,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
         return e;
     double2* S[2] = {S_less, S_greater};
     for (int t = 0; t < 2; ++t) {
+        if (g_ready && (e = cudaStreamWaitEvent(st, g_ready[t], 0)) != cudaSuccess) return e;
         // 1. G^t -> G^
         e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
                        gcols, d.Nkz, st);
@@ -1641,10 +1647,18 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                       symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        if (s_done && (e = cudaEventRecord(s_done[t], st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 }  // namespace
+
+cudaError_t spectral_fwd_pipelined(const Problem& p, bool fp32, double2* S_less, double2* S_greater, unsigned* status,
+                                   void* ws, size_t ws_bytes, cudaStream_t st, const cudaEvent_t g_ready[2],
+                                   const cudaEvent_t s_done[2]) {
+    return fp32 ? spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st, g_ready, s_done)
+                : spectral_fwd_t<double>(p, S_less, S_greater, status, ws, ws_bytes, st, g_ready, s_done);
+}
 
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                          size_t ws_bytes, cudaStream_t st) {

@@ -141,3 +141,17 @@ def test_bwd_g_rejects_bad_arguments_on_host():
         args.update(over)
         assert B.sse_sigma_bwd_g(d, stream=0, **args) == status, over
     assert B.sse_sigma_bwd_g_workspace_bytes(d, 3, 0) > 256
+
+
+def test_fwd_host_checks_before_any_device_work():
+    d = good_dims()
+    n = B.sse_sigma_fwd_host_bytes(d, 3, 0)
+    assert n > 256
+    base = dict(nbr=FAKE, dH=FAKE, D_less=FAKE, D_greater=FAKE, G_less=FAKE, G_greater=FAKE, scale=0.1, mode=3,
+                flags=0, S_less=FAKE, S_greater=FAKE, device_buf=FAKE, buf_bytes=n)
+    for over, status in ((dict(S_less=0), 1), (dict(G_less=FAKE + 4), 1), (dict(buf_bytes=n - 1), 6),
+                         (dict(device_buf=FAKE + 64), 6), (dict(mode=9), 1)):
+        args = dict(base)
+        args.update(over)
+        assert B.sse_sigma_fwd_host(d, stream=0, copy_stream=1, **args) == status, over
+    assert B.sse_sigma_fwd_host(d, stream=0, copy_stream=0, **base) == 1  # the overlap needs two streams
