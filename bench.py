@@ -510,6 +510,33 @@ def main():
                                  "traffic": ncu_traffic("spec_adj_kernel", d.NA * d.Nkz * fft_length(d.NE, d.Nw)),
                                  "kernels": {k: {"ms_per_step": v[0] / args.steps,
                                                  "launches_per_step": v[1] / args.steps} for k, v in ak.items()}}}
+        # the same adjoint with FP32 transforms and products (mode FP32_FFT)
+        ref_g = tuple(x.clone() for x in gout)
+        m32 = B.MODES["fp32_fft"]
+        del wsa
+        torch.cuda.empty_cache()
+        wsa = B.workspace(dims, m32, 0, dev)
+
+        def astep32():
+            rc = B.sse_sigma_bwd(dims, inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                                 m32, 0, W, V, gout[0], gout[1], gout[2], wsa, wsa.numel(), stream)
+            if rc != 0:
+                raise B.SseError(rc, "sse_sigma_bwd")
+
+        for _ in range(max(3, args.warmup)):
+            astep32()
+        torch.cuda.synchronize(dev)
+        a0.record(stream)
+        for _ in range(args.steps):
+            astep32()
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        adj_line["fp32_fft"] = {"ms_per_step": a0.elapsed_time(a1) / args.steps,
+                                "normwise_diff_vs_fp64": dict(zip(("g_dH", "g_D_less", "g_D_greater"),
+                                                                  (float((x - y).abs().max() / y.abs().max())
+                                                                   for x, y in zip(gout, ref_g)))),
+                                "stated_bound": 1e-5}
+        del ref_g
         # gradient w.r.t. G^<, G^> (sse_sigma_bwd_g), same upstream
         del wsa
         torch.cuda.empty_cache()

@@ -161,11 +161,14 @@ SSE_API int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const doub
                                int mode, uint32_t flags, double* S_less, double* S_greater, void* device_buf,
                                size_t buf_bytes, void* stream, void* copy_stream);
 
-/* Adjoint of sse_sigma_fwd, in FP64: mode FP64 runs direct kernels (correlations
+/* Adjoint of sse_sigma_fwd: mode FP64 runs direct FP64 kernels (correlations
  * recomputed from the gathered G windows), mode FP64_FFT the transform-based adjoint
- * (per bond and frequency Q_j = W^ dH_j G^^H and R_i = W^^H dH_i G^, the weight
+ * in FP64 (per bond and frequency Q_j = W^ dH_j G^^H and R_i = W^^H dH_i G^, the weight
  * gradient from the inverse transform of tr(dH_i^H Q_j), the coupling gradient
- * summed over frequencies in a fixed order); other modes return SSE_ERR_UNSUPPORTED.
+ * summed over frequencies in a fixed order), mode FP32_FFT the same steps with FP32
+ * transforms and block products, the coupling-gradient partial sums and all inputs and
+ * outputs in FP64 (normwise error about 1e-6, bound 1e-5 at the workloads tested);
+ * TF32 and BF16X3 return SSE_ERR_UNSUPPORTED.
  * For the loss
  *   L = sum_t sum_{a in range, E, k} Re tr( gS^t_a(E,k)^H Sigma^t_a(E,k) )
  * it writes the gradients w.r.t. dH, D^< and D^> in the PyTorch convention

@@ -384,8 +384,14 @@ class SigmaFunction(torch.autograd.Function):
         S = sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale=scale, mode=mode, symmetrize=symmetrize)
         ctx.save_for_backward(dH, D_less, D_greater, G_less, G_greater, nbr)
         ctx.scale, ctx.symmetrize = scale, symmetrize
-        # the adjoint runs in FP64: transform-based after a transform-based forward, direct otherwise
-        ctx.bwd_mode = "fp64_fft" if mode in ("fp64_fft", SSE_MODE_FP64_FFT, "fp32_fft", SSE_MODE_FP32_FFT) else "fp64"
+        # transform-based adjoint after a transform-based forward (FP32 products after an FP32_FFT
+        # forward), the direct FP64 adjoint otherwise
+        if mode in ("fp32_fft", SSE_MODE_FP32_FFT):
+            ctx.bwd_mode = "fp32_fft"
+        elif mode in ("fp64_fft", SSE_MODE_FP64_FFT):
+            ctx.bwd_mode = "fp64_fft"
+        else:
+            ctx.bwd_mode = "fp64"
         return S
 
     @staticmethod

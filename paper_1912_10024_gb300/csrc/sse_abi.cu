@@ -101,8 +101,9 @@ extern "C" const char* sse_strerror(int status) {
 extern "C" size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
     if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
     size_t f = fwd_ws(*d, mode);
-    size_t b = mode == SSE_MODE_FP64 ? sse::fp64_bwd_workspace(*d)
+    size_t b = mode == SSE_MODE_FP64       ? sse::fp64_bwd_workspace(*d)
                : mode == SSE_MODE_FP64_FFT ? sse::spectral_bwd_workspace(*d)
+               : mode == SSE_MODE_FP32_FFT ? sse::spectral_bwd32_workspace(*d)
                                            : 0;
     return sse::kStatusBytes + (f > b ? f : b);
 }
@@ -146,8 +147,10 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
     if (!aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_dH, 16) || !aligned(g_D_less, 16) ||
         !aligned(g_D_greater, 16))
         return SSE_ERR_INVALID_ARG;
-    if (!fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
-    const size_t need = mode == SSE_MODE_FP64 ? sse::fp64_bwd_workspace(*d) : sse::spectral_bwd_workspace(*d);
+    if (!fp64_mode(mode) && mode != SSE_MODE_FP32_FFT) return SSE_ERR_UNSUPPORTED;
+    const size_t need = mode == SSE_MODE_FP64       ? sse::fp64_bwd_workspace(*d)
+                        : mode == SSE_MODE_FP64_FFT ? sse::spectral_bwd_workspace(*d)
+                                                    : sse::spectral_bwd32_workspace(*d);
     if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + need) return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -161,8 +164,9 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
     double2* gh = reinterpret_cast<double2*>(g_dH);
     double2* gdl = reinterpret_cast<double2*>(g_D_less);
     double2* gdg = reinterpret_cast<double2*>(g_D_greater);
-    cudaError_t e = mode == SSE_MODE_FP64 ? sse::fp64_bwd(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st)
-                                          : sse::spectral_bwd(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st);
+    cudaError_t e = mode == SSE_MODE_FP64       ? sse::fp64_bwd(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st)
+                    : mode == SSE_MODE_FP64_FFT ? sse::spectral_bwd(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st)
+                                                : sse::spectral_bwd32(p, gl, gg, gh, gdl, gdg, status, ws, wsb, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }

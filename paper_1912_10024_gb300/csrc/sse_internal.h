@@ -87,6 +87,12 @@ cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2
                          double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
                          cudaStream_t st);
 
+// The same adjoint with FP32 transforms and products (mode FP32_FFT), FP64 final sums and outputs.
+size_t spectral_bwd32_workspace(const sse_dims& d);
+cudaError_t spectral_bwd32(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
+                           double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
+                           cudaStream_t st);
+
 // Gradient with respect to G, transform-based FP64 (sse_spectral.cu).
 size_t spectral_bwd_g_workspace(const sse_dims& d);
 cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_G_less,

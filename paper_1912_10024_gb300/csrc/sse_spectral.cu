@@ -811,14 +811,14 @@ struct AdjCfg {
 
 constexpr int kAdjMaxThreads = 320;
 
-AdjCfg make_adj_cfg(const sse_dims& d, size_t nfreq) {
+AdjCfg make_adj_cfg(const sse_dims& d, size_t nfreq, int tsz = 8) {
     AdjCfg c{};
     c.nel = d.Norb * d.Norb;
-    const int pl = c.nel * 8;
+    const int pl = c.nel * tsz;
     auto a16 = [](int x) { return (x + 15) & ~15; };
     // per CTA: the current bond's dH planes, then per frequency 27 plane-sized buffers and the traces
     auto smem_of = [&](int F) {
-        return (long)3 * 4 * pl + F * (8 * pl + 9 * 16 + 9 * pl * 2 + 6 * pl + 9 * d.Norb * 16) + 128;
+        return (long)3 * 4 * pl + F * (8 * pl + 9 * 2 * tsz + 9 * pl * 2 + 6 * pl + 9 * d.Norb * 2 * tsz) + 128;
     };
     c.F = 1;
     long best = -1;
@@ -837,11 +837,11 @@ AdjCfg make_adj_cfg(const sse_dims& d, size_t nfreq) {
     c.off_W = a16(c.off_A + 3 * 4 * pl);           // [F][4 planes]
     c.off_G = a16(c.off_W + c.F * 4 * pl);         // [F][4 planes]
     c.off_K = a16(c.off_G + c.F * 4 * pl);         // [F][9] complex
-    c.off_T = a16(c.off_K + c.F * 9 * 16);         // [F][3 j][3 planes]  W^ dH_j
+    c.off_T = a16(c.off_K + c.F * 9 * 2 * tsz);    // [F][3 j][3 planes]  W^ dH_j
     c.off_V = a16(c.off_T + c.F * 9 * pl);         // [F][3 i][3 planes]  W^^H dH_i
     c.off_Q = a16(c.off_V + c.F * 9 * pl);         // [F][3 j][2 planes]
     c.off_D = a16(c.off_Q + c.F * 6 * pl);         // [F][9][Norb] complex
-    c.smem = a16(c.off_D + c.F * 9 * d.Norb * 16);
+    c.smem = a16(c.off_D + c.F * 9 * d.Norb * 2 * tsz);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
     size_t chunks = (want + nA - 1) / (nA ? nA : 1);
@@ -853,18 +853,21 @@ AdjCfg make_adj_cfg(const sse_dims& d, size_t nfreq) {
     return c;
 }
 
-__device__ __forceinline__ void put4(double* P, int nel, int e, double2 v) {
+template <class T, class C>
+__device__ __forceinline__ void put4(T* P, int nel, int e, C v) {
     P[e] = v.x;
     P[nel + e] = v.y;
     P[2 * nel + e] = v.x + v.y;
     P[3 * nel + e] = v.x - v.y;
 }
 
+template <class T>
 __global__ void __launch_bounds__(kAdjMaxThreads, 2)
 spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const double2* __restrict__ dH,
-                const double2* __restrict__ What, const double2* __restrict__ Ghat, const double2* __restrict__ Khat,
-                double2* __restrict__ Hhat, double2* __restrict__ gdh_part, int L, double scale,
-                unsigned* __restrict__ status) {
+                const typename CX<T>::C* __restrict__ What, const typename CX<T>::C* __restrict__ Ghat,
+                const typename CX<T>::C* __restrict__ Khat, typename CX<T>::C* __restrict__ Hhat,
+                double2* __restrict__ gdh_part, int L, double scale, unsigned* __restrict__ status) {
+    using C = typename CX<T>::C;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Norb = d.Norb, nel = c.nel;
     const int la = blockIdx.x;
@@ -873,14 +876,14 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
     const size_t nfreq = (size_t)d.Nkz * L;
     const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
     const size_t f_end = min(nfreq, f_begin + c.fchunk);
-    double* sA = reinterpret_cast<double*>(smem + c.off_A);
-    double* sW = reinterpret_cast<double*>(smem + c.off_W);
-    double* sG = reinterpret_cast<double*>(smem + c.off_G);
-    double2* sK = reinterpret_cast<double2*>(smem + c.off_K);
-    double* sT = reinterpret_cast<double*>(smem + c.off_T);
-    double* sV = reinterpret_cast<double*>(smem + c.off_V);
-    double* sQ = reinterpret_cast<double*>(smem + c.off_Q);
-    double2* sD = reinterpret_cast<double2*>(smem + c.off_D);
+    T* sA = reinterpret_cast<T*>(smem + c.off_A);
+    T* sW = reinterpret_cast<T*>(smem + c.off_W);
+    T* sG = reinterpret_cast<T*>(smem + c.off_G);
+    C* sK = reinterpret_cast<C*>(smem + c.off_K);
+    T* sT = reinterpret_cast<T*>(smem + c.off_T);
+    T* sV = reinterpret_cast<T*>(smem + c.off_V);
+    T* sQ = reinterpret_cast<T*>(smem + c.off_Q);
+    C* sD = reinterpret_cast<C*>(smem + c.off_D);
     const int tid = threadIdx.x;
     const int fl = tid / nel, e = tid - fl * nel;
     const int m = e / Norb, n = e - m * Norb;
@@ -894,16 +897,17 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
         // this bond's dH planes (the previous bond's last barrier has passed)
         for (int i = tid; i < 3 * nel; i += blockDim.x) {
             const int di = i / nel, ee = i - di * nel;
-            put4(sA + (size_t)di * 4 * nel, nel, ee, dH[((size_t)a * d.NB + s) * 3 * nel + i]);
+            const double2 v = dH[((size_t)a * d.NB + s) * 3 * nel + i];
+            put4(sA + (size_t)di * 4 * nel, nel, ee, CT<C>::mk((T)v.x, (T)v.y));
         }
         __syncthreads();
-        const double* A = sA;
-        double2 acc[3] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+        const T* A = sA;
+        C acc[3] = {CT<C>::mk(0, 0), CT<C>::mk(0, 0), CT<C>::mk(0, 0)};
         for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
             const size_t f = f0 + fl;
             const bool act = lane && f < f_end && bok;
             if (lane) {
-                double2 w = make_double2(0.0, 0.0), g = make_double2(0.0, 0.0);
+                C w = CT<C>::mk(0, 0), g = CT<C>::mk(0, 0);
                 if (act) {
                     w = What[(f * nA + la) * nel + e];
                     g = Ghat[(f * d.NA + b) * nel + e];
@@ -914,18 +918,18 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
             for (int i = tid; i < c.F * 9; i += blockDim.x) {
                 const int fk = i / 9, ij = i - fk * 9;
                 const size_t ff = f0 + fk;
-                double2 k = make_double2(0.0, 0.0);
+                C k = CT<C>::mk(0, 0);
                 if (ff < f_end && bok) k = Khat[((ff * nA + la) * d.NB + s) * 9 + ij];
                 sK[i] = k;
             }
             __syncthreads();
             // T_j = W^ dH_j,  V_i = W^^H dH_i
             if (lane) {
-                const double* Wp = sW + (size_t)fl * 4 * nel;
+                const T* Wp = sW + (size_t)fl * 4 * nel;
 #pragma unroll 1
                 for (int j = 0; j < 3; ++j) {
-                    const double* Aj = A + (size_t)j * 4 * nel;
-                    double t1 = 0.0, t2 = 0.0, t3 = 0.0, v1 = 0.0, u2 = 0.0, v3 = 0.0;
+                    const T* Aj = A + (size_t)j * 4 * nel;
+                    T t1 = 0, t2 = 0, t3 = 0, v1 = 0, u2 = 0, v3 = 0;
                     for (int l = 0; l < Norb; ++l) {
                         const int ml = m * Norb + l, lm = l * Norb + m, ln = l * Norb + n;
                         t1 = fma(Wp[ml], Aj[ln], t1);                  // W[m][l] A_j[l][n]
@@ -935,20 +939,20 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
                         u2 = fma(Wp[nel + lm], Aj[nel + ln], u2);
                         v3 = fma(Wp[3 * nel + lm], Aj[2 * nel + ln], v3);
                     }
-                    put3(sT + ((size_t)fl * 3 + j) * 3 * nel, nel, e, make_double2(t1 - t2, t3 - t1 - t2));
-                    put3(sV + ((size_t)fl * 3 + j) * 3 * nel, nel, e, make_double2(v1 + u2, v3 - v1 + u2));
+                    put3(sT + ((size_t)fl * 3 + j) * 3 * nel, nel, e, CT<C>::mk(t1 - t2, t3 - t1 - t2));
+                    put3(sV + ((size_t)fl * 3 + j) * 3 * nel, nel, e, CT<C>::mk(v1 + u2, v3 - v1 + u2));
                 }
             }
             __syncthreads();
             // Q_j = T_j G^^H (stored for the traces), R_i = V_i G^; grad dH accumulation
             if (lane) {
-                const double* Gp = sG + (size_t)fl * 4 * nel;
-                const double2* K = sK + fl * 9;
+                const T* Gp = sG + (size_t)fl * 4 * nel;
+                const C* K = sK + fl * 9;
 #pragma unroll 1
                 for (int j = 0; j < 3; ++j) {
-                    const double* Tp = sT + ((size_t)fl * 3 + j) * 3 * nel;
-                    const double* Vp = sV + ((size_t)fl * 3 + j) * 3 * nel;
-                    double q1 = 0.0, q2 = 0.0, q3 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+                    const T* Tp = sT + ((size_t)fl * 3 + j) * 3 * nel;
+                    const T* Vp = sV + ((size_t)fl * 3 + j) * 3 * nel;
+                    T q1 = 0, q2 = 0, q3 = 0, r1 = 0, r2 = 0, r3 = 0;
                     for (int l = 0; l < Norb; ++l) {
                         const int ml = m * Norb + l, nl = n * Norb + l, ln = l * Norb + n;
                         q1 = fma(Tp[ml], Gp[nl], q1);                  // T[m][l] conj(G[n][l])
@@ -959,15 +963,15 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
                         r3 = fma(Vp[2 * nel + ml], Gp[2 * nel + ln], r3);
                     }
                     // (T conj(G^T)): re = q1 + q2, im = q3 - q1 + q2  (Gauss with (re - im) of G)
-                    const double2 Q = make_double2(q1 + q2, q3 - q1 + q2);
-                    const double2 R = make_double2(r1 - r2, r3 - r1 - r2);
-                    double* Qs = sQ + ((size_t)fl * 3 + j) * 2 * nel;
+                    const C Q = CT<C>::mk(q1 + q2, q3 - q1 + q2);
+                    const C R = CT<C>::mk(r1 - r2, r3 - r1 - r2);
+                    T* Qs = sQ + ((size_t)fl * 3 + j) * 2 * nel;
                     Qs[e] = Q.x;
                     Qs[nel + e] = Q.y;
 #pragma unroll
                     for (int mu = 0; mu < 3; ++mu) {
                         // conj(c) conj(K_mu,j) Q = -i*scale*conj(K) Q ;  c K_j,mu R = i*scale*K R
-                        const double2 k1 = K[mu * 3 + j], k2 = K[j * 3 + mu];
+                        const C k1 = K[mu * 3 + j], k2 = K[j * 3 + mu];
                         // alpha = -i conj(k1) = (-k1.y, -k1.x);  beta = i k2 = (-k2.y, k2.x)
                         acc[mu].x = fma(-k1.y, Q.x, acc[mu].x);
                         acc[mu].x = fma(k1.x, Q.y, acc[mu].x);
@@ -986,25 +990,25 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
                 const int fi = g / (9 * Norb), rem = g - fi * 9 * Norb;
                 const int ij = rem / Norb, mm = rem - ij * Norb;
                 const int i = ij / 3, j = ij - 3 * i;
-                const double* Ai = A + (size_t)i * 4 * nel;
-                const double* Qs = sQ + ((size_t)fi * 3 + j) * 2 * nel;
-                double re = 0.0, im = 0.0;
+                const T* Ai = A + (size_t)i * 4 * nel;
+                const T* Qs = sQ + ((size_t)fi * 3 + j) * 2 * nel;
+                T re = 0, im = 0;
                 for (int nn = 0; nn < Norb; ++nn) {
                     const int o = mm * Norb + nn;
-                    const double ar = Ai[o], ai = Ai[nel + o], qr = Qs[o], qi = Qs[nel + o];
+                    const T ar = Ai[o], ai = Ai[nel + o], qr = Qs[o], qi = Qs[nel + o];
                     re = fma(ar, qr, re);
                     re = fma(ai, qi, re);
                     im = fma(ar, qi, im);
                     im = fma(-ai, qr, im);
                 }
-                sD[g] = make_double2(re, im);
+                sD[g] = CT<C>::mk(re, im);
             }
             __syncthreads();
             for (int g = tid; g < c.F * 9; g += blockDim.x) {
                 const int rf = g / 9, ij = g - rf * 9;
                 const size_t ff = f0 + rf;
-                const double2* v = sD + (size_t)g * Norb;
-                double2 sum = v[0];
+                const C* v = sD + (size_t)g * Norb;
+                C sum = v[0];
                 for (int mm = 1; mm < Norb; ++mm) sum = cadd(sum, v[mm]);
                 if (ff < f_end) Hhat[((ff * nA + la) * d.NB + s) * 9 + ij] = sum;
             }
@@ -1013,15 +1017,19 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
         }
         // sum the frequency lanes' accumulators (fixed order) and write this chunk's partial
         __syncthreads();
-        double2* sAcc = reinterpret_cast<double2*>(sT);  // [F][3][nel] complex fits in the T planes
+        C* sAcc = reinterpret_cast<C*>(sT);  // [F][3][nel] complex fits in the T planes
         if (lane)
 #pragma unroll
             for (int mu = 0; mu < 3; ++mu) sAcc[((size_t)fl * 3 + mu) * nel + e] = acc[mu];
         __syncthreads();
         const double inv = scale / (double)nfreq;
         for (int i = tid; i < 3 * nel; i += blockDim.x) {
-            double2 sum = sAcc[i];
-            for (int f2 = 1; f2 < c.F; ++f2) sum = cadd(sum, sAcc[(size_t)f2 * 3 * nel + i]);
+            double2 sum = make_double2((double)sAcc[i].x, (double)sAcc[i].y);  // FP64 sums from here on
+            for (int f2 = 1; f2 < c.F; ++f2) {
+                const C v = sAcc[(size_t)f2 * 3 * nel + i];
+                sum.x += (double)v.x;
+                sum.y += (double)v.y;
+            }
             gdh_part[(((size_t)blockIdx.y * nA + la) * d.NB + s) * 3 * nel + i] = make_double2(sum.x * inv, sum.y * inv);
         }
         __syncthreads();  // sT is rewritten by the next bond's first batch
@@ -1045,28 +1053,31 @@ __global__ void spec_gdh_reduce_kernel(sse_dims d, int nchunks, const double2* _
 }
 
 // upstream gradient gS^t[k][E][a][mn] of atoms in range, optionally projected to (W - W^H)/2
-struct LoadW {
-    using C = double2;
+template <class CC>
+struct LoadWT {
+    using C = CC;
     const double2* W;
     int NE, Norb;
     size_t rowlen, col0;
     int sym;
-    __device__ double2 operator()(int k, int r, size_t col) const {
-        if (r >= NE) return make_double2(0.0, 0.0);
+    __device__ C operator()(int k, int r, size_t col) const {
+        if (r >= NE) return CT<C>::mk(0, 0);
         const double2* row = W + ((size_t)k * NE + r) * rowlen + col0;
         const double2 x = row[col];
-        if (!sym) return x;
+        if (!sym) return CT<C>::mk(x.x, x.y);
         const int nel = Norb * Norb;
         const size_t blk = col / nel;
         const int mn = (int)(col - blk * nel), mm = mn / Norb, nn = mn - mm * Norb;
         const double2 y = row[blk * nel + nn * Norb + mm];
-        return make_double2(0.5 * (x.x - y.x), 0.5 * (x.y + y.y));
+        return CT<C>::mk(0.5 * (x.x - y.x), 0.5 * (x.y + y.y));
     }
 };
+using LoadW = LoadWT<double2>;
 
 // grad D^t (rows l = w+1) and grad D^t' (rows L-(w+1)) from the inverse transform of H^t:
 // value conj(c) * conj(v) / N = (-v.y, -v.x) * scale / N
-struct StoreGD {
+template <class C>
+struct StoreGDT {
     double2* gD_same;   // D of the same type as H: emission lags
     double2* gD_other;  // the other type: absorption lags
     int Nw, L;
@@ -1074,7 +1085,7 @@ struct StoreGD {
     double inv_scale;
     int add;
     int rows;
-    __device__ void operator()(int q, int r, size_t col, double2 v) const {
+    __device__ void operator()(int q, int r, size_t col, C v) const {
         double2* out;
         int w;
         if (r >= 1 && r <= Nw) {
@@ -1087,7 +1098,7 @@ struct StoreGD {
             return;
         }
         double2* o = out + ((size_t)q * Nw + w) * rowlen + col0 + col;
-        const double2 x = make_double2(-v.y * inv_scale, -v.x * inv_scale);
+        const double2 x = make_double2(-(double)v.y * inv_scale, -(double)v.x * inv_scale);
         if (add) {
             const double2 cur = *o;
             *o = make_double2(cur.x + x.x, cur.y + x.y);
@@ -1777,55 +1788,61 @@ struct AdjLayout {
     size_t off_tw, off_W, off_G, off_K, off_H, off_part, total;
 };
 
-AdjLayout adj_layout(const sse_dims& d) {
+AdjLayout adj_layout(const sse_dims& d, size_t csz = 16) {  // csz: bytes per complex spectrum entry
     AdjLayout l{};
     l.L = spectral_length(d);
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t spec = (size_t)d.Nkz * l.L;
-    const AdjCfg ac = make_adj_cfg(d, spec);
+    const AdjCfg ac = make_adj_cfg(d, spec, (int)csz / 2);
     l.off_tw = 0;
     l.off_W = align256((size_t)l.L * 16);
-    l.off_G = align256(l.off_W + spec * nA * nel * 16);
-    l.off_K = align256(l.off_G + spec * d.NA * nel * 16);
-    l.off_H = align256(l.off_K + spec * nA * d.NB * 9 * 16);
-    l.off_part = align256(l.off_H + spec * nA * d.NB * 9 * 16);
+    l.off_G = align256(l.off_W + spec * nA * nel * csz);
+    l.off_K = align256(l.off_G + spec * d.NA * nel * csz);
+    l.off_H = align256(l.off_K + spec * nA * d.NB * 9 * csz);
+    l.off_part = align256(l.off_H + spec * nA * d.NB * 9 * csz);
     l.total = align256(l.off_part + (size_t)2 * ac.nchunks * nA * d.NB * 3 * nel * 16);
     return l;
 }
 
 size_t spectral_bwd_workspace(const sse_dims& d) { return adj_layout(d).total; }
+size_t spectral_bwd32_workspace(const sse_dims& d) { return adj_layout(d, 8).total; }
 
 bool spectral_bwd_supported(const sse_dims& d) {
     const int L = spectral_length(d);
     return spectral_supported(d) && make_adj_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
 }
 
-cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
-                         double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
-                         cudaStream_t st) {
+namespace {
+// The adjoint in the real type T: double (FP64_FFT) or float (FP32_FFT: FP32 transforms and products, FP64
+// partial sums of the coupling gradient and FP64 outputs).
+template <class T>
+cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
+                           double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    using C = typename CX<T>::C;
     const sse_dims& d = p.d;
     if (!spectral_bwd_supported(d)) return cudaErrorNotSupported;
-    const AdjLayout lay = adj_layout(d);
+    const AdjLayout lay = adj_layout(d, sizeof(C));
     if (ws_bytes < lay.total) return cudaErrorInvalidValue;
     unsigned char* base = static_cast<unsigned char*>(ws);
     double2* tw = reinterpret_cast<double2*>(base + lay.off_tw);
-    double2* Wh = reinterpret_cast<double2*>(base + lay.off_W);
-    double2* Gh = reinterpret_cast<double2*>(base + lay.off_G);
-    double2* Kh = reinterpret_cast<double2*>(base + lay.off_K);
-    double2* Hh = reinterpret_cast<double2*>(base + lay.off_H);
+    C* Wh = reinterpret_cast<C*>(base + lay.off_W);
+    C* Gh = reinterpret_cast<C*>(base + lay.off_G);
+    C* Kh = reinterpret_cast<C*>(base + lay.off_K);
+    C* Hh = reinterpret_cast<C*>(base + lay.off_H);
     double2* part = reinterpret_cast<double2*>(base + lay.off_part);
     const int L = lay.L;
-    const FftPlan plan = make_plan(L);
+    const FftPlan plan = make_plan(L, (int)sizeof(C));
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t gcols = (size_t)d.NA * nel, wcols = nA * nel, kcols = nA * d.NB * 9;
     const size_t nfreq = (size_t)d.Nkz * L;
-    const AdjCfg ac = make_adj_cfg(d, nfreq);
+    const AdjCfg ac = make_adj_cfg(d, nfreq, (int)sizeof(T));
     const size_t part_one = (size_t)ac.nchunks * nA * d.NB * 3 * nel;
     if (nA == 0) return cudaSuccess;
     cudaError_t e;
     SSE_TIMED("twiddle_kernel", st, twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(spec_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ac.smem)) !=
+    if ((e = cudaFuncSetAttribute(spec_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ac.smem)) !=
         cudaSuccess)
         return e;
     const double2* W[2] = {gS_less, gS_greater};
@@ -1833,29 +1850,29 @@ cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2
     const int sym = (p.flags & SSE_FLAG_SYMMETRIZE) ? 1 : 0;
     for (int t = 0; t < 2; ++t) {
         e = launch_fft("fft_e_kernel(W)", plan, tw,
-                       LoadW{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
-                       StoreSpec{Wh, L, wcols, L}, wcols, d.Nkz, st);
+                       LoadWT<C>{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
+                       StoreSpecT<C>{Wh, L, wcols, L}, wcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(W)", st,
                   dft_k_kernel<<<grid_for((size_t)L * wcols, 256), 256, 0, st>>>(Wh, d.Nkz, d.Nkz, (size_t)L * wcols,
                                                                                  0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadG{p.G[t], d.NE, gcols}, StoreSpec{Gh, L, gcols, L}, gcols,
-                       d.Nkz, st);
+        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
+                       gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(G)", st,
                   dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols,
                                                                                  0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        LoadLag ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpec{Kh, L, kcols, L}, kcols, d.Nqz, st);
+        LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
+        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(K)", st,
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols,
                                                                                  0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         SSE_TIMED("spec_adj_kernel", st,
-                  spec_adj_kernel<<<dim3((unsigned)nA, (unsigned)ac.nchunks), ac.threads, ac.smem, st>>>(
+                  spec_adj_kernel<T><<<dim3((unsigned)nA, (unsigned)ac.nchunks), ac.threads, ac.smem, st>>>(
                       ac, d, p.nbr, p.dH, Wh, Gh, Kh, Hh, part + (size_t)t * part_one, L, p.scale, status));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // grad D from H^t: emission lags -> D^t, absorption lags -> D^t'
@@ -1863,15 +1880,28 @@ cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Hh, d.Nkz, d.Nkz, (size_t)L * kcols,
                                                                                  1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        StoreGD sg{gD[t], gD[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9,
-                   p.scale / (double)nfreq, t, L};
-        e = launch_fft("fft_e_kernel(H)", plan, tw, LoadSpecConj{Hh, L, kcols}, sg, kcols, d.Nqz, st);
+        StoreGDT<C> sg{gD[t], gD[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9,
+                       p.scale / (double)nfreq, t, L};
+        e = launch_fft("fft_e_kernel(H)", plan, tw, LoadSpecConjT<C>{Hh, L, kcols}, sg, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
     }
     SSE_TIMED("spec_gdh_reduce_kernel", st,
               spec_gdh_reduce_kernel<<<grid_for(nA * d.NB * 3 * nel, 256), 256, 0, st>>>(d, ac.nchunks, part,
                                                                                          part + part_one, g_dH));
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
+                         double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
+                         cudaStream_t st) {
+    return spectral_bwd_t<double>(p, gS_less, gS_greater, g_dH, g_D_less, g_D_greater, status, ws, ws_bytes, st);
+}
+
+cudaError_t spectral_bwd32(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
+                           double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
+                           cudaStream_t st) {
+    return spectral_bwd_t<float>(p, gS_less, gS_greater, g_dH, g_D_less, g_D_greater, status, ws, ws_bytes, st);
 }
 
 struct GradGLayout {

@@ -1,6 +1,8 @@
-"""Transform-based FP64 adjoint (sse_sigma_bwd, mode FP64_FFT) against the oracle and the direct FP64 adjoint.
+"""Transform-based adjoint (sse_sigma_bwd, modes FP64_FFT and FP32_FFT) against the oracle and the direct FP64
+adjoint.
 
-Tolerance: normwise 1e-12 per gradient tensor (g_dH, g_D^<, g_D^>), as for the direct FP64 adjoint.
+Tolerance: normwise 1e-12 per gradient tensor (g_dH, g_D^<, g_D^>) for FP64_FFT, as for the direct FP64 adjoint;
+the stated FP32_FFT bound below for the mixed adjoint.
 """
 import math
 
@@ -87,3 +89,55 @@ def test_adjoint_workload_vs_direct():
     for x, y in zip(got, ref):
         err = float((x - y).abs().max() / y.abs().max())
         assert err <= TOL, err
+
+
+# FP32 transforms and products: per-frequency relative error ~1e-7 (unit roundoff 6e-8 times the transform
+# depth); the coupling gradient sums Nkz*L frequency terms that partly cancel, so its normwise error grows with
+# the size (9e-7 at the adjoint workload, 3e-6 at FinFET). Stated bound for every workload tested: 1e-5.
+FP32_BOUND = 1e-5
+
+
+@pytest.mark.parametrize("dims", [
+    TINY,
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),
+    Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11),
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),
+], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nkz{d.Nkz}")
+def test_fp32_adjoint_vs_oracle(dims):
+    """Mode FP32_FFT of sse_sigma_bwd: FP32 transforms and products, FP64 partial sums."""
+    nbr = ring_neighbours(dims.NA, dims.NB) if dims is not TINY else None
+    inp = make_inputs(dims, seed=dims.Norb + 900, nbr=nbr)
+    W, V = make_upstream(dims, seed=dims.Norb + 901)
+    got = gpu_grad(inp, W, V, mode="fp32_fft", check=True)
+    ref = oracle_grad(inp, W, V)
+    errs = [normwise(x.cpu().numpy(), y) for x, y in zip(got, ref)]
+    print("fp32 adjoint", dims, errs)
+    assert max(errs) <= FP32_BOUND
+
+
+def test_fp32_adjoint_workload_vs_fp64():
+    inp = make_inputs(ADJOINT, seed=7, device="cuda")
+    W, V = make_upstream(ADJOINT, seed=8, device="cuda")
+    args = (inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, W, V)
+    got = B.sigma_grad(*args, mode="fp32_fft", check=True)
+    ref = B.sigma_grad(*args, mode="fp64_fft")
+    errs = [float((x - y).abs().max() / y.abs().max()) for x, y in zip(got, ref)]
+    print("fp32 adjoint at the adjoint workload", errs)
+    assert max(errs) <= FP32_BOUND
+
+
+def test_fp32_autograd_end_to_end():
+    """sigma_autograd with mode fp32_fft: FP32_FFT forward and FP32_FFT adjoint, gradients for every input
+    (G through sse_sigma_bwd_g in FP64) within the FP32 bound of the oracle."""
+    d = Dims(NA=6, NB=2, Norb=3, NE=20, Nkz=3, Nqz=2, Nw=4)
+    inp = make_inputs(d, seed=31, nbr=ring_neighbours(6, 2))
+    W, V = make_upstream(d, seed=32)
+    g = inp.to("cuda")
+    leaves = [t.clone().requires_grad_(True) for t in (g.dH, g.D_less, g.D_greater, g.G_less, g.G_greater)]
+    Sl, Sg = B.sigma_autograd(*leaves, g.nbr, SCALE, "fp32_fft")
+    loss = (W.cuda().conj() * Sl).real.sum() + (V.cuda().conj() * Sg).real.sum()
+    loss.backward()
+    ref = tuple(oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, W, V))
+    ref += tuple(oracle.sigma_grad_G(inp.nbr, inp.dH, inp.D_less, inp.D_greater, SCALE, W, V))
+    for leaf, r in zip(leaves, ref):
+        assert normwise(leaf.grad.cpu().numpy(), r) <= FP32_BOUND
