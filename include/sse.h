@@ -178,8 +178,8 @@ SSE_API int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const doub
  *   g_dH_m(a,s)         = sum_{t,E,k,q,w,sigma} sum_j conj(i*scale*D_mj) gS dH_j G^H
  *                                              + sum_i i*scale*D_im gS^H dH_i G
  * gS_less / gS_greater have the layout of S^t. Gradient blocks of atoms in
- * [a_begin, a_end) are fully overwritten; others are untouched. G is not
- * differentiated. The gathered G tiles are recomputed, not stored. */
+ * [a_begin, a_end) are fully overwritten; others are untouched. The gradient with respect
+ * to G is sse_sigma_bwd_g's. The gathered G tiles are recomputed, not stored. */
 SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
                   const double* D_greater, const double* G_less, const double* G_greater, double scale, int mode,
                   uint32_t flags, const double* gS_less, const double* gS_greater, double* g_dH, double* g_D_less,
@@ -191,8 +191,10 @@ SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* d
  *                     over (q, w, sigma) with E = E' + sigma*(w+1) in [0, NE), k = (k'+q) mod Nkz:
  *                     sum_ij conj(i*scale * D^tau_ij(q,w,a,s)) dH_i(a,s)^H gS^t_a(E,k) dH_j(a,s).
  * g_G_less / g_G_greater have the layout of G and are fully overwritten for every atom (zero where
- * no bond in range reaches). FP64 through the transforms (modes FP64 and FP64_FFT): per atom and
- * frequency, the bonds into it in (a, s) order from a list built on the device (deterministic sums).
+ * no bond in range reaches). Through the transforms, in FP64 (modes FP64 and FP64_FFT) or with FP32
+ * transforms and block products (mode FP32_FFT; FP64 inputs and outputs); TF32 and BF16X3 return
+ * SSE_ERR_UNSUPPORTED. Per atom and frequency, the bonds into it in (a, s) order from a list built on
+ * the device (deterministic sums).
  * SYMMETRIZE projects gS as in sse_sigma_bwd. Workspace: sse_sigma_bwd_g_workspace_bytes(). */
 SSE_API size_t sse_sigma_bwd_g_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
 SSE_API int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,

@@ -353,20 +353,22 @@ def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 
 
 def sigma_grad_G(dH, D_less, D_greater, nbr, gS_less, gS_greater, scale: float = 1.0 / (2.0 * math.pi),
                  symmetrize: bool = False, check: bool = False, atoms=None, ws: Optional[torch.Tensor] = None,
-                 stream=None, profile: bool = False):
-    """Gradients (g_G_less, g_G_greater) of sum_t Re tr(gS^t^H Sigma^t) with respect to G via sse_sigma_bwd_g."""
+                 stream=None, profile: bool = False, mode="fp64_fft"):
+    """Gradients (g_G_less, g_G_greater) of sum_t Re tr(gS^t^H Sigma^t) with respect to G via sse_sigma_bwd_g
+    (mode fp64_fft: FP64 transforms; fp32_fft: FP32 transforms and products)."""
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
     d = dims_of(gS_less, D_less, dH, atoms)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
     flags |= SSE_FLAG_PROFILE if profile else 0
     gSl, gSg = gS_less.contiguous(), gS_greater.contiguous()
     g_Gl, g_Gg = torch.empty_like(gSl), torch.empty_like(gSg)
     if ws is None:
-        n = sse_sigma_bwd_g_workspace_bytes(d, SSE_MODE_FP64_FFT, flags)
+        n = sse_sigma_bwd_g_workspace_bytes(d, m, flags)
         if n == 0:
             raise ValueError("invalid or unsupported problem sizes for libsse")
         ws = torch.empty(n, dtype=torch.uint8, device=dH.device)
-    rc = sse_sigma_bwd_g(d, nbr, dH, D_less, D_greater, scale, SSE_MODE_FP64_FFT, flags, gSl, gSg, g_Gl, g_Gg, ws,
-                         ws.numel(), stream)
+    rc = sse_sigma_bwd_g(d, nbr, dH, D_less, D_greater, scale, m, flags, gSl, gSg, g_Gl, g_Gg, ws, ws.numel(),
+                         stream)
     if rc != 0:
         raise SseError(rc, "sse_sigma_bwd_g")
     return g_Gl, g_Gg
@@ -405,7 +407,8 @@ class SigmaFunction(torch.autograd.Function):
                        symmetrize=ctx.symmetrize, mode=ctx.bwd_mode)
         gG = (None, None)
         if ctx.needs_input_grad[3] or ctx.needs_input_grad[4]:
-            gG = sigma_grad_G(dH, D_less, D_greater, nbr, gSl, gSg, scale=ctx.scale, symmetrize=ctx.symmetrize)
+            gG = sigma_grad_G(dH, D_less, D_greater, nbr, gSl, gSg, scale=ctx.scale, symmetrize=ctx.symmetrize,
+                              mode="fp32_fft" if ctx.bwd_mode == "fp32_fft" else "fp64_fft")
         return g[0], g[1], g[2], gG[0], gG[1], None, None, None, None
 
 

@@ -245,9 +245,16 @@ extern "C" int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* d
     return finish(e, status, flags, st);
 }
 
+namespace {
+// FP64 and FP64_FFT: FP64 transforms; FP32_FFT: FP32 transforms and products.
+size_t gradg_workspace(const sse_dims& d, int mode) {
+    return mode == SSE_MODE_FP32_FFT ? sse::spectral_bwd_g32_workspace(d) : sse::spectral_bwd_g_workspace(d);
+}
+}  // namespace
+
 extern "C" size_t sse_sigma_bwd_g_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
     if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
-    return sse::kStatusBytes + sse::spectral_bwd_g_workspace(*d);
+    return sse::kStatusBytes + gradg_workspace(*d, mode);
 }
 
 extern "C" int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
@@ -261,19 +268,18 @@ extern "C" int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const doub
     if (!aligned(nbr, 4) || !aligned(dH, 16) || !aligned(D_less, 16) || !aligned(D_greater, 16) ||
         !aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_G_less, 16) || !aligned(g_G_greater, 16))
         return SSE_ERR_INVALID_ARG;
-    if (!supported_dims(d) || !fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
-    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::spectral_bwd_g_workspace(*d))
+    if (!supported_dims(d) || !(fp64_mode(mode) || mode == SSE_MODE_FP32_FFT)) return SSE_ERR_UNSUPPORTED;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + gradg_workspace(*d, mode))
         return SSE_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned* status = static_cast<unsigned*>(workspace);
     if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
     // G does not enter the gradient (Sigma is linear in G); the Problem's G pointers stay null
     const sse::Problem p = make_problem(d, nbr, dH, D_less, D_greater, nullptr, nullptr, scale, flags);
-    cudaError_t e = sse::spectral_bwd_g(p, reinterpret_cast<const double2*>(gS_less),
-                                        reinterpret_cast<const double2*>(gS_greater),
-                                        reinterpret_cast<double2*>(g_G_less), reinterpret_cast<double2*>(g_G_greater),
-                                        status, static_cast<char*>(workspace) + sse::kStatusBytes,
-                                        ws_bytes - sse::kStatusBytes, st);
+    auto* run = mode == SSE_MODE_FP32_FFT ? sse::spectral_bwd_g32 : sse::spectral_bwd_g;
+    cudaError_t e = run(p, reinterpret_cast<const double2*>(gS_less), reinterpret_cast<const double2*>(gS_greater),
+                        reinterpret_cast<double2*>(g_G_less), reinterpret_cast<double2*>(g_G_greater), status,
+                        static_cast<char*>(workspace) + sse::kStatusBytes, ws_bytes - sse::kStatusBytes, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }

@@ -93,10 +93,15 @@ cudaError_t spectral_bwd32(const Problem& p, const double2* gS_less, const doubl
                            double2* g_D_less, double2* g_D_greater, unsigned* status, void* ws, size_t ws_bytes,
                            cudaStream_t st);
 
-// Gradient with respect to G, transform-based FP64 (sse_spectral.cu).
+// Gradient with respect to G, transform-based: FP64 (spectral_bwd_g) or FP32 transforms and products with FP64
+// inputs and outputs (spectral_bwd_g32) (sse_spectral.cu).
 size_t spectral_bwd_g_workspace(const sse_dims& d);
 cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_G_less,
                            double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t spectral_bwd_g32_workspace(const sse_dims& d);
+cudaError_t spectral_bwd_g32(const Problem& p, const double2* gS_less, const double2* gS_greater,
+                             double2* g_G_less, double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes,
+                             cudaStream_t st);
 
 // Phonon self-energy of Eq. (4), transform-based FP64 (sse_spectral.cu).
 size_t spectral_pi_workspace(const sse_dims& d);

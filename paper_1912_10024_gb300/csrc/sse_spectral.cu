@@ -1148,10 +1148,12 @@ __global__ void inbond_fill_kernel(sse_dims d, const int32_t* __restrict__ nbr, 
     }
 }
 
+template <class T>
 __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__ off, const int* __restrict__ list,
-                                  const double2* __restrict__ dH, const double2* __restrict__ What,
-                                  const double2* __restrict__ Khat, double2* __restrict__ Rhat, int L,
-                                  double scale) {
+                                  const double2* __restrict__ dH, const typename CX<T>::C* __restrict__ What,
+                                  const typename CX<T>::C* __restrict__ Khat, typename CX<T>::C* __restrict__ Rhat,
+                                  int L, double scale) {
+    using C = typename CX<T>::C;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Norb = d.Norb, nel = c.nel;
     const int b = blockIdx.x;  // target atom
@@ -1160,11 +1162,11 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
     const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
     const size_t f_end = min(nfreq, f_begin + c.fchunk);
     // region reuse of the forward's layout: A = one bond's 3 x 4 planes, G = W^ planes, W = B_i planes, U = U_i
-    double* sA = reinterpret_cast<double*>(smem + c.off_A);
-    double* sWa = reinterpret_cast<double*>(smem + c.off_G);
-    double2* sK = reinterpret_cast<double2*>(smem + c.off_K);
-    double* sB = reinterpret_cast<double*>(smem + c.off_W);
-    double* sU = reinterpret_cast<double*>(smem + c.off_U);
+    T* sA = reinterpret_cast<T*>(smem + c.off_A);
+    T* sWa = reinterpret_cast<T*>(smem + c.off_G);
+    C* sK = reinterpret_cast<C*>(smem + c.off_K);
+    T* sB = reinterpret_cast<T*>(smem + c.off_W);
+    T* sU = reinterpret_cast<T*>(smem + c.off_U);
     const int tid = threadIdx.x;
     const int fl = tid / nel, e = tid - fl * nel;
     const int m = e / Norb, n = e - m * Norb;
@@ -1174,34 +1176,35 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
     for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
         const size_t f = f0 + fl;
         const bool act = lane && f < f_end;
-        double T1 = 0.0, T2 = 0.0, T3 = 0.0;
+        T T1 = 0, T2 = 0, T3 = 0;
         for (int ib = i0; ib < i1; ++ib) {
             const int bond = list[ib];  // (a - a_begin) * NB + s
             const int la = bond / d.NB;
             __syncthreads();  // previous bond done with sA, sWa, sK, sB, sU
             for (int i = tid; i < 3 * nel; i += blockDim.x) {
                 const double2 v = dH[((size_t)d.a_begin * d.NB + bond) * 3 * nel + i];
-                double* P = sA + (size_t)(i / nel) * 4 * nel;
+                T* P = sA + (size_t)(i / nel) * 4 * nel;
                 const int ee = i % nel;
-                P[ee] = v.x;
-                P[nel + ee] = v.y;
-                P[2 * nel + ee] = v.x + v.y;
-                P[3 * nel + ee] = v.x - v.y;
+                const T vr = (T)v.x, vi = (T)v.y;
+                P[ee] = vr;
+                P[nel + ee] = vi;
+                P[2 * nel + ee] = vr + vi;
+                P[3 * nel + ee] = vr - vi;
             }
             if (lane) {
-                double2 w = make_double2(0.0, 0.0);
+                C w = CT<C>::mk(0, 0);
                 if (act) w = What[(f * nA + la) * nel + e];
                 put3(sWa + (size_t)fl * 3 * nel, nel, e, w);
             }
             for (int i = tid; i < c.F * 9; i += blockDim.x) {
                 const int fk = i / 9, ij = i - fk * 9;
                 const size_t ff = f0 + fk;
-                sK[i] = ff < f_end ? Khat[(ff * nA * d.NB + bond) * 9 + ij] : make_double2(0.0, 0.0);
+                sK[i] = ff < f_end ? Khat[(ff * nA * d.NB + bond) * 9 + ij] : CT<C>::mk(0, 0);
             }
             __syncthreads();
             // B_i[m][n] = sum_j conj(K_ij) A_j[m][n]
             if (lane) {
-                double ar[3], ai[3];
+                T ar[3], ai[3];
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     ar[j] = sA[(size_t)j * 4 * nel + e];
@@ -1209,10 +1212,10 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
                 }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    double2 acc = make_double2(0.0, 0.0);
+                    C acc = CT<C>::mk(0, 0);
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        const double2 k = sK[fl * 9 + i * 3 + j];  // conj(k) A = (kx ar + ky ai, kx ai - ky ar)
+                        const C k = sK[fl * 9 + i * 3 + j];  // conj(k) A = (kx ar + ky ai, kx ai - ky ar)
                         acc.x = fma(k.x, ar[j], acc.x);
                         acc.x = fma(k.y, ai[j], acc.x);
                         acc.y = fma(k.x, ai[j], acc.y);
@@ -1224,18 +1227,18 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
             __syncthreads();
             // U_i = W^ B_i
             if (lane) {
-                const double* Wp = sWa + (size_t)fl * 3 * nel;
+                const T* Wp = sWa + (size_t)fl * 3 * nel;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    const double* Bp = sB + ((size_t)fl * 3 + i) * 3 * nel;
-                    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+                    const T* Bp = sB + ((size_t)fl * 3 + i) * 3 * nel;
+                    T t1 = 0, t2 = 0, t3 = 0;
                     for (int l = 0; l < Norb; ++l) {
                         const int ml = m * Norb + l, ln = l * Norb + n;
                         t1 = fma(Wp[ml], Bp[ln], t1);
                         t2 = fma(Wp[nel + ml], Bp[nel + ln], t2);
                         t3 = fma(Wp[2 * nel + ml], Bp[2 * nel + ln], t3);
                     }
-                    put3(sU + ((size_t)fl * 3 + i) * 3 * nel, nel, e, make_double2(t1 - t2, t3 - t1 - t2));
+                    put3(sU + ((size_t)fl * 3 + i) * 3 * nel, nel, e, CT<C>::mk(t1 - t2, t3 - t1 - t2));
                 }
             }
             __syncthreads();
@@ -1243,8 +1246,8 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
             if (lane) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    const double* Ap = sA + (size_t)i * 4 * nel;
-                    const double* Up = sU + ((size_t)fl * 3 + i) * 3 * nel;
+                    const T* Ap = sA + (size_t)i * 4 * nel;
+                    const T* Up = sU + ((size_t)fl * 3 + i) * 3 * nel;
                     for (int l = 0; l < Norb; ++l) {
                         const int lm = l * Norb + m, ln = l * Norb + n;
                         T1 = fma(Ap[lm], Up[ln], T1);
@@ -1256,8 +1259,8 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
         }
         if (act) {
             // sum conj(A) U: re = T1 + T2, im = T3 - T1 + T2; times conj(c) = -i*scale
-            const double re = T1 + T2, im = T3 - T1 + T2;
-            Rhat[(f * d.NA + b) * nel + e] = make_double2(scale * im, -scale * re);
+            const T re = T1 + T2, im = T3 - T1 + T2;
+            Rhat[(f * d.NA + b) * nel + e] = CT<C>::mk((T)(scale * im), (T)(-scale * re));
         }
     }
 }
@@ -1909,16 +1912,16 @@ struct GradGLayout {
     size_t off_tw, off_W, off_K, off_R, off_cnt, off_off, off_list, total;
 };
 
-GradGLayout gradg_layout(const sse_dims& d) {
+GradGLayout gradg_layout(const sse_dims& d, size_t csz = 16) {  // csz: bytes per complex spectrum entry
     GradGLayout l{};
     l.L = spectral_length(d);
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t spec = (size_t)d.Nkz * l.L;
     l.off_tw = 0;
     l.off_W = align256((size_t)l.L * 16);
-    l.off_K = align256(l.off_W + spec * nA * nel * 16);
-    l.off_R = align256(l.off_K + spec * nA * d.NB * 9 * 16);
-    l.off_cnt = align256(l.off_R + spec * d.NA * nel * 16);
+    l.off_K = align256(l.off_W + spec * nA * nel * csz);
+    l.off_R = align256(l.off_K + spec * nA * d.NB * 9 * csz);
+    l.off_cnt = align256(l.off_R + spec * d.NA * nel * csz);
     l.off_off = align256(l.off_cnt + (size_t)d.NA * 4);
     l.off_list = align256(l.off_off + ((size_t)d.NA + 1) * 4);
     l.total = align256(l.off_list + nA * d.NB * 4 + 4);
@@ -1926,23 +1929,30 @@ GradGLayout gradg_layout(const sse_dims& d) {
 }
 
 size_t spectral_bwd_g_workspace(const sse_dims& d) { return gradg_layout(d).total; }
+size_t spectral_bwd_g32_workspace(const sse_dims& d) { return gradg_layout(d, 8).total; }
 
-cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_G_less,
-                           double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+namespace {
+// The gradient with respect to G in the real type T: double (FP64_FFT) or float (FP32_FFT: FP32 transforms and
+// products, FP64 inputs and outputs).
+template <class T>
+cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const double2* gS_greater,
+                             double2* g_G_less, double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+    using C = typename CX<T>::C;
     const sse_dims& d = p.d;
     if (!spectral_supported(d)) return cudaErrorNotSupported;
-    const GradGLayout lay = gradg_layout(d);
+    const GradGLayout lay = gradg_layout(d, sizeof(C));
     if (ws_bytes < lay.total) return cudaErrorInvalidValue;
     unsigned char* base = static_cast<unsigned char*>(ws);
     double2* tw = reinterpret_cast<double2*>(base + lay.off_tw);
-    double2* Wh = reinterpret_cast<double2*>(base + lay.off_W);
-    double2* Kh = reinterpret_cast<double2*>(base + lay.off_K);
-    double2* Rh = reinterpret_cast<double2*>(base + lay.off_R);
+    C* Wh = reinterpret_cast<C*>(base + lay.off_W);
+    C* Kh = reinterpret_cast<C*>(base + lay.off_K);
+    C* Rh = reinterpret_cast<C*>(base + lay.off_R);
     int* cnt = reinterpret_cast<int*>(base + lay.off_cnt);
     int* offs = reinterpret_cast<int*>(base + lay.off_off);
     int* list = reinterpret_cast<int*>(base + lay.off_list);
     const int L = lay.L;
-    const FftPlan plan = make_plan(L);
+    const FftPlan plan = make_plan(L, (int)sizeof(C));
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t gcols = (size_t)d.NA * nel, wcols = nA * nel, kcols = nA * d.NB * 9;
     const size_t nfreq = (size_t)d.Nkz * L;
@@ -1962,9 +1972,9 @@ cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const doubl
     dall.a_begin = 0;
     dall.a_end = d.NA;
     dall.NB = d.NB < 2 ? 2 : d.NB;  // the A region holds one bond's 3 x 4 planes (>= 12 Norb^2 doubles)
-    ProdCfg pc = make_prod_cfg(dall, nfreq);
+    ProdCfg pc = make_prod_cfg(dall, nfreq, (int)sizeof(T));
     if (pc.smem > 227 * 1024) return cudaErrorNotSupported;
-    if ((e = cudaFuncSetAttribute(spec_gradg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
+    if ((e = cudaFuncSetAttribute(spec_gradg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
         cudaSuccess)
         return e;
     const double2* W[2] = {gS_less, gS_greater};
@@ -1973,15 +1983,15 @@ cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const doubl
     for (int t = 0; t < 2; ++t) {
         if (nA > 0) {
             e = launch_fft("fft_e_kernel(W)", plan, tw,
-                           LoadW{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
-                           StoreSpec{Wh, L, wcols, L}, wcols, d.Nkz, st);
+                           LoadWT<C>{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
+                           StoreSpecT<C>{Wh, L, wcols, L}, wcols, d.Nkz, st);
             if (e != cudaSuccess) return e;
             SSE_TIMED("dft_k_kernel(W)", st,
                       dft_k_kernel<<<grid_for((size_t)L * wcols, 256), 256, 0, st>>>(Wh, d.Nkz, d.Nkz,
                                                                                      (size_t)L * wcols, 0));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            LoadLag ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-            e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpec{Kh, L, kcols, L}, kcols, d.Nqz, st);
+            LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
+            e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
             if (e != cudaSuccess) return e;
             SSE_TIMED("dft_k_kernel(K)", st,
                       dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz,
@@ -1990,7 +2000,7 @@ cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const doubl
         }
         const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
         SSE_TIMED("spec_gradg_kernel", st,
-                  spec_gradg_kernel<<<dim3((unsigned)d.NA, (unsigned)gy), pc.threads, pc.smem, st>>>(
+                  spec_gradg_kernel<T><<<dim3((unsigned)d.NA, (unsigned)gy), pc.threads, pc.smem, st>>>(
                       pc, d, offs, list, p.dH, Wh, Kh, Rh, L, p.scale));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(R)", st,
@@ -1998,11 +2008,23 @@ cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const doubl
                                                                                  1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
-        e = launch_fft("fft_e_kernel(R)", plan, tw, LoadSpecConj{Rh, L, gcols},
-                       StoreSigma{gG[t], d.NE, gcols, 0, inv, d.NE}, gcols, d.Nkz, st);
+        e = launch_fft("fft_e_kernel(R)", plan, tw, LoadSpecConjT<C>{Rh, L, gcols},
+                       StoreSigmaT<C>{gG[t], d.NE, gcols, 0, inv, d.NE}, gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_G_less,
+                           double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st) {
+    return spectral_bwd_g_t<double>(p, gS_less, gS_greater, g_G_less, g_G_greater, status, ws, ws_bytes, st);
+}
+
+cudaError_t spectral_bwd_g32(const Problem& p, const double2* gS_less, const double2* gS_greater,
+                             double2* g_G_less, double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+    return spectral_bwd_g_t<float>(p, gS_less, gS_greater, g_G_less, g_G_greater, status, ws, ws_bytes, st);
 }
 
 }  // namespace sse

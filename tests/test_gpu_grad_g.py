@@ -1,6 +1,7 @@
-"""Gradient of Eq. (3) with respect to G (sse_sigma_bwd_g, FP64 through the transforms) against the oracle.
+"""Gradient of Eq. (3) with respect to G (sse_sigma_bwd_g through the transforms, FP64 and FP32_FFT) against the
+oracle.
 
-Tolerance: normwise 1e-12 per gradient tensor. At the adjoint workload, where the oracle would take too long
+Tolerance: normwise 1e-12 per gradient tensor in FP64; the stated FP32_FFT bound below for the FP32 path. At the adjoint workload, where the oracle would take too long
 for every atom, the identity Re <grad_G, dG> = sum_t Re tr(W^t^H Sigma^t(dG)) (Sigma is linear in G) is
 checked with the GPU forward on random dG.
 """
@@ -99,3 +100,36 @@ def test_adjoint_workload_dot_product():
     lhs = float((W.conj() * Sl).real.sum() + (V.conj() * Sg).real.sum())
     rhs = float((gl.conj() * dl).real.sum() + (gg.conj() * dg).real.sum())
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+
+
+# mode FP32_FFT: FP32 transforms and block products (per-frequency relative error ~1e-7); stated bound 1e-5,
+# as for the FP32 adjoint of sse_sigma_bwd
+FP32_BOUND = 1e-5
+
+
+@pytest.mark.parametrize("dims", [
+    TINY,
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),
+    Dims(NA=5, NB=2, Norb=10, NE=24, Nkz=3, Nqz=2, Nw=7),
+    Dims(NA=6, NB=3, Norb=1, NE=40, Nkz=1, Nqz=1, Nw=9),
+], ids=lambda d: f"NB{d.NB}_Norb{d.Norb}_NE{d.NE}_Nkz{d.Nkz}")
+def test_fp32_vs_oracle(dims):
+    nbr = None if dims is TINY else ring_neighbours(dims.NA, dims.NB)
+    inp = make_inputs(dims, seed=dims.Norb + 520, nbr=nbr)
+    W, V = make_upstream(dims, seed=dims.Norb + 521)
+    got = gpu(inp, W, V, check=True, mode="fp32_fft")
+    ref = orc(inp, W, V)
+    errs = [normwise(x.cpu().numpy(), y) for x, y in zip(got, ref)]
+    print("fp32 grad G", dims, errs)
+    assert max(errs) <= FP32_BOUND
+
+
+def test_fp32_adjoint_workload_vs_fp64():
+    inp = make_inputs(ADJOINT, seed=60, device="cuda")
+    W, V = make_upstream(ADJOINT, seed=61, device="cuda")
+    args = (inp.dH, inp.D_less, inp.D_greater, inp.nbr, W, V)
+    got = B.sigma_grad_G(*args, check=True, mode="fp32_fft")
+    ref = B.sigma_grad_G(*args)
+    errs = [float((x - y).abs().max() / y.abs().max()) for x, y in zip(got, ref)]
+    print("fp32 grad G at the adjoint workload", errs)
+    assert max(errs) <= FP32_BOUND
