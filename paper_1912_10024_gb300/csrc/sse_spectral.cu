@@ -33,17 +33,25 @@
 namespace sse {
 namespace {
 
-constexpr int kFftThreads = 256;
-constexpr int kFftSmemBudget = 100 * 1024;  // two CTAs per SM
-constexpr int kFftLoadBatch = 8;             // global loads in flight per thread
+// Transform CTAs: 512 threads and at most 100 KB of shared memory, two CTAs (32 warps) per SM; each thread keeps
+// 8 global loads in flight. The FP32 transforms are bound by the latency of those loads (the shape was chosen by
+// timing 256/512/1024 threads and 8/12/16 loads), the FP64 ones by the FP64 pipe.
+constexpr int kFftThreads = 512;
+constexpr int kFftSmemBudget = 100 * 1024;
+constexpr int kFftLoadBatch = 8;
 constexpr int kMaxStages = 24;
 constexpr int kMaxNk = 16;  // kz grid sizes handled by the small DFT pass
 
 struct FftPlan {
     int L, C, nst;
     int radix[kMaxStages];
-    int smem;  // two L x C buffers + the twiddle table
+    int ns[kMaxStages];           // product of the earlier stages' radices
+    int ns_shift[kMaxStages];     // log2(ns) if ns is a power of two, else -1
+    unsigned ns_mul[kMaxStages];  // floor(2^32 / ns) + 1: j / ns = umulhi(j, ns_mul), exact for j, ns < 2^16
+    int smem;                     // two L x C buffers + the twiddle table
 };
+
+constexpr int kFftMaxLength = 1 << 16;  // bound of the umulhi quotient
 
 FftPlan make_plan(int L, int esz = 16) {
     FftPlan p{};
@@ -52,6 +60,15 @@ FftPlan make_plan(int L, int esz = 16) {
     while (m % 4 == 0) p.radix[p.nst++] = 4, m /= 4;
     while (m % 2 == 0) p.radix[p.nst++] = 2, m /= 2;
     while (m % 3 == 0) p.radix[p.nst++] = 3, m /= 3;
+    int ns = 1;
+    for (int s = 0; s < p.nst; ++s) {
+        p.ns[s] = ns;
+        p.ns_shift[s] = -1;
+        for (int b = 0; b < 31; ++b)
+            if ((1 << b) == ns) p.ns_shift[s] = b;
+        p.ns_mul[s] = (unsigned)((1ull << 32) / (unsigned long long)ns + 1ull);
+        ns *= p.radix[s];
+    }
     p.C = 16;
     while (p.C > 1 && (2 * (size_t)L * p.C + L) * esz > (size_t)kFftSmemBudget) p.C /= 2;
     p.smem = (int)((2 * (size_t)L * p.C + L) * esz);
@@ -105,14 +122,14 @@ __global__ void twiddle_kernel(int L, double2* __restrict__ tw) {
     }
 }
 
-// In-place forward DFT of R values (R in {2, 3, 4}); tw is the length-L table.
-template <class C>
-__device__ __forceinline__ void dft_small(int R, C* v, const C* tw, int L) {
-    if (R == 2) {
+// In-place forward DFT of R values (R in {2, 3, 4}); w3 = exp(-2 pi i / 3) from the twiddle table.
+template <int R, class C>
+__device__ __forceinline__ void dft_small(C* v, C w3) {
+    if constexpr (R == 2) {
         const C a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
-    } else if (R == 4) {
+    } else if constexpr (R == 4) {
         const C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
         const C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
         const C md13 = CT<C>::mk(d13.y, -d13.x);  // -i * d13
@@ -120,42 +137,57 @@ __device__ __forceinline__ void dft_small(int R, C* v, const C* tw, int L) {
         v[2] = csub(s02, s13);
         v[1] = cadd(d02, md13);
         v[3] = csub(d02, md13);
-    } else if (R == 3) {
-        const C w1 = tw[L / 3];  // exp(-2 pi i / 3) = (-1/2, -sqrt(3)/2)
+    } else {
+        static_assert(R == 3, "radix 2, 3 or 4");
         const C t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
-        const C m = CT<C>::mk(v[0].x + w1.x * t.x, v[0].y + w1.x * t.y);
-        const C r = CT<C>::mk(-w1.y * d.y, w1.y * d.x);  // i * Im(w1) * d
+        const C m = CT<C>::mk(v[0].x + w3.x * t.x, v[0].y + w3.x * t.y);
+        const C r = CT<C>::mk(-w3.y * d.y, w3.y * d.x);  // i * Im(w3) * d
         v[0] = cadd(v[0], t);
         v[1] = cadd(m, r);
         v[2] = csub(m, r);
     }
 }
 
-// Stockham autosort FFT of C columns stored [L][C] in `src`; returns the buffer holding the result.
-template <class C>
+// One Stockham stage of radix R on CC columns stored [L][CC]: butterfly j = q * Ns + k reads rows j + r * L/R,
+// multiplies by the twiddles exp(-2 pi i r k / (Ns R)) and writes rows q * Ns * R + k + r * Ns.
+template <int R, int CC, class C>
+__device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restrict__ dst, const C* __restrict__ tw,
+                                          int L, int Ns, int ns_shift, unsigned ns_mul) {
+    constexpr int lgC = CC == 1 ? 0 : CC == 2 ? 1 : CC == 4 ? 2 : CC == 8 ? 3 : 4;
+    static_assert((1 << lgC) == CC, "CC in {1, 2, 4, 8, 16}");
+    const int nb = L / R;
+    const int span = nb / Ns;  // L / (Ns R)
+    const C w3 = tw[L / 3 * (R == 3)];
+    for (int it = threadIdx.x; it < nb * CC; it += blockDim.x) {
+        const int c = it & (CC - 1), j = it >> lgC;
+        const int q = ns_shift >= 0 ? (j >> ns_shift) : (int)__umulhi((unsigned)j, ns_mul);
+        const int k = j - q * Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * CC + c];
+        if (k > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * span]);
+        }
+        dft_small<R>(v, w3);
+        const int d0 = q * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(d0 + r * Ns) * CC + c] = v[r];
+    }
+}
+
+// Stockham autosort FFT of CC columns stored [L][CC] in `src`; returns the buffer holding the result.
+template <int CC, class C>
 __device__ C* fft_columns(const FftPlan& p, C* src, C* dst, const C* tw) {
-    int Ns = 1;
     for (int st = 0; st < p.nst; ++st) {
         const int R = p.radix[st];
-        const int nb = p.L / R;
-        const int span = p.L / (Ns * R);
-        for (int it = threadIdx.x; it < nb * p.C; it += blockDim.x) {
-            const int j = it / p.C, c = it - j * p.C;
-            const int k = j % Ns;
-            C v[4];
-            for (int r = 0; r < R; ++r) {
-                v[r] = src[(size_t)(j + r * nb) * p.C + c];
-                if (r > 0 && k > 0) v[r] = cmul(v[r], tw[r * k * span]);
-            }
-            dft_small(R, v, tw, p.L);
-            const int d0 = (j / Ns) * Ns * R + k;
-            for (int r = 0; r < R; ++r) dst[(size_t)(d0 + r * Ns) * p.C + c] = v[r];
-        }
+        if (R == 4) fft_stage<4, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
+        else if (R == 2) fft_stage<2, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
+        else fft_stage<3, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
         __syncthreads();
         C* t = src;
         src = dst;
         dst = t;
-        Ns *= R;
     }
     return src;
 }
@@ -229,24 +261,25 @@ struct StoreSigmaT {  // S[k][E][a_begin*nel + col] = conj(v) * inv in FP64, E <
 };
 using StoreSigma = StoreSigmaT<double2>;
 
-template <class Load, class Store>
+template <class Load, class Store, int CC>
 __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const double2* __restrict__ tw_g, Load ld,
                                                             Store sv, size_t ncols) {
     using C = typename Load::C;
+    constexpr int lgC = CC == 1 ? 0 : CC == 2 ? 1 : CC == 4 ? 2 : CC == 8 ? 3 : 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + (size_t)p.L * p.C;
-    C* tw = b1 + (size_t)p.L * p.C;
-    const size_t col0 = (size_t)blockIdx.x * p.C;
+    C* b1 = b0 + p.L * CC;
+    C* tw = b1 + p.L * CC;
+    const size_t col0 = (size_t)blockIdx.x * CC;
     const int batch = blockIdx.y;
     for (int m = threadIdx.x; m < p.L; m += blockDim.x) tw[m] = CT<C>::mk(tw_g[m].x, tw_g[m].y);
-    const int n = p.L * p.C;
+    const int n = p.L * CC;
     for (int base = threadIdx.x; base < n; base += kFftLoadBatch * blockDim.x) {
         C v[kFftLoadBatch];
 #pragma unroll
         for (int u = 0; u < kFftLoadBatch; ++u) {
             const int it = base + u * blockDim.x;
-            const int r = it / p.C, c = it - r * p.C;
+            const int r = it >> lgC, c = it & (CC - 1);
             v[u] = (it < n && col0 + c < ncols) ? ld(batch, r, col0 + c) : CT<C>::mk(0, 0);
         }
 #pragma unroll
@@ -256,9 +289,9 @@ __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const dou
         }
     }
     __syncthreads();
-    const C* res = fft_columns<C>(p, b0, b1, tw);
-    for (int it = threadIdx.x; it < sv.rows * p.C; it += blockDim.x) {
-        const int r = it / p.C, c = it - r * p.C;
+    const C* res = fft_columns<CC>(p, b0, b1, tw);
+    for (int it = threadIdx.x; it < sv.rows * CC; it += blockDim.x) {
+        const int r = it >> lgC, c = it & (CC - 1);
         if (col0 + c < ncols) sv(batch, r, col0 + c, res[it]);
     }
 }
@@ -1278,6 +1311,9 @@ struct Prod32Cfg {
     int off_A, off_G, off_K, off_W, off_U, smem;
 };
 
+// FP32 products use the 4-multiply complex MAC on (re, im) planes: with shared-memory bandwidth, not the FP32
+// pipe, the limit, two planes per operand (4 loads per 16 FMAs of a 2 x 2 tile) beat the 3-multiply form's
+// three planes (6 loads per 12 FMAs).
 Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     Prod32Cfg c{};
     c.Np = d.Norb + (d.Norb & 1);
@@ -1286,14 +1322,14 @@ Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     c.pl = c.Np * c.Np;
     const int pb = c.pl * 4;  // bytes per plane
     auto a16 = [](int x) { return (x + 15) & ~15; };
-    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 9 * pb + F * (21 * pb + 9 * 8) + 64; });
+    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 6 * pb + F * (14 * pb + 9 * 8) + 64; });
     c.threads = ((c.F * c.T + 31) / 32) * 32;
-    c.off_A = 0;                                  // [NB][3 dir][3 planes] dH transposed: AT[l][m] = dH[m][l]
-    c.off_G = a16(c.off_A + d.NB * 9 * pb);       // [F][3 planes] G^ transposed: GT[l][m] = G^[m][l]
-    c.off_K = a16(c.off_G + c.F * 3 * pb);        // [F][9] float2
-    c.off_W = a16(c.off_K + c.F * 9 * 8);         // [F][3 i][3 planes] W_i row-major
-    c.off_U = a16(c.off_W + c.F * 9 * pb);        // [F][3 i][3 planes] U_i row-major
-    c.smem = a16(c.off_U + c.F * 9 * pb);
+    c.off_A = 0;                                  // [NB][3 dir][2 planes] dH transposed: AT[l][m] = dH[m][l]
+    c.off_G = a16(c.off_A + d.NB * 6 * pb);       // [F][2 planes] G^ transposed: GT[l][m] = G^[m][l]
+    c.off_K = a16(c.off_G + c.F * 2 * pb);        // [F][9] float2
+    c.off_W = a16(c.off_K + c.F * 9 * 8);         // [F][3 i][2 planes] W_i row-major
+    c.off_U = a16(c.off_W + c.F * 6 * pb);        // [F][3 i][2 planes] U_i row-major
+    c.smem = a16(c.off_U + c.F * 6 * pb);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
     size_t chunks = (want + nA - 1) / (nA ? nA : 1);
@@ -1306,6 +1342,22 @@ Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
 
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+
+// acc (2 x 2 complex tile, re/im of entries (0,0), (0,1), (1,0), (1,1)) += x y^T for the column pair
+// x = (xr, xi) and the row pair y = (yr, yi): 16 FMAs
+__device__ __forceinline__ void cmac_2x2(float* ar, float* ai, float2 xr, float2 xi, float2 yr, float2 yi) {
+    const float xrv[2] = {xr.x, xr.y}, xiv[2] = {xi.x, xi.y}, yrv[2] = {yr.x, yr.y}, yiv[2] = {yi.x, yi.y};
+#pragma unroll
+    for (int dm = 0; dm < 2; ++dm)
+#pragma unroll
+        for (int dn = 0; dn < 2; ++dn) {
+            const int q = dm * 2 + dn;
+            ar[q] = fmaf(xrv[dm], yrv[dn], ar[q]);
+            ar[q] = fmaf(-xiv[dm], yiv[dn], ar[q]);
+            ai[q] = fmaf(xrv[dm], yiv[dn], ai[q]);
+            ai[q] = fmaf(xiv[dm], yrv[dn], ai[q]);
+        }
+}
 
 __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ nbr,
                                    const double2* __restrict__ dH, const float2* __restrict__ Ghat,
@@ -1334,10 +1386,9 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
         const int l = e / Np, m = e - l * Np;
         double2 v = make_double2(0.0, 0.0);
         if (l < Norb && m < Norb) v = dH[((size_t)a * d.NB * 3 + sd) * nel + m * Norb + l];
-        float* P = sA + (size_t)sd * 3 * pl;
+        float* P = sA + (size_t)sd * 2 * pl;
         P[e] = (float)v.x;
         P[pl + e] = (float)v.y;
-        P[2 * pl + e] = (float)(v.x + v.y);
     }
     for (int s = 0; s < d.NB; ++s) {
         const int b = nbr[(size_t)a * d.NB + s];
@@ -1348,14 +1399,13 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
     for (size_t i0 = i_begin; i0 < i_end; i0 += c.F) {
         const bool act = lane && i0 + fl < i_end;
         const size_t f = act ? freq_of(fm, i0 + fl) : 0;
-        // accumulators of the 2 x 2 tile, Gauss components (re*re, im*im, (re+im)(re+im))
-        float T1[4] = {0, 0, 0, 0}, T2[4] = {0, 0, 0, 0}, T3[4] = {0, 0, 0, 0};
+        float accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};  // the 2 x 2 tile of sum_s sum_i dH_i U_i
         for (int s = 0; s < d.NB; ++s) {
             const int b = nbr[(size_t)a * d.NB + s];
             const bool bok = b >= 0 && b < d.NA;
             // G^_b(f) -> GT planes: element (m, n) goes to GT[n][m]
             if (lane) {
-                float* Gp = sG + (size_t)fl * 3 * pl;
+                float* Gp = sG + (size_t)fl * 2 * pl;
 #pragma unroll
                 for (int dm = 0; dm < 2; ++dm)
 #pragma unroll
@@ -1366,7 +1416,6 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                         const int o = n * Np + m;
                         Gp[o] = g.x;
                         Gp[pl + o] = g.y;
-                        Gp[2 * pl + o] = g.x + g.y;
                     }
             }
             for (int i = tid; i < c.F * 9; i += blockDim.x) {
@@ -1376,7 +1425,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                 sK[i] = k;
             }
             __syncthreads();
-            const float* A = sA + (size_t)s * 9 * pl;
+            const float* A = sA + (size_t)s * 6 * pl;
             // W_i[m][n] = sum_j K_ij conj(dH_j[n][m]) = sum_j K_ij conj(AT_j[m][n])
             if (lane) {
                 const float2* K = sK + fl * 9;
@@ -1386,8 +1435,8 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                     float2 ar[3], ai[3];
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        ar[j] = ld2(A + (size_t)j * 3 * pl + m * Np + n0);
-                        ai[j] = ld2(A + (size_t)j * 3 * pl + pl + m * Np + n0);
+                        ar[j] = ld2(A + (size_t)j * 2 * pl + m * Np + n0);
+                        ai[j] = ld2(A + (size_t)j * 2 * pl + pl + m * Np + n0);
                     }
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
@@ -1404,64 +1453,49 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                             wi1 = fmaf(k.y, ar[j].y, wi1);
                             wi1 = fmaf(-k.x, ai[j].y, wi1);
                         }
-                        float* Wp = sW + ((size_t)fl * 3 + i) * 3 * pl + m * Np + n0;
+                        float* Wp = sW + ((size_t)fl * 3 + i) * 2 * pl + m * Np + n0;
                         st2(Wp, wr0, wr1);
                         st2(Wp + pl, wi0, wi1);
-                        st2(Wp + 2 * pl, wr0 + wi0, wr1 + wi1);
                     }
                 }
             }
             __syncthreads();
-            // U_i = G^ W_i on the tile: U[m][n] = sum_l GT[l][m] W_i[l][n]
+            // U_i = G^ W_i for the three i together (one G^ load per l): U[m][n] = sum_l GT[l][m] W_i[l][n]
             if (lane) {
-                const float* Gp = sG + (size_t)fl * 3 * pl;
-#pragma unroll 1
-                for (int i = 0; i < 3; ++i) {
-                    const float* Wp = sW + ((size_t)fl * 3 + i) * 3 * pl;
-                    float u1[4] = {0, 0, 0, 0}, u2[4] = {0, 0, 0, 0}, u3[4] = {0, 0, 0, 0};
-                    for (int l = 0; l < Norb; ++l) {
-                        const float2 gr = ld2(Gp + l * Np + m0), gi = ld2(Gp + pl + l * Np + m0),
-                                     gs = ld2(Gp + 2 * pl + l * Np + m0);
-                        const float2 wr = ld2(Wp + l * Np + n0), wi = ld2(Wp + pl + l * Np + n0),
-                                     ws = ld2(Wp + 2 * pl + l * Np + n0);
-                        u1[0] = fmaf(gr.x, wr.x, u1[0]); u1[1] = fmaf(gr.x, wr.y, u1[1]);
-                        u1[2] = fmaf(gr.y, wr.x, u1[2]); u1[3] = fmaf(gr.y, wr.y, u1[3]);
-                        u2[0] = fmaf(gi.x, wi.x, u2[0]); u2[1] = fmaf(gi.x, wi.y, u2[1]);
-                        u2[2] = fmaf(gi.y, wi.x, u2[2]); u2[3] = fmaf(gi.y, wi.y, u2[3]);
-                        u3[0] = fmaf(gs.x, ws.x, u3[0]); u3[1] = fmaf(gs.x, ws.y, u3[1]);
-                        u3[2] = fmaf(gs.y, ws.x, u3[2]); u3[3] = fmaf(gs.y, ws.y, u3[3]);
+                const float* Gp = sG + (size_t)fl * 2 * pl;
+                const float* Wp = sW + (size_t)fl * 6 * pl;
+                float ur[3][4] = {}, ui[3][4] = {};
+                for (int l = 0; l < Norb; ++l) {
+                    const float2 gr = ld2(Gp + l * Np + m0), gi = ld2(Gp + pl + l * Np + m0);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const float2 wr = ld2(Wp + i * 2 * pl + l * Np + n0);
+                        const float2 wi = ld2(Wp + i * 2 * pl + pl + l * Np + n0);
+                        cmac_2x2(ur[i], ui[i], gr, gi, wr, wi);
                     }
-                    float* Up = sU + ((size_t)fl * 3 + i) * 3 * pl;
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
 #pragma unroll
                     for (int dm = 0; dm < 2; ++dm) {
-                        const int q0 = dm * 2, q1 = dm * 2 + 1;
-                        const float r0 = u1[q0] - u2[q0], i0v = u3[q0] - u1[q0] - u2[q0];
-                        const float r1 = u1[q1] - u2[q1], i1v = u3[q1] - u1[q1] - u2[q1];
                         float* o = Up + (m0 + dm) * Np + n0;
-                        st2(o, r0, r1);
-                        st2(o + pl, i0v, i1v);
-                        st2(o + 2 * pl, r0 + i0v, r1 + i1v);
+                        st2(o, ur[i][dm * 2], ur[i][dm * 2 + 1]);
+                        st2(o + pl, ui[i][dm * 2], ui[i][dm * 2 + 1]);
                     }
                 }
             }
             __syncthreads();
             // acc += sum_i dH_i U_i: acc[m][n] += sum_l AT_i[l][m] U_i[l][n]
             if (lane) {
-#pragma unroll 1
+#pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    const float* Ap = A + (size_t)i * 3 * pl;
-                    const float* Up = sU + ((size_t)fl * 3 + i) * 3 * pl;
+                    const float* Ap = A + (size_t)i * 2 * pl;
+                    const float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
                     for (int l = 0; l < Norb; ++l) {
-                        const float2 ar = ld2(Ap + l * Np + m0), ai = ld2(Ap + pl + l * Np + m0),
-                                     as = ld2(Ap + 2 * pl + l * Np + m0);
-                        const float2 ur = ld2(Up + l * Np + n0), ui = ld2(Up + pl + l * Np + n0),
-                                     us = ld2(Up + 2 * pl + l * Np + n0);
-                        T1[0] = fmaf(ar.x, ur.x, T1[0]); T1[1] = fmaf(ar.x, ur.y, T1[1]);
-                        T1[2] = fmaf(ar.y, ur.x, T1[2]); T1[3] = fmaf(ar.y, ur.y, T1[3]);
-                        T2[0] = fmaf(ai.x, ui.x, T2[0]); T2[1] = fmaf(ai.x, ui.y, T2[1]);
-                        T2[2] = fmaf(ai.y, ui.x, T2[2]); T2[3] = fmaf(ai.y, ui.y, T2[3]);
-                        T3[0] = fmaf(as.x, us.x, T3[0]); T3[1] = fmaf(as.x, us.y, T3[1]);
-                        T3[2] = fmaf(as.y, us.x, T3[2]); T3[3] = fmaf(as.y, us.y, T3[3]);
+                        const float2 ar = ld2(Ap + l * Np + m0), ai = ld2(Ap + pl + l * Np + m0);
+                        const float2 vr = ld2(Up + l * Np + n0), vi = ld2(Up + pl + l * Np + n0);
+                        cmac_2x2(accr, acci, ar, ai, vr, vi);
                     }
                 }
             }
@@ -1472,10 +1506,8 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int m = m0 + q / 2, n = n0 + (q & 1);
-                if (m < Norb && n < Norb) {
-                    const float re = T1[q] - T2[q], im = T3[q] - T1[q] - T2[q];
-                    Shat[(f * nA + la) * nel + m * Norb + n] = make_float2(-sc * im, sc * re);
-                }
+                if (m < Norb && n < Norb)  // i*scale*(re + i im)
+                    Shat[(f * nA + la) * nel + m * Norb + n] = make_float2(-sc * acci[q], sc * accr[q]);
             }
         }
     }
@@ -1526,17 +1558,31 @@ unsigned grid_for(size_t work, int threads) {
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+template <int CC, class Load, class Store>
+cudaError_t launch_fft_c(const char* name, const FftPlan& p, const double2* tw, Load ld, Store sv, size_t ncols,
+                         int batches, cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(fft_e_kernel<Load, Store, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+    if (e != cudaSuccess) return e;
+    const size_t gx = (ncols + CC - 1) / CC;
+    if (gx > 0x7fffffffu || batches > 65535) return cudaErrorInvalidValue;
+    SSE_TIMED(name, st,
+              fft_e_kernel<Load, Store, CC><<<dim3((unsigned)gx, (unsigned)batches), kFftThreads, p.smem, st>>>(
+                  p, tw, ld, sv, ncols));
+    return cudaGetLastError();
+}
+
 template <class Load, class Store>
 cudaError_t launch_fft(const char* name, const FftPlan& p, const double2* tw, Load ld, Store sv, size_t ncols,
                        int batches, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(fft_e_kernel<Load, Store>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
-    if (e != cudaSuccess) return e;
-    const size_t gx = (ncols + p.C - 1) / p.C;
-    if (gx > 0x7fffffffu || batches > 65535) return cudaErrorInvalidValue;
-    SSE_TIMED(name, st,
-              fft_e_kernel<Load, Store><<<dim3((unsigned)gx, (unsigned)batches), kFftThreads, p.smem, st>>>(
-                  p, tw, ld, sv, ncols));
-    return cudaGetLastError();
+    switch (p.C) {
+        case 16: return launch_fft_c<16>(name, p, tw, ld, sv, ncols, batches, st);
+        case 8: return launch_fft_c<8>(name, p, tw, ld, sv, ncols, batches, st);
+        case 4: return launch_fft_c<4>(name, p, tw, ld, sv, ncols, batches, st);
+        case 2: return launch_fft_c<2>(name, p, tw, ld, sv, ncols, batches, st);
+        case 1: return launch_fft_c<1>(name, p, tw, ld, sv, ncols, batches, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -1552,7 +1598,7 @@ int spectral_length(const sse_dims& d) {
 
 bool spectral_supported(const sse_dims& d) {
     const int L = spectral_length(d);
-    return d.Nkz <= kMaxNk && make_plan(L).smem <= 227 * 1024 && d.NB <= 16 &&
+    return d.Nkz <= kMaxNk && L < kFftMaxLength && make_plan(L).smem <= 227 * 1024 && d.NB <= 16 &&
            make_prod_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
 }
 
@@ -1707,7 +1753,7 @@ size_t spectral_pi_workspace(const sse_dims& d) { return pi_layout(d).total; }
 
 bool spectral_pi_supported(const sse_dims& d) {
     const int L = spectral_length(d);
-    return d.Nkz <= kMaxNk && make_plan(L).smem <= 227 * 1024 && d.NB <= 16 &&
+    return d.Nkz <= kMaxNk && L < kFftMaxLength && make_plan(L).smem <= 227 * 1024 && d.NB <= 16 &&
            make_pi_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
 }
 
