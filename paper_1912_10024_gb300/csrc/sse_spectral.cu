@@ -88,6 +88,9 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// 8-byte shared-memory access of two consecutive floats
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 
 // complex element type of the transforms: double2 (FP64 modes) or float2 (FP32_FFT)
 template <class C>
@@ -1069,6 +1072,295 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 adjoint (mode FP32_FFT): the steps of spec_adj_kernel on 2 x 2 register tiles with 4-multiply complex
+// MACs on (re, im) planes; the three T_j = W^ A_j and V_j = W^^H A_j share the W^ loads, the three
+// Q_j = T_j G^^H and R_j = V_j G^ the G^ loads. Trace partials come from the Q_j tiles in registers and are
+// summed over the tile threads in a fixed order; the coupling-gradient partial sums go to FP64 as in the FP64
+// kernel.
+// ---------------------------------------------------------------------------
+struct Adj32Cfg {
+    int Np, TN, T, pl, F, threads, fchunk, nchunks;
+    int off_A, off_W, off_G, off_K, off_T, off_V, smem;
+};
+
+constexpr int kAdj32MaxThreads = 256;
+
+Adj32Cfg make_adj32_cfg(const sse_dims& d, size_t nfreq) {
+    Adj32Cfg c{};
+    c.Np = d.Norb + (d.Norb & 1);
+    c.TN = c.Np / 2;
+    c.T = c.TN * c.TN;
+    c.pl = c.Np * c.Np;
+    const int pb = c.pl * 4;
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    // per CTA: the bond's 3 dH (2 planes); per frequency W^ and G^ in both layouts (8 planes), K (9 float2),
+    // T_j and V_j transposed (12 planes; the trace partials reuse the T_j planes)
+    auto smem_of = [&](int F) { return (long)6 * pb + F * (20L * pb + 9 * 8) + 96; };
+    c.F = 1;
+    long best = -1, best_sm = 0;
+    for (int F = 1; F * c.T <= kAdj32MaxThreads; ++F) {
+        const int threads = ((F * c.T + 31) / 32) * 32;
+        const long sm = smem_of(F);
+        if (sm > 227 * 1024) break;
+        long ctas = (228L * 1024) / (sm + 1024);
+        ctas = ctas < 2048 / threads ? ctas : 2048 / threads;
+        ctas = ctas < 65536 / (threads * 128) ? ctas : 65536 / (threads * 128);  // <= 128 registers
+        const long useful = ctas * F * c.T;
+        if (useful > best || (useful == best && sm < best_sm)) best = useful, best_sm = sm, c.F = F;
+    }
+    c.threads = ((c.F * c.T + 31) / 32) * 32;
+    c.off_A = 0;                                  // [3 j][2 planes] A_j row-major
+    c.off_W = a16(c.off_A + 6 * pb);              // [F][4 planes] W^ row-major (re, im), transposed (re, im)
+    c.off_G = a16(c.off_W + c.F * 4 * pb);        // [F][4 planes] G^ likewise
+    c.off_K = a16(c.off_G + c.F * 4 * pb);        // [F][9] float2
+    c.off_T = a16(c.off_K + c.F * 9 * 8);         // [F][3 j][2 planes] T_j transposed
+    c.off_V = a16(c.off_T + c.F * 6 * pb);        // [F][3 j][2 planes] V_j transposed
+    c.smem = a16(c.off_V + c.F * 6 * pb);
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    size_t want = (size_t)152 * 2 * 8;
+    size_t chunks = (want + nA - 1) / (nA ? nA : 1);
+    if (chunks < 1) chunks = 1;
+    size_t fc = (nfreq + chunks - 1) / chunks;
+    fc = ((fc + c.F - 1) / c.F) * c.F;
+    c.fchunk = (int)(fc < 1 ? 1 : fc);
+    c.nchunks = (int)((nfreq + c.fchunk - 1) / c.fchunk);
+    return c;
+}
+
+// acc[dm][dn] (re/im in ar/ai, index dm * 2 + dn) += x[dm] * y[dn], x or y conjugated on request: 16 FMAs
+template <bool CONJX, bool CONJY>
+__device__ __forceinline__ void cmac2x2(float* ar, float* ai, float2 xr, float2 xi, float2 yr, float2 yi) {
+    const float sx = CONJX ? -1.f : 1.f, sy = CONJY ? -1.f : 1.f;
+    const float xrv[2] = {xr.x, xr.y}, xiv[2] = {sx * xi.x, sx * xi.y};
+    const float yrv[2] = {yr.x, yr.y}, yiv[2] = {sy * yi.x, sy * yi.y};
+#pragma unroll
+    for (int dm = 0; dm < 2; ++dm)
+#pragma unroll
+        for (int dn = 0; dn < 2; ++dn) {
+            const int q = dm * 2 + dn;
+            ar[q] = fmaf(xrv[dm], yrv[dn], ar[q]);
+            ar[q] = fmaf(-xiv[dm], yiv[dn], ar[q]);
+            ai[q] = fmaf(xrv[dm], yiv[dn], ai[q]);
+            ai[q] = fmaf(xiv[dm], yrv[dn], ai[q]);
+        }
+}
+
+__global__ void __launch_bounds__(kAdj32MaxThreads, 2)
+spec_adj32_kernel(Adj32Cfg c, sse_dims d, const int32_t* __restrict__ nbr, const double2* __restrict__ dH,
+                  const float2* __restrict__ What, const float2* __restrict__ Ghat, const float2* __restrict__ Khat,
+                  float2* __restrict__ Hhat, double2* __restrict__ gdh_part, int L, double scale,
+                  unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Norb = d.Norb, Np = c.Np, pl = c.pl, nel = Norb * Norb, T = c.T;
+    const int la = blockIdx.x;
+    const int a = d.a_begin + la;
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const size_t nfreq = (size_t)d.Nkz * L;
+    const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
+    const size_t f_end = min(nfreq, f_begin + c.fchunk);
+    float* sA = reinterpret_cast<float*>(smem + c.off_A);
+    float* sW = reinterpret_cast<float*>(smem + c.off_W);
+    float* sG = reinterpret_cast<float*>(smem + c.off_G);
+    float2* sK = reinterpret_cast<float2*>(smem + c.off_K);
+    float* sT = reinterpret_cast<float*>(smem + c.off_T);
+    float* sV = reinterpret_cast<float*>(smem + c.off_V);
+    const int tid = threadIdx.x;
+    const int fl = tid / T, tt = tid - fl * T;
+    const int m0 = 2 * (tt / c.TN), n0 = 2 * (tt % c.TN);
+    const bool lane = fl < c.F;
+
+    for (int s = 0; s < d.NB; ++s) {
+        const int b = nbr[(size_t)a * d.NB + s];
+        const bool bok = b >= 0 && b < d.NA;
+        if (!bok && tid == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
+        // this bond's dH planes, zero-padded to Np x Np (the previous bond's last barrier has passed)
+        for (int i = tid; i < 3 * pl; i += blockDim.x) {
+            const int j = i / pl, e = i - j * pl;
+            const int l = e / Np, n = e - l * Np;
+            double2 v = make_double2(0.0, 0.0);
+            if (l < Norb && n < Norb) v = dH[(((size_t)a * d.NB + s) * 3 + j) * nel + l * Norb + n];
+            sA[(size_t)j * 2 * pl + e] = (float)v.x;
+            sA[(size_t)j * 2 * pl + pl + e] = (float)v.y;
+        }
+        float accr[3][4] = {}, acci[3][4] = {};  // grad dH_mu on the tile, this bond
+        for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
+            const size_t f = f0 + fl;
+            const bool act = lane && f < f_end && bok;
+            // W^_a(f) and G^_b(f), both layouts, zero-padded
+            if (lane) {
+                float* Wp = sW + (size_t)fl * 4 * pl;
+                float* Gp = sG + (size_t)fl * 4 * pl;
+#pragma unroll
+                for (int dm = 0; dm < 2; ++dm)
+#pragma unroll
+                    for (int dn = 0; dn < 2; ++dn) {
+                        const int m = m0 + dm, n = n0 + dn;
+                        float2 w = make_float2(0.f, 0.f), g = make_float2(0.f, 0.f);
+                        if (act && m < Norb && n < Norb) {
+                            w = What[(f * nA + la) * nel + m * Norb + n];
+                            g = Ghat[(f * d.NA + b) * nel + m * Norb + n];
+                        }
+                        const int o = m * Np + n, ot = n * Np + m;
+                        Wp[o] = w.x;
+                        Wp[pl + o] = w.y;
+                        Wp[2 * pl + ot] = w.x;
+                        Wp[3 * pl + ot] = w.y;
+                        Gp[o] = g.x;
+                        Gp[pl + o] = g.y;
+                        Gp[2 * pl + ot] = g.x;
+                        Gp[3 * pl + ot] = g.y;
+                    }
+            }
+            for (int i = tid; i < c.F * 9; i += blockDim.x) {
+                const int fk = i / 9, ij = i - fk * 9;
+                const size_t ff = f0 + fk;
+                float2 k = make_float2(0.f, 0.f);
+                if (ff < f_end && bok) k = Khat[((ff * nA + la) * d.NB + s) * 9 + ij];
+                sK[i] = k;
+            }
+            __syncthreads();
+            // T_j[m][n] = sum_l W^[m][l] A_j[l][n],  V_j[m][n] = sum_l conj(W^[l][m]) A_j[l][n]
+            if (lane) {
+                const float* Wp = sW + (size_t)fl * 4 * pl;
+                float tr[3][4] = {}, ti[3][4] = {}, vr[3][4] = {}, vi[3][4] = {};
+                for (int l = 0; l < Norb; ++l) {
+                    const float2 xr = ld2(Wp + 2 * pl + l * Np + m0), xi = ld2(Wp + 3 * pl + l * Np + m0);
+                    const float2 zr = ld2(Wp + l * Np + m0), zi = ld2(Wp + pl + l * Np + m0);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float2 ar = ld2(sA + (size_t)j * 2 * pl + l * Np + n0);
+                        const float2 ai = ld2(sA + (size_t)j * 2 * pl + pl + l * Np + n0);
+                        cmac2x2<false, false>(tr[j], ti[j], xr, xi, ar, ai);
+                        cmac2x2<true, false>(vr[j], vi[j], zr, zi, ar, ai);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    float* Tp = sT + ((size_t)fl * 3 + j) * 2 * pl;
+                    float* Vp = sV + ((size_t)fl * 3 + j) * 2 * pl;
+#pragma unroll
+                    for (int dn = 0; dn < 2; ++dn) {  // transposed: (T[m0][n], T[m0+1][n]) at row n
+                        const int o = (n0 + dn) * Np + m0;
+                        st2(Tp + o, tr[j][dn], tr[j][2 + dn]);
+                        st2(Tp + pl + o, ti[j][dn], ti[j][2 + dn]);
+                        st2(Vp + o, vr[j][dn], vr[j][2 + dn]);
+                        st2(Vp + pl + o, vi[j][dn], vi[j][2 + dn]);
+                    }
+                }
+            }
+            __syncthreads();
+            // Q_j[m][n] = sum_l T_j[m][l] conj(G^[n][l]),  R_j[m][n] = sum_l V_j[m][l] G^[l][n]
+            float hp[9][2];  // this tile's part of tr(A_i^H Q_j)
+            if (lane) {
+                const float* Gp = sG + (size_t)fl * 4 * pl;
+                float qr[3][4] = {}, qi[3][4] = {}, rr[3][4] = {}, ri[3][4] = {};
+                for (int l = 0; l < Norb; ++l) {
+                    const float2 yr = ld2(Gp + 2 * pl + l * Np + n0), yi = ld2(Gp + 3 * pl + l * Np + n0);
+                    const float2 gr = ld2(Gp + l * Np + n0), gi = ld2(Gp + pl + l * Np + n0);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float* Tp = sT + ((size_t)fl * 3 + j) * 2 * pl;
+                        const float* Vp = sV + ((size_t)fl * 3 + j) * 2 * pl;
+                        cmac2x2<false, true>(qr[j], qi[j], ld2(Tp + l * Np + m0), ld2(Tp + pl + l * Np + m0), yr, yi);
+                        cmac2x2<false, false>(rr[j], ri[j], ld2(Vp + l * Np + m0), ld2(Vp + pl + l * Np + m0), gr,
+                                              gi);
+                    }
+                }
+                // grad dH_mu += sum_j -i conj(K_mu,j) Q_j + i K_j,mu R_j
+                const float2* K = sK + fl * 9;
+#pragma unroll
+                for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float2 k1 = K[mu * 3 + j], k2 = K[j * 3 + mu];
+                        const float alr = -k1.y, ali = -k1.x, ber = -k2.y, bei = k2.x;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            accr[mu][q] = fmaf(alr, qr[j][q], accr[mu][q]);
+                            accr[mu][q] = fmaf(-ali, qi[j][q], accr[mu][q]);
+                            acci[mu][q] = fmaf(alr, qi[j][q], acci[mu][q]);
+                            acci[mu][q] = fmaf(ali, qr[j][q], acci[mu][q]);
+                            accr[mu][q] = fmaf(ber, rr[j][q], accr[mu][q]);
+                            accr[mu][q] = fmaf(-bei, ri[j][q], accr[mu][q]);
+                            acci[mu][q] = fmaf(ber, ri[j][q], acci[mu][q]);
+                            acci[mu][q] = fmaf(bei, rr[j][q], acci[mu][q]);
+                        }
+                    }
+                // trace parts: sum over the tile of conj(A_i[m][n]) Q_j[m][n]
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float ar[4], ai[4];
+#pragma unroll
+                    for (int dm = 0; dm < 2; ++dm) {
+                        const float2 r2 = ld2(sA + (size_t)i * 2 * pl + (m0 + dm) * Np + n0);
+                        const float2 i2 = ld2(sA + (size_t)i * 2 * pl + pl + (m0 + dm) * Np + n0);
+                        ar[dm * 2] = r2.x;
+                        ar[dm * 2 + 1] = r2.y;
+                        ai[dm * 2] = i2.x;
+                        ai[dm * 2 + 1] = i2.y;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        float hr = 0.f, hi = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            hr = fmaf(ar[q], qr[j][q], hr);
+                            hr = fmaf(ai[q], qi[j][q], hr);
+                            hi = fmaf(ar[q], qi[j][q], hi);
+                            hi = fmaf(-ai[q], qr[j][q], hi);
+                        }
+                        hp[i * 3 + j][0] = hr;
+                        hp[i * 3 + j][1] = hi;
+                    }
+                }
+            }
+            __syncthreads();  // every read of sT, sV, sG, sK, sW for this batch is done
+            float2* sP = reinterpret_cast<float2*>(sT);  // [F][T][9] trace parts (fit in the T_j planes)
+            if (lane)
+#pragma unroll
+                for (int ij = 0; ij < 9; ++ij) sP[((size_t)fl * T + tt) * 9 + ij] = make_float2(hp[ij][0], hp[ij][1]);
+            __syncthreads();
+            for (int g = tid; g < c.F * 9; g += blockDim.x) {
+                const int fk = g / 9, ij = g - fk * 9;
+                const size_t ff = f0 + fk;
+                float2 sum = sP[(size_t)fk * T * 9 + ij];
+                for (int u = 1; u < T; ++u) {
+                    const float2 v = sP[((size_t)fk * T + u) * 9 + ij];
+                    sum.x += v.x;
+                    sum.y += v.y;
+                }
+                if (ff < f_end) Hhat[((ff * nA + la) * d.NB + s) * 9 + ij] = sum;
+            }
+            // the next batch writes sW, sG, sK before its first barrier and sT (sP) only after it
+        }
+        // sum the frequency lanes' accumulators (fixed order, FP64) and write this chunk's partial
+        __syncthreads();
+        float2* sAcc = reinterpret_cast<float2*>(sT);  // [F][3][nel]
+        if (lane)
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int m = m0 + q / 2, n = n0 + (q & 1);
+                    if (m < Norb && n < Norb)
+                        sAcc[((size_t)fl * 3 + mu) * nel + m * Norb + n] = make_float2(accr[mu][q], acci[mu][q]);
+                }
+        __syncthreads();
+        const double inv = scale / (double)nfreq;
+        for (int i = tid; i < 3 * nel; i += blockDim.x) {
+            double2 sum = make_double2(0.0, 0.0);
+            for (int f2 = 0; f2 < c.F; ++f2) {
+                const float2 v = sAcc[(size_t)f2 * 3 * nel + i];
+                sum.x += (double)v.x;
+                sum.y += (double)v.y;
+            }
+            gdh_part[(((size_t)blockIdx.y * nA + la) * d.NB + s) * 3 * nel + i] = make_double2(sum.x * inv, sum.y * inv);
+        }
+        __syncthreads();  // sA and sT are rewritten by the next bond
+    }
+}
+
 // grad dH = sum over types and frequency chunks (fixed order) of the partials
 __global__ void spec_gdh_reduce_kernel(sse_dims d, int nchunks, const double2* __restrict__ part0,
                                        const double2* __restrict__ part1, double2* __restrict__ g_dH) {
@@ -1339,9 +1631,6 @@ Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     c.fchunk = (int)(fc < 1 ? 1 : fc);
     return c;
 }
-
-__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 
 // acc (2 x 2 complex tile, re/im of entries (0,0), (0,1), (1,0), (1,1)) += x y^T for the column pair
 // x = (xr, xi) and the row pair y = (yr, yi): 16 FMAs
@@ -1842,14 +2131,14 @@ AdjLayout adj_layout(const sse_dims& d, size_t csz = 16) {  // csz: bytes per co
     l.L = spectral_length(d);
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t spec = (size_t)d.Nkz * l.L;
-    const AdjCfg ac = make_adj_cfg(d, spec, (int)csz / 2);
+    const int nchunks = csz == 8 ? make_adj32_cfg(d, spec).nchunks : make_adj_cfg(d, spec).nchunks;
     l.off_tw = 0;
     l.off_W = align256((size_t)l.L * 16);
     l.off_G = align256(l.off_W + spec * nA * nel * csz);
     l.off_K = align256(l.off_G + spec * d.NA * nel * csz);
     l.off_H = align256(l.off_K + spec * nA * d.NB * 9 * csz);
     l.off_part = align256(l.off_H + spec * nA * d.NB * 9 * csz);
-    l.total = align256(l.off_part + (size_t)2 * ac.nchunks * nA * d.NB * 3 * nel * 16);
+    l.total = align256(l.off_part + (size_t)2 * nchunks * nA * d.NB * 3 * nel * 16);
     return l;
 }
 
@@ -1858,7 +2147,8 @@ size_t spectral_bwd32_workspace(const sse_dims& d) { return adj_layout(d, 8).tot
 
 bool spectral_bwd_supported(const sse_dims& d) {
     const int L = spectral_length(d);
-    return spectral_supported(d) && make_adj_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
+    return spectral_supported(d) && make_adj_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024 &&
+           make_adj32_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
 }
 
 namespace {
@@ -1885,15 +2175,20 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t gcols = (size_t)d.NA * nel, wcols = nA * nel, kcols = nA * d.NB * 9;
     const size_t nfreq = (size_t)d.Nkz * L;
+    constexpr bool fp32 = sizeof(T) == 4;
     const AdjCfg ac = make_adj_cfg(d, nfreq, (int)sizeof(T));
-    const size_t part_one = (size_t)ac.nchunks * nA * d.NB * 3 * nel;
+    const Adj32Cfg ac32 = make_adj32_cfg(d, nfreq);
+    const int nchunks = fp32 ? ac32.nchunks : ac.nchunks;
+    const size_t part_one = (size_t)nchunks * nA * d.NB * 3 * nel;
     if (nA == 0) return cudaSuccess;
     cudaError_t e;
     SSE_TIMED("twiddle_kernel", st, twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(spec_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ac.smem)) !=
-        cudaSuccess)
-        return e;
+    if constexpr (fp32)
+        e = cudaFuncSetAttribute(spec_adj32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ac32.smem);
+    else
+        e = cudaFuncSetAttribute(spec_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ac.smem);
+    if (e != cudaSuccess) return e;
     const double2* W[2] = {gS_less, gS_greater};
     double2* gD[2] = {g_D_less, g_D_greater};
     const int sym = (p.flags & SSE_FLAG_SYMMETRIZE) ? 1 : 0;
@@ -1920,9 +2215,15 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols,
                                                                                  0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        SSE_TIMED("spec_adj_kernel", st,
-                  spec_adj_kernel<T><<<dim3((unsigned)nA, (unsigned)ac.nchunks), ac.threads, ac.smem, st>>>(
-                      ac, d, p.nbr, p.dH, Wh, Gh, Kh, Hh, part + (size_t)t * part_one, L, p.scale, status));
+        if constexpr (fp32) {
+            SSE_TIMED("spec_adj_kernel", st,
+                      spec_adj32_kernel<<<dim3((unsigned)nA, (unsigned)ac32.nchunks), ac32.threads, ac32.smem, st>>>(
+                          ac32, d, p.nbr, p.dH, Wh, Gh, Kh, Hh, part + (size_t)t * part_one, L, p.scale, status));
+        } else {
+            SSE_TIMED("spec_adj_kernel", st,
+                      spec_adj_kernel<T><<<dim3((unsigned)nA, (unsigned)ac.nchunks), ac.threads, ac.smem, st>>>(
+                          ac, d, p.nbr, p.dH, Wh, Gh, Kh, Hh, part + (size_t)t * part_one, L, p.scale, status));
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // grad D from H^t: emission lags -> D^t, absorption lags -> D^t'
         SSE_TIMED("dft_k_kernel(H)", st,
@@ -1935,7 +2236,7 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
         if (e != cudaSuccess) return e;
     }
     SSE_TIMED("spec_gdh_reduce_kernel", st,
-              spec_gdh_reduce_kernel<<<grid_for(nA * d.NB * 3 * nel, 256), 256, 0, st>>>(d, ac.nchunks, part,
+              spec_gdh_reduce_kernel<<<grid_for(nA * d.NB * 3 * nel, 256), 256, 0, st>>>(d, nchunks, part,
                                                                                          part + part_one, g_dH));
     return cudaGetLastError();
 }
