@@ -92,6 +92,25 @@ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 
+// acc[dm][dn] (re/im in ar/ai, index dm * 2 + dn) += x[dm] * y[dn], x or y conjugated on request: 16 FMAs
+template <bool CONJX, bool CONJY>
+__device__ __forceinline__ void cmac2x2(float* ar, float* ai, float2 xr, float2 xi, float2 yr, float2 yi) {
+    const float sx = CONJX ? -1.f : 1.f, sy = CONJY ? -1.f : 1.f;
+    const float xrv[2] = {xr.x, xr.y}, xiv[2] = {sx * xi.x, sx * xi.y};
+    const float yrv[2] = {yr.x, yr.y}, yiv[2] = {sy * yi.x, sy * yi.y};
+#pragma unroll
+    for (int dm = 0; dm < 2; ++dm)
+#pragma unroll
+        for (int dn = 0; dn < 2; ++dn) {
+            const int q = dm * 2 + dn;
+            ar[q] = fmaf(xrv[dm], yrv[dn], ar[q]);
+            ar[q] = fmaf(-xiv[dm], yiv[dn], ar[q]);
+            ai[q] = fmaf(xrv[dm], yiv[dn], ai[q]);
+            ai[q] = fmaf(xiv[dm], yrv[dn], ai[q]);
+        }
+}
+
+
 // complex element type of the transforms: double2 (FP64 modes) or float2 (FP32_FFT)
 template <class C>
 struct CT;
@@ -1073,6 +1092,158 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
 }
 
 // ---------------------------------------------------------------------------
+// FP32 gradient with respect to G (mode FP32_FFT): per target atom b and frequency, over the bonds (a, s)
+// into b, P_j = W^_a A_j for the three j at once on 2 x 2 register tiles (4-multiply MACs on (re, im)
+// planes), U_i = sum_j conj(K^_ij) P_j in registers, then acc += sum_i A_i^H U_i; the result is
+// conj(c) acc = -i scale acc, as in spec_gradg_kernel.
+// ---------------------------------------------------------------------------
+struct GradG32Cfg {
+    int Np, TN, T, pl, F, threads, fchunk;
+    int off_A, off_W, off_K, off_U, smem;
+};
+
+GradG32Cfg make_gradg32_cfg(const sse_dims& d, size_t nfreq) {
+    GradG32Cfg c{};
+    c.Np = d.Norb + (d.Norb & 1);
+    c.TN = c.Np / 2;
+    c.T = c.TN * c.TN;
+    c.pl = c.Np * c.Np;
+    const int pb = c.pl * 4;
+    auto a16 = [](int x) { return (x + 15) & ~15; };
+    c.F = pick_frequencies(c.T, [&](int F) { return (long)6 * pb + F * (8L * pb + 9 * 8) + 64; });
+    c.threads = ((c.F * c.T + 31) / 32) * 32;
+    c.off_A = 0;                            // [3 j][2 planes] the current bond's A_j row-major
+    c.off_W = a16(c.off_A + 6 * pb);        // [F][2 planes] W^_a transposed: WT[l][m] = W^[m][l]
+    c.off_K = a16(c.off_W + c.F * 2 * pb);  // [F][9] float2
+    c.off_U = a16(c.off_K + c.F * 9 * 8);   // [F][3 i][2 planes] U_i row-major
+    c.smem = a16(c.off_U + c.F * 6 * pb);
+    // every target atom gets a CTA column: enough frequency chunks for ~8 waves of 2 CTAs per SM
+    size_t want = (size_t)152 * 2 * 8;
+    size_t chunks = (want + (size_t)d.NA - 1) / (size_t)(d.NA ? d.NA : 1);
+    if (chunks < 1) chunks = 1;
+    size_t fc = (nfreq + chunks - 1) / chunks;
+    fc = ((fc + c.F - 1) / c.F) * c.F;
+    c.fchunk = (int)(fc < 1 ? 1 : fc);
+    return c;
+}
+
+__global__ void spec_gradg32_kernel(GradG32Cfg c, sse_dims d, const int* __restrict__ off,
+                                    const int* __restrict__ list, const double2* __restrict__ dH,
+                                    const float2* __restrict__ What, const float2* __restrict__ Khat,
+                                    float2* __restrict__ Rhat, int L, double scale) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Norb = d.Norb, Np = c.Np, pl = c.pl, nel = Norb * Norb;
+    const int b = blockIdx.x;  // target atom
+    const size_t nA = (size_t)(d.a_end - d.a_begin);
+    const size_t nfreq = (size_t)d.Nkz * L;
+    const size_t f_begin = (size_t)blockIdx.y * c.fchunk;
+    const size_t f_end = min(nfreq, f_begin + c.fchunk);
+    float* sA = reinterpret_cast<float*>(smem + c.off_A);
+    float* sW = reinterpret_cast<float*>(smem + c.off_W);
+    float2* sK = reinterpret_cast<float2*>(smem + c.off_K);
+    float* sU = reinterpret_cast<float*>(smem + c.off_U);
+    const int tid = threadIdx.x;
+    const int fl = tid / c.T, tt = tid - fl * c.T;
+    const int m0 = 2 * (tt / c.TN), n0 = 2 * (tt % c.TN);
+    const bool lane = fl < c.F;
+    const int i0 = off[b], i1 = off[b + 1];
+
+    for (size_t f0 = f_begin; f0 < f_end; f0 += c.F) {
+        const size_t f = f0 + fl;
+        const bool act = lane && f < f_end;
+        float accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
+        for (int ib = i0; ib < i1; ++ib) {
+            const int bond = list[ib];  // (a - a_begin) * NB + s
+            const int la = bond / d.NB;
+            // this bond's A_j (zero-padded), W^_a(f) transposed, K^(f) of the bond
+            for (int i = tid; i < 3 * pl; i += blockDim.x) {
+                const int j = i / pl, e = i - j * pl;
+                const int l = e / Np, n = e - l * Np;
+                double2 v = make_double2(0.0, 0.0);
+                if (l < Norb && n < Norb) v = dH[(((size_t)d.a_begin * d.NB + bond) * 3 + j) * nel + l * Norb + n];
+                sA[(size_t)j * 2 * pl + e] = (float)v.x;
+                sA[(size_t)j * 2 * pl + pl + e] = (float)v.y;
+            }
+            if (lane) {
+                float* Wp = sW + (size_t)fl * 2 * pl;
+#pragma unroll
+                for (int dm = 0; dm < 2; ++dm)
+#pragma unroll
+                    for (int dn = 0; dn < 2; ++dn) {
+                        const int m = m0 + dm, n = n0 + dn;
+                        float2 w = make_float2(0.f, 0.f);
+                        if (act && m < Norb && n < Norb) w = What[(f * nA + la) * nel + m * Norb + n];
+                        Wp[n * Np + m] = w.x;
+                        Wp[pl + n * Np + m] = w.y;
+                    }
+            }
+            for (int i = tid; i < c.F * 9; i += blockDim.x) {
+                const int fk = i / 9, ij = i - fk * 9;
+                const size_t ff = f0 + fk;
+                sK[i] = ff < f_end ? Khat[(ff * nA * d.NB + bond) * 9 + ij] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            // P_j = W^ A_j (three at once), U_i = sum_j conj(K_ij) P_j
+            if (lane) {
+                const float* Wp = sW + (size_t)fl * 2 * pl;
+                float pr[3][4] = {}, pi[3][4] = {};
+                for (int l = 0; l < Norb; ++l) {
+                    const float2 xr = ld2(Wp + l * Np + m0), xi = ld2(Wp + pl + l * Np + m0);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        cmac2x2<false, false>(pr[j], pi[j], xr, xi, ld2(sA + (size_t)j * 2 * pl + l * Np + n0),
+                                              ld2(sA + (size_t)j * 2 * pl + pl + l * Np + n0));
+                }
+                const float2* K = sK + fl * 9;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float ur[4] = {0, 0, 0, 0}, ui[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float2 k = K[i * 3 + j];  // conj(k) P = (kx pr + ky pi, kx pi - ky pr)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            ur[q] = fmaf(k.x, pr[j][q], ur[q]);
+                            ur[q] = fmaf(k.y, pi[j][q], ur[q]);
+                            ui[q] = fmaf(k.x, pi[j][q], ui[q]);
+                            ui[q] = fmaf(-k.y, pr[j][q], ui[q]);
+                        }
+                    }
+                    float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
+#pragma unroll
+                    for (int dm = 0; dm < 2; ++dm) {
+                        st2(Up + (m0 + dm) * Np + n0, ur[dm * 2], ur[dm * 2 + 1]);
+                        st2(Up + pl + (m0 + dm) * Np + n0, ui[dm * 2], ui[dm * 2 + 1]);
+                    }
+                }
+            }
+            __syncthreads();
+            // acc += sum_i A_i^H U_i: acc[m][n] += sum_l conj(A_i[l][m]) U_i[l][n]
+            if (lane) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float* Ap = sA + (size_t)i * 2 * pl;
+                    const float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
+                    for (int l = 0; l < Norb; ++l)
+                        cmac2x2<true, false>(accr, acci, ld2(Ap + l * Np + m0), ld2(Ap + pl + l * Np + m0),
+                                             ld2(Up + l * Np + n0), ld2(Up + pl + l * Np + n0));
+                }
+            }
+            __syncthreads();  // sA, sW, sK, sU are rewritten for the next bond
+        }
+        if (act) {
+            const float sc = (float)scale;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + q / 2, n = n0 + (q & 1);
+                if (m < Norb && n < Norb)  // -i*scale*(re + i im)
+                    Rhat[(f * d.NA + b) * nel + m * Norb + n] = make_float2(sc * acci[q], -sc * accr[q]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // FP32 adjoint (mode FP32_FFT): the steps of spec_adj_kernel on 2 x 2 register tiles with 4-multiply complex
 // MACs on (re, im) planes; the three T_j = W^ A_j and V_j = W^^H A_j share the W^ loads, the three
 // Q_j = T_j G^^H and R_j = V_j G^ the G^ loads. Trace partials come from the Q_j tiles in registers and are
@@ -1126,24 +1297,6 @@ Adj32Cfg make_adj32_cfg(const sse_dims& d, size_t nfreq) {
     c.fchunk = (int)(fc < 1 ? 1 : fc);
     c.nchunks = (int)((nfreq + c.fchunk - 1) / c.fchunk);
     return c;
-}
-
-// acc[dm][dn] (re/im in ar/ai, index dm * 2 + dn) += x[dm] * y[dn], x or y conjugated on request: 16 FMAs
-template <bool CONJX, bool CONJY>
-__device__ __forceinline__ void cmac2x2(float* ar, float* ai, float2 xr, float2 xi, float2 yr, float2 yi) {
-    const float sx = CONJX ? -1.f : 1.f, sy = CONJY ? -1.f : 1.f;
-    const float xrv[2] = {xr.x, xr.y}, xiv[2] = {sx * xi.x, sx * xi.y};
-    const float yrv[2] = {yr.x, yr.y}, yiv[2] = {sy * yi.x, sy * yi.y};
-#pragma unroll
-    for (int dm = 0; dm < 2; ++dm)
-#pragma unroll
-        for (int dn = 0; dn < 2; ++dn) {
-            const int q = dm * 2 + dn;
-            ar[q] = fmaf(xrv[dm], yrv[dn], ar[q]);
-            ar[q] = fmaf(-xiv[dm], yiv[dn], ar[q]);
-            ai[q] = fmaf(xrv[dm], yiv[dn], ai[q]);
-            ai[q] = fmaf(xiv[dm], yrv[dn], ai[q]);
-        }
 }
 
 __global__ void __launch_bounds__(kAdj32MaxThreads, 2)
@@ -1632,22 +1785,6 @@ Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     return c;
 }
 
-// acc (2 x 2 complex tile, re/im of entries (0,0), (0,1), (1,0), (1,1)) += x y^T for the column pair
-// x = (xr, xi) and the row pair y = (yr, yi): 16 FMAs
-__device__ __forceinline__ void cmac_2x2(float* ar, float* ai, float2 xr, float2 xi, float2 yr, float2 yi) {
-    const float xrv[2] = {xr.x, xr.y}, xiv[2] = {xi.x, xi.y}, yrv[2] = {yr.x, yr.y}, yiv[2] = {yi.x, yi.y};
-#pragma unroll
-    for (int dm = 0; dm < 2; ++dm)
-#pragma unroll
-        for (int dn = 0; dn < 2; ++dn) {
-            const int q = dm * 2 + dn;
-            ar[q] = fmaf(xrv[dm], yrv[dn], ar[q]);
-            ar[q] = fmaf(-xiv[dm], yiv[dn], ar[q]);
-            ai[q] = fmaf(xrv[dm], yiv[dn], ai[q]);
-            ai[q] = fmaf(xiv[dm], yrv[dn], ai[q]);
-        }
-}
-
 __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ nbr,
                                    const double2* __restrict__ dH, const float2* __restrict__ Ghat,
                                    const float2* __restrict__ Khat, float2* __restrict__ Shat, double scale,
@@ -1760,7 +1897,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                     for (int i = 0; i < 3; ++i) {
                         const float2 wr = ld2(Wp + i * 2 * pl + l * Np + n0);
                         const float2 wi = ld2(Wp + i * 2 * pl + pl + l * Np + n0);
-                        cmac_2x2(ur[i], ui[i], gr, gi, wr, wi);
+                        cmac2x2<false, false>(ur[i], ui[i], gr, gi, wr, wi);
                     }
                 }
 #pragma unroll
@@ -1784,7 +1921,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                     for (int l = 0; l < Norb; ++l) {
                         const float2 ar = ld2(Ap + l * Np + m0), ai = ld2(Ap + pl + l * Np + m0);
                         const float2 vr = ld2(Up + l * Np + n0), vi = ld2(Up + pl + l * Np + n0);
-                        cmac_2x2(accr, acci, ar, ai, vr, vi);
+                        cmac2x2<false, false>(accr, acci, ar, ai, vr, vi);
                     }
                 }
             }
@@ -2319,11 +2456,15 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
     dall.a_begin = 0;
     dall.a_end = d.NA;
     dall.NB = d.NB < 2 ? 2 : d.NB;  // the A region holds one bond's 3 x 4 planes (>= 12 Norb^2 doubles)
-    ProdCfg pc = make_prod_cfg(dall, nfreq, (int)sizeof(T));
-    if (pc.smem > 227 * 1024) return cudaErrorNotSupported;
-    if ((e = cudaFuncSetAttribute(spec_gradg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem)) !=
-        cudaSuccess)
-        return e;
+    constexpr bool fp32 = sizeof(T) == 4;
+    const ProdCfg pc = make_prod_cfg(dall, nfreq, (int)sizeof(T));
+    const GradG32Cfg gc = make_gradg32_cfg(d, nfreq);
+    if ((fp32 ? gc.smem : pc.smem) > 227 * 1024) return cudaErrorNotSupported;
+    if constexpr (fp32)
+        e = cudaFuncSetAttribute(spec_gradg32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gc.smem);
+    else
+        e = cudaFuncSetAttribute(spec_gradg_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, pc.smem);
+    if (e != cudaSuccess) return e;
     const double2* W[2] = {gS_less, gS_greater};
     double2* gG[2] = {g_G_less, g_G_greater};
     const int sym = (p.flags & SSE_FLAG_SYMMETRIZE) ? 1 : 0;
@@ -2345,10 +2486,17 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
                                                                                      (size_t)L * kcols, 0));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
-        SSE_TIMED("spec_gradg_kernel", st,
-                  spec_gradg_kernel<T><<<dim3((unsigned)d.NA, (unsigned)gy), pc.threads, pc.smem, st>>>(
-                      pc, d, offs, list, p.dH, Wh, Kh, Rh, L, p.scale));
+        if constexpr (fp32) {
+            const size_t gy = (nfreq + gc.fchunk - 1) / gc.fchunk;
+            SSE_TIMED("spec_gradg_kernel", st,
+                      spec_gradg32_kernel<<<dim3((unsigned)d.NA, (unsigned)gy), gc.threads, gc.smem, st>>>(
+                          gc, d, offs, list, p.dH, Wh, Kh, Rh, L, p.scale));
+        } else {
+            const size_t gy = (nfreq + pc.fchunk - 1) / pc.fchunk;
+            SSE_TIMED("spec_gradg_kernel", st,
+                      spec_gradg_kernel<T><<<dim3((unsigned)d.NA, (unsigned)gy), pc.threads, pc.smem, st>>>(
+                          pc, d, offs, list, p.dH, Wh, Kh, Rh, L, p.scale));
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(R)", st,
                   dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Rh, d.Nkz, d.Nkz, (size_t)L * gcols,
