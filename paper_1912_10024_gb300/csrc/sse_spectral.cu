@@ -81,7 +81,6 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -1753,12 +1752,13 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
 struct Prod32Cfg {
     int Np, TN, T, F, threads, fchunk;
     int pl;  // floats per Np x Np plane
-    int off_A, off_G, off_K, off_W, off_U, smem;
+    int off_A, off_G, off_K, off_U, smem;
 };
 
 // FP32 products use the 4-multiply complex MAC on (re, im) planes: with shared-memory bandwidth, not the FP32
 // pipe, the limit, two planes per operand (4 loads per 16 FMAs of a 2 x 2 tile) beat the 3-multiply form's
-// three planes (6 loads per 12 FMAs).
+// three planes (6 loads per 12 FMAs). U_i = G^ W_i is formed as sum_j K_ij P_j with P_j = G^ A_j^H, so the
+// weight blocks W_i never pass through shared memory.
 Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     Prod32Cfg c{};
     c.Np = d.Norb + (d.Norb & 1);
@@ -1767,13 +1767,12 @@ Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     c.pl = c.Np * c.Np;
     const int pb = c.pl * 4;  // bytes per plane
     auto a16 = [](int x) { return (x + 15) & ~15; };
-    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 6 * pb + F * (14 * pb + 9 * 8) + 64; });
+    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 6 * pb + F * (8 * pb + 9 * 8) + 64; });
     c.threads = ((c.F * c.T + 31) / 32) * 32;
     c.off_A = 0;                                  // [NB][3 dir][2 planes] dH transposed: AT[l][m] = dH[m][l]
     c.off_G = a16(c.off_A + d.NB * 6 * pb);       // [F][2 planes] G^ transposed: GT[l][m] = G^[m][l]
     c.off_K = a16(c.off_G + c.F * 2 * pb);        // [F][9] float2
-    c.off_W = a16(c.off_K + c.F * 9 * 8);         // [F][3 i][2 planes] W_i row-major
-    c.off_U = a16(c.off_W + c.F * 6 * pb);        // [F][3 i][2 planes] U_i row-major
+    c.off_U = a16(c.off_K + c.F * 9 * 8);         // [F][3 i][2 planes] U_i row-major
     c.smem = a16(c.off_U + c.F * 6 * pb);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
@@ -1799,7 +1798,6 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
     float* sA = reinterpret_cast<float*>(smem + c.off_A);
     float* sG = reinterpret_cast<float*>(smem + c.off_G);
     float2* sK = reinterpret_cast<float2*>(smem + c.off_K);
-    float* sW = reinterpret_cast<float*>(smem + c.off_W);
     float* sU = reinterpret_cast<float*>(smem + c.off_U);
     const int tid = threadIdx.x;
     const int fl = tid / c.T, tt = tid - fl * c.T;
@@ -1852,62 +1850,39 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
             }
             __syncthreads();
             const float* A = sA + (size_t)s * 6 * pl;
-            // W_i[m][n] = sum_j K_ij conj(dH_j[n][m]) = sum_j K_ij conj(AT_j[m][n])
-            if (lane) {
-                const float2* K = sK + fl * 9;
-#pragma unroll
-                for (int dm = 0; dm < 2; ++dm) {
-                    const int m = m0 + dm;
-                    float2 ar[3], ai[3];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        ar[j] = ld2(A + (size_t)j * 2 * pl + m * Np + n0);
-                        ai[j] = ld2(A + (size_t)j * 2 * pl + pl + m * Np + n0);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        float wr0 = 0.f, wi0 = 0.f, wr1 = 0.f, wi1 = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            const float2 k = K[i * 3 + j];
-                            wr0 = fmaf(k.x, ar[j].x, wr0);
-                            wr0 = fmaf(k.y, ai[j].x, wr0);
-                            wi0 = fmaf(k.y, ar[j].x, wi0);
-                            wi0 = fmaf(-k.x, ai[j].x, wi0);
-                            wr1 = fmaf(k.x, ar[j].y, wr1);
-                            wr1 = fmaf(k.y, ai[j].y, wr1);
-                            wi1 = fmaf(k.y, ar[j].y, wi1);
-                            wi1 = fmaf(-k.x, ai[j].y, wi1);
-                        }
-                        float* Wp = sW + ((size_t)fl * 3 + i) * 2 * pl + m * Np + n0;
-                        st2(Wp, wr0, wr1);
-                        st2(Wp + pl, wi0, wi1);
-                    }
-                }
-            }
-            __syncthreads();
-            // U_i = G^ W_i for the three i together (one G^ load per l): U[m][n] = sum_l GT[l][m] W_i[l][n]
+            // P_j = G^ A_j^H for the three j at once: P_j[m][n] = sum_l GT[l][m] conj(AT_j[l][n]);
+            // U_i = G^ W_i = sum_j K_ij P_j
             if (lane) {
                 const float* Gp = sG + (size_t)fl * 2 * pl;
-                const float* Wp = sW + (size_t)fl * 6 * pl;
-                float ur[3][4] = {}, ui[3][4] = {};
+                float pr[3][4] = {}, pim[3][4] = {};
                 for (int l = 0; l < Norb; ++l) {
                     const float2 gr = ld2(Gp + l * Np + m0), gi = ld2(Gp + pl + l * Np + m0);
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        const float2 wr = ld2(Wp + i * 2 * pl + l * Np + n0);
-                        const float2 wi = ld2(Wp + i * 2 * pl + pl + l * Np + n0);
-                        cmac2x2<false, false>(ur[i], ui[i], gr, gi, wr, wi);
-                    }
+                    for (int j = 0; j < 3; ++j)
+                        cmac2x2<false, true>(pr[j], pim[j], gr, gi, ld2(A + (size_t)j * 2 * pl + l * Np + n0),
+                                             ld2(A + (size_t)j * 2 * pl + pl + l * Np + n0));
                 }
+                const float2* K = sK + fl * 9;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
+                    float ur[4] = {0, 0, 0, 0}, ui[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float2 k = K[i * 3 + j];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            ur[q] = fmaf(k.x, pr[j][q], ur[q]);
+                            ur[q] = fmaf(-k.y, pim[j][q], ur[q]);
+                            ui[q] = fmaf(k.x, pim[j][q], ui[q]);
+                            ui[q] = fmaf(k.y, pr[j][q], ui[q]);
+                        }
+                    }
                     float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
 #pragma unroll
                     for (int dm = 0; dm < 2; ++dm) {
                         float* o = Up + (m0 + dm) * Np + n0;
-                        st2(o, ur[i][dm * 2], ur[i][dm * 2 + 1]);
-                        st2(o + pl, ui[i][dm * 2], ui[i][dm * 2 + 1]);
+                        st2(o, ur[dm * 2], ur[dm * 2 + 1]);
+                        st2(o + pl, ui[dm * 2], ui[dm * 2 + 1]);
                     }
                 }
             }
@@ -1925,7 +1900,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                     }
                 }
             }
-            __syncthreads();  // sG, sK, sW, sU are rewritten for the next bond
+            __syncthreads();  // sG, sK, sU are rewritten for the next bond
         }
         if (act) {
             const float sc = (float)scale;
@@ -2053,7 +2028,6 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
     const FftPlan plan = make_plan(L, (int)sizeof(C));
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t gcols = (size_t)d.NA * nel, kcols = nA * d.NB * 9, scols = nA * nel;
-    const size_t nfreq = (size_t)d.Nkz * L;
     cudaError_t e;
     if (nA == 0) return cudaSuccess;
 
@@ -2197,7 +2171,6 @@ cudaError_t spectral_pi(const sse_dims& d, const int32_t* nbr, const double2* dH
     const FftPlan plan = make_plan(L);
     const size_t nA = (size_t)(d.a_end - d.a_begin), nel = (size_t)d.Norb * d.Norb;
     const size_t gcols = (size_t)d.NA * nel, ccols = nA * (d.NB + 1) * 9;
-    const size_t nfreq = (size_t)d.Nkz * L;
     if (nA == 0) return cudaSuccess;
     cudaError_t e;
     SSE_TIMED("twiddle_kernel", st, twiddle_kernel<<<grid_for(L, 256), 256, 0, st>>>(L, tw));
