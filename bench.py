@@ -472,7 +472,30 @@ def main():
                                 "traffic": ncu_traffic("spec_pi_kernel", 2 * d.NA * freq_count(d, args.antihermitian)),
                                 "kernels": {k: {"ms_per_step": v[0] / args.steps,
                                                 "launches_per_step": v[1] / args.steps} for k, v in pk.items()}}}
-        del wsp, Pout
+        # the same Pi with FP32 transforms and products (mode FP32_FFT), compared with the FP64 result
+        ref_p = tuple(x.clone() for x in Pout)
+        del wsp
+        torch.cuda.empty_cache()
+        m32 = B.MODES["fp32_fft"]
+        wsp = torch.empty(B.sse_pi_workspace_bytes(pd, m32, 0), dtype=torch.uint8, device=dev)
+
+        def pstep32():
+            B.pi(inp.G_less, inp.G_greater, inp.dH, inp.nbr, d.Nqz, d.Nw, scale=SCALE, out=Pout, ws=wsp,
+                 stream=stream, antihermitian=args.antihermitian, mode="fp32_fft")
+
+        for _ in range(max(3, args.warmup)):
+            pstep32()
+        torch.cuda.synchronize(dev)
+        p0.record(stream)
+        for _ in range(args.steps):
+            pstep32()
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        pi_line["fp32_fft"] = {"ms_per_step": p0.elapsed_time(p1) / args.steps,
+                               "normwise_diff_vs_fp64": max(float((x - y).abs().max() / y.abs().max())
+                                                            for x, y in zip(Pout, ref_p)),
+                               "stated_bound": 2e-6}
+        del wsp, Pout, ref_p
         torch.cuda.empty_cache()
 
     # ---- the FP64 adjoint (transform-based) on the same inputs ----

@@ -211,9 +211,11 @@ SSE_API int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const double*
  *   t' the other type; energies with E or E+(w+1) outside [0, NE) contribute zero;
  *   the diagonal block sums the NB bond terms (the sum over l of Eq. (4); an
  *   off-diagonal block keeps l = b). `scale` is the energy-integration weight.
- * Modes FP64 and FP64_FFT (both evaluate it with the convolution theorem in FP64:
- * per frequency 6 block products and 9 traces per bond, then one inverse
- * transform per (bond, i, j)); other modes return SSE_ERR_UNSUPPORTED.
+ * Modes FP64 and FP64_FFT evaluate it with the convolution theorem in FP64 (per
+ * frequency 6 block products and 9 traces per bond, then one inverse transform per
+ * (bond, i, j)); mode FP32_FFT takes the same steps with FP32 transforms and block
+ * products (FP64 inputs and outputs; normwise error a few 1e-7); TF32 and BF16X3
+ * return SSE_ERR_UNSUPPORTED.
  * Flags: SYMMETRIZE replaces each 3x3 block B by (B - B^H)/2; CHECK, PROFILE as above.
  * Rows of other atoms are untouched. Workspace: sse_pi_workspace_bytes(). */
 SSE_API size_t sse_pi_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);

@@ -318,12 +318,14 @@ def sigma_host(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0
 
 def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 * math.pi),
        symmetrize: bool = False, check: bool = False, atoms=None, out=None, ws: Optional[torch.Tensor] = None,
-       stream=None, profile: bool = False, antihermitian: bool = False):
-    """Pi^<, Pi^> of Eq. (4) on the current CUDA device via sse_pi_fwd (FP64).
+       stream=None, profile: bool = False, antihermitian: bool = False, mode="fp64"):
+    """Pi^<, Pi^> of Eq. (4) on the current CUDA device via sse_pi_fwd (modes fp64 / fp64_fft: FP64 transforms;
+    fp32_fft: FP32 transforms and products, FP64 inputs and outputs).
 
     Returns (P_less, P_greater), complex128 [Nqz, Nw, NA, NB+1, 3, 3]: slot s < NB is the block for
     b = nbr[a][s], slot NB the diagonal block.
     """
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
     c128 = torch.complex128
     Nkz, NE, NA, Norb, _ = G_less.shape
     NB = dH.shape[1]
@@ -340,12 +342,11 @@ def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 
         alloc = torch.empty if atoms is None else torch.zeros
         out = (alloc(shape, dtype=c128, device=G_less.device), alloc(shape, dtype=c128, device=G_less.device))
     if ws is None:
-        n = sse_pi_workspace_bytes(d, SSE_MODE_FP64, flags)
+        n = sse_pi_workspace_bytes(d, m, flags)
         if n == 0:
             raise ValueError("invalid or unsupported problem sizes for libsse")
         ws = torch.empty(n, dtype=torch.uint8, device=G_less.device)
-    rc = sse_pi_fwd(d, nbr, dH, G_less, G_greater, scale, SSE_MODE_FP64, flags, out[0], out[1], ws, ws.numel(),
-                    stream)
+    rc = sse_pi_fwd(d, nbr, dH, G_less, G_greater, scale, m, flags, out[0], out[1], ws, ws.numel(), stream)
     if rc != 0:
         raise SseError(rc, "sse_pi_fwd")
     return out

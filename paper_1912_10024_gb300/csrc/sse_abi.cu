@@ -214,9 +214,16 @@ extern "C" int sse_dcomb_bwd(const sse_dims* d, const int32_t* nbr, const double
     return finish(e, status, flags, st);
 }
 
+namespace {
+// FP64 and FP64_FFT: FP64 transforms; FP32_FFT: FP32 transforms and products.
+size_t pi_workspace(const sse_dims& d, int mode) {
+    return mode == SSE_MODE_FP32_FFT ? sse::spectral_pi32_workspace(d) : sse::spectral_pi_workspace(d);
+}
+}  // namespace
+
 extern "C" size_t sse_pi_workspace_bytes(const sse_dims* d, int mode, uint32_t flags) {
     if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags) || !supported_dims(d)) return 0;
-    return sse::kStatusBytes + sse::spectral_pi_workspace(*d);
+    return sse::kStatusBytes + pi_workspace(*d, mode);
 }
 
 extern "C" int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* G_less,
@@ -228,19 +235,18 @@ extern "C" int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* d
     if (!aligned(nbr, 4) || !aligned(dH, 16) || !aligned(G_less, 16) || !aligned(G_greater, 16) ||
         !aligned(P_less, 16) || !aligned(P_greater, 16))
         return SSE_ERR_INVALID_ARG;
-    if (!supported_dims(d) || !fp64_mode(mode)) return SSE_ERR_UNSUPPORTED;
-    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + sse::spectral_pi_workspace(*d))
+    if (!supported_dims(d) || !(fp64_mode(mode) || mode == SSE_MODE_FP32_FFT)) return SSE_ERR_UNSUPPORTED;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + pi_workspace(*d, mode))
         return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned* status = static_cast<unsigned*>(workspace);
     if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SSE_ERR_CUDA;
-    cudaError_t e = sse::spectral_pi(*d, nbr, reinterpret_cast<const double2*>(dH),
-                                     reinterpret_cast<const double2*>(G_less),
-                                     reinterpret_cast<const double2*>(G_greater), scale, flags,
-                                     reinterpret_cast<double2*>(P_less), reinterpret_cast<double2*>(P_greater), status,
-                                     static_cast<char*>(workspace) + sse::kStatusBytes,
-                                     ws_bytes - sse::kStatusBytes, st);
+    auto* run = mode == SSE_MODE_FP32_FFT ? sse::spectral_pi32 : sse::spectral_pi;
+    cudaError_t e = run(*d, nbr, reinterpret_cast<const double2*>(dH), reinterpret_cast<const double2*>(G_less),
+                        reinterpret_cast<const double2*>(G_greater), scale, flags, reinterpret_cast<double2*>(P_less),
+                        reinterpret_cast<double2*>(P_greater), status,
+                        static_cast<char*>(workspace) + sse::kStatusBytes, ws_bytes - sse::kStatusBytes, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
 }

@@ -103,12 +103,17 @@ cudaError_t spectral_bwd_g32(const Problem& p, const double2* gS_less, const dou
                              double2* g_G_less, double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes,
                              cudaStream_t st);
 
-// Phonon self-energy of Eq. (4), transform-based FP64 (sse_spectral.cu).
+// Phonon self-energy of Eq. (4), transform-based: FP64 (spectral_pi) or FP32 transforms and products with FP64
+// inputs and outputs (spectral_pi32) (sse_spectral.cu).
 size_t spectral_pi_workspace(const sse_dims& d);
 bool spectral_pi_supported(const sse_dims& d);
 cudaError_t spectral_pi(const sse_dims& d, const int32_t* nbr, const double2* dH, const double2* G_less,
                         const double2* G_greater, double scale, uint32_t flags, double2* P_less, double2* P_greater,
                         unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t spectral_pi32_workspace(const sse_dims& d);
+cudaError_t spectral_pi32(const sse_dims& d, const int32_t* nbr, const double2* dH, const double2* G_less,
+                          const double2* G_greater, double scale, uint32_t flags, double2* P_less,
+                          double2* P_greater, unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st);
 
 // Bond weights D_ba - D_bb - D_aa + D_ab from raw phonon Green's functions (sse_dcomb.cu).
 cudaError_t dcomb_fwd(const sse_dims& d, const int32_t* nbr, const double2* raw_l, const double2* raw_g,

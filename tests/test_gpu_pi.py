@@ -1,6 +1,8 @@
-"""Phonon self-energy Pi of Eq. (4) (sse_pi_fwd, FP64 through the convolution theorem) against the oracle.
+"""Phonon self-energy Pi of Eq. (4) (sse_pi_fwd through the convolution theorem, FP64 and FP32_FFT) against the
+oracle.
 
-Tolerance: normwise max|gpu - oracle| / max|oracle| <= 1e-12 per output tensor.
+Tolerance: normwise max|gpu - oracle| / max|oracle| <= 1e-12 per output tensor in FP64; the stated FP32_FFT bound
+below for the FP32 path.
 Cases: every FFT radix (2, 3, 4), Nqz < Nkz, a single kz point, Norb from 1 to 16,
 atom ranges, the symmetrisation flag, a bad neighbour index, and the
 adjoint and FinFET workloads on sampled atoms (exact sub-problems: the atom
@@ -154,3 +156,58 @@ def test_antihermitian_half_spectrum(dims):
     with pytest.raises(B.SseError) as e:
         gpu_pi(inp, dims, antihermitian=True, check=True)
     assert e.value.status == 5
+
+
+# mode FP32_FFT: FP32 transforms and products (FP64 inputs and outputs); the per-frequency traces carry a relative
+# error of a few unit roundoffs times the transform depth, so a few 1e-7 normwise; stated bound 2e-6 as for the
+# FP32_FFT forward of Eq. (3)
+FP32_BOUND = 2e-6
+
+
+@pytest.mark.parametrize("dims", [
+    TINY,
+    Dims(NA=7, NB=2, Norb=3, NE=61, Nkz=4, Nqz=3, Nw=5),      # Nqz < Nkz, L = 72
+    Dims(NA=6, NB=4, Norb=5, NE=47, Nkz=3, Nqz=3, Nw=9),      # odd Norb (padded tiles), L = 64
+    Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11),    # L = 54
+    Dims(NA=3, NB=2, Norb=16, NE=45, Nkz=2, Nqz=2, Nw=40),    # L = 96
+    Dims(NA=6, NB=3, Norb=1, NE=100, Nkz=9, Nqz=4, Nw=25),    # Norb = 1, L = 128
+], ids=lambda d: f"Norb{d.Norb}_NE{d.NE}_Nw{d.Nw}_Nkz{d.Nkz}")
+@pytest.mark.parametrize("antihermitian", [False, True])
+def test_fp32_vs_oracle(dims, antihermitian):
+    nbr = None if dims is TINY else ring_neighbours(dims.NA, dims.NB)
+    inp = make_inputs(dims, seed=dims.Norb + 800, nbr=nbr)
+    Pl, Pg = gpu_pi(inp, dims, check=True, mode="fp32_fft", antihermitian=antihermitian)
+    Ol, Og = oracle_pi(inp, dims)
+    errs = [normwise(Pl.cpu().numpy(), Ol), normwise(Pg.cpu().numpy(), Og)]
+    print("fp32 pi", dims, antihermitian, errs)
+    assert max(errs) <= FP32_BOUND
+
+
+def test_fp32_atom_range_and_symmetrize():
+    inp = make_inputs(TINY, seed=13)
+    g = inp.to("cuda")
+    shape = (TINY.Nqz, TINY.Nw, TINY.NA, TINY.NB + 1, 3, 3)
+    out = (torch.full(shape, 7 + 7j, dtype=torch.complex128, device="cuda"),
+           torch.full(shape, 7 + 7j, dtype=torch.complex128, device="cuda"))
+    B.pi(g.G_less, g.G_greater, g.dH, g.nbr, TINY.Nqz, TINY.Nw, atoms=(3, 9), out=out, mode="fp32_fft")
+    Ol, Og = oracle_pi(inp, TINY, a_range=(3, 9))
+    for P, O in zip(out, (Ol, Og)):
+        P = P.cpu().numpy()
+        assert normwise(P[:, :, 3:9], O[:, :, 3:9]) <= FP32_BOUND
+        assert np.all(P[:, :, :3] == 7 + 7j) and np.all(P[:, :, 9:] == 7 + 7j)
+    inp.G_less = inp.G_less * (1 + 0.3j)
+    Pl, _ = gpu_pi(inp, TINY, symmetrize=True, mode="fp32_fft")
+    Ol, _ = oracle_pi(inp, TINY)
+    assert normwise(Pl.cpu().numpy(), 0.5 * (Ol - np.swapaxes(Ol.conj(), -1, -2))) <= FP32_BOUND
+
+
+def test_fp32_finfet_workload_vs_fp64():
+    """NA=1024, Norb=10, NE=512, Nkz=Nqz=7, Nw=32: the FP32_FFT result against the FP64 one (itself pinned to the
+    oracle on sampled atoms above)."""
+    inp = make_inputs(FINFET, seed=0, device="cuda")
+    args = (inp.G_less, inp.G_greater, inp.dH, inp.nbr, FINFET.Nqz, FINFET.Nw)
+    ref = B.pi(*args)
+    got = B.pi(*args, mode="fp32_fft", check=True)
+    errs = [float((x - y).abs().max() / y.abs().max()) for x, y in zip(got, ref)]
+    print("fp32 pi at FinFET", errs)
+    assert max(errs) <= FP32_BOUND
