@@ -99,6 +99,14 @@ def spectral_prod_flops(d, half: bool = False) -> float:
     return 2.0 * d.NA * d.NB * freq_count(d, half) * nel * (36 + 18 * d.Norb)
 
 
+def spectral_prod32_flops(d, half: bool = False) -> float:
+    """FP32 flops one spec_prod32_kernel launch (one type) executes: per (atom, slot, frequency) and element of
+    the block padded to an even order Np, P_j = G^ dH_j^H and sum_i dH_i U_i (3 Norb complex MACs each at
+    4 FMA) and U_i = sum_j K_ij P_j (9 complex MACs at 4 FMA); 2 flops per FMA."""
+    Np = d.Norb + (d.Norb & 1)
+    return 2.0 * d.NA * d.NB * freq_count(d, half) * Np * Np * (36 + 24 * d.Norb)
+
+
 def spectral_pi_flops(d, half: bool = False) -> float:
     """FP64 flops one spec_pi_kernel launch (both types) executes: per (type, atom, slot, frequency) and block
     element, the half products dH_i^H G^ and dH_j G^ (3 Norb complex MACs each at 3 FMA) and the 9 trace
@@ -134,24 +142,42 @@ def mixed_tensor_flops(d, mode: str) -> float:
 
 # DRAM bytes (read + write) per unit of work measured by ncu for the transform-path kernels
 # (profiles/spec_*_adjoint_ncu_full.md), valid for the kernel source they were taken on.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit from one ncu capture at the adjoint workload,
+# with the sha256 prefix of the captured kernel's own source text: the figure is dropped (None) once that kernel
+# has changed.
 NCU_TRAFFIC = {
-    "spec_prod_kernel": (4815.4, "2ba2b18d9ccb2e47", "atom-frequency of one type"),
-    "spec_pi_kernel": (5033.6, "2ba2b18d9ccb2e47", "type-atom-frequency"),
-    "spec_adj_kernel": (13877.8, "2ba2b18d9ccb2e47", "atom-frequency of one type"),
-    "spec_prod32_kernel": (1949.4, "2ba2b18d9ccb2e47", "atom-frequency of one type"),
+    "spec_prod_kernel": (4815.4, "a19635f8b1e45065", "atom-frequency of one type"),
+    "spec_pi_kernel": (5033.6, "9a225dfc2cb7d028", "type-atom-frequency"),
+    "spec_adj_kernel": (13897.1, "3cadf5d36e3c5bb6", "atom-frequency of one type"),
+    "spec_prod32_kernel": (1921.4, "e6a1c46d02ca7b4d", "atom-frequency of one type"),
+    "spec_adj32_kernel": (7534.4, "30d825477df7deb4", "atom-frequency of one type"),
+    "spec_pi32_kernel": (2115.9, "bb24b43dfebce1f6", "type-atom-frequency"),
+    "spec_gradg32_kernel": (1862.2, "83df7f0c3695b0a5", "atom-frequency of one type"),
 }
+
+
+def kernel_source_sha(kernel: str) -> str:
+    """sha256 prefix of a kernel's source text in sse_spectral.cu: from the line that opens its definition
+    (`__global__ ... <kernel>(`) to the first closing brace in column 0."""
+    import hashlib
+    import re
+    with open(os.path.join(ROOT, "paper_1912_10024_gb300", "csrc", "sse_spectral.cu")) as f:
+        src = f.read()
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\(", src)
+    if m is None:
+        return ""
+    end = src.find("\n}\n", m.end())
+    return hashlib.sha256(src[m.start():end + 3].encode()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, units: float):
     """Per-launch DRAM traffic scaled from the ncu capture by the units one launch processes, or None
-    when the kernel source changed since the capture."""
-    import hashlib
+    when the kernel's source changed since the capture."""
     if kernel not in NCU_TRAFFIC:
         return None
     per, sha, _ = NCU_TRAFFIC[kernel]
-    with open(os.path.join(ROOT, "paper_1912_10024_gb300", "csrc", "sse_spectral.cu"), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != sha:
-            return None
+    if kernel_source_sha(kernel) != sha:
+        return None
     return per * units
 
 
@@ -625,7 +651,7 @@ def main():
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
         elif args.mode == "fp32_fft":
             ks, n = kernel_s("spec_prod_kernel")
-            achieved = spectral_prod_flops(d, args.antihermitian) / ks / 1e12
+            achieved = spectral_prod32_flops(d, args.antihermitian) / ks / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_PEAK_TFLOPS,
                     "traffic": ncu_traffic("spec_prod32_kernel", d.NA * freq_count(d, args.antihermitian)),

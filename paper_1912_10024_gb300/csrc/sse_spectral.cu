@@ -277,7 +277,9 @@ struct StoreSigmaT {  // S[k][E][a_begin*nel + col] = conj(v) * inv in FP64, E <
     double inv;
     int rows;
     __device__ void operator()(int k, int r, size_t col, C v) const {
-        S[((size_t)k * NE + r) * rowlen + col0 + col] = make_double2((double)v.x * inv, -(double)v.y * inv);
+        using R = typename CT<C>::R;
+        const R s = (R)inv;  // scaled in the transform's precision, then widened
+        S[((size_t)k * NE + r) * rowlen + col0 + col] = make_double2((double)(v.x * s), (double)(-v.y * s));
     }
 };
 using StoreSigma = StoreSigmaT<double2>;
