@@ -1969,9 +1969,14 @@ __global__ void spec_gradg_kernel(ProdCfg c, sse_dims d, const int* __restrict__
 // ---------------------------------------------------------------------------
 struct Prod32Cfg {
     int Np, TN, T, F, threads, fchunk;
-    int pl;  // floats per Np x Np plane
+    int pl;      // floats per Np x Np plane
+    int gs, us;  // floats per frequency of the G^ and U regions, padded to 16 mod 32 (see below)
     int off_A, off_G, off_K, off_U, smem;
 };
+
+// A warp holds the tile threads of two adjacent frequencies; per-frequency strides of 16 mod 32 floats put their
+// rows of a plane on disjoint shared-memory banks.
+inline int bank_pad16(int floats) { return floats + ((16 - floats % 32) + 32) % 32; }
 
 // FP32 products use the 4-multiply complex MAC on (re, im) planes: with shared-memory bandwidth, not the FP32
 // pipe, the limit, two planes per operand (4 loads per 16 FMAs of a 2 x 2 tile) beat the 3-multiply form's
@@ -1985,13 +1990,15 @@ Prod32Cfg make_prod32_cfg(const sse_dims& d, size_t nfreq) {
     c.pl = c.Np * c.Np;
     const int pb = c.pl * 4;  // bytes per plane
     auto a16 = [](int x) { return (x + 15) & ~15; };
-    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 6 * pb + F * (8 * pb + 9 * 8) + 64; });
+    c.gs = bank_pad16(2 * c.pl);
+    c.us = bank_pad16(6 * c.pl);
+    c.F = pick_frequencies(c.T, [&](int F) { return (long)d.NB * 6 * pb + F * (4L * (c.gs + c.us) + 9 * 8) + 64; });
     c.threads = ((c.F * c.T + 31) / 32) * 32;
     c.off_A = 0;                                  // [NB][3 dir][2 planes] dH transposed: AT[l][m] = dH[m][l]
-    c.off_G = a16(c.off_A + d.NB * 6 * pb);       // [F][2 planes] G^ transposed: GT[l][m] = G^[m][l]
-    c.off_K = a16(c.off_G + c.F * 2 * pb);        // [F][9] float2
-    c.off_U = a16(c.off_K + c.F * 9 * 8);         // [F][3 i][2 planes] U_i row-major
-    c.smem = a16(c.off_U + c.F * 6 * pb);
+    c.off_G = a16(c.off_A + d.NB * 6 * pb);       // [F][gs] G^ transposed (2 planes): GT[l][m] = G^[m][l]
+    c.off_K = a16(c.off_G + c.F * c.gs * 4);      // [F][9] float2
+    c.off_U = a16(c.off_K + c.F * 9 * 8);         // [F][us] U_i row-major (3 i x 2 planes)
+    c.smem = a16(c.off_U + c.F * c.us * 4);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
     size_t chunks = (want + nA - 1) / (nA ? nA : 1);
@@ -2047,7 +2054,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
             const bool bok = b >= 0 && b < d.NA;
             // G^_b(f) -> GT planes: element (m, n) goes to GT[n][m]
             if (lane) {
-                float* Gp = sG + (size_t)fl * 2 * pl;
+                float* Gp = sG + (size_t)fl * c.gs;
 #pragma unroll
                 for (int dm = 0; dm < 2; ++dm)
 #pragma unroll
@@ -2071,7 +2078,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
             // P_j = G^ A_j^H for the three j at once: P_j[m][n] = sum_l GT[l][m] conj(AT_j[l][n]);
             // U_i = G^ W_i = sum_j K_ij P_j
             if (lane) {
-                const float* Gp = sG + (size_t)fl * 2 * pl;
+                const float* Gp = sG + (size_t)fl * c.gs;
                 float pr[3][4] = {}, pim[3][4] = {};
                 for (int l = 0; l < Norb; ++l) {
                     const float2 gr = ld2(Gp + l * Np + m0), gi = ld2(Gp + pl + l * Np + m0);
@@ -2095,7 +2102,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
                             ui[q] = fmaf(k.y, pr[j][q], ui[q]);
                         }
                     }
-                    float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
+                    float* Up = sU + (size_t)fl * c.us + (size_t)i * 2 * pl;
 #pragma unroll
                     for (int dm = 0; dm < 2; ++dm) {
                         float* o = Up + (m0 + dm) * Np + n0;
@@ -2110,7 +2117,7 @@ __global__ void spec_prod32_kernel(Prod32Cfg c, sse_dims d, FreqMap fm, const in
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     const float* Ap = A + (size_t)i * 2 * pl;
-                    const float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
+                    const float* Up = sU + (size_t)fl * c.us + (size_t)i * 2 * pl;
                     for (int l = 0; l < Norb; ++l) {
                         const float2 ar = ld2(Ap + l * Np + m0), ai = ld2(Ap + pl + l * Np + m0);
                         const float2 vr = ld2(Up + l * Np + n0), vi = ld2(Up + pl + l * Np + n0);

@@ -6,7 +6,8 @@ checked against the FP64 oracle on sampled blocks (grid edges, window
 boundaries, interior); the phonon self-energy Pi on a sampled atom; the
 FP64 adjoint on a subset of atoms checked against central differences of the
 FP64 forward; and the transform-based adjoint on a subset of atoms against
-the direct one.
+the direct one. The FP32_FFT forward, Pi and adjoint are checked the same way
+to their stated bounds (2e-6, 2e-6, 1e-5).
 """
 import math
 
@@ -144,5 +145,59 @@ def test_large_fp64_fft_adjoint_atom_subset(large):
     for x, y, sl in zip(got, ref, (np.s_[100:108], np.s_[:, :, 100:108], np.s_[:, :, 100:108])):
         err = float((x[sl] - y[sl]).abs().max() / y[sl].abs().max())
         assert err <= 1e-12, err
+    del W, V
+    torch.cuda.empty_cache()
+
+
+def test_large_fp32_fft_sampled(large):
+    """FP32_FFT forward at the large sizes (L = 1152): sampled blocks against the oracle to the mode's bound 2e-6."""
+    inp = large
+    Sl, Sg = B.sigma(inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, mode="fp32_fft",
+                     check=True)
+    torch.cuda.synchronize()
+    errs = []
+    for (a, E0, E1) in [(0, 0, 2), (4095, 1022, 1024), (2047, 511, 513), (77, 700, 702)]:
+        Ol, Og = oracle_blocks(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, a,
+                               E0, E1)
+        for S, O in ((Sl, Ol), (Sg, Og)):
+            errs.append(normwise(S[:, E0:E1, a].cpu().numpy(), O))
+    print("large fp32_fft sampled errors", errs)
+    assert max(errs) <= 2e-6
+    del Sl, Sg
+    torch.cuda.empty_cache()
+
+
+def test_large_fp32_pi_sampled(large):
+    """FP32_FFT Pi at the large sizes on one atom against the oracle's exact sub-problem (bound 2e-6)."""
+    import oracle
+    inp = large
+    Pl, Pg = B.pi(inp.G_less, inp.G_greater, inp.dH, inp.nbr, LARGE.Nqz, LARGE.Nw, check=True, mode="fp32_fft")
+    torch.cuda.synchronize()
+    a = 1234
+    nb = [int(x) for x in inp.nbr[a].cpu()]
+    idx = torch.tensor([a] + nb, device="cuda")
+    nbr = torch.zeros((len(nb) + 1, len(nb)), dtype=torch.int32)
+    nbr[0] = torch.arange(1, len(nb) + 1, dtype=torch.int32)
+    Ol, Og = oracle.pi(nbr, inp.dH.index_select(0, idx).cpu(), inp.G_less.index_select(2, idx).cpu(),
+                       inp.G_greater.index_select(2, idx).cpu(), SCALE, LARGE.Nqz, LARGE.Nw, a_range=(0, 1))
+    errs = [normwise(P[:, :, a].cpu().numpy(), O[:, :, 0]) for P, O in ((Pl, Ol), (Pg, Og))]
+    print("large fp32 pi errors", errs)
+    assert max(errs) <= 2e-6
+    del Pl, Pg
+    torch.cuda.empty_cache()
+
+
+def test_large_fp32_fft_adjoint_atom_subset(large):
+    """FP32_FFT adjoint at the large sizes for atoms [100, 108) against the direct FP64 adjoint (bound 1e-5)."""
+    inp = large
+    W, V = make_upstream(LARGE, seed=10, device="cuda")
+    args = (inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr, W, V)
+    got = B.sigma_grad(*args, mode="fp32_fft", atoms=(100, 108), check=True)
+    ref = B.sigma_grad(*args, mode="fp64", atoms=(100, 108))
+    errs = []
+    for x, y, sl in zip(got, ref, (np.s_[100:108], np.s_[:, :, 100:108], np.s_[:, :, 100:108])):
+        errs.append(float((x[sl] - y[sl]).abs().max() / y[sl].abs().max()))
+    print("large fp32 adjoint errors", errs)
+    assert max(errs) <= 1e-5
     del W, V
     torch.cuda.empty_cache()
