@@ -157,17 +157,20 @@ NCU_TRAFFIC = {
 
 
 def kernel_source_sha(kernel: str) -> str:
-    """sha256 prefix of a kernel's source text in sse_spectral.cu: from the line that opens its definition
+    """sha256 prefix of a kernel's source text in the library's sources: from the line that opens its definition
     (`__global__ ... <kernel>(`) to the first closing brace in column 0."""
+    import glob
     import hashlib
     import re
-    with open(os.path.join(ROOT, "paper_1912_10024_gb300", "csrc", "sse_spectral.cu")) as f:
-        src = f.read()
-    m = re.search(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\(", src)
-    if m is None:
-        return ""
-    end = src.find("\n}\n", m.end())
-    return hashlib.sha256(src[m.start():end + 3].encode()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_1912_10024_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(path) as f:
+            src = f.read()
+        m = re.search(r"__global__[^;{]*?\b" + re.escape(kernel) + r"\(", src)
+        if m is not None:
+            end = src.find("\n}\n", m.end())
+            return hashlib.sha256(src[m.start():end + 3].encode()).hexdigest()[:16]
+    return ""
 
 
 def ncu_traffic(kernel: str, units: float):

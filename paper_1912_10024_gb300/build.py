@@ -39,7 +39,8 @@ def _sources():
 def _fingerprint() -> str:
     h = hashlib.sha1()
     h.update(" ".join(NVCC_FLAGS).encode())
-    for f in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))):
+    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+    for f in _sources() + sorted(headers + glob.glob(os.path.join(INCLUDE, "*.h"))):
         h.update(f.encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

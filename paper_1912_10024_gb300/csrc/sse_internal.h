@@ -64,7 +64,7 @@ size_t mixed_fwd_workspace(const sse_dims& d, int mode);
 cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status,
                       void* ws, size_t ws_bytes, cudaStream_t st);
 
-// Transform-based FP64 forward (sse_spectral.cu): FFT length along E, size limits, workspace.
+// Transform-based forward (sse_spectral_fwd.cu): FFT length along E, size limits, workspace.
 int spectral_length(const sse_dims& d);
 bool spectral_supported(const sse_dims& d);
 size_t spectral_fwd_workspace(const sse_dims& d);
@@ -80,7 +80,7 @@ size_t spectral_fwd32_workspace(const sse_dims& d);
 cudaError_t spectral_fwd32(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                            size_t ws_bytes, cudaStream_t st);
 
-// Transform-based FP64 adjoint of Eq. (3) (sse_spectral.cu).
+// Transform-based adjoint of Eq. (3), FP64 and FP32 (sse_spectral_adj.cu).
 size_t spectral_bwd_workspace(const sse_dims& d);
 bool spectral_bwd_supported(const sse_dims& d);
 cudaError_t spectral_bwd(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_dH,
@@ -94,7 +94,7 @@ cudaError_t spectral_bwd32(const Problem& p, const double2* gS_less, const doubl
                            cudaStream_t st);
 
 // Gradient with respect to G, transform-based: FP64 (spectral_bwd_g) or FP32 transforms and products with FP64
-// inputs and outputs (spectral_bwd_g32) (sse_spectral.cu).
+// inputs and outputs (spectral_bwd_g32) (sse_spectral_adj.cu).
 size_t spectral_bwd_g_workspace(const sse_dims& d);
 cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_G_less,
                            double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st);
@@ -104,7 +104,7 @@ cudaError_t spectral_bwd_g32(const Problem& p, const double2* gS_less, const dou
                              cudaStream_t st);
 
 // Phonon self-energy of Eq. (4), transform-based: FP64 (spectral_pi) or FP32 transforms and products with FP64
-// inputs and outputs (spectral_pi32) (sse_spectral.cu).
+// inputs and outputs (spectral_pi32) (sse_spectral_pi.cu).
 size_t spectral_pi_workspace(const sse_dims& d);
 bool spectral_pi_supported(const sse_dims& d);
 cudaError_t spectral_pi(const sse_dims& d, const int32_t* nbr, const double2* dH, const double2* G_less,
