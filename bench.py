@@ -149,10 +149,10 @@ NCU_TRAFFIC = {
     "spec_prod_kernel": (4815.4, "a19635f8b1e45065", "atom-frequency of one type"),
     "spec_pi_kernel": (5033.6, "9a225dfc2cb7d028", "type-atom-frequency"),
     "spec_adj_kernel": (13897.1, "3cadf5d36e3c5bb6", "atom-frequency of one type"),
-    "spec_prod32_kernel": (1921.4, "e6a1c46d02ca7b4d", "atom-frequency of one type"),
-    "spec_adj32_kernel": (7534.4, "30d825477df7deb4", "atom-frequency of one type"),
-    "spec_pi32_kernel": (2115.9, "bb24b43dfebce1f6", "type-atom-frequency"),
-    "spec_gradg32_kernel": (1862.2, "83df7f0c3695b0a5", "atom-frequency of one type"),
+    "spec_prod32_kernel": (1923.2, "f34fb6e78487019a", "atom-frequency of one type"),
+    "spec_adj32_kernel": (7533.4, "8e9f1b2f0231170c", "atom-frequency of one type"),
+    "spec_pi32_kernel": (2121.4, "3f8eabc933beac4b", "type-atom-frequency"),
+    "spec_gradg32_kernel": (1863.7, "aa646c7c1d04f57d", "atom-frequency of one type"),
 }
 
 

@@ -539,6 +539,10 @@ __device__ __forceinline__ void put3(T* P, int nel, int e, C v) {
     P[2 * nel + e] = v.x + v.y;
 }
 
+// The FP32 tile kernels place the tile threads of two adjacent frequencies in one warp; per-frequency strides of
+// 16 mod 32 floats put their rows of a plane on disjoint shared-memory banks.
+inline int bank_pad16(int floats) { return floats + ((16 - floats % 32) + 32) % 32; }
+
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 inline unsigned grid_for(size_t work, int threads) {

@@ -255,6 +255,7 @@ spec_adj_kernel(AdjCfg c, sse_dims d, const int32_t* __restrict__ nbr, const dou
 // ---------------------------------------------------------------------------
 struct GradG32Cfg {
     int Np, TN, T, pl, F, threads, fchunk;
+    int ws, us;  // floats per frequency of the W^ and U regions, bank-padded
     int off_A, off_W, off_K, off_U, smem;
 };
 
@@ -266,13 +267,15 @@ GradG32Cfg make_gradg32_cfg(const sse_dims& d, size_t nfreq) {
     c.pl = c.Np * c.Np;
     const int pb = c.pl * 4;
     auto a16 = [](int x) { return (x + 15) & ~15; };
-    c.F = pick_frequencies(c.T, [&](int F) { return (long)6 * pb + F * (8L * pb + 9 * 8) + 64; });
+    c.ws = bank_pad16(2 * c.pl);
+    c.us = bank_pad16(6 * c.pl);
+    c.F = pick_frequencies(c.T, [&](int F) { return (long)6 * pb + F * (4L * (c.ws + c.us) + 9 * 8) + 64; });
     c.threads = ((c.F * c.T + 31) / 32) * 32;
-    c.off_A = 0;                            // [3 j][2 planes] the current bond's A_j row-major
-    c.off_W = a16(c.off_A + 6 * pb);        // [F][2 planes] W^_a transposed: WT[l][m] = W^[m][l]
-    c.off_K = a16(c.off_W + c.F * 2 * pb);  // [F][9] float2
-    c.off_U = a16(c.off_K + c.F * 9 * 8);   // [F][3 i][2 planes] U_i row-major
-    c.smem = a16(c.off_U + c.F * 6 * pb);
+    c.off_A = 0;                             // [3 j][2 planes] the current bond's A_j row-major
+    c.off_W = a16(c.off_A + 6 * pb);         // [F][ws] W^_a transposed (2 planes): WT[l][m] = W^[m][l]
+    c.off_K = a16(c.off_W + c.F * c.ws * 4);  // [F][9] float2
+    c.off_U = a16(c.off_K + c.F * 9 * 8);    // [F][us] U_i row-major (3 i x 2 planes)
+    c.smem = a16(c.off_U + c.F * c.us * 4);
     // every target atom gets a CTA column: enough frequency chunks for ~8 waves of 2 CTAs per SM
     size_t want = (size_t)152 * 2 * 8;
     size_t chunks = (want + (size_t)d.NA - 1) / (size_t)(d.NA ? d.NA : 1);
@@ -321,7 +324,7 @@ __global__ void spec_gradg32_kernel(GradG32Cfg c, sse_dims d, const int* __restr
                 sA[(size_t)j * 2 * pl + pl + e] = (float)v.y;
             }
             if (lane) {
-                float* Wp = sW + (size_t)fl * 2 * pl;
+                float* Wp = sW + (size_t)fl * c.ws;
 #pragma unroll
                 for (int dm = 0; dm < 2; ++dm)
 #pragma unroll
@@ -341,7 +344,7 @@ __global__ void spec_gradg32_kernel(GradG32Cfg c, sse_dims d, const int* __restr
             __syncthreads();
             // P_j = W^ A_j (three at once), U_i = sum_j conj(K_ij) P_j
             if (lane) {
-                const float* Wp = sW + (size_t)fl * 2 * pl;
+                const float* Wp = sW + (size_t)fl * c.ws;
                 float pr[3][4] = {}, pi[3][4] = {};
                 for (int l = 0; l < Norb; ++l) {
                     const float2 xr = ld2(Wp + l * Np + m0), xi = ld2(Wp + pl + l * Np + m0);
@@ -365,7 +368,7 @@ __global__ void spec_gradg32_kernel(GradG32Cfg c, sse_dims d, const int* __restr
                             ui[q] = fmaf(-k.y, pr[j][q], ui[q]);
                         }
                     }
-                    float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
+                    float* Up = sU + (size_t)fl * c.us + (size_t)i * 2 * pl;
 #pragma unroll
                     for (int dm = 0; dm < 2; ++dm) {
                         st2(Up + (m0 + dm) * Np + n0, ur[dm * 2], ur[dm * 2 + 1]);
@@ -379,7 +382,7 @@ __global__ void spec_gradg32_kernel(GradG32Cfg c, sse_dims d, const int* __restr
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     const float* Ap = sA + (size_t)i * 2 * pl;
-                    const float* Up = sU + ((size_t)fl * 3 + i) * 2 * pl;
+                    const float* Up = sU + (size_t)fl * c.us + (size_t)i * 2 * pl;
                     for (int l = 0; l < Norb; ++l)
                         cmac2x2<true, false>(accr, acci, ld2(Ap + l * Np + m0), ld2(Ap + pl + l * Np + m0),
                                              ld2(Up + l * Np + n0), ld2(Up + pl + l * Np + n0));
@@ -408,6 +411,7 @@ __global__ void spec_gradg32_kernel(GradG32Cfg c, sse_dims d, const int* __restr
 // ---------------------------------------------------------------------------
 struct Adj32Cfg {
     int Np, TN, T, pl, F, threads, fchunk, nchunks;
+    int qs, ss;  // floats per frequency of the W^ / G^ regions (4 planes) and the T_j / V_j regions (6), bank-padded
     int off_A, off_W, off_G, off_K, off_T, off_V, smem;
 };
 
@@ -423,7 +427,9 @@ Adj32Cfg make_adj32_cfg(const sse_dims& d, size_t nfreq) {
     auto a16 = [](int x) { return (x + 15) & ~15; };
     // per CTA: the bond's 3 dH (2 planes); per frequency W^ and G^ in both layouts (8 planes), K (9 float2),
     // T_j and V_j transposed (12 planes; the trace partials reuse the T_j planes)
-    auto smem_of = [&](int F) { return (long)6 * pb + F * (20L * pb + 9 * 8) + 96; };
+    c.qs = bank_pad16(4 * c.pl);
+    c.ss = bank_pad16(6 * c.pl);
+    auto smem_of = [&](int F) { return (long)6 * pb + F * (4L * (2 * c.qs + 2 * c.ss) + 9 * 8) + 96; };
     c.F = 1;
     long best = -1, best_sm = 0;
     for (int F = 1; F * c.T <= kAdj32MaxThreads; ++F) {
@@ -438,12 +444,12 @@ Adj32Cfg make_adj32_cfg(const sse_dims& d, size_t nfreq) {
     }
     c.threads = ((c.F * c.T + 31) / 32) * 32;
     c.off_A = 0;                                  // [3 j][2 planes] A_j row-major
-    c.off_W = a16(c.off_A + 6 * pb);              // [F][4 planes] W^ row-major (re, im), transposed (re, im)
-    c.off_G = a16(c.off_W + c.F * 4 * pb);        // [F][4 planes] G^ likewise
-    c.off_K = a16(c.off_G + c.F * 4 * pb);        // [F][9] float2
-    c.off_T = a16(c.off_K + c.F * 9 * 8);         // [F][3 j][2 planes] T_j transposed
-    c.off_V = a16(c.off_T + c.F * 6 * pb);        // [F][3 j][2 planes] V_j transposed
-    c.smem = a16(c.off_V + c.F * 6 * pb);
+    c.off_W = a16(c.off_A + 6 * pb);              // [F][qs] W^ row-major (re, im), transposed (re, im)
+    c.off_G = a16(c.off_W + c.F * c.qs * 4);      // [F][qs] G^ likewise
+    c.off_K = a16(c.off_G + c.F * c.qs * 4);      // [F][9] float2
+    c.off_T = a16(c.off_K + c.F * 9 * 8);         // [F][ss] T_j transposed (3 j x 2 planes)
+    c.off_V = a16(c.off_T + c.F * c.ss * 4);      // [F][ss] V_j transposed
+    c.smem = a16(c.off_V + c.F * c.ss * 4);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
     size_t chunks = (want + nA - 1) / (nA ? nA : 1);
@@ -498,8 +504,8 @@ spec_adj32_kernel(Adj32Cfg c, sse_dims d, const int32_t* __restrict__ nbr, const
             const bool act = lane && f < f_end && bok;
             // W^_a(f) and G^_b(f), both layouts, zero-padded
             if (lane) {
-                float* Wp = sW + (size_t)fl * 4 * pl;
-                float* Gp = sG + (size_t)fl * 4 * pl;
+                float* Wp = sW + (size_t)fl * c.qs;
+                float* Gp = sG + (size_t)fl * c.qs;
 #pragma unroll
                 for (int dm = 0; dm < 2; ++dm)
 #pragma unroll
@@ -531,7 +537,7 @@ spec_adj32_kernel(Adj32Cfg c, sse_dims d, const int32_t* __restrict__ nbr, const
             __syncthreads();
             // T_j[m][n] = sum_l W^[m][l] A_j[l][n],  V_j[m][n] = sum_l conj(W^[l][m]) A_j[l][n]
             if (lane) {
-                const float* Wp = sW + (size_t)fl * 4 * pl;
+                const float* Wp = sW + (size_t)fl * c.qs;
                 float tr[3][4] = {}, ti[3][4] = {}, vr[3][4] = {}, vi[3][4] = {};
                 for (int l = 0; l < Norb; ++l) {
                     const float2 xr = ld2(Wp + 2 * pl + l * Np + m0), xi = ld2(Wp + 3 * pl + l * Np + m0);
@@ -546,8 +552,8 @@ spec_adj32_kernel(Adj32Cfg c, sse_dims d, const int32_t* __restrict__ nbr, const
                 }
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    float* Tp = sT + ((size_t)fl * 3 + j) * 2 * pl;
-                    float* Vp = sV + ((size_t)fl * 3 + j) * 2 * pl;
+                    float* Tp = sT + (size_t)fl * c.ss + (size_t)j * 2 * pl;
+                    float* Vp = sV + (size_t)fl * c.ss + (size_t)j * 2 * pl;
 #pragma unroll
                     for (int dn = 0; dn < 2; ++dn) {  // transposed: (T[m0][n], T[m0+1][n]) at row n
                         const int o = (n0 + dn) * Np + m0;
@@ -562,15 +568,15 @@ spec_adj32_kernel(Adj32Cfg c, sse_dims d, const int32_t* __restrict__ nbr, const
             // Q_j[m][n] = sum_l T_j[m][l] conj(G^[n][l]),  R_j[m][n] = sum_l V_j[m][l] G^[l][n]
             float hp[9][2];  // this tile's part of tr(A_i^H Q_j)
             if (lane) {
-                const float* Gp = sG + (size_t)fl * 4 * pl;
+                const float* Gp = sG + (size_t)fl * c.qs;
                 float qr[3][4] = {}, qi[3][4] = {}, rr[3][4] = {}, ri[3][4] = {};
                 for (int l = 0; l < Norb; ++l) {
                     const float2 yr = ld2(Gp + 2 * pl + l * Np + n0), yi = ld2(Gp + 3 * pl + l * Np + n0);
                     const float2 gr = ld2(Gp + l * Np + n0), gi = ld2(Gp + pl + l * Np + n0);
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        const float* Tp = sT + ((size_t)fl * 3 + j) * 2 * pl;
-                        const float* Vp = sV + ((size_t)fl * 3 + j) * 2 * pl;
+                        const float* Tp = sT + (size_t)fl * c.ss + (size_t)j * 2 * pl;
+                        const float* Vp = sV + (size_t)fl * c.ss + (size_t)j * 2 * pl;
                         cmac2x2<false, true>(qr[j], qi[j], ld2(Tp + l * Np + m0), ld2(Tp + pl + l * Np + m0), yr, yi);
                         cmac2x2<false, false>(rr[j], ri[j], ld2(Vp + l * Np + m0), ld2(Vp + pl + l * Np + m0), gr,
                                               gi);

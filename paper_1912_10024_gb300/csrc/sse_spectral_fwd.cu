@@ -145,9 +145,6 @@ struct Prod32Cfg {
     int off_A, off_G, off_K, off_U, smem;
 };
 
-// A warp holds the tile threads of two adjacent frequencies; per-frequency strides of 16 mod 32 floats put their
-// rows of a plane on disjoint shared-memory banks.
-inline int bank_pad16(int floats) { return floats + ((16 - floats % 32) + 32) % 32; }
 
 // FP32 products use the 4-multiply complex MAC on (re, im) planes: with shared-memory bandwidth, not the FP32
 // pipe, the limit, two planes per operand (4 loads per 16 FMAs of a 2 x 2 tile) beat the 3-multiply form's

@@ -178,6 +178,7 @@ constexpr int kPi32MaxThreads = 256;  // <= 128 registers at two CTAs per SM
 
 struct Pi32Cfg {
     int Np, TN, T, pl, F, threads, fchunk;
+    int xs, rs;  // floats per frequency of the X^ / Y^ regions and the R_j region, bank-padded
     int off_A, off_X, off_Y, off_R, off_self, smem;
 };
 
@@ -191,14 +192,17 @@ Pi32Cfg make_pi32_cfg(const sse_dims& d, size_t nfreq) {
     auto a16 = [](int x) { return (x + 15) & ~15; };
     // per CTA: every bond's dH row-major and transposed (12 planes per bond); per frequency X^, Y^ (4 planes),
     // R_j transposed (6 planes; the trace parts reuse them) and the diagonal-block sums (9 float2)
+    c.xs = bank_pad16(2 * c.pl);
+    c.rs = bank_pad16(6 * c.pl);
     c.F = pick_frequencies(
-        c.T, [&](int F) { return (long)d.NB * 12 * pb + F * (10L * pb + 9 * 8) + 96; }, 128, kPi32MaxThreads);
+        c.T, [&](int F) { return (long)d.NB * 12 * pb + F * (4L * (2 * c.xs + c.rs) + 9 * 8) + 96; }, 128,
+        kPi32MaxThreads);
     c.threads = ((c.F * c.T + 31) / 32) * 32;
     c.off_A = 0;                               // [NB][3][4 planes: re, im row-major; re, im transposed]
-    c.off_X = a16(c.off_A + d.NB * 12 * pb);   // [F][2 planes] X^ row-major
-    c.off_Y = a16(c.off_X + c.F * 2 * pb);     // [F][2 planes] Y^ row-major
-    c.off_R = a16(c.off_Y + c.F * 2 * pb);     // [F][3 j][2 planes] R_j transposed
-    c.off_self = a16(c.off_R + c.F * 6 * pb);  // [F][9] float2
+    c.off_X = a16(c.off_A + d.NB * 12 * pb);     // [F][xs] X^ row-major (2 planes)
+    c.off_Y = a16(c.off_X + c.F * c.xs * 4);     // [F][xs] Y^ row-major
+    c.off_R = a16(c.off_Y + c.F * c.xs * 4);     // [F][rs] R_j transposed (3 j x 2 planes)
+    c.off_self = a16(c.off_R + c.F * c.rs * 4);  // [F][9] float2
     c.smem = a16(c.off_self + c.F * 9 * 8);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
@@ -263,7 +267,7 @@ spec_pi32_kernel(Pi32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ 
         const size_t fneg = act ? freq_neg(fm, f) : 0;
         __syncthreads();  // the previous batch is done with sX and sSelf
         if (lane) {
-            float* Xp = sX + (size_t)fl * 2 * pl;
+            float* Xp = sX + (size_t)fl * c.xs;
 #pragma unroll
             for (int dm = 0; dm < 2; ++dm)
 #pragma unroll
@@ -280,7 +284,7 @@ spec_pi32_kernel(Pi32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ 
             const int b = nbr[(size_t)a * d.NB + s];
             const bool bok = b >= 0 && b < d.NA;
             if (lane) {
-                float* Yp = sY + (size_t)fl * 2 * pl;
+                float* Yp = sY + (size_t)fl * c.xs;
 #pragma unroll
                 for (int dm = 0; dm < 2; ++dm)
 #pragma unroll
@@ -297,8 +301,8 @@ spec_pi32_kernel(Pi32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ 
             // P_i[m][n] = sum_l conj(A_i[l][m]) X[l][n];  R_j[m][n] = sum_l A_j[m][l] Y[l][n] (= AT_j[l][m])
             float pr[3][4] = {}, pim[3][4] = {};
             if (lane) {
-                const float* Xp = sX + (size_t)fl * 2 * pl;
-                const float* Yp = sY + (size_t)fl * 2 * pl;
+                const float* Xp = sX + (size_t)fl * c.xs;
+                const float* Yp = sY + (size_t)fl * c.xs;
                 float rr[3][4] = {}, ri[3][4] = {};
                 for (int l = 0; l < Norb; ++l) {
                     const float2 xr = ld2(Xp + l * Np + n0), xi = ld2(Xp + pl + l * Np + n0);
@@ -313,7 +317,7 @@ spec_pi32_kernel(Pi32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ 
                 }
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    float* Rp = sR + ((size_t)fl * 3 + j) * 2 * pl;
+                    float* Rp = sR + (size_t)fl * c.rs + (size_t)j * 2 * pl;
 #pragma unroll
                     for (int dn = 0; dn < 2; ++dn) {  // transposed: (R[m0][n], R[m0+1][n]) at row n
                         const int o = (n0 + dn) * Np + m0;
@@ -328,7 +332,7 @@ spec_pi32_kernel(Pi32Cfg c, sse_dims d, FreqMap fm, const int32_t* __restrict__ 
             if (lane) {
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const float* Rp = sR + ((size_t)fl * 3 + j) * 2 * pl;
+                    const float* Rp = sR + (size_t)fl * c.rs + (size_t)j * 2 * pl;
                     float tr[4], ti[4];
 #pragma unroll
                     for (int dm = 0; dm < 2; ++dm) {
