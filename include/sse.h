@@ -148,9 +148,11 @@ SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* d
 /* sse_sigma_fwd with every array in HOST memory (page-locked for asynchronous copies):
  * the call copies nbr, dH, D^<, D^>, G^< and G^> into `device_buf` on `copy_stream`,
  * computes on `stream` and copies S^<, S^> (rows of atoms [a_begin, a_end) only) back on
- * `copy_stream`. With modes FP64_FFT and FP32_FFT the upload of G^> overlaps the
- * computation of Sigma^< and the download of Sigma^< the computation of Sigma^>; other modes
- * start after the last upload. `device_buf`: caller-owned device memory of
+ * `copy_stream`, G and Sigma one kz slice at a time. With modes FP64_FFT and FP32_FFT the
+ * lag kernels are transformed while G^< arrives, each kz slice of G is transformed as soon as
+ * it is on the device, the upload of G^> overlaps the computation of Sigma^<, and each slice
+ * of Sigma is downloaded as soon as its inverse transform has written it; other modes start
+ * after the last upload. `device_buf`: caller-owned device memory of
  * sse_sigma_fwd_host_bytes() (256-byte aligned; inputs, outputs and workspace). `stream` and
  * `copy_stream` must differ; all work is ordered after earlier work on `stream`, and `stream`
  * observes the completion of the copies (synchronise it before reading S_less / S_greater).

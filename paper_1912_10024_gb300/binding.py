@@ -286,7 +286,8 @@ def sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greate
 
 def sigma_host(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2.0 * math.pi),
                mode: str = "fp64_fft", symmetrize: bool = False, check: bool = False, atoms=None, out=None,
-               device_buf: Optional[torch.Tensor] = None, stream=None, copy_stream=None, device=None):
+               device_buf: Optional[torch.Tensor] = None, stream=None, copy_stream=None, device=None,
+               antihermitian: bool = False):
     """Sigma^<, Sigma^> from HOST (CPU, ideally pinned) tensors via sse_sigma_fwd_host: uploads, compute and
     downloads overlap on two streams. Returns host tensors (S_less, S_greater); synchronises the stream."""
     c128 = torch.complex128
@@ -298,6 +299,7 @@ def sigma_host(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0
     d = dims_of(G_less, D_less, dH, atoms)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
+    flags |= SSE_FLAG_ANTIHERMITIAN if antihermitian else 0
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     if out is None:
         out = (torch.zeros(G_less.shape, dtype=c128).pin_memory(), torch.zeros(G_less.shape, dtype=c128).pin_memory())

@@ -5,6 +5,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "sse.h"
 #include "sse_internal.h"
 
@@ -343,31 +345,39 @@ extern "C" int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const d
     char* base = static_cast<char*>(device_buf);
     const sse_dims& dd = *d;
     const size_t nel = (size_t)dd.Norb * dd.Norb;
-    const size_t gb = (size_t)dd.Nkz * dd.NE * dd.NA * nel * 16;
+    const size_t slice = (size_t)dd.NE * dd.NA * nel * 16;  // one kz slice of G or Sigma
     const size_t db = (size_t)dd.Nqz * dd.Nw * dd.NA * dd.NB * 9 * 16;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // G^< in, G^> in, S^< done, S^> done, out
-    for (auto& e : ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SSE_ERR_CUDA;
+    // events: inputs, then per type and kz slice "G slice on the device" and "Sigma slice written", then "out"
+    const int nk = dd.Nkz;
+    std::vector<cudaEvent_t> ev((size_t)2 + 4 * nk, nullptr);
     auto cleanup = [&](int code) {
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);  // released once the recorded work completes
         return code;
     };
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
+    cudaEvent_t ev_in = ev[0], ev_out = ev[1];
+    cudaEvent_t* ev_g[2] = {ev.data() + 2, ev.data() + 2 + nk};
+    cudaEvent_t* ev_s[2] = {ev.data() + 2 + 2 * nk, ev.data() + 2 + 3 * nk};
     unsigned* status = reinterpret_cast<unsigned*>(base + L.status);
     if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
-    // inputs on the copy stream: the small tensors and G^<, then G^>
-    if (cudaEventRecord(ev[4], st) != cudaSuccess || cudaStreamWaitEvent(cp, ev[4], 0) != cudaSuccess)
+    // inputs on the copy stream: the small tensors, then G^< and G^> one kz slice at a time
+    if (cudaEventRecord(ev_out, st) != cudaSuccess || cudaStreamWaitEvent(cp, ev_out, 0) != cudaSuccess)
         return cleanup(SSE_ERR_CUDA);  // the device buffer is free once earlier work on `stream` is done
-    const bool ok_in = cudaMemcpyAsync(base + L.nbr, nbr, (size_t)dd.NA * dd.NB * 4, cudaMemcpyHostToDevice, cp) ==
-                           cudaSuccess &&
-                       cudaMemcpyAsync(base + L.dH, dH, (size_t)dd.NA * dd.NB * 3 * nel * 16, cudaMemcpyHostToDevice,
-                                       cp) == cudaSuccess &&
-                       cudaMemcpyAsync(base + L.D[0], D_less, db, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
-                       cudaMemcpyAsync(base + L.D[1], D_greater, db, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
-                       cudaMemcpyAsync(base + L.G[0], G_less, gb, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
-                       cudaEventRecord(ev[0], cp) == cudaSuccess &&
-                       cudaMemcpyAsync(base + L.G[1], G_greater, gb, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
-                       cudaEventRecord(ev[1], cp) == cudaSuccess;
+    bool ok_in = cudaMemcpyAsync(base + L.nbr, nbr, (size_t)dd.NA * dd.NB * 4, cudaMemcpyHostToDevice, cp) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(base + L.dH, dH, (size_t)dd.NA * dd.NB * 3 * nel * 16, cudaMemcpyHostToDevice, cp) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(base + L.D[0], D_less, db, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                 cudaMemcpyAsync(base + L.D[1], D_greater, db, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                 cudaEventRecord(ev_in, cp) == cudaSuccess;
+    const double* Gh[2] = {G_less, G_greater};
+    for (int t = 0; t < 2 && ok_in; ++t)
+        for (int k = 0; k < nk && ok_in; ++k)
+            ok_in = cudaMemcpyAsync(base + L.G[t] + (size_t)k * slice, reinterpret_cast<const char*>(Gh[t]) + k * slice,
+                                    slice, cudaMemcpyHostToDevice, cp) == cudaSuccess &&
+                    cudaEventRecord(ev_g[t][k], cp) == cudaSuccess;
     if (!ok_in) return cleanup(SSE_ERR_CUDA);
     const sse::Problem p = make_problem(d, reinterpret_cast<const int32_t*>(base + L.nbr),
                                         reinterpret_cast<const double*>(base + L.dH),
@@ -380,27 +390,30 @@ extern "C" int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const d
     const size_t wsb = L.total - L.ws;
     cudaError_t e;
     if (mode == SSE_MODE_FP64_FFT || mode == SSE_MODE_FP32_FFT) {
-        e = sse::spectral_fwd_pipelined(p, mode == SSE_MODE_FP32_FFT, Sd[0], Sd[1], status, ws, wsb, st, ev, ev + 2);
-    } else {  // one kernel sequence for both types: wait for every input, one hand-off at the end
-        if (cudaStreamWaitEvent(st, ev[1], 0) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
+        const sse::FwdPipe pipe{ev_in, {ev_g[0], ev_g[1]}, {ev_s[0], ev_s[1]}};
+        e = sse::spectral_fwd_pipelined(p, mode == SSE_MODE_FP32_FFT, Sd[0], Sd[1], status, ws, wsb, st, pipe);
+    } else {  // one kernel sequence for both types: wait for every input, hand every slice over at the end
+        if (cudaStreamWaitEvent(st, ev_g[1][nk - 1], 0) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
         e = mode == SSE_MODE_FP64 ? sse::fp64_fwd(p, Sd[0], Sd[1], status, ws, wsb, st)
                                   : sse::mixed_fwd(p, mode, Sd[0], Sd[1], status, ws, wsb, st);
-        if (e == cudaSuccess && (cudaEventRecord(ev[2], st) != cudaSuccess || cudaEventRecord(ev[3], st) != cudaSuccess))
-            e = cudaErrorUnknown;
+        for (int t = 0; t < 2 && e == cudaSuccess; ++t)
+            for (int k = 0; k < nk && e == cudaSuccess; ++k) e = cudaEventRecord(ev_s[t][k], st);
     }
     if (e == cudaErrorNotSupported) return cleanup(SSE_ERR_UNSUPPORTED);
     if (e != cudaSuccess) return cleanup(SSE_ERR_CUDA);
-    // results back on the copy stream, rows of the atom range only (pitched copies)
+    // results back on the copy stream, slice by slice as written, rows of the atom range only (pitched copies)
     const size_t pitch = (size_t)dd.NA * nel * 16, off = (size_t)dd.a_begin * nel * 16;
-    const size_t width = (size_t)(dd.a_end - dd.a_begin) * nel * 16, rows = (size_t)dd.Nkz * dd.NE;
+    const size_t width = (size_t)(dd.a_end - dd.a_begin) * nel * 16;
     double* Sh[2] = {S_less, S_greater};
     for (int t = 0; t < 2; ++t)
-        if (cudaStreamWaitEvent(cp, ev[2 + t], 0) != cudaSuccess ||
-            cudaMemcpy2DAsync(reinterpret_cast<char*>(Sh[t]) + off, pitch, base + L.S[t] + off, pitch, width, rows,
-                              cudaMemcpyDeviceToHost, cp) != cudaSuccess)
-            return cleanup(SSE_ERR_CUDA);
+        for (int k = 0; k < nk; ++k)
+            if (cudaStreamWaitEvent(cp, ev_s[t][k], 0) != cudaSuccess ||
+                cudaMemcpy2DAsync(reinterpret_cast<char*>(Sh[t]) + k * slice + off, pitch,
+                                  base + L.S[t] + k * slice + off, pitch, width, (size_t)dd.NE,
+                                  cudaMemcpyDeviceToHost, cp) != cudaSuccess)
+                return cleanup(SSE_ERR_CUDA);
     // `stream` observes the completion of the copies
-    if (cudaEventRecord(ev[4], cp) != cudaSuccess || cudaStreamWaitEvent(st, ev[4], 0) != cudaSuccess)
+    if (cudaEventRecord(ev_out, cp) != cudaSuccess || cudaStreamWaitEvent(st, ev_out, 0) != cudaSuccess)
         return cleanup(SSE_ERR_CUDA);
     return cleanup(finish(cudaSuccess, status, flags, st));
 }

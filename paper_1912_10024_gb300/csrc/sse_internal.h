@@ -70,11 +70,16 @@ bool spectral_supported(const sse_dims& d);
 size_t spectral_fwd_workspace(const sse_dims& d);
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                          size_t ws_bytes, cudaStream_t st);
-// The transform forward with stream-ordered hand-offs: waits for g_ready[t] before reading G^t (g_ready[0] also
-// covers the other inputs) and records s_done[t] once Sigma^t is written.
+// Stream-ordered hand-offs between the copies of the host-buffer entry point and the transform forward, per kz
+// slice: the forward waits for `inputs` (nbr, dH, D^<, D^>) before the lag-kernel transforms and for g[t][k]
+// before transforming slice k of G^t, and records s[t][k] once slice k of Sigma^t is written.
+struct FwdPipe {
+    cudaEvent_t inputs;
+    const cudaEvent_t* g[2];  // [Nkz] each
+    const cudaEvent_t* s[2];  // [Nkz] each
+};
 cudaError_t spectral_fwd_pipelined(const Problem& p, bool fp32, double2* S_less, double2* S_greater, unsigned* status,
-                                   void* ws, size_t ws_bytes, cudaStream_t st, const cudaEvent_t g_ready[2],
-                                   const cudaEvent_t s_done[2]);
+                                   void* ws, size_t ws_bytes, cudaStream_t st, const FwdPipe& pipe);
 // FP32 transforms and block products (mode FP32_FFT), FP64 inputs and outputs.
 size_t spectral_fwd32_workspace(const sse_dims& d);
 cudaError_t spectral_fwd32(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,

@@ -369,9 +369,10 @@ namespace {
 // products on the FP32 pipe, FP64 inputs and outputs).
 template <class T>
 cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
-                           size_t ws_bytes, cudaStream_t st, const cudaEvent_t* g_ready = nullptr,
-                           const cudaEvent_t* s_done = nullptr) {
-    // g_ready[t]: G^t (and, for t = 0, every other input) is on the device; s_done[t]: Sigma^t is written.
+                           size_t ws_bytes, cudaStream_t st, const FwdPipe* pipe = nullptr) {
+    // With `pipe` (inputs arriving from the host): the lag kernel is transformed first, G^t slice by slice as its
+    // kz slices arrive, and the inverse E-transform of Sigma^t runs slice by slice so that each slice's download
+    // can start; without it every transform is one launch over all slices.
     using C = typename CX<T>::C;
     const sse_dims& d = p.d;
     if (!spectral_supported(d)) return cudaErrorNotSupported;
@@ -394,9 +395,8 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
     const bool half = (p.flags & SSE_FLAG_ANTIHERMITIAN) != 0;
     const FreqMap fm = make_freq_map(d.Nkz, L, half);
     if (half && (p.flags & SSE_FLAG_CHECK)) {
-        if (g_ready)
-            for (int t = 0; t < 2; ++t)
-                if ((e = cudaStreamWaitEvent(st, g_ready[t], 0)) != cudaSuccess) return e;
+        if (pipe)  // every input (the copies are issued in order on one stream)
+            if ((e = cudaStreamWaitEvent(st, pipe->g[1][d.Nkz - 1], 0)) != cudaSuccess) return e;
         for (int t = 0; t < 2; ++t) {
             SSE_TIMED("check_antiherm_kernel", st,
                       check_antiherm_kernel<<<grid_for((size_t)d.Nkz * d.NE * d.NA * nel, 256), 256, 0, st>>>(
@@ -416,21 +416,30 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                                           pc.smem)) != cudaSuccess)
         return e;
     double2* S[2] = {S_less, S_greater};
+    if (pipe && (e = cudaStreamWaitEvent(st, pipe->inputs, 0)) != cudaSuccess) return e;
     for (int t = 0; t < 2; ++t) {
-        if (g_ready && (e = cudaStreamWaitEvent(st, g_ready[t], 0)) != cudaSuccess) return e;
-        // 1. G^t -> G^
-        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
-                       gcols, d.Nkz, st);
-        if (e != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(G)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        // 2. lag kernel -> K^
+        // 1. lag kernel -> K^ (needs only D; with `pipe` it runs while G^t is still arriving)
         LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
         e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(K)", st,
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // 2. G^t -> G^ (E-transform per kz slice as the slices arrive, then the kz DFT)
+        if (pipe) {
+            for (int k = 0; k < d.Nkz; ++k) {
+                if ((e = cudaStreamWaitEvent(st, pipe->g[t][k], 0)) != cudaSuccess) return e;
+                e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t] + (size_t)k * d.NE * gcols, d.NE, gcols},
+                               StoreSpecT<C>{Gh + (size_t)k * L * gcols, L, gcols, L}, gcols, 1, st);
+                if (e != cudaSuccess) return e;
+            }
+        } else {
+            e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols},
+                           StoreSpecT<C>{Gh, L, gcols, L}, gcols, d.Nkz, st);
+            if (e != cudaSuccess) return e;
+        }
+        SSE_TIMED("dft_k_kernel(G)", st,
+                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
         if (tiled) {
@@ -456,26 +465,43 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                   dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
-        e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh, L, scols},
-                       StoreSigmaT<C>{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols,
-                       d.Nkz, st);
-        if (e != cudaSuccess) return e;
-        if (p.flags & SSE_FLAG_SYMMETRIZE) {
-            SSE_TIMED("symmetrize_kernel", st,
-                      symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]));
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const bool sym = (p.flags & SSE_FLAG_SYMMETRIZE) != 0;
+        if (pipe) {  // slice by slice, each handed to its download as soon as it is written
+            sse_dims dk = d;
+            dk.Nkz = 1;
+            for (int k = 0; k < d.Nkz; ++k) {
+                double2* Sk = S[t] + (size_t)k * d.NE * d.NA * nel;
+                e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh + (size_t)k * L * scols, L, scols},
+                               StoreSigmaT<C>{Sk, d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE},
+                               scols, 1, st);
+                if (e != cudaSuccess) return e;
+                if (sym) {
+                    SSE_TIMED("symmetrize_kernel", st,
+                              symmetrize_kernel<<<grid_for((size_t)d.NE * nA * nel, 256), 256, 0, st>>>(dk, Sk));
+                    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                }
+                if ((e = cudaEventRecord(pipe->s[t][k], st)) != cudaSuccess) return e;
+            }
+        } else {
+            e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh, L, scols},
+                           StoreSigmaT<C>{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols,
+                           d.Nkz, st);
+            if (e != cudaSuccess) return e;
+            if (sym) {
+                SSE_TIMED("symmetrize_kernel", st,
+                          symmetrize_kernel<<<grid_for((size_t)d.Nkz * d.NE * nA * nel, 256), 256, 0, st>>>(d, S[t]));
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            }
         }
-        if (s_done && (e = cudaEventRecord(s_done[t], st)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 }  // namespace
 
 cudaError_t spectral_fwd_pipelined(const Problem& p, bool fp32, double2* S_less, double2* S_greater, unsigned* status,
-                                   void* ws, size_t ws_bytes, cudaStream_t st, const cudaEvent_t g_ready[2],
-                                   const cudaEvent_t s_done[2]) {
-    return fp32 ? spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st, g_ready, s_done)
-                : spectral_fwd_t<double>(p, S_less, S_greater, status, ws, ws_bytes, st, g_ready, s_done);
+                                   void* ws, size_t ws_bytes, cudaStream_t st, const FwdPipe& pipe) {
+    return fp32 ? spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st, &pipe)
+                : spectral_fwd_t<double>(p, S_less, S_greater, status, ws, ws_bytes, st, &pipe);
 }
 
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,

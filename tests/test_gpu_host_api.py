@@ -1,5 +1,6 @@
-"""Host-buffer forward (sse_sigma_fwd_host): uploads, compute and downloads on two streams give the same bytes
-as the device-pointer entry point, for every kind of mode, and write only the rows of the atom range."""
+"""Host-buffer forward (sse_sigma_fwd_host): uploads, compute and downloads on two streams, G and Sigma handed over
+one kz slice at a time, give the same bytes as the device-pointer entry point, for every kind of mode and with the
+symmetrisation and anti-Hermitian flags, and write only the rows of the atom range."""
 import pytest
 import torch
 
@@ -45,3 +46,17 @@ def test_one_stream_is_refused():
     with pytest.raises(B.SseError) as e:
         B.sigma_host(Gl, Gg, dH, Dl, Dg, nbr, stream=s, copy_stream=s)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("mode", ["fp64_fft", "fp32_fft"])
+@pytest.mark.parametrize("flags", [("symmetrize",), ("antihermitian",), ("symmetrize", "antihermitian")])
+def test_flags_same_bytes_many_slices(mode, flags):
+    """Nkz = 9 kz slices: the per-slice transforms, symmetrisation and downloads match the device call bit for bit."""
+    d = Dims(NA=7, NB=2, Norb=3, NE=50, Nkz=9, Nqz=4, Nw=7)
+    inp = make_inputs(d, seed=64, nbr=ring_neighbours(7, 2))
+    Gl, Gg, dH, Dl, Dg, nbr = host_inputs(inp, True)
+    kw = {f: True for f in flags}
+    Hl, Hg = B.sigma_host(Gl, Gg, dH, Dl, Dg, nbr, mode=mode, check=True, **kw)
+    g = inp.to("cuda")
+    Sl, Sg = B.sigma(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, mode=mode, check=True, **kw)
+    assert torch.equal(Hl, Sl.cpu()) and torch.equal(Hg, Sg.cpu())
