@@ -38,7 +38,8 @@ from paper_1912_10024_gb300 import binding as B  # noqa: E402
 from paper_1912_10024_gb300.inputs import WORKLOADS, make_inputs, make_upstream  # noqa: E402
 
 SCALE = 1.0 / (2.0 * math.pi)
-# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2070 MHz (derivation in the design doc).
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2070 MHz (unit count and maximum SM clock; a DFMA
+# throughput probe measured 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # FP32 pipe: 152 SMs x 128 FP32 FMA/clock x 2 flop x 2070 MHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12

@@ -58,7 +58,9 @@ class Dims:
 
 
 # Workloads. Shapes follow the paper's OMEN validation structure (Norb=10,
-# NB=4) and its Table 2 orders of magnitude; see the design doc for the recipe.
+# NB=4) and its Table 2 orders of magnitude: tiny (ring neighbour list), the
+# Si-FinFET-shaped problem (4x4x8 diamond cells), the adjoint workload (2x2x8
+# cells) and the large workload (8x8x8 cells); values from make_inputs below.
 TINY = Dims(NA=16, NB=4, Norb=4, NE=32, Nkz=3, Nqz=3, Nw=4)
 FINFET = Dims(NA=1024, NB=4, Norb=10, NE=512, Nkz=7, Nqz=7, Nw=32)
 ADJOINT = Dims(NA=256, NB=4, Norb=10, NE=256, Nkz=5, Nqz=5, Nw=16)

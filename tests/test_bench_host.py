@@ -1,0 +1,83 @@
+"""Host-side checks of bench.py (no GPU): the flop counts and frequency counts it reports are recomputed by
+brute-force enumeration, the kernel-source hashes resolve, and the reference arm (the FP64 oracle timed on the
+host cores) prints one JSON line with the contract's keys."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1912_10024_gb300.inputs import TINY, Dims  # noqa: E402
+
+
+@pytest.mark.parametrize("d", [TINY, Dims(NA=3, NB=2, Norb=3, NE=9, Nkz=2, Nqz=2, Nw=4)])
+def test_useful_flops_is_the_term_count(d):
+    """Per (type, atom, slot, kz, E): 24 Norb^3 per in-range (q, w, sigma) term of Eq. (3) plus 24 Norb^3 for the
+    final multiply; the terms are enumerated one by one."""
+    total = 0
+    for _t in range(2):
+        for _a in range(d.NA):
+            for _s in range(d.NB):
+                for _k in range(d.Nkz):
+                    for E in range(d.NE):
+                        terms = sum(1 for _q in range(d.Nqz) for w in range(d.Nw) for sigma in (1, -1)
+                                    if 0 <= E - sigma * (w + 1) < d.NE)
+                        total += 24 * d.Norb ** 3 * (terms + 1)
+    assert bench.useful_flops(d) == total
+
+
+def test_fft_length_is_the_smallest_2a3b():
+    smooth = sorted(2 ** a * 3 ** b for a in range(14) for b in range(9))
+    for NE in (1, 7, 32, 61, 256, 512, 1000, 1024):
+        for Nw in (1, 4, 16, 32, 64):
+            want = next(x for x in smooth if x >= NE + Nw)
+            assert bench.fft_length(NE, Nw) == want
+
+
+@pytest.mark.parametrize("Nkz", [1, 2, 3, 4, 7, 9])
+@pytest.mark.parametrize("NE,Nw", [(32, 4), (61, 5), (70, 5), (512, 32)])
+def test_half_spectrum_count_is_one_per_pair(Nkz, NE, Nw):
+    """With anti-Hermitian inputs one frequency of each (f, -f) pair is evaluated: the count equals the number of
+    orbits of f -> -f on the (kz, E) frequency grid."""
+    d = Dims(NA=1, NB=1, Norb=1, NE=NE, Nkz=Nkz, Nqz=1, Nw=Nw)
+    L = bench.fft_length(NE, Nw)
+    seen, orbits = set(), 0
+    for kap in range(Nkz):
+        for eps in range(L):
+            if (kap, eps) in seen:
+                continue
+            orbits += 1
+            seen.add((kap, eps))
+            seen.add(((Nkz - kap) % Nkz, (L - eps) % L))
+    assert bench.freq_count(d, True) == orbits
+    assert bench.freq_count(d, False) == Nkz * L
+
+
+def test_kernel_sources_resolve():
+    for k in list(bench.NCU_TRAFFIC) + ["spec_prod_kernel", "fft_e_kernel", "dft_k_kernel", "spec_gradg_kernel"]:
+        assert len(bench.kernel_source_sha(k)) == 16, k
+    assert bench.kernel_source_sha("no_such_kernel") == ""
+    assert bench.ncu_traffic("no_such_kernel", 1.0) is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "tiny",
+                        "--steps", "1", "--warmup", "1", "--cpu-seconds", "1"],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "scaling",
+                "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["value"] > 0 and out["higher_is_better"] is True
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
+    assert out["config"]["workload"] == "tiny"
