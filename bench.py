@@ -185,6 +185,28 @@ def ncu_traffic(kernel: str, units: float):
     return per * units
 
 
+def gpu_local_cpus(dev):
+    """Host CPUs on the GPU's own NUMA node (sysfs local_cpulist of its PCI device), intersected with the CPUs this
+    process may use; None when the system does not say."""
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        path = "/sys/bus/pci/devices/%04x:%02x:%02x.0/local_cpulist" % (pr.pci_domain_id, pr.pci_bus_id,
+                                                                        pr.pci_device_id)
+        with open(path) as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except (AttributeError, OSError, ValueError):
+        return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -380,6 +402,12 @@ def main():
     # stream and overlap the compute of the other type (transform modes)
     e2e = None
     if not args.no_e2e:
+        # page-locked buffers allocated (first touch) from the CPUs of the GPU's own NUMA node where known, as a
+        # NUMA-aware caller would; the binding is reported
+        local = gpu_local_cpus(dev)
+        saved = os.sched_getaffinity(0)
+        if local:
+            os.sched_setaffinity(0, local)
         host = {n: getattr(inp, n).cpu().pin_memory() for n in ("nbr", "dH", "D_less", "D_greater", "G_less",
                                                                   "G_greater")}
         hSl = torch.empty(Sl.shape, dtype=Sl.dtype).pin_memory()
@@ -399,11 +427,26 @@ def main():
 
         hstep()  # warm-up
         torch.cuda.synchronize(dev)
+        # the host link as seen from these buffers: one plain copy of G^< each way
+        l0, l1, l2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        gdev = dbuf[:host["G_less"].numel() * host["G_less"].element_size()].view(torch.complex128).view(
+            host["G_less"].shape)
+        l0.record(stream)
+        gdev.copy_(host["G_less"], non_blocking=True)
+        l1.record(stream)
+        hSl.copy_(gdev, non_blocking=True)
+        l2.record(stream)
+        torch.cuda.synchronize(dev)
+        gbytes = host["G_less"].numel() * host["G_less"].element_size()
+        link = {"h2d_gbs": gbytes / (l0.elapsed_time(l1) * 1e-3) / 1e9,
+                "d2h_gbs": gbytes / (l1.elapsed_time(l2) * 1e-3) / 1e9}
+        del gdev
         barrier()
+        nsteps = max(args.steps, 3)  # host copies vary more than kernels: time at least three steps
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(nsteps):
             hstep()
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -414,11 +457,13 @@ def main():
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = float(t.item())
         same = bool(torch.equal(hSl, Sl.cpu()) and torch.equal(hSg, Sg.cpu()))
-        e2e = {"value": world * uf * args.steps / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
-               "api": "sse_sigma_fwd_host (pinned host buffers, copies on a second stream)",
-               "same_bytes_as_device_call": same}
+        e2e = {"value": world * uf * nsteps / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / nsteps,
+               "steps": nsteps, "api": "sse_sigma_fwd_host (pinned host buffers, copies on a second stream)",
+               "same_bytes_as_device_call": same, "host_link": link,
+               "host_cpus": ("GPU-local NUMA node, %d CPUs" % len(local)) if local else "unbound"}
         del host, hSl, hSg, dbuf
+        os.sched_setaffinity(0, saved)
 
     # ---- the other modes on the same inputs (the metric's FP64-versus-mixed comparison) ----
     compare = None
