@@ -351,6 +351,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+        # the other modes, Pi and the adjoint are single-GPU diagnostics: skipped at N > 1 so that the N GPUs are
+        # held only for the scaled measurement
+        args.no_compare = args.no_pi = args.no_adjoint = True
 
     def barrier():
         if world > 1:
@@ -734,7 +737,8 @@ def main():
                "dtype": {"fp64": "f64", "fp64_fft": "f64", "fp32_fft": "f32", "tf32": "tf32+f64",
                          "bf16x3": "bf16x3+f64"}[args.mode],
                "data": "synthetic (seeded; Si-FinFET-shaped)",
-               "config": bench_config(args, d),
+               "config": {**bench_config(args, d),
+                          "parallelism": f"{world} rank(s), one independent problem of this size each"},
                "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
                "gpu_launches": sum(v[1] for v in kernels.values())}
         if compare:
