@@ -204,14 +204,63 @@ __device__ __forceinline__ void fft_stage(const C* __restrict__ src, C* __restri
     }
 }
 
+// The same stage for FP32 tiles of at least two columns: each thread takes the adjacent columns (c, c+1) of a
+// butterfly with one 16-byte shared access per row, sharing the index arithmetic and the twiddles.
+template <int R, int CC>
+__device__ __forceinline__ void fft_stage_pairs(const float2* __restrict__ src, float2* __restrict__ dst,
+                                                const float2* __restrict__ tw, int L, int Ns, int ns_shift,
+                                                unsigned ns_mul) {
+    constexpr int CP = CC / 2;  // column pairs per row
+    constexpr int lgP = CP == 1 ? 0 : CP == 2 ? 1 : CP == 4 ? 2 : 3;
+    static_assert(CC >= 2 && (1 << lgP) == CP, "CC in {2, 4, 8, 16}");
+    const int nb = L / R;
+    const int span = nb / Ns;
+    const float2 w3 = tw[L / 3 * (R == 3)];
+    for (int it = threadIdx.x; it < nb * CP; it += blockDim.x) {
+        const int c = (it & (CP - 1)) * 2, j = it >> lgP;
+        const int q = ns_shift >= 0 ? (j >> ns_shift) : (int)__umulhi((unsigned)j, ns_mul);
+        const int k = j - q * Ns;
+        float2 a[R], b[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float4 v = *reinterpret_cast<const float4*>(src + (j + r * nb) * CC + c);
+            a[r] = make_float2(v.x, v.y);
+            b[r] = make_float2(v.z, v.w);
+        }
+        if (k > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 w = tw[r * k * span];
+                a[r] = cmul(a[r], w);
+                b[r] = cmul(b[r], w);
+            }
+        }
+        dft_small<R>(a, w3);
+        dft_small<R>(b, w3);
+        const int d0 = q * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            *reinterpret_cast<float4*>(dst + (d0 + r * Ns) * CC + c) = make_float4(a[r].x, a[r].y, b[r].x, b[r].y);
+    }
+}
+
+template <int R, int CC, class C>
+__device__ __forceinline__ void fft_stage_any(const C* src, C* dst, const C* tw, int L, int Ns, int ns_shift,
+                                              unsigned ns_mul) {
+    if constexpr (sizeof(C) == 8 && CC >= 2)
+        fft_stage_pairs<R, CC>(src, dst, tw, L, Ns, ns_shift, ns_mul);
+    else
+        fft_stage<R, CC>(src, dst, tw, L, Ns, ns_shift, ns_mul);
+}
+
 // Stockham autosort FFT of CC columns stored [L][CC] in `src`; returns the buffer holding the result.
 template <int CC, class C>
 __device__ C* fft_columns(const FftPlan& p, C* src, C* dst, const C* tw) {
     for (int st = 0; st < p.nst; ++st) {
         const int R = p.radix[st];
-        if (R == 4) fft_stage<4, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
-        else if (R == 2) fft_stage<2, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
-        else fft_stage<3, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
+        if (R == 4) fft_stage_any<4, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
+        else if (R == 2) fft_stage_any<2, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
+        else fft_stage_any<3, CC>(src, dst, tw, p.L, p.ns[st], p.ns_shift[st], p.ns_mul[st]);
         __syncthreads();
         C* t = src;
         src = dst;
