@@ -81,8 +81,10 @@ typedef struct sse_dims {
  *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~4800.
  *   FP32_FFT : the same transforms and per-frequency block products in FP32 on the
  *            CUDA cores' FP32 pipe (about 60x the FP64 pipe on GB300), FP64 inputs
- *            and outputs; forward only (the adjoint runs in FP64). Workspace half
- *            of FP64_FFT's. Error (normwise) a few 1e-7; tested to 2e-6. */
+ *            and outputs; for sse_sigma_fwd, sse_sigma_bwd, sse_sigma_bwd_g and
+ *            sse_pi_fwd. Spectra take half of FP64_FFT's workspace. Error (normwise)
+ *            a few 1e-7, tested to 2e-6; the adjoint's dH gradient, a sum over
+ *            Nkz*L frequencies, to 1e-5. */
 typedef enum sse_mode {
     SSE_MODE_FP64 = 0,
     SSE_MODE_TF32 = 1,
