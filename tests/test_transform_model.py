@@ -1,0 +1,136 @@
+"""The transform (convolution-theorem) evaluation of Eqs. (3) and (4), written out with numpy FFTs on the CPU and
+compared with the FP64 oracle: the algebra behind the FP64_FFT / FP32_FFT modes, independent of the CUDA kernels.
+
+Eq. (3) per bond (a, s), b = nbr[a][s]: Sigma^t_a(E,k) = c sum_ij sum_{q,l} K_ij(q,l) dH_i G^t_b(E-l, k-q) dH_j^H with
+the lag kernel K(q, +(w+1)) = D^t(q,w), K(q, -(w+1)) = D^t'(q,w) and c = i*scale. G is zero outside [0, NE) in E and
+cyclic in kz, so with G zero-padded to L >= NE + Nw the linear convolution along E equals the cyclic one of period L
+on [0, NE); after 2-D DFTs over (kz, E) the convolution is a product per frequency.
+
+Eq. (4): Pi^t_{a,s}(q,w)_ij = -i*scale sum_{k,E} tr(dH_i^H G^t_a(E+l, k+q) dH_j G^t'_b(E, k)), l = w+1, a
+cross-correlation: C_ij(q,l) = IDFT[tr(dH_i^H G^_a(f) dH_j G^_b(-f))](q,l); the diagonal slot sums the bonds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1912_10024_gb300.inputs import TINY, Dims, make_inputs, ring_neighbours
+
+SCALE = 1.0 / (2.0 * math.pi)
+
+
+def smallest_2a3b(n):
+    while True:
+        m = n
+        for p in (2, 3):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return n
+        n += 1
+
+
+def sigma_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale):
+    Nkz, NE, NA, Norb, _ = Gl.shape
+    Nqz, Nw = Dl.shape[0], Dl.shape[1]
+    NB = nbr.shape[1]
+    L = smallest_2a3b(NE + Nw)
+    out = []
+    for G, Dt, Dtb in ((Gl, Dl, Dg), (Gg, Dg, Dl)):
+        Gp = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+        Gp[:, :NE] = G
+        Gh = np.fft.fft2(Gp, axes=(0, 1))                        # [kappa][eps][atom]
+        K = np.zeros((Nkz, L, NA, NB, 3, 3), complex)            # lag kernel, q padded to Nkz
+        for w in range(Nw):
+            K[:Nqz, w + 1] = Dt[:, w]                             # emission: G at E - (w+1), same type
+            K[:Nqz, L - (w + 1)] = Dtb[:, w]                      # absorption: G at E + (w+1), other type
+        Kh = np.fft.fft2(K, axes=(0, 1))
+        Sh = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+        for a in range(NA):
+            for s in range(NB):
+                b = nbr[a, s]
+                A = dH[a, s]                                      # [3][Norb][Norb]
+                for i in range(3):
+                    for j in range(3):
+                        prod = A[i] @ Gh[:, :, b] @ A[j].conj().T  # per frequency, broadcast over (kappa, eps)
+                        Sh[:, :, a] += Kh[:, :, a, s, i, j][..., None, None] * prod
+        S = np.fft.ifft2(Sh, axes=(0, 1))[:, :NE]
+        out.append(1j * scale * S)
+    return out
+
+
+def pi_by_transforms(nbr, dH, Gl, Gg, scale, Nqz, Nw):
+    Nkz, NE, NA, Norb, _ = Gl.shape
+    NB = nbr.shape[1]
+    L = smallest_2a3b(NE + Nw)
+    spec = []
+    for G in (Gl, Gg):
+        Gp = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+        Gp[:, :NE] = G
+        spec.append(np.fft.fft2(Gp, axes=(0, 1)))
+    neg_k = (-np.arange(Nkz)) % Nkz
+    neg_e = (-np.arange(L)) % L
+    out = []
+    for t in range(2):
+        X, Y = spec[t], spec[1 - t]                               # G^t of atom a, G^t' of the neighbour
+        P = np.zeros((Nqz, Nw, NA, NB + 1, 3, 3), complex)
+        for a in range(NA):
+            diag = np.zeros((Nkz, L, 3, 3), complex)
+            for s in range(NB):
+                b = nbr[a, s]
+                A = dH[a, s]
+                Yneg = Y[neg_k][:, neg_e, b]                      # G^_b(-f)
+                Ch = np.zeros((Nkz, L, 3, 3), complex)
+                for i in range(3):
+                    for j in range(3):
+                        Ch[..., i, j] = np.trace(A[i].conj().T @ X[:, :, a] @ A[j] @ Yneg, axis1=-2, axis2=-1)
+                diag += Ch
+                C = np.fft.ifft2(Ch, axes=(0, 1))                 # C(q, l), positive exponent, 1/(Nkz L)
+                P[:, :, a, s] = -1j * scale * C[:Nqz, 1:Nw + 1]
+            C = np.fft.ifft2(diag, axes=(0, 1))
+            P[:, :, a, NB] = -1j * scale * C[:Nqz, 1:Nw + 1]
+        out.append(P)
+    return out
+
+
+CASES = [TINY, Dims(NA=5, NB=2, Norb=3, NE=13, Nkz=4, Nqz=3, Nw=4), Dims(NA=4, NB=1, Norb=2, NE=9, Nkz=1, Nqz=1, Nw=3)]
+
+
+@pytest.mark.parametrize("d", CASES, ids=lambda d: f"NE{d.NE}_Nkz{d.Nkz}_Nqz{d.Nqz}")
+def test_sigma_transform_model_equals_the_oracle(d):
+    nbr = None if d is TINY else ring_neighbours(d.NA, d.NB)
+    x = make_inputs(d, seed=d.NE + 3, nbr=nbr)
+    arrs = [t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less, x.G_greater)]
+    got = sigma_by_transforms(*arrs, SCALE)
+    ref = oracle.sigma(*arrs, SCALE)
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("d", CASES, ids=lambda d: f"NE{d.NE}_Nkz{d.Nkz}_Nqz{d.Nqz}")
+def test_pi_transform_model_equals_the_oracle(d):
+    nbr = None if d is TINY else ring_neighbours(d.NA, d.NB)
+    x = make_inputs(d, seed=d.NE + 4, nbr=nbr)
+    nb, dH, Gl, Gg = (t.numpy() for t in (x.nbr, x.dH, x.G_less, x.G_greater))
+    got = pi_by_transforms(nb, dH, Gl, Gg, SCALE, d.Nqz, d.Nw)
+    ref = oracle.pi(nb, dH, Gl, Gg, SCALE, d.Nqz, d.Nw)
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max()
+
+
+def test_padding_below_ne_plus_nw_aliases():
+    """The bound L >= NE + Nw is needed: with L = NE the cyclic wrap of the lags brings energies from the other end
+    of the grid into the sum, and the transform result no longer equals Eq. (3)."""
+    d = Dims(NA=4, NB=1, Norb=2, NE=9, Nkz=1, Nqz=1, Nw=3)
+    x = make_inputs(d, seed=11, nbr=ring_neighbours(4, 1))
+    arrs = [t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less, x.G_greater)]
+    ref = oracle.sigma(*arrs, SCALE)
+    global smallest_2a3b
+    keep = smallest_2a3b
+    try:
+        smallest_2a3b = lambda n: d.NE  # noqa: E731  (too short on purpose)
+        bad = sigma_by_transforms(*arrs, SCALE)
+    finally:
+        smallest_2a3b = keep
+    assert np.abs(bad[0] - ref[0]).max() > 1e-3 * np.abs(ref[0]).max()
