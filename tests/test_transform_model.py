@@ -8,6 +8,9 @@ on [0, NE); after 2-D DFTs over (kz, E) the convolution is a product per frequen
 
 Eq. (4): Pi^t_{a,s}(q,w)_ij = -i*scale sum_{k,E} tr(dH_i^H G^t_a(E+l, k+q) dH_j G^t'_b(E, k)), l = w+1, a
 cross-correlation: C_ij(q,l) = IDFT[tr(dH_i^H G^_a(f) dH_j G^_b(-f))](q,l); the diagonal slot sums the bonds.
+
+The adjoint of Eq. (3) (gradients with respect to dH, D^< and D^>) is a correlation of the upstream gradient with G
+and with the lag kernel, modelled the same way.
 """
 import math
 
@@ -134,3 +137,67 @@ def test_padding_below_ne_plus_nw_aliases():
     finally:
         smallest_2a3b = keep
     assert np.abs(bad[0] - ref[0]).max() > 1e-3 * np.abs(ref[0]).max()
+
+
+def sigma_grad_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale, Wl, Wg):
+    """Adjoint of Eq. (3) through the transforms, for L = sum_t Re tr(W^t^H Sigma^t) (PyTorch convention): per bond
+    and frequency Q_j = W^ dH_j G^^H and R_i = W^^H dH_i G^; the weight gradient is conj(c) times the inverse
+    transform of tr(dH_i^H Q_j) at the emission lags (same type) and the absorption lags (other type); the coupling
+    gradient is (scale / N) sum_f sum_j [-i conj(K^_mj) Q_j + i K^_jm R_j]."""
+    Nkz, NE, NA, Norb, _ = Gl.shape
+    Nqz, Nw = Dl.shape[0], Dl.shape[1]
+    NB = nbr.shape[1]
+    L = smallest_2a3b(NE + Nw)
+    N = Nkz * L
+    cc = -1j * scale                                              # conj(c)
+    g_dH = np.zeros(dH.shape, complex)
+    g_D = [np.zeros(Dl.shape, complex), np.zeros(Dg.shape, complex)]
+
+    def spectrum(X):
+        Xp = np.zeros((Nkz, L) + X.shape[2:], complex)
+        Xp[:, :NE] = X
+        return np.fft.fft2(Xp, axes=(0, 1))
+
+    for t, (G, W, Dt, Dtb) in enumerate(((Gl, Wl, Dl, Dg), (Gg, Wg, Dg, Dl))):
+        Gh, Wh = spectrum(G), spectrum(W)
+        K = np.zeros((Nkz, L, NA, NB, 3, 3), complex)
+        for w in range(Nw):
+            K[:Nqz, w + 1] = Dt[:, w]
+            K[:Nqz, L - (w + 1)] = Dtb[:, w]
+        Kh = np.fft.fft2(K, axes=(0, 1))
+        for a in range(NA):
+            Wa = Wh[:, :, a]
+            for s in range(NB):
+                b = nbr[a, s]
+                A = dH[a, s]
+                Gb = Gh[:, :, b]
+                Q = [Wa @ A[j] @ np.conj(np.swapaxes(Gb, -1, -2)) for j in range(3)]
+                R = [np.conj(np.swapaxes(Wa, -1, -2)) @ A[i] @ Gb for i in range(3)]
+                Hh = np.zeros((Nkz, L, 3, 3), complex)
+                for i in range(3):
+                    for j in range(3):
+                        Hh[..., i, j] = np.trace(A[i].conj().T @ Q[j], axis1=-2, axis2=-1)
+                H = np.fft.ifft2(Hh, axes=(0, 1))
+                for w in range(Nw):
+                    g_D[t][:, w, a, s] += cc * H[:Nqz, w + 1]
+                    g_D[1 - t][:, w, a, s] += cc * H[:Nqz, L - (w + 1)]
+                for m in range(3):
+                    acc = np.zeros((Norb, Norb), complex)
+                    for j in range(3):
+                        acc += np.einsum("kl,klxy->xy", -1j * np.conj(Kh[:, :, a, s, m, j]), Q[j])
+                        acc += np.einsum("kl,klxy->xy", 1j * Kh[:, :, a, s, j, m], R[j])
+                    g_dH[a, s, m] += scale / N * acc
+    return g_dH, g_D[0], g_D[1]
+
+
+@pytest.mark.parametrize("d", CASES, ids=lambda d: f"NE{d.NE}_Nkz{d.Nkz}_Nqz{d.Nqz}")
+def test_adjoint_transform_model_equals_the_oracle(d):
+    from paper_1912_10024_gb300.inputs import make_upstream
+    nbr = None if d is TINY else ring_neighbours(d.NA, d.NB)
+    x = make_inputs(d, seed=d.NE + 5, nbr=nbr)
+    W, V = make_upstream(d, seed=d.NE + 6)
+    arrs = [t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less, x.G_greater)]
+    got = sigma_grad_by_transforms(*arrs, SCALE, W.numpy(), V.numpy())
+    ref = oracle.sigma_grad(*arrs, SCALE, W.numpy(), V.numpy())
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max()
