@@ -9,8 +9,8 @@ on [0, NE); after 2-D DFTs over (kz, E) the convolution is a product per frequen
 Eq. (4): Pi^t_{a,s}(q,w)_ij = -i*scale sum_{k,E} tr(dH_i^H G^t_a(E+l, k+q) dH_j G^t'_b(E, k)), l = w+1, a
 cross-correlation: C_ij(q,l) = IDFT[tr(dH_i^H G^_a(f) dH_j G^_b(-f))](q,l); the diagonal slot sums the bonds.
 
-The adjoint of Eq. (3) (gradients with respect to dH, D^< and D^>) is a correlation of the upstream gradient with G
-and with the lag kernel, modelled the same way.
+The adjoint of Eq. (3) (gradients with respect to dH, D^< and D^>) and the gradient with respect to G are
+correlations of the upstream gradient with G and with the lag kernel, modelled the same way.
 """
 import math
 
@@ -199,5 +199,49 @@ def test_adjoint_transform_model_equals_the_oracle(d):
     arrs = [t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less, x.G_greater)]
     got = sigma_grad_by_transforms(*arrs, SCALE, W.numpy(), V.numpy())
     ref = oracle.sigma_grad(*arrs, SCALE, W.numpy(), V.numpy())
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max()
+
+
+def sigma_grad_G_by_transforms(nbr, dH, Dl, Dg, scale, Wl, Wg):
+    """Gradient of L = sum_t Re tr(W^t^H Sigma^t) with respect to G^t (PyTorch convention), Sigma being linear in G:
+    per atom b and frequency, conj(c) sum over bonds (a, s) into b of sum_i dH_i^H W^_a B_i with
+    B_i = sum_j conj(K^_ij) dH_j, then the inverse transforms (rows E < NE)."""
+    Nkz, NE, NA, Norb, _ = Wl.shape
+    Nqz, Nw = Dl.shape[0], Dl.shape[1]
+    NB = nbr.shape[1]
+    L = smallest_2a3b(NE + Nw)
+    cc = -1j * scale
+    out = []
+    for W, Dt, Dtb in ((Wl, Dl, Dg), (Wg, Dg, Dl)):
+        Wp = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+        Wp[:, :NE] = W
+        Wh = np.fft.fft2(Wp, axes=(0, 1))
+        K = np.zeros((Nkz, L, NA, NB, 3, 3), complex)
+        for w in range(Nw):
+            K[:Nqz, w + 1] = Dt[:, w]
+            K[:Nqz, L - (w + 1)] = Dtb[:, w]
+        Kh = np.fft.fft2(K, axes=(0, 1))
+        Rh = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+        for a in range(NA):
+            for s in range(NB):
+                b = nbr[a, s]
+                A = dH[a, s]
+                for i in range(3):
+                    Bi = sum(np.conj(Kh[:, :, a, s, i, j])[..., None, None] * A[j] for j in range(3))
+                    Rh[:, :, b] += cc * (A[i].conj().T @ Wh[:, :, a] @ Bi)
+        out.append(np.fft.ifft2(Rh, axes=(0, 1))[:, :NE])
+    return out
+
+
+@pytest.mark.parametrize("d", CASES, ids=lambda d: f"NE{d.NE}_Nkz{d.Nkz}_Nqz{d.Nqz}")
+def test_grad_G_transform_model_equals_the_oracle(d):
+    from paper_1912_10024_gb300.inputs import make_upstream
+    nbr = None if d is TINY else ring_neighbours(d.NA, d.NB)
+    x = make_inputs(d, seed=d.NE + 7, nbr=nbr)
+    W, V = make_upstream(d, seed=d.NE + 8)
+    nb, dH, Dl, Dg = (t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater))
+    got = sigma_grad_G_by_transforms(nb, dH, Dl, Dg, SCALE, W.numpy(), V.numpy())
+    ref = oracle.sigma_grad_G(nb, dH, Dl, Dg, SCALE, W.numpy(), V.numpy())
     for g, r in zip(got, ref):
         assert np.abs(g - r).max() <= 1e-12 * np.abs(r).max()
