@@ -416,6 +416,10 @@ struct Adj32Cfg {
 };
 
 constexpr int kAdj32MaxThreads = 256;
+// Each lane adds its frequencies' coupling-gradient terms in FP32; chunks of at most this many terms per lane keep
+// that sum short (the chunks are then added in FP64 in a fixed order). At the FinFET workload 269 terms per lane put
+// the coupling gradient 2.6e-6 from the FP64 result, 32 terms 7.9e-7.
+constexpr int kAdj32LaneTerms = 32;
 
 Adj32Cfg make_adj32_cfg(const sse_dims& d, size_t nfreq) {
     Adj32Cfg c{};
@@ -456,6 +460,7 @@ Adj32Cfg make_adj32_cfg(const sse_dims& d, size_t nfreq) {
     if (chunks < 1) chunks = 1;
     size_t fc = (nfreq + chunks - 1) / chunks;
     fc = ((fc + c.F - 1) / c.F) * c.F;
+    if (fc > (size_t)kAdj32LaneTerms * c.F) fc = (size_t)kAdj32LaneTerms * c.F;
     c.fchunk = (int)(fc < 1 ? 1 : fc);
     c.nchunks = (int)((nfreq + c.fchunk - 1) / c.fchunk);
     return c;

@@ -140,7 +140,7 @@ def test_padding_below_ne_plus_nw_aliases():
     assert np.abs(bad[0] - ref[0]).max() > 1e-3 * np.abs(ref[0]).max()
 
 
-def sigma_grad_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale, Wl, Wg):
+def sigma_grad_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale, Wl, Wg, dt=np.complex128):
     """Adjoint of Eq. (3) through the transforms, for L = sum_t Re tr(W^t^H Sigma^t) (PyTorch convention): per bond
     and frequency Q_j = W^ dH_j G^^H and R_i = W^^H dH_i G^; the weight gradient is conj(c) times the inverse
     transform of tr(dH_i^H Q_j) at the emission lags (same type) and the absorption lags (other type); the coupling
@@ -155,13 +155,13 @@ def sigma_grad_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale, Wl, Wg):
     g_D = [np.zeros(Dl.shape, complex), np.zeros(Dg.shape, complex)]
 
     def spectrum(X):
-        Xp = np.zeros((Nkz, L) + X.shape[2:], complex)
+        Xp = np.zeros((Nkz, L) + X.shape[2:], dt)
         Xp[:, :NE] = X
         return np.fft.fft2(Xp, axes=(0, 1))
 
     for t, (G, W, Dt, Dtb) in enumerate(((Gl, Wl, Dl, Dg), (Gg, Wg, Dg, Dl))):
         Gh, Wh = spectrum(G), spectrum(W)
-        K = np.zeros((Nkz, L, NA, NB, 3, 3), complex)
+        K = np.zeros((Nkz, L, NA, NB, 3, 3), dt)
         for w in range(Nw):
             K[:Nqz, w + 1] = Dt[:, w]
             K[:Nqz, L - (w + 1)] = Dtb[:, w]
@@ -170,7 +170,7 @@ def sigma_grad_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale, Wl, Wg):
             Wa = Wh[:, :, a]
             for s in range(NB):
                 b = nbr[a, s]
-                A = dH[a, s]
+                A = dH[a, s].astype(dt)
                 Gb = Gh[:, :, b]
                 Q = [Wa @ A[j] @ np.conj(np.swapaxes(Gb, -1, -2)) for j in range(3)]
                 R = [np.conj(np.swapaxes(Wa, -1, -2)) @ A[i] @ Gb for i in range(3)]
@@ -182,11 +182,12 @@ def sigma_grad_by_transforms(nbr, dH, Dl, Dg, Gl, Gg, scale, Wl, Wg):
                 for w in range(Nw):
                     g_D[t][:, w, a, s] += cc * H[:Nqz, w + 1]
                     g_D[1 - t][:, w, a, s] += cc * H[:Nqz, L - (w + 1)]
-                for m in range(3):
+                for m in range(3):  # per-frequency terms in dt, the sum over frequencies in FP64 (as the kernels)
                     acc = np.zeros((Norb, Norb), complex)
                     for j in range(3):
-                        acc += np.einsum("kl,klxy->xy", -1j * np.conj(Kh[:, :, a, s, m, j]), Q[j])
-                        acc += np.einsum("kl,klxy->xy", 1j * Kh[:, :, a, s, j, m], R[j])
+                        tq = (-1j * np.conj(Kh[:, :, a, s, m, j]))[..., None, None] * Q[j]
+                        tr = (1j * Kh[:, :, a, s, j, m])[..., None, None] * R[j]
+                        acc += (tq + tr).astype(np.complex128).sum(axis=(0, 1))
                     g_dH[a, s, m] += scale / N * acc
     return g_dH, g_D[0], g_D[1]
 
@@ -259,3 +260,72 @@ def test_fp32_arithmetic_error_is_within_the_stated_bound():
     ref = oracle.sigma(*arrs, SCALE)
     errs = [np.abs(g - r).max() / np.abs(r).max() for g, r in zip(got, ref)]
     assert 1e-8 < max(errs) <= 2e-6, errs
+
+
+def coupling_gradient_terms(nbr, dH, Dl, Dg, Gl, Wl, dt):
+    """Per-frequency terms of the coupling gradient of one type (the summand of grad dH_m above), in the complex
+    type dt: [bond][m][frequency][Norb][Norb]."""
+    Nkz, NE, NA, Norb, _ = Gl.shape
+    Nqz, Nw = Dl.shape[0], Dl.shape[1]
+    NB = nbr.shape[1]
+    L = smallest_2a3b(NE + Nw)
+
+    def spectrum(X):
+        Xp = np.zeros((Nkz, L) + X.shape[2:], dt)
+        Xp[:, :NE] = X
+        return np.fft.fft2(Xp, axes=(0, 1))
+
+    Gh, Wh = spectrum(Gl), spectrum(Wl)
+    K = np.zeros((Nkz, L, NA, NB, 3, 3), dt)
+    for w in range(Nw):
+        K[:Nqz, w + 1] = Dl[:, w]
+        K[:Nqz, L - (w + 1)] = Dg[:, w]
+    Kh = np.fft.fft2(K, axes=(0, 1))
+    terms = []
+    for a in range(NA):
+        for s in range(NB):
+            A, Wa, Gb = dH[a, s].astype(dt), Wh[:, :, a], Gh[:, :, nbr[a, s]]
+            Q = [Wa @ A[j] @ np.conj(np.swapaxes(Gb, -1, -2)) for j in range(3)]
+            R = [np.conj(np.swapaxes(Wa, -1, -2)) @ A[i] @ Gb for i in range(3)]
+            terms.append([sum((-1j * np.conj(Kh[:, :, a, s, m, j]))[..., None, None] * Q[j]
+                              + (1j * Kh[:, :, a, s, j, m])[..., None, None] * R[j] for j in range(3))
+                          .reshape(Nkz * L, Norb, Norb) for m in range(3)])
+    return terms
+
+
+def lane_sums_fp32(x, chunk, lanes):
+    """The kernel's order: chunks of `chunk` frequencies; within a chunk lane f adds frequencies f, f + lanes, ...
+    one after another in FP32; lanes and chunks are then added in FP64."""
+    total = np.zeros(x.shape[1:], np.complex128)
+    for c0 in range(0, x.shape[0], chunk):
+        for f in range(lanes):
+            acc = np.zeros(x.shape[1:], np.complex64)
+            for v in x[c0 + f:min(x.shape[0], c0 + chunk):lanes]:
+                acc = (acc + v).astype(np.complex64)
+            total += acc
+    return total
+
+
+def test_fp32_coupling_gradient_needs_short_lane_sums():
+    """On a FinFET-sized frequency grid (Nkz = 7, L = 576, 4032 frequencies) the coupling-gradient terms computed in
+    FP32 and added per lane in FP32 drift from the FP64 sums when a lane adds ~270 terms (the chunks of three per atom
+    at 1024 atoms, 5 lanes); chunks of at most 32 terms per lane, added in FP64, stay close to the floor set by the
+    FP32 terms themselves."""
+    from paper_1912_10024_gb300.inputs import make_upstream
+    d = Dims(NA=2, NB=2, Norb=10, NE=512, Nkz=7, Nqz=7, Nw=32)
+    x = make_inputs(d, seed=41, nbr=ring_neighbours(d.NA, d.NB))
+    W, _ = make_upstream(d, seed=42)
+    arrs = [t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less)] + [W.numpy()]
+    ref = np.array([[t.sum(0) for t in b] for b in coupling_gradient_terms(*arrs, np.complex128)])
+    t32 = coupling_gradient_terms(*arrs, np.complex64)
+    nfreq = t32[0][0].shape[0]
+    lanes = 5
+
+    def err(sums):
+        return np.abs(np.array(sums) - ref).max() / np.abs(ref).max()
+
+    floor = err([[t.astype(np.complex128).sum(0) for t in b] for b in t32])
+    long_chunks = err([[lane_sums_fp32(t, nfreq // 3, lanes) for t in b] for b in t32])
+    short_chunks = err([[lane_sums_fp32(t, 32 * lanes, lanes) for t in b] for b in t32])
+    assert long_chunks > 2 * short_chunks, (floor, long_chunks, short_chunks)
+    assert short_chunks < 2 * floor, (floor, long_chunks, short_chunks)
