@@ -329,3 +329,73 @@ def test_fp32_coupling_gradient_needs_short_lane_sums():
     short_chunks = err([[lane_sums_fp32(t, 32 * lanes, lanes) for t in b] for b in t32])
     assert long_chunks > 2 * short_chunks, (floor, long_chunks, short_chunks)
     assert short_chunks < 2 * floor, (floor, long_chunks, short_chunks)
+
+
+def sigma_spectrum(nbr, dH, Dt, Dtb, G, Nw):
+    """S^(kappa, eps) of one type before the inverse transform (the product step of the forward model)."""
+    Nkz, NE, NA, Norb, _ = G.shape
+    Nqz = Dt.shape[0]
+    NB = nbr.shape[1]
+    L = smallest_2a3b(NE + Nw)
+    Gp = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+    Gp[:, :NE] = G
+    Gh = np.fft.fft2(Gp, axes=(0, 1))
+    K = np.zeros((Nkz, L, NA, NB, 3, 3), complex)
+    for w in range(Nw):
+        K[:Nqz, w + 1] = Dt[:, w]
+        K[:Nqz, L - (w + 1)] = Dtb[:, w]
+    Kh = np.fft.fft2(K, axes=(0, 1))
+    Sh = np.zeros((Nkz, L, NA, Norb, Norb), complex)
+    for a in range(NA):
+        for s in range(NB):
+            A = dH[a, s]
+            for i in range(3):
+                for j in range(3):
+                    Sh[:, :, a] += Kh[:, :, a, s, i, j][..., None, None] * (A[i] @ Gh[:, :, nbr[a, s]] @ A[j].conj().T)
+    return 1j * Sh
+
+
+@pytest.mark.parametrize("Nkz,NE", [(3, 13), (4, 13), (1, 9)])
+def test_half_spectrum_mirror_relation(Nkz, NE):
+    """With anti-Hermitian G and D blocks (as lesser and greater functions are) the spectrum of Sigma obeys
+    S^(-f) = -S^(f)^H, so one frequency of each (f, -f) pair determines the other (the SSE_FLAG_ANTIHERMITIAN path);
+    a G block that is not anti-Hermitian breaks the relation."""
+    d = Dims(NA=4, NB=2, Norb=3, NE=NE, Nkz=Nkz, Nqz=min(Nkz, 2), Nw=3)
+    x = make_inputs(d, seed=NE + Nkz, nbr=ring_neighbours(d.NA, d.NB))
+    nb, dH, Dl, Dg, Gl = (t.numpy() for t in (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less))
+    L = smallest_2a3b(NE + d.Nw)
+    neg = np.ix_((-np.arange(Nkz)) % Nkz, (-np.arange(L)) % L)
+
+    def mirror_error(G):
+        Sh = sigma_spectrum(nb, dH, Dl, Dg, G, d.Nw)
+        mirrored = -np.conj(np.swapaxes(Sh, -1, -2))[neg]
+        return np.abs(Sh - mirrored).max() / np.abs(Sh).max()
+
+    assert mirror_error(Gl) <= 1e-13
+    broken = Gl.copy()
+    broken[0, 2, 1] += 0.1  # one block gains a Hermitian part
+    assert mirror_error(broken) > 1e-4
+
+
+def test_pi_half_spectrum_mirror_relation():
+    """For Eq. (4) with anti-Hermitian G the per-frequency traces obey C^(-f) = C^(f)^H (3x3 blocks)."""
+    d = Dims(NA=4, NB=2, Norb=3, NE=13, Nkz=4, Nqz=2, Nw=3)
+    x = make_inputs(d, seed=77, nbr=ring_neighbours(d.NA, d.NB))
+    nb, dH, Gl, Gg = (t.numpy() for t in (x.nbr, x.dH, x.G_less, x.G_greater))
+    L = smallest_2a3b(d.NE + d.Nw)
+    spec = []
+    for G in (Gl, Gg):
+        Gp = np.zeros((d.Nkz, L, d.NA, d.Norb, d.Norb), complex)
+        Gp[:, :d.NE] = G
+        spec.append(np.fft.fft2(Gp, axes=(0, 1)))
+    neg_k, neg_e = (-np.arange(d.Nkz)) % d.Nkz, (-np.arange(L)) % L
+    X, Y = spec
+    a, s = 1, 0
+    A = dH[a, s]
+    Yneg = Y[neg_k][:, neg_e, nb[a, s]]
+    Ch = np.zeros((d.Nkz, L, 3, 3), complex)
+    for i in range(3):
+        for j in range(3):
+            Ch[..., i, j] = np.trace(A[i].conj().T @ X[:, :, a] @ A[j] @ Yneg, axis1=-2, axis2=-1)
+    mirrored = np.conj(np.swapaxes(Ch, -1, -2))[np.ix_(neg_k, neg_e)]
+    assert np.abs(Ch - mirrored).max() <= 1e-13 * np.abs(Ch).max()
