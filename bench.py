@@ -726,7 +726,8 @@ def main():
             achieved = mixed_tensor_flops(d, args.mode) / (n / args.steps) / ks / 1e12
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None, "kernel": "sigma_mixed_kernel",
-                    "peak_source": f"{src} {key}" + ("" if args.mode == "bf16x3" else " x 1.1/2.25 (tf32/bf16 nominal)")}
+                    "peak_source": f"{src} {key}" + ("" if args.mode == "bf16x3"
+                                                     else " x 1.1/2.25 (tf32/bf16 nominal)")}
         roof["launch_ms"] = ks * 1e3
         roof["kernel_share_of_step"] = kernels[roof["kernel"]][0] / total_ms
         roof["kernels"] = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}

@@ -10,7 +10,6 @@ too large to run whole. Only indexing and copies happen here.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 

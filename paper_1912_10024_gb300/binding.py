@@ -21,7 +21,8 @@ SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE, SSE_FLAG_ANTIHERMITIAN = 
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT,
          "fp32_fft": SSE_MODE_FP32_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
-            "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes", "sse_sigma_bwd_g",
+            "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes",
+            "sse_sigma_bwd_g",
             "sse_sigma_fwd_host_bytes", "sse_sigma_fwd_host", "sse_profile_read", "sse_strerror")
 SSE_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -438,7 +439,8 @@ def dcomb(Draw_less, Draw_greater, nbr, check: bool = False, atoms=None, stream=
     d = _dcomb_dims(Draw_less, nbr, atoms)
     shape = tuple(Draw_less.shape[:3]) + (NB, 3, 3)
     alloc = torch.empty if atoms is None else torch.zeros
-    out = (alloc(shape, dtype=torch.complex128, device=nbr.device), alloc(shape, dtype=torch.complex128, device=nbr.device))
+    out = (alloc(shape, dtype=torch.complex128, device=nbr.device),
+           alloc(shape, dtype=torch.complex128, device=nbr.device))
     ws = torch.empty(256, dtype=torch.uint8, device=nbr.device)
     rc = sse_dcomb_fwd(d, nbr, Draw_less, Draw_greater, out[0], out[1], SSE_FLAG_CHECK if check else 0, ws, 256,
                        stream)

@@ -40,7 +40,8 @@ def halo_atoms(nbr: torch.Tensor, a0: int, a1: int) -> List[int]:
     return sorted(b for b in need if not a0 <= b < a1)
 
 
-def exchange_halo(G_owned: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int, group=None) -> Dict[int, List[torch.Tensor]]:
+def exchange_halo(G_owned: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int,
+                  group=None) -> Dict[int, List[torch.Tensor]]:
     """Fetch the G blocks of this rank's halo atoms from their owners.
 
     G_owned: the owned slices [Nkz, NE, a1-a0, Norb, Norb] of G^< and G^>.

@@ -3,7 +3,6 @@
 The library must load, export every symbol include/sse.h declares, and
 reject invalid arguments before touching the device.
 """
-import ctypes
 import os
 import re
 

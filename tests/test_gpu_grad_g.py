@@ -1,8 +1,8 @@
 """Gradient of Eq. (3) with respect to G (sse_sigma_bwd_g through the transforms, FP64 and FP32_FFT) against the
 oracle.
 
-Tolerance: normwise 1e-12 per gradient tensor in FP64; the stated FP32_FFT bound below for the FP32 path. At the adjoint workload, where the oracle would take too long
-for every atom, the identity Re <grad_G, dG> = sum_t Re tr(W^t^H Sigma^t(dG)) (Sigma is linear in G) is
+Tolerance: normwise 1e-12 per gradient tensor in FP64; the stated FP32_FFT bound below for the FP32 path. At the
+adjoint workload, where the oracle would take too long for every atom, the identity Re <grad_G, dG> = sum_t Re tr(W^t^H Sigma^t(dG)) (Sigma is linear in G) is
 checked with the GPU forward on random dG.
 """
 import math
