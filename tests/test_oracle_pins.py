@@ -273,3 +273,26 @@ def test_literal_einsum_tiny():
                     ref[:, E] += c * np.einsum("qasij,asiml,kqaslp,asjnp->kamn", Dt, A, Gg, A.conj(),
                                                optimize=True)
         assert normwise(S, ref) < 1e-13
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """Sigma, Pi and the gradient in G sum every output block in one thread in a fixed order: bit-identical for any
+    thread count. The adjoint splits the energies among the threads (private partial sums, then a fixed-order
+    reduction), so its summation order follows the thread count: equal to rounding (1e-13 relative)."""
+    import math
+    from paper_1912_10024_gb300.inputs import make_upstream
+    d = TINY
+    x = make_inputs(d, seed=91)
+    W, V = make_upstream(d, seed=92)
+    scale = 1.0 / (2.0 * math.pi)
+    args = (x.nbr, x.dH, x.D_less, x.D_greater, x.G_less, x.G_greater, scale)
+    runs = {
+        "sigma": lambda n: oracle.sigma(*args, nthreads=n),
+        "pi": lambda n: oracle.pi(x.nbr, x.dH, x.G_less, x.G_greater, scale, d.Nqz, d.Nw, nthreads=n),
+        "grad_G": lambda n: oracle.sigma_grad_G(x.nbr, x.dH, x.D_less, x.D_greater, scale, W, V, nthreads=n),
+    }
+    for name, run in runs.items():
+        for a, b in zip(run(1), run(7)):
+            assert np.array_equal(a, b), name
+    for a, b in zip(oracle.sigma_grad(*args, W, V, nthreads=1), oracle.sigma_grad(*args, W, V, nthreads=7)):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
