@@ -154,3 +154,24 @@ def test_fwd_host_checks_before_any_device_work():
         args.update(over)
         assert B.sse_sigma_fwd_host(d, stream=0, copy_stream=1, **args) == status, over
     assert B.sse_sigma_fwd_host(d, stream=0, copy_stream=0, **base) == 1  # the overlap needs two streams
+
+
+def test_fp32_workspaces_are_smaller_and_tensor_modes_unsupported():
+    """FP32_FFT keeps its spectra in complex64: every transform workspace is smaller than the FP64 one, about half
+    where the spectra are all of it."""
+    d = B.sse_dims(256, 4, 10, 256, 5, 5, 16, 0, 256)
+    fft64, fft32 = B.SSE_MODE_FP64_FFT, B.SSE_MODE_FP32_FFT
+    for fn in (B.sse_workspace_bytes, B.sse_pi_workspace_bytes, B.sse_sigma_bwd_g_workspace_bytes,
+               B.sse_sigma_fwd_host_bytes):
+        w64, w32 = fn(d, fft64, 0), fn(d, fft32, 0)
+        assert 0 < w32 < w64, fn
+    # the spectra dominate: FP32 needs a little over half (the FP64 partial sums of the adjoint stay FP64)
+    assert B.sse_pi_workspace_bytes(d, fft32, 0) < 0.51 * B.sse_pi_workspace_bytes(d, fft64, 0)
+    assert B.sse_sigma_bwd_g_workspace_bytes(d, fft32, 0) < 0.51 * B.sse_sigma_bwd_g_workspace_bytes(d, fft64, 0)
+
+
+def test_bwd_g_refuses_tensor_modes():
+    d = good_dims()
+    for mode in (B.SSE_MODE_TF32, B.SSE_MODE_BF16X3):
+        rc = B.sse_sigma_bwd_g(d, FAKE, FAKE, FAKE, FAKE, 0.1, mode, 0, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 30, 0)
+        assert rc == 2, mode  # SSE_ERR_UNSUPPORTED, before any device work
