@@ -2,9 +2,11 @@
 
 Each rank owns a contiguous atom range and only its own G blocks, fetches
 the halo blocks with paper_1912_10024_gb300.parallel.exchange_halo, and
-evaluates its shard of Sigma (Eq. 3) and of Pi (Eq. 4: the same atom halo)
-with the CPU oracle. The gathered shards must equal the unsharded oracle
-results bit for bit (same arithmetic, same order).
+evaluates its shard of Sigma (Eq. 3), of Pi (Eq. 4: the same atom halo) and
+of the adjoint of Eq. (3) (gradients of its own atoms' dH and D: owned per
+atom, so no reduction across ranks) with the CPU oracle. The gathered shards
+must equal the unsharded oracle results bit for bit (same arithmetic, same
+order).
 """
 import os
 import socket
@@ -14,7 +16,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_1912_10024_gb300.inputs import TINY, Dims, diamond_neighbours, make_inputs
+from paper_1912_10024_gb300.inputs import TINY, Dims, diamond_neighbours, make_inputs, make_upstream
 from paper_1912_10024_gb300 import parallel as P
 
 SCALE = 0.15915494309189535
@@ -44,7 +46,15 @@ def _worker(rank, world, port, dims, seed, nbr, q):
         Sl, Sg = oracle.sigma(*local, SCALE, a_range=(0, a1 - a0), nthreads=2)
         Pl, Pg = oracle.pi(local[0], local[1], local[4], local[5], SCALE, dims.Nqz, dims.Nw, a_range=(0, a1 - a0),
                            nthreads=2)
+        # adjoint of the shard: the upstream gradient of the owned atoms, zero on the halo atoms
+        W, V = make_upstream(dims, seed=seed + 1)
+        n_own = a1 - a0
+        Wl, Vl = torch.zeros_like(local[4]), torch.zeros_like(local[5])
+        Wl[:, :, :n_own], Vl[:, :, :n_own] = W[:, :, a0:a1], V[:, :, a0:a1]
+        g_dH, g_Dl, g_Dg = oracle.sigma_grad(*local, SCALE, Wl, Vl, a_range=(0, n_own), nthreads=2)
         shard = [torch.from_numpy(X[:, :, : a1 - a0]).contiguous() for X in (Sl, Sg, Pl, Pg)]
+        shard += [torch.from_numpy(g_dH[:n_own]).contiguous()] + [torch.from_numpy(X[:, :, :n_own]).contiguous()
+                                                                 for X in (g_Dl, g_Dg)]
         gathered = [None] * world
         dist.all_gather_object(gathered, (a0, a1, shard))
         if rank == 0:
@@ -52,10 +62,15 @@ def _worker(rank, world, port, dims, seed, nbr, q):
                                 nthreads=2)
             full = tuple(full) + tuple(oracle.pi(inp.nbr, inp.dH, inp.G_less, inp.G_greater, SCALE, dims.Nqz,
                                                  dims.Nw, nthreads=2))
+            grads = oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                                      W, V, nthreads=2)
             ok = True
             for (b0, b1, sh) in gathered:
                 for t in range(4):
                     ok &= np.array_equal(sh[t].numpy(), full[t][:, :, b0:b1])
+                ok &= np.array_equal(sh[4].numpy(), grads[0][b0:b1])
+                for t in (1, 2):
+                    ok &= np.array_equal(sh[4 + t].numpy(), grads[t][:, :, b0:b1])
             q.put(ok)
     finally:
         dist.destroy_process_group()
