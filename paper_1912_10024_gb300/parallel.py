@@ -4,7 +4,10 @@ The communication-avoiding decomposition of Sec. 4.2 tiles the atoms of the
 device: a rank that owns atoms [a0, a1) computes Sigma_a for exactly those
 atoms and needs, besides its own G blocks, the G blocks of the neighbours of
 its atoms that other ranks own (the "+N_b atom halo"). One exchange step
-brings those blocks in; Sigma needs no reduction afterwards.
+brings those blocks in; Sigma, Pi and the gradients with respect to dH and D
+need no reduction afterwards. The gradient with respect to G does: a rank's
+bonds also reach the G blocks of its halo atoms, so ``reduce_halo_grad`` sends
+those contributions back to their owners.
 
 On one GPU the shard primitive is sse_sigma_fwd's atom range; across GPUs the
 exchange below runs over torch.distributed (NCCL for CUDA tensors, gloo for
@@ -100,3 +103,47 @@ def local_problem(nbr: torch.Tensor, a0: int, a1: int, G_owned: Sequence[torch.T
         Dl[:, :, :n_own] = D
         Ds.append(Dl)
     return nbr_l.to(dH_owned.device), dH_l, Ds[0], Ds[1], Gs[0], Gs[1]
+
+
+def reduce_halo_grad(gG_local: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int,
+                     group=None) -> List[torch.Tensor]:
+    """The exchange step of the gradient with respect to G: the reverse of ``exchange_halo``.
+
+    gG_local: the rank's gradients with respect to G^< and G^> in the layout of ``local_problem``
+    ([Nkz, NE, n_loc, Norb, Norb], owned atoms first, then the halo atoms in sorted order), each computed from the
+    rank's own bonds only. A bond (a, s) contributes to the gradient of G_b for b = nbr[a][s], which another rank may
+    own: every rank sends the blocks of its halo atoms to their owners, and each owner adds what it receives to its
+    own blocks in rank order (deterministic). Returns the owned slices [Nkz, NE, a1-a0, Norb, Norb] with every
+    bond's contribution.
+    """
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    a0, a1 = atom_range(NA, world, rank)
+    n_own = a1 - a0
+    mine = halo_atoms(nbr, a0, a1)
+    halos: List[List[int]] = [None] * world  # type: ignore[list-item]
+    dist.all_gather_object(halos, mine, group=group)
+    out = [g[:, :, :n_own].clone() for g in gG_local]
+    ops, recv = [], []
+    for peer in range(world):
+        if peer == rank:
+            continue
+        # my halo blocks that the peer owns, in my (sorted) halo order
+        for idx, b in enumerate(mine):
+            if owner(b, NA, world) == peer:
+                for g in gG_local:
+                    ops.append(dist.P2POp(dist.isend, g[:, :, n_own + idx].contiguous(), peer, group))
+        # the peer's halo blocks that I own, in the peer's order
+        for b in halos[peer]:
+            if a0 <= b < a1:
+                bufs = [torch.empty_like(g[:, :, 0]) for g in gG_local]
+                recv.append((peer, b, bufs))
+                for buf in bufs:
+                    ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    for _peer, b, bufs in sorted(recv, key=lambda x: (x[0], x[1])):
+        for t, buf in enumerate(bufs):
+            out[t][:, :, b - a0] += buf
+    return out

@@ -101,3 +101,56 @@ def test_atom_ranges_partition():
             assert rs[0][0] == 0 and rs[-1][1] == NA
             assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
             assert max(b - a for a, b in rs) - min(b - a for a, b in rs) <= 1
+
+
+def _grad_g_worker(rank, world, port, dims, seed, nbr, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed, nbr=nbr)
+        W, V = make_upstream(dims, seed=seed + 1)
+        a0, a1 = P.atom_range(dims.NA, world, rank)
+        n_own = a1 - a0
+        G_owned = [inp.G_less[:, :, a0:a1].clone(), inp.G_greater[:, :, a0:a1].clone()]
+        halo = P.exchange_halo(G_owned, inp.nbr, dims.NA)
+        local = P.local_problem(inp.nbr, a0, a1, G_owned, halo, inp.dH[a0:a1],
+                                (inp.D_less[:, :, a0:a1], inp.D_greater[:, :, a0:a1]))
+        Wl, Vl = torch.zeros_like(local[4]), torch.zeros_like(local[5])
+        Wl[:, :, :n_own], Vl[:, :, :n_own] = W[:, :, a0:a1], V[:, :, a0:a1]
+        # the gradient in G from this rank's bonds only, for owned and halo atoms alike
+        gl, gg = oracle.sigma_grad_G(local[0], local[1], local[2], local[3], SCALE, Wl, Vl, a_range=(0, n_own),
+                                     nthreads=2)
+        owned = P.reduce_halo_grad([torch.from_numpy(gl), torch.from_numpy(gg)], inp.nbr, dims.NA)
+        # control: bonds of the other rank reach some of this rank's atoms, so the reduction changes something
+        assert float((owned[0] - torch.from_numpy(gl[:, :, :n_own])).abs().max()) > 0
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (a0, a1, [t.contiguous() for t in owned]))
+        if rank == 0:
+            full = oracle.sigma_grad_G(inp.nbr, inp.dH, inp.D_less, inp.D_greater, SCALE, W, V, nthreads=2)
+            ok = True
+            for (b0, b1, sh) in gathered:
+                for t in range(2):
+                    ref = full[t][:, :, b0:b1]
+                    ok &= bool(np.abs(sh[t].numpy() - ref).max() <= 1e-13 * np.abs(full[t]).max())
+            q.put(ok)
+    finally:
+        dist.destroy_process_group()
+
+
+def _run_grad_g(dims, world, seed, nbr=None):
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    mp.start_processes(_grad_g_worker, args=(world, _free_port(), dims, seed, nbr, q), nprocs=world, join=True,
+                       start_method="spawn")
+    return q.get()
+
+
+def test_two_ranks_gradient_in_G_reduces_the_halo():
+    """The gradient with respect to G, sharded by atoms: each rank's bonds reach halo atoms that other ranks own, and
+    reduce_halo_grad returns those contributions to the owners (equal to the unsharded oracle up to the order of the
+    additions)."""
+    assert _run_grad_g(TINY, 2, seed=3)
+    d = Dims(NA=128, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2)
+    assert _run_grad_g(d, 2, seed=6, nbr=diamond_neighbours(2, 2, 4))
