@@ -147,3 +147,69 @@ def reduce_halo_grad(gG_local: Sequence[torch.Tensor], nbr: torch.Tensor, NA: in
         for t, buf in enumerate(bufs):
             out[t][:, :, b - a0] += buf
     return out
+
+
+# ---------------------------------------------------------------------------
+# Energy windows (the other axis of the Sec. 4.2 tiling). Sigma(E) reads G at E -/+ (w+1), w < Nw, so a rank that
+# owns the energy window [E0, E1) needs the Nw rows on each side (the "+2 N_w energy halo"); with them, Sigma on
+# [E0, E1) is exact (rows beyond the grid contribute zero as in Eq. (3)). The direct evaluations (FP64 correlation,
+# tensor-core windows) shard this way; the transform evaluation needs every energy of a column and shards by atoms.
+# ---------------------------------------------------------------------------
+def energy_range(NE: int, world: int, rank: int) -> Tuple[int, int]:
+    """Balanced contiguous energy window of ``rank``."""
+    return atom_range(NE, world, rank)
+
+
+def energy_owner(E: int, NE: int, world: int) -> int:
+    return owner(E, NE, world)
+
+
+def exchange_energy_halo(G_window: Sequence[torch.Tensor], NE: int, Nw: int, group=None):
+    """Extend this rank's energy window of G^< and G^> ([Nkz, E1-E0, ...]) by the Nw rows on each side that other
+    ranks own. Returns (e0, [G^< rows e0..e1-1, G^> rows e0..e1-1]) with e0 = max(0, E0-Nw), e1 = min(NE, E1+Nw)."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    E0, E1 = energy_range(NE, world, rank)
+    e0, e1 = max(0, E0 - Nw), min(NE, E1 + Nw)
+    ranges: List[Tuple[int, int]] = [None] * world  # type: ignore[list-item]
+    dist.all_gather_object(ranges, (e0, e1), group=group)
+    out = []
+    for G in G_window:
+        X = torch.empty((G.shape[0], e1 - e0) + tuple(G.shape[2:]), dtype=G.dtype, device=G.device)
+        X[:, E0 - e0:E1 - e0] = G
+        out.append(X)
+    ops, pending = [], []
+    for peer in range(world):
+        if peer == rank:
+            continue
+        # my rows inside the peer's extended window, then the peer's rows inside mine (the same interval
+        # arithmetic on both sides, so the messages of each direction match in order)
+        s0, s1 = max(E0, ranges[peer][0]), min(E1, ranges[peer][1])
+        if s0 < s1:
+            for G in G_window:
+                ops.append(dist.P2POp(dist.isend, G[:, s0 - E0:s1 - E0].contiguous(), peer, group))
+        p0, p1 = energy_range(NE, world, peer)
+        r0, r1 = max(p0, e0), min(p1, e1)
+        if r0 < r1:
+            for t in range(len(G_window)):
+                buf = torch.empty_like(out[t][:, r0 - e0:r1 - e0])
+                ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+                pending.append((t, r0 - e0, r1 - e0, buf))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    for t, lo, hi, buf in pending:
+        out[t][:, lo:hi] = buf
+    return e0, out
+
+
+def reduce_in_rank_order(x: torch.Tensor, group=None) -> torch.Tensor:
+    """Sum of ``x`` over the ranks, added in rank order on every rank (deterministic): the reduction that gradients
+    summed over energies (dH, D) need when the energies are split."""
+    world = dist.get_world_size(group)
+    parts = [torch.empty_like(x) for _ in range(world)]
+    dist.all_gather(parts, x.contiguous(), group=group)
+    total = parts[0].clone()
+    for p in parts[1:]:
+        total += p
+    return total
