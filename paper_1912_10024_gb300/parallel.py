@@ -1,4 +1,4 @@
-"""Atom-tile sharding of Eq. (3) across ranks with a halo exchange of G.
+"""Atom-tile and energy-window sharding of Eq. (3) across ranks with halo exchanges of G.
 
 The communication-avoiding decomposition of Sec. 4.2 tiles the atoms of the
 device: a rank that owns atoms [a0, a1) computes Sigma_a for exactly those
