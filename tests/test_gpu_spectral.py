@@ -181,3 +181,29 @@ def test_antihermitian_check_reports_violations():
     with pytest.raises(B.SseError) as e:
         gpu_sigma(inp, antihermitian=True, check=True)
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("dims", [
+    Dims(NA=3, NB=2, Norb=2, NE=2000, Nkz=2, Nqz=2, Nw=5),   # L = 2048: one column per FP64 transform CTA
+    Dims(NA=4, NB=2, Norb=3, NE=30, Nkz=16, Nqz=16, Nw=4),   # the largest kz grid of the transform path
+], ids=lambda d: f"NE{d.NE}_Nkz{d.Nkz}")
+def test_maximum_lengths(dims):
+    """The transform path at its size limits: a long energy grid (the one-column FFT variant in FP64, column pairs in
+    FP32) and Nkz = Nqz = 16 (the kz DFT's largest grid): Sigma in FP64_FFT and FP32_FFT, Pi and the adjoint in
+    FP64_FFT, each against the oracle."""
+    inp = make_inputs(dims, seed=dims.NE + dims.Nkz, nbr=ring_neighbours(dims.NA, dims.NB))
+    W, V = make_upstream(dims, seed=dims.NE + dims.Nkz + 1)
+    g = inp.to("cuda")
+    Ol, Og = oracle_sigma(inp)
+    for mode, bound in (("fp64_fft", TOL), ("fp32_fft", 2e-6)):
+        Sl, Sg = B.sigma(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, mode=mode, check=True)
+        assert normwise(Sl.cpu().numpy(), Ol) <= bound, mode
+        assert normwise(Sg.cpu().numpy(), Og) <= bound, mode
+    Pl, Pg = B.pi(g.G_less, g.G_greater, g.dH, g.nbr, dims.Nqz, dims.Nw, check=True)
+    Ql, Qg = oracle.pi(inp.nbr, inp.dH, inp.G_less, inp.G_greater, SCALE, dims.Nqz, dims.Nw)
+    assert normwise(Pl.cpu().numpy(), Ql) <= TOL and normwise(Pg.cpu().numpy(), Qg) <= TOL
+    got = B.sigma_grad(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, W.cuda(), V.cuda(),
+                       mode="fp64_fft", check=True)
+    ref = oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, W, V)
+    for x, y in zip(got, ref):
+        assert normwise(x.cpu().numpy(), y) <= TOL
