@@ -78,7 +78,12 @@ typedef struct sse_dims {
  *            the result is transformed back. Same values as FP64 up to the
  *            rounding of the transforms (normwise ~1e-15), far fewer flops;
  *            workspace Nkz*L*(NA + 2*nA)*Norb^2*16 + Nkz*L*nA*NB*9*16 bytes
- *            (nA = a_end - a_begin). Needs Nkz <= 16, NB <= 16, L <= ~4800.
+ *            (nA = a_end - a_begin). Size limits, the same for FP32_FFT and for
+ *            every entry point that runs transforms: Nkz <= 16, L <= 4608
+ *            (NE + Nw <= 4608), NB <= 16, and for the widest blocks
+ *            NB <= 14, 12, 10 at Norb = 14, 15, 16 (sse_pi_fwd: NB <= 15, 12,
+ *            10, 9, 7 at Norb = 12 .. 16). Beyond them the host checks return
+ *            SSE_ERR_UNSUPPORTED before any device work.
  *   FP32_FFT : the same transforms and per-frequency block products in FP32 on the
  *            CUDA cores' FP32 pipe (about 60x the FP64 pipe on GB300), FP64 inputs
  *            and outputs; for sse_sigma_fwd, sse_sigma_bwd, sse_sigma_bwd_g and

@@ -36,6 +36,21 @@ bool valid_mode(int mode) {
            mode == SSE_MODE_FP32_FFT;
 }
 bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
+
+// The kernels' own limits for these sizes in this mode (transform length, kz DFT size, shared memory of the
+// configurations): host-only functions of the sizes, tested before any device work. The direct FP64 and
+// tensor-core kernels choose configurations that fit; their drivers keep their own checks.
+enum class Op { Fwd, Bwd, BwdG, Pi };
+bool op_supported(const sse_dims& d, int mode, Op op) {
+    const bool fp32 = mode == SSE_MODE_FP32_FFT;
+    switch (op) {
+        case Op::Fwd: return (mode != SSE_MODE_FP64_FFT && !fp32) || sse::spectral_fwd_supported(d, fp32);
+        case Op::Bwd: return mode == SSE_MODE_FP64 || sse::spectral_bwd_supported(d);
+        case Op::BwdG: return sse::spectral_bwd_g_supported(d, fp32);  // transforms in every mode it takes
+        case Op::Pi: return sse::spectral_pi_supported(d);              // limits of the FP64 and FP32 kernels
+    }
+    return false;
+}
 bool valid_flags(uint32_t f) {
     return (f & ~(uint32_t)(SSE_FLAG_SYMMETRIZE | SSE_FLAG_CHECK | SSE_FLAG_PROFILE | SSE_FLAG_ANTIHERMITIAN)) == 0;
 }
@@ -118,6 +133,7 @@ extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double
     int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
+    if (!op_supported(*d, mode, Op::Fwd)) return SSE_ERR_UNSUPPORTED;
     if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + fwd_ws(*d, mode))
         return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;
@@ -150,6 +166,7 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
         !aligned(g_D_greater, 16))
         return SSE_ERR_INVALID_ARG;
     if (!fp64_mode(mode) && mode != SSE_MODE_FP32_FFT) return SSE_ERR_UNSUPPORTED;
+    if (!op_supported(*d, mode, Op::Bwd)) return SSE_ERR_UNSUPPORTED;
     const size_t need = mode == SSE_MODE_FP64       ? sse::fp64_bwd_workspace(*d)
                         : mode == SSE_MODE_FP64_FFT ? sse::spectral_bwd_workspace(*d)
                                                     : sse::spectral_bwd32_workspace(*d);
@@ -238,6 +255,7 @@ extern "C" int sse_pi_fwd(const sse_dims* d, const int32_t* nbr, const double* d
         !aligned(P_less, 16) || !aligned(P_greater, 16))
         return SSE_ERR_INVALID_ARG;
     if (!supported_dims(d) || !(fp64_mode(mode) || mode == SSE_MODE_FP32_FFT)) return SSE_ERR_UNSUPPORTED;
+    if (!op_supported(*d, mode, Op::Pi)) return SSE_ERR_UNSUPPORTED;
     if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + pi_workspace(*d, mode))
         return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;
@@ -277,6 +295,7 @@ extern "C" int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const doub
         !aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_G_less, 16) || !aligned(g_G_greater, 16))
         return SSE_ERR_INVALID_ARG;
     if (!supported_dims(d) || !(fp64_mode(mode) || mode == SSE_MODE_FP32_FFT)) return SSE_ERR_UNSUPPORTED;
+    if (!op_supported(*d, mode, Op::BwdG)) return SSE_ERR_UNSUPPORTED;
     if (!workspace || !aligned(workspace, 256) || ws_bytes < sse::kStatusBytes + gradg_workspace(*d, mode))
         return SSE_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -337,6 +356,7 @@ extern "C" int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const d
     int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
+    if (!op_supported(*d, mode, Op::Fwd)) return SSE_ERR_UNSUPPORTED;
     const HostLayout L = host_layout(*d, mode);
     if (!device_buf || !aligned(device_buf, 256) || buf_bytes < L.total) return SSE_ERR_WORKSPACE;
     if (d->a_begin == d->a_end) return SSE_OK;

@@ -67,6 +67,9 @@ cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_gr
 // Transform-based forward (sse_spectral_fwd.cu): FFT length along E, size limits, workspace.
 int spectral_length(const sse_dims& d);
 bool spectral_supported(const sse_dims& d);
+// The forward's limits for FP64 (fp32 = false) or FP32 (true) transforms and block products; like every
+// *_supported predicate below, a host-only function of the sizes that the entry points test before any device work.
+bool spectral_fwd_supported(const sse_dims& d, bool fp32);
 size_t spectral_fwd_workspace(const sse_dims& d);
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                          size_t ws_bytes, cudaStream_t st);
@@ -101,6 +104,7 @@ cudaError_t spectral_bwd32(const Problem& p, const double2* gS_less, const doubl
 // Gradient with respect to G, transform-based: FP64 (spectral_bwd_g) or FP32 transforms and products with FP64
 // inputs and outputs (spectral_bwd_g32) (sse_spectral_adj.cu).
 size_t spectral_bwd_g_workspace(const sse_dims& d);
+bool spectral_bwd_g_supported(const sse_dims& d, bool fp32);
 cudaError_t spectral_bwd_g(const Problem& p, const double2* gS_less, const double2* gS_greater, double2* g_G_less,
                            double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes, cudaStream_t st);
 size_t spectral_bwd_g32_workspace(const sse_dims& d);

@@ -1070,6 +1070,25 @@ size_t spectral_bwd_g_workspace(const sse_dims& d) { return gradg_layout(d).tota
 size_t spectral_bwd_g32_workspace(const sse_dims& d) { return gradg_layout(d, 8).total; }
 
 namespace {
+// Sizes the FP64 G-gradient's product kernel is configured for: its grid covers every atom b (also those no bond
+// reaches: they get zero), and its A region holds one bond's 3 x 4 planes (>= 12 Norb^2 doubles), hence NB >= 2.
+sse_dims gradg_prod_dims(const sse_dims& d) {
+    sse_dims dall = d;
+    dall.a_begin = 0;
+    dall.a_end = d.NA;
+    dall.NB = d.NB < 2 ? 2 : d.NB;
+    return dall;
+}
+}  // namespace
+
+bool spectral_bwd_g_supported(const sse_dims& d, bool fp32) {
+    if (!spectral_supported(d)) return false;
+    const size_t nfreq = (size_t)d.Nkz * spectral_length(d);
+    const int smem = fp32 ? make_gradg32_cfg(d, nfreq).smem : make_prod_cfg(gradg_prod_dims(d), nfreq, 8).smem;
+    return smem <= 227 * 1024;
+}
+
+namespace {
 // The gradient with respect to G in the real type T: double (FP64_FFT) or float (FP32_FFT: FP32 transforms and
 // products, FP64 inputs and outputs).
 template <class T>
@@ -1077,8 +1096,9 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
                              double2* g_G_less, double2* g_G_greater, unsigned* status, void* ws, size_t ws_bytes,
                              cudaStream_t st) {
     using C = typename CX<T>::C;
+    constexpr bool fp32 = sizeof(T) == 4;
     const sse_dims& d = p.d;
-    if (!spectral_supported(d)) return cudaErrorNotSupported;
+    if (!spectral_bwd_g_supported(d, fp32)) return cudaErrorNotSupported;
     const GradGLayout lay = gradg_layout(d, sizeof(C));
     if (ws_bytes < lay.total) return cudaErrorInvalidValue;
     unsigned char* base = static_cast<unsigned char*>(ws);
@@ -1105,15 +1125,8 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
     SSE_TIMED("inbond_fill_kernel", st,
               inbond_fill_kernel<<<grid_for(d.NA, 128), 128, 0, st>>>(d, p.nbr, offs, list));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the product kernel's grid: every atom b (also those no bond reaches: they get zero)
-    sse_dims dall = d;
-    dall.a_begin = 0;
-    dall.a_end = d.NA;
-    dall.NB = d.NB < 2 ? 2 : d.NB;  // the A region holds one bond's 3 x 4 planes (>= 12 Norb^2 doubles)
-    constexpr bool fp32 = sizeof(T) == 4;
-    const ProdCfg pc = make_prod_cfg(dall, nfreq, (int)sizeof(T));
+    const ProdCfg pc = make_prod_cfg(gradg_prod_dims(d), nfreq, (int)sizeof(T));
     const GradG32Cfg gc = make_gradg32_cfg(d, nfreq);
-    if ((fp32 ? gc.smem : pc.smem) > 227 * 1024) return cudaErrorNotSupported;
     if constexpr (fp32)
         e = cudaFuncSetAttribute(spec_gradg32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, gc.smem);
     else

@@ -361,6 +361,10 @@ bool spectral_supported(const sse_dims& d) {
            make_prod_cfg(d, (size_t)d.Nkz * L).smem <= 227 * 1024;
 }
 
+bool spectral_fwd_supported(const sse_dims& d, bool fp32) {
+    return spectral_supported(d) && (!fp32 || make_prod32_cfg(d, 1).smem <= 227 * 1024);
+}
+
 size_t spectral_fwd_workspace(const sse_dims& d) { return spec_layout(d).total; }
 size_t spectral_fwd32_workspace(const sse_dims& d) { return spec_layout(d, 8).total; }
 
@@ -375,7 +379,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
     // can start; without it every transform is one launch over all slices.
     using C = typename CX<T>::C;
     const sse_dims& d = p.d;
-    if (!spectral_supported(d)) return cudaErrorNotSupported;
+    if (!spectral_fwd_supported(d, sizeof(T) == 4)) return cudaErrorNotSupported;
     const SpecLayout lay = spec_layout(d, sizeof(C));
     if (ws_bytes < lay.total) return cudaErrorInvalidValue;
     unsigned char* base = static_cast<unsigned char*>(ws);

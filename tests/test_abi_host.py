@@ -175,3 +175,50 @@ def test_bwd_g_refuses_tensor_modes():
     for mode in (B.SSE_MODE_TF32, B.SSE_MODE_BF16X3):
         rc = B.sse_sigma_bwd_g(d, FAKE, FAKE, FAKE, FAKE, 0.1, mode, 0, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 30, 0)
         assert rc == 2, mode  # SSE_ERR_UNSUPPORTED, before any device work
+
+
+# Largest NB the transform kernels take per Norb = 1 .. 16 (their shared-memory configurations): the limits the
+# header documents for FP64_FFT and FP32_FFT.
+NB_MAX = [16] * 13 + [14, 12, 10]
+NB_MAX_PI = [16] * 11 + [15, 12, 10, 9, 7]
+
+
+def transform_entries():
+    """Every entry point that runs transforms, called with a 16-byte workspace: SSE_ERR_WORKSPACE (6) means the sizes
+    passed the support checks (which come first), SSE_ERR_UNSUPPORTED (2) that they did not; neither touches the
+    device."""
+    fwd = lambda d, m: call_fwd(d, mode=m, ws_bytes=16)  # noqa: E731
+    host = lambda d, m: B.sse_sigma_fwd_host(  # noqa: E731
+        d, nbr=FAKE, dH=FAKE, D_less=FAKE, D_greater=FAKE, G_less=FAKE, G_greater=FAKE, scale=0.1, mode=m, flags=0,
+        S_less=FAKE, S_greater=FAKE, device_buf=FAKE, buf_bytes=16, stream=0, copy_stream=1)
+    bwd = lambda d, m: B.sse_sigma_bwd(d, *[FAKE] * 6, 0.1, m, 0, *[FAKE] * 6, 16, 0)  # noqa: E731
+    pi = lambda d, m: call_pi(d, mode=m, ws_bytes=16)  # noqa: E731
+    bwd_g = lambda d, m: B.sse_sigma_bwd_g(  # noqa: E731
+        d, nbr=FAKE, dH=FAKE, D_less=FAKE, D_greater=FAKE, scale=0.1, mode=m, flags=0, gS_less=FAKE, gS_greater=FAKE,
+        g_G_less=FAKE, g_G_greater=FAKE, workspace=FAKE, ws_bytes=16, stream=0)
+    return [("fwd", fwd, NB_MAX), ("fwd_host", host, NB_MAX), ("bwd", bwd, NB_MAX), ("pi", pi, NB_MAX_PI),
+            ("bwd_g", bwd_g, NB_MAX)]
+
+
+@pytest.mark.parametrize("mode", [B.SSE_MODE_FP64_FFT, B.SSE_MODE_FP32_FFT])
+def test_transform_size_limits_are_checked_on_host(mode):
+    """The transform evaluations' limits (Nkz <= 16 for the kz DFT pass, L = NE + Nw rounded up to 2^a 3^b <= 4608
+    for the shared-memory FFT, NB by Norb for the product kernels) are refused with SSE_ERR_UNSUPPORTED before any
+    device work, by every entry point, and sizes inside them pass."""
+    for name, fn, nb_max in transform_entries():
+        for Norb in range(1, 17):
+            for NB in (nb_max[Norb - 1], nb_max[Norb - 1] + 1):
+                want = 6 if NB == nb_max[Norb - 1] else 2
+                assert fn(B.sse_dims(16, NB, Norb, 64, 4, 1, 4, 0, 16), mode) == want, (name, Norb, NB)
+        assert fn(B.sse_dims(16, 4, 10, 64, 16, 1, 4, 0, 16), mode) == 6, name
+        assert fn(B.sse_dims(16, 4, 10, 64, 17, 1, 4, 0, 16), mode) == 2, name
+        assert fn(B.sse_dims(16, 4, 10, 4576, 4, 1, 32, 0, 16), mode) == 6, name  # L = 4608 = 2^9 3^2
+        assert fn(B.sse_dims(16, 4, 10, 4577, 4, 1, 32, 0, 16), mode) == 2, name  # L = 5184
+
+
+def test_direct_fp64_adjoint_has_no_transform_limits():
+    """Mode FP64 of sse_sigma_bwd runs the direct kernels: no kz, length or NB limit beyond the common ones."""
+    bwd = dict((n, f) for n, f, _ in transform_entries())["bwd"]
+    for d in (B.sse_dims(16, 17, 16, 64, 4, 1, 4, 0, 16), B.sse_dims(16, 4, 10, 64, 17, 1, 4, 0, 16),
+              B.sse_dims(16, 4, 10, 6000, 4, 1, 32, 0, 16)):
+        assert bwd(d, B.SSE_MODE_FP64) == 6
