@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "sse.h"
@@ -17,6 +18,7 @@ namespace {
 struct Rec {
     const char* name;
     int dev;
+    std::thread::id owner;  // the host thread that launched the kernel
     cudaEvent_t e0, e1;
     bool closed;
 };
@@ -53,7 +55,7 @@ void prof_begin(const char* name, cudaStream_t st) {
     if (g_recs.size() >= kMaxRecs) return;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
-    Rec r{name, dev, nullptr, nullptr, false};
+    Rec r{name, dev, std::this_thread::get_id(), nullptr, nullptr, false};
     if (!take_event(dev, &r.e0)) return;
     if (!take_event(dev, &r.e1)) {
         g_free.push_back({dev, r.e0});
@@ -70,8 +72,10 @@ void prof_begin(const char* name, cudaStream_t st) {
 void prof_end(cudaStream_t st) {
     if (!t_on) return;
     std::lock_guard<std::mutex> lk(g_mu);
+    // this thread's open record (other threads may be between their own begin and end)
+    const std::thread::id me = std::this_thread::get_id();
     for (size_t i = g_recs.size(); i-- > 0;)
-        if (!g_recs[i].closed) {
+        if (!g_recs[i].closed && g_recs[i].owner == me) {
             g_recs[i].closed = cudaEventRecord(g_recs[i].e1, st) == cudaSuccess;
             if (!g_recs[i].closed) {  // drop the record
                 g_free.push_back({g_recs[i].dev, g_recs[i].e0});
