@@ -204,28 +204,62 @@ def dims_of(G: torch.Tensor, D: torch.Tensor, dH: torch.Tensor, atoms: Optional[
     return sse_dims(NA, dH.shape[1], Norb, NE, Nkz, D.shape[0], D.shape[1], a0, a1)
 
 
-def _check_tensor(name, x, dtype, shape):
-    if not isinstance(x, torch.Tensor) or not x.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
+def _check_tensor(name, x, dtype, shape, cuda: bool = True, contiguous: bool = True, device=None):
+    """Every pointer the library receives covers exactly the bytes of its documented layout: right place (a CUDA
+    tensor on the inputs' device, or a host tensor for the host-buffer entry point), dtype, shape and contiguity."""
+    if not isinstance(x, torch.Tensor) or x.is_cuda != cuda:
+        raise TypeError(f"{name} must be a {'CUDA' if cuda else 'host'} tensor")
+    if device is not None and x.device != device:
+        raise ValueError(f"{name} is on {x.device}, the inputs on {device}")
     if x.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
     if tuple(x.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
-    if not x.is_contiguous():
+    if contiguous and not x.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
 
 
-def check_inputs(G_less, G_greater, dH, D_less, D_greater, nbr):
+def check_inputs(G_less, G_greater, dH, D_less, D_greater, nbr, cuda: bool = True):
+    for name, x, rank in (("G_less", G_less, 5), ("dH", dH, 5), ("D_less", D_less, 6)):
+        if not isinstance(x, torch.Tensor) or x.dim() != rank:
+            raise ValueError(f"{name} must be a tensor of rank {rank}")
     Nkz, NE, NA, Norb, _ = G_less.shape
     NB = dH.shape[1]
     Nqz, Nw = D_less.shape[0], D_less.shape[1]
     c128 = torch.complex128
-    _check_tensor("G_less", G_less, c128, (Nkz, NE, NA, Norb, Norb))
-    _check_tensor("G_greater", G_greater, c128, (Nkz, NE, NA, Norb, Norb))
-    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb))
-    _check_tensor("D_less", D_less, c128, (Nqz, Nw, NA, NB, 3, 3))
-    _check_tensor("D_greater", D_greater, c128, (Nqz, Nw, NA, NB, 3, 3))
-    _check_tensor("nbr", nbr, torch.int32, (NA, NB))
+    dev = G_less.device if cuda else None
+    _check_tensor("G_less", G_less, c128, (Nkz, NE, NA, Norb, Norb), cuda)
+    _check_tensor("G_greater", G_greater, c128, (Nkz, NE, NA, Norb, Norb), cuda, device=dev)
+    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb), cuda, device=dev)
+    _check_tensor("D_less", D_less, c128, (Nqz, Nw, NA, NB, 3, 3), cuda, device=dev)
+    _check_tensor("D_greater", D_greater, c128, (Nqz, Nw, NA, NB, 3, 3), cuda, device=dev)
+    _check_tensor("nbr", nbr, torch.int32, (NA, NB), cuda, device=dev)
+
+
+def _check_grads(gS_less, gS_greater, G_shape, device):
+    """Upstream gradients shaped like G (any strides: autograd may hand over expanded views); returns contiguous
+    copies where needed."""
+    out = []
+    for name, g in (("gS_less", gS_less), ("gS_greater", gS_greater)):
+        _check_tensor(name, g, torch.complex128, G_shape, contiguous=False, device=device)
+        out.append(g.contiguous())
+    return out
+
+
+def _check_outputs(out, shape, device=None, cuda: bool = True):
+    if not isinstance(out, (tuple, list)) or len(out) != 2:
+        raise TypeError("out must be a pair of tensors")
+    for name, x in zip(("out[0]", "out[1]"), out):
+        _check_tensor(name, x, torch.complex128, shape, cuda, device=device)
+
+
+def _buffer_bytes(name, buf, device) -> int:
+    """Size in bytes of a caller-provided workspace: a contiguous CUDA tensor on the inputs' device."""
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or buf.device != device:
+        raise TypeError(f"{name} must be a CUDA tensor on {device}")
+    if not buf.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return buf.numel() * buf.element_size()
 
 
 def workspace(d: sse_dims, mode: int, flags: int, device) -> torch.Tensor:
@@ -250,14 +284,17 @@ def sigma(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0 / (2
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
     flags |= (SSE_FLAG_PROFILE if profile else 0) | (SSE_FLAG_ANTIHERMITIAN if antihermitian else 0)
+    dev = G_less.device
     if out is None:
         alloc = torch.empty if atoms is None else torch.zeros
-        out = (alloc(G_less.shape, dtype=torch.complex128, device=G_less.device),
-               alloc(G_less.shape, dtype=torch.complex128, device=G_less.device))
+        out = (alloc(G_less.shape, dtype=torch.complex128, device=dev),
+               alloc(G_less.shape, dtype=torch.complex128, device=dev))
+    _check_outputs(out, G_less.shape, dev)
     if ws is None:
-        ws = workspace(d, m, flags, G_less.device)
-    rc = sse_sigma_fwd(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, out[0], out[1], ws,
-                       ws.numel(), stream)
+        ws = workspace(d, m, flags, dev)
+    with torch.cuda.device(dev):  # the library works on the current device
+        rc = sse_sigma_fwd(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, out[0], out[1], ws,
+                           _buffer_bytes("ws", ws, dev), stream)
     if rc != 0:
         raise SseError(rc, "sse_sigma_fwd")
     return out
@@ -271,15 +308,17 @@ def sigma_grad(G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greate
     d = dims_of(G_less, D_less, dH, atoms)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
-    gSl, gSg = gS_less.contiguous(), gS_greater.contiguous()
+    dev = G_less.device
+    gSl, gSg = _check_grads(gS_less, gS_greater, G_less.shape, dev)
     alloc = torch.empty if atoms is None else torch.zeros
-    g_dH = alloc(dH.shape, dtype=torch.complex128, device=dH.device)
-    g_Dl = alloc(D_less.shape, dtype=torch.complex128, device=dH.device)
-    g_Dg = alloc(D_greater.shape, dtype=torch.complex128, device=dH.device)
+    g_dH = alloc(dH.shape, dtype=torch.complex128, device=dev)
+    g_Dl = alloc(D_less.shape, dtype=torch.complex128, device=dev)
+    g_Dg = alloc(D_greater.shape, dtype=torch.complex128, device=dev)
     if ws is None:
-        ws = workspace(d, m, flags, dH.device)
-    rc = sse_sigma_bwd(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, gSl, gSg, g_dH, g_Dl,
-                       g_Dg, ws, ws.numel(), stream)
+        ws = workspace(d, m, flags, dev)
+    with torch.cuda.device(dev):
+        rc = sse_sigma_bwd(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, gSl, gSg, g_dH, g_Dl,
+                           g_Dg, ws, _buffer_bytes("ws", ws, dev), stream)
     if rc != 0:
         raise SseError(rc, "sse_sigma_bwd")
     return g_dH, g_Dl, g_Dg
@@ -292,11 +331,9 @@ def sigma_host(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0
     """Sigma^<, Sigma^> from HOST (CPU, ideally pinned) tensors via sse_sigma_fwd_host: uploads, compute and
     downloads overlap on two streams. Returns host tensors (S_less, S_greater); synchronises the stream."""
     c128 = torch.complex128
-    Nkz, NE, NA, Norb, _ = G_less.shape
-    for name, x in (("G_less", G_less), ("G_greater", G_greater), ("dH", dH), ("D_less", D_less),
-                    ("D_greater", D_greater), ("nbr", nbr)):
-        if x.is_cuda or not x.is_contiguous():
-            raise TypeError(f"{name} must be a contiguous host tensor")
+    check_inputs(G_less, G_greater, dH, D_less, D_greater, nbr, cuda=False)
+    if out is not None:
+        _check_outputs(out, G_less.shape, cuda=False)
     d = dims_of(G_less, D_less, dH, atoms)
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
@@ -309,10 +346,12 @@ def sigma_host(G_less, G_greater, dH, D_less, D_greater, nbr, scale: float = 1.0
         if n == 0:
             raise ValueError("invalid or unsupported problem sizes for libsse")
         device_buf = torch.empty(n, dtype=torch.uint8, device=dev)
+    nbuf = _buffer_bytes("device_buf", device_buf, dev)
     st = torch.cuda.current_stream(dev) if stream is None else stream
     cp = torch.cuda.Stream(device=dev) if copy_stream is None else copy_stream
-    rc = sse_sigma_fwd_host(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, out[0], out[1],
-                            device_buf, device_buf.numel(), st, cp)
+    with torch.cuda.device(dev):
+        rc = sse_sigma_fwd_host(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, m, flags, out[0], out[1],
+                                device_buf, nbuf, st, cp)
     if rc != 0:
         raise SseError(rc, "sse_sigma_fwd_host")
     st.synchronize()
@@ -330,12 +369,16 @@ def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 
     """
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     c128 = torch.complex128
+    for name, x, rank in (("G_less", G_less, 5), ("dH", dH, 5)):
+        if not isinstance(x, torch.Tensor) or x.dim() != rank:
+            raise ValueError(f"{name} must be a tensor of rank {rank}")
     Nkz, NE, NA, Norb, _ = G_less.shape
     NB = dH.shape[1]
     _check_tensor("G_less", G_less, c128, (Nkz, NE, NA, Norb, Norb))
-    _check_tensor("G_greater", G_greater, c128, (Nkz, NE, NA, Norb, Norb))
-    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb))
-    _check_tensor("nbr", nbr, torch.int32, (NA, NB))
+    dev = G_less.device
+    _check_tensor("G_greater", G_greater, c128, (Nkz, NE, NA, Norb, Norb), device=dev)
+    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb), device=dev)
+    _check_tensor("nbr", nbr, torch.int32, (NA, NB), device=dev)
     a0, a1 = (0, NA) if atoms is None else atoms
     d = sse_dims(NA, NB, Norb, NE, Nkz, int(Nqz), int(Nw), a0, a1)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
@@ -343,13 +386,16 @@ def pi(G_less, G_greater, dH, nbr, Nqz: int, Nw: int, scale: float = 1.0 / (2.0 
     shape = (int(Nqz), int(Nw), NA, NB + 1, 3, 3)
     if out is None:
         alloc = torch.empty if atoms is None else torch.zeros
-        out = (alloc(shape, dtype=c128, device=G_less.device), alloc(shape, dtype=c128, device=G_less.device))
+        out = (alloc(shape, dtype=c128, device=dev), alloc(shape, dtype=c128, device=dev))
+    _check_outputs(out, shape, dev)
     if ws is None:
         n = sse_pi_workspace_bytes(d, m, flags)
         if n == 0:
             raise ValueError("invalid or unsupported problem sizes for libsse")
-        ws = torch.empty(n, dtype=torch.uint8, device=G_less.device)
-    rc = sse_pi_fwd(d, nbr, dH, G_less, G_greater, scale, m, flags, out[0], out[1], ws, ws.numel(), stream)
+        ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        rc = sse_pi_fwd(d, nbr, dH, G_less, G_greater, scale, m, flags, out[0], out[1], ws,
+                        _buffer_bytes("ws", ws, dev), stream)
     if rc != 0:
         raise SseError(rc, "sse_pi_fwd")
     return out
@@ -361,18 +407,31 @@ def sigma_grad_G(dH, D_less, D_greater, nbr, gS_less, gS_greater, scale: float =
     """Gradients (g_G_less, g_G_greater) of sum_t Re tr(gS^t^H Sigma^t) with respect to G via sse_sigma_bwd_g
     (mode fp64_fft: FP64 transforms; fp32_fft: FP32 transforms and products)."""
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    d = dims_of(gS_less, D_less, dH, atoms)
+    c128 = torch.complex128
+    for name, x, rank in (("gS_less", gS_less, 5), ("dH", dH, 5), ("D_less", D_less, 6)):
+        if not isinstance(x, torch.Tensor) or x.dim() != rank:
+            raise ValueError(f"{name} must be a tensor of rank {rank}")
+    NA, NB, _, Norb, _ = dH.shape
+    Nqz, Nw = D_less.shape[0], D_less.shape[1]
+    _check_tensor("dH", dH, c128, (NA, NB, 3, Norb, Norb))
+    dev = dH.device
+    _check_tensor("D_less", D_less, c128, (Nqz, Nw, NA, NB, 3, 3), device=dev)
+    _check_tensor("D_greater", D_greater, c128, (Nqz, Nw, NA, NB, 3, 3), device=dev)
+    _check_tensor("nbr", nbr, torch.int32, (NA, NB), device=dev)
+    G_shape = (gS_less.shape[0], gS_less.shape[1], NA, Norb, Norb)
+    gSl, gSg = _check_grads(gS_less, gS_greater, G_shape, dev)
+    d = dims_of(gSl, D_less, dH, atoms)
     flags = (SSE_FLAG_SYMMETRIZE if symmetrize else 0) | (SSE_FLAG_CHECK if check else 0)
     flags |= SSE_FLAG_PROFILE if profile else 0
-    gSl, gSg = gS_less.contiguous(), gS_greater.contiguous()
     g_Gl, g_Gg = torch.empty_like(gSl), torch.empty_like(gSg)
     if ws is None:
         n = sse_sigma_bwd_g_workspace_bytes(d, m, flags)
         if n == 0:
             raise ValueError("invalid or unsupported problem sizes for libsse")
-        ws = torch.empty(n, dtype=torch.uint8, device=dH.device)
-    rc = sse_sigma_bwd_g(d, nbr, dH, D_less, D_greater, scale, m, flags, gSl, gSg, g_Gl, g_Gg, ws, ws.numel(),
-                         stream)
+        ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        rc = sse_sigma_bwd_g(d, nbr, dH, D_less, D_greater, scale, m, flags, gSl, gSg, g_Gl, g_Gg, ws,
+                             _buffer_bytes("ws", ws, dev), stream)
     if rc != 0:
         raise SseError(rc, "sse_sigma_bwd_g")
     return g_Gl, g_Gg
