@@ -491,18 +491,22 @@ def _dcomb_dims(raw_or_bond: torch.Tensor, nbr: torch.Tensor, atoms=None) -> sse
 
 def dcomb(Draw_less, Draw_greater, nbr, check: bool = False, atoms=None, stream=None):
     """D^t(a,s) = D_ba - D_bb - D_aa + D_ab of Eq. (3) from raw [Nqz,Nw,NA,NB+1,3,3] tensors."""
+    if not isinstance(nbr, torch.Tensor) or nbr.dim() != 2 or not isinstance(Draw_less, torch.Tensor) or \
+            Draw_less.dim() != 6:
+        raise ValueError("nbr must be a tensor of rank 2 and Draw_less of rank 6")
     NB = nbr.shape[1]
-    _check_tensor("Draw_less", Draw_less, torch.complex128, Draw_less.shape[:3] + (NB + 1, 3, 3))
-    _check_tensor("Draw_greater", Draw_greater, torch.complex128, Draw_less.shape[:3] + (NB + 1, 3, 3))
     _check_tensor("nbr", nbr, torch.int32, (Draw_less.shape[2], NB))
+    dev = nbr.device
+    _check_tensor("Draw_less", Draw_less, torch.complex128, Draw_less.shape[:3] + (NB + 1, 3, 3), device=dev)
+    _check_tensor("Draw_greater", Draw_greater, torch.complex128, Draw_less.shape[:3] + (NB + 1, 3, 3), device=dev)
     d = _dcomb_dims(Draw_less, nbr, atoms)
     shape = tuple(Draw_less.shape[:3]) + (NB, 3, 3)
     alloc = torch.empty if atoms is None else torch.zeros
-    out = (alloc(shape, dtype=torch.complex128, device=nbr.device),
-           alloc(shape, dtype=torch.complex128, device=nbr.device))
-    ws = torch.empty(256, dtype=torch.uint8, device=nbr.device)
-    rc = sse_dcomb_fwd(d, nbr, Draw_less, Draw_greater, out[0], out[1], SSE_FLAG_CHECK if check else 0, ws, 256,
-                       stream)
+    out = (alloc(shape, dtype=torch.complex128, device=dev), alloc(shape, dtype=torch.complex128, device=dev))
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        rc = sse_dcomb_fwd(d, nbr, Draw_less, Draw_greater, out[0], out[1], SSE_FLAG_CHECK if check else 0, ws, 256,
+                           stream)
     if rc != 0:
         raise SseError(rc, "sse_dcomb_fwd")
     return out
@@ -510,16 +514,23 @@ def dcomb(Draw_less, Draw_greater, nbr, check: bool = False, atoms=None, stream=
 
 def dcomb_grad(gD_less, gD_greater, nbr, check: bool = False, stream=None):
     """Gradients w.r.t. the raw tensors from the gradients w.r.t. the bond weights."""
+    if not isinstance(nbr, torch.Tensor) or nbr.dim() != 2 or not isinstance(gD_less, torch.Tensor) or \
+            gD_less.dim() != 6:
+        raise ValueError("nbr must be a tensor of rank 2 and gD_less of rank 6")
     NB = nbr.shape[1]
-    _check_tensor("gD_less", gD_less, torch.complex128, gD_less.shape[:3] + (NB, 3, 3))
-    _check_tensor("gD_greater", gD_greater, torch.complex128, gD_less.shape[:3] + (NB, 3, 3))
+    _check_tensor("nbr", nbr, torch.int32, (gD_less.shape[2], NB))
+    dev = nbr.device
+    # autograd may hand over expanded gradients: any strides, copied contiguous below
+    _check_tensor("gD_less", gD_less, torch.complex128, gD_less.shape[:3] + (NB, 3, 3), contiguous=False, device=dev)
+    _check_tensor("gD_greater", gD_greater, torch.complex128, gD_less.shape[:3] + (NB, 3, 3), contiguous=False,
+                  device=dev)
     d = _dcomb_dims(gD_less, nbr)
     shape = tuple(gD_less.shape[:3]) + (NB + 1, 3, 3)
-    out = (torch.empty(shape, dtype=torch.complex128, device=nbr.device),
-           torch.empty(shape, dtype=torch.complex128, device=nbr.device))
-    ws = torch.empty(256, dtype=torch.uint8, device=nbr.device)
-    rc = sse_dcomb_bwd(d, nbr, gD_less.contiguous(), gD_greater.contiguous(), out[0], out[1],
-                       SSE_FLAG_CHECK if check else 0, ws, 256, stream)
+    out = (torch.empty(shape, dtype=torch.complex128, device=dev), torch.empty(shape, dtype=torch.complex128, device=dev))
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    with torch.cuda.device(dev):
+        rc = sse_dcomb_bwd(d, nbr, gD_less.contiguous(), gD_greater.contiguous(), out[0], out[1],
+                           SSE_FLAG_CHECK if check else 0, ws, 256, stream)
     if rc != 0:
         raise SseError(rc, "sse_dcomb_bwd")
     return out

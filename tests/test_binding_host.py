@@ -67,3 +67,16 @@ def test_host_entry_checks_the_outputs(inp):
                                                                                 dtype=torch.complex128)), ValueError)):
         with pytest.raises(err):
             B.sigma_host(*args, out=out)
+
+
+def test_dcomb_refuses_host_tensors_and_wrong_ranks():
+    nbr = torch.tensor([[1], [0]], dtype=torch.int32)
+    raw = torch.zeros((1, 2, 2, 2, 3, 3), dtype=torch.complex128)
+    with pytest.raises(TypeError, match="CUDA"):
+        B.dcomb(raw, raw, nbr)
+    with pytest.raises(TypeError, match="CUDA"):
+        B.dcomb_grad(raw[:, :, :, :1], raw[:, :, :, :1], nbr)
+    with pytest.raises(ValueError, match="rank"):
+        B.dcomb(raw[0], raw[0], nbr)
+    with pytest.raises(ValueError, match="rank"):
+        B.dcomb_grad(raw, raw, nbr[0])
