@@ -2,7 +2,9 @@
 
 Each .cu translation unit is compiled in parallel, then linked into
 paper_1912_10024_gb300/_build/libsse.so. The result is cached by a hash of the
-sources and flags, so repeated calls are free.
+sources and flags, so repeated calls are free. Objects go to a directory of
+their own per build and the library and its stamp are renamed into place, so
+processes that build at the same time do not mix their files.
 """
 from __future__ import annotations
 
@@ -12,6 +14,7 @@ import hashlib
 import os
 import shutil
 import subprocess
+import tempfile
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -55,10 +58,10 @@ def build(verbose: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    objs = []
+    work = tempfile.mkdtemp(prefix="objs.", dir=BUILD)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(work, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -69,15 +72,20 @@ def build(verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(stamp, "w") as f:
-        f.write(fp)
+    try:
+        with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+            objs = list(ex.map(compile_one, _sources()))
+        tmp = os.path.join(work, "libsse.so")
+        r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"], capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
+        with open(os.path.join(work, "stamp"), "w") as f:
+            f.write(fp)
+        os.replace(os.path.join(work, "stamp"), stamp)
+    finally:
+        shutil.rmtree(work, ignore_errors=True)
     return LIB
 
 
