@@ -1,4 +1,4 @@
-"""Atom-sharded evaluation with a halo exchange, world_size 2 over gloo on the CPU.
+"""Atom-sharded evaluation with a halo exchange, world sizes 2 and 3 over gloo on the CPU.
 
 Each rank owns a contiguous atom range and only its own G blocks, fetches
 the halo blocks with paper_1912_10024_gb300.parallel.exchange_halo, and
@@ -92,6 +92,16 @@ def test_two_ranks_diamond_slab():
     """Symmetric diamond-lattice neighbour list: halo atoms come from both sides."""
     d = Dims(NA=128, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2)  # 2x2x4 cells
     assert _run(d, 2, seed=5, nbr=diamond_neighbours(2, 2, 4))
+
+
+def test_three_ranks_uneven_tiles():
+    """World size 3 on 16 atoms (tiles of 6, 5, 5): with the diamond list each rank's halo has several owners, and
+    the G-gradient's halo blocks go back to more than one rank."""
+    d = Dims(NA=16, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2)
+    nbr = diamond_neighbours(1, 1, 2)  # 1x1x2 cells: 16 atoms
+    assert nbr.shape == (16, 4)
+    assert _run(d, 3, seed=11, nbr=nbr)
+    assert _run_grad_g(d, 3, seed=12, nbr=nbr)
 
 
 def test_atom_ranges_partition():
