@@ -39,8 +39,10 @@
 //   warps 6-9  epilogue: drain each slice with tcgen05.ld into FP64, then the
 //              FP64 final multiply and store, overlapping the next slice's MMAs.
 // The rings are mbarrier pipelines. Every wait is bounded: a wait that gives
-// up sets SSE_ERR_TIMEOUT's status bit and all later waits return at once, so
-// the kernel always terminates.
+// up sets SSE_ERR_TIMEOUT's status bit and all later waits of the pipelines
+// return at once, so the kernel always terminates; before TMEM and shared
+// memory are released, the CTA still waits (bounded) for the TMA loads and
+// MMAs it has issued.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -214,6 +216,14 @@ __device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, vol
     for (uint32_t it = 0; it < kWaitIters; ++it)
         if (mbar_try_wait(bar, parity)) return;
     *abort_flag = 1;
+    atomicOr(status, DEV_TIMEOUT);
+}
+
+// Bounded wait that ignores the abort flag: at the end of the kernel, for the CTA's own TMA loads and MMAs still in
+// flight, so that none of them writes shared memory or TMEM after the CTA has released it.
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, unsigned* status) {
+    for (uint32_t it = 0; it < kWaitIters; ++it)
+        if (mbar_try_wait(bar, parity)) return;
     atomicOr(status, DEV_TIMEOUT);
 }
 
@@ -413,6 +423,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
         if (lane == 0) {
             const uint32_t win_bytes = (uint32_t)(c.nch * c.wr * 16);
             uint32_t wcnt = 0;
+            uint32_t issued = 0, last_parity = 0;  // per window stage: loads issued, parity of the last phase
             for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
                 const Item it = decode(item, d, c, win);
                 if (it.wend_p + it.wend_m == 0) continue;
@@ -437,6 +448,8 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                                         for (int bk = 0; bk < c.nblk; ++bk)
                                             tma_load_3d(dst + (uint32_t)(ch * c.wr + bk * c.rb) * 16, &tmap, 0,
                                                         start + bk * c.rb, slice * c.nch + ch, B_(WF + st));
+                                    issued |= 1u << st;
+                                    last_parity = (last_parity & ~(1u << st)) | (((wcnt >> 1) & 1u) << st);
                                 }
                                 ++wcnt;
                             }
@@ -444,6 +457,9 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                     }
                 }
             }
+            // the last loads of each stage have landed (at once when the MMA warp has consumed them)
+            for (int st = 0; st < 2; ++st)
+                if ((issued >> st) & 1u) drain_wait(B_(WF + st), (last_parity >> st) & 1u, status);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
@@ -507,7 +523,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                 }
             }
             umma_commit(B_(MD));
-            wait_or_abort(B_(MD), 0, abort_flag, status);  // nothing in flight when TMEM is released
+            drain_wait(B_(MD), 0, status);  // nothing in flight when TMEM is released, also after an abort
         }
     } else if (warp < 6) {
         // ------------------------------------------------------------- W-tile producers
