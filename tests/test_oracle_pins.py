@@ -249,8 +249,15 @@ def test_term_count_matches_paper_flop_model():
 # literal 9-term einsum (cross-check, not a pin on its own)
 # --------------------------------------------------------------------------
 
-def test_literal_einsum_tiny():
-    d = TINY
+@pytest.mark.parametrize("d", [
+    TINY,
+    Dims(NA=5, NB=1, Norb=1, NE=7, Nkz=1, Nqz=1, Nw=6),   # scalar blocks, one kz, Nw = NE - 1 (every lag)
+    Dims(NA=7, NB=3, Norb=5, NE=11, Nkz=4, Nqz=2, Nw=3),  # Nqz < Nkz, odd orbitals, ragged everything
+    Dims(NA=4, NB=2, Norb=2, NE=2, Nkz=5, Nqz=5, Nw=1),   # the shortest energy grid
+], ids=["tiny", "scalar_all_lags", "ragged_nqz_lt_nkz", "two_energies"])
+def test_literal_einsum(d):
+    """Eq. (3) written out as one einsum per (E, w, sigma) term over the whole (kz, qz, a, s, i, j) index space, on
+    shapes that reach its edge cases."""
     inp = make_inputs(d, seed=0)
     Sl, Sg = run(inp)
     nbr = inp.nbr.numpy()
