@@ -164,3 +164,29 @@ def test_equals_sigma_adjoint_weight_gradient(nbr_kind):
     # Pi^>: t = >, u = <
     _, gDl, _ = oracle.sigma_grad(nbr, dH, D0, D0, herm(Gl), Gg, SCALE, Gg, zero)
     assert normwise(Pg[:, :, :, :NB], gDl) < 1e-13
+
+
+@pytest.mark.parametrize("d", [
+    Dims(NA=6, NB=2, Norb=3, NE=10, Nkz=3, Nqz=3, Nw=3),
+    Dims(NA=5, NB=3, Norb=2, NE=7, Nkz=4, Nqz=2, Nw=6),   # Nqz < Nkz, Nw = NE - 1 (the last lag pairs one energy)
+    Dims(NA=3, NB=1, Norb=1, NE=4, Nkz=1, Nqz=1, Nw=2),   # scalar blocks, one kz
+], ids=["square", "ragged_all_lags", "scalar"])
+def test_literal_einsum(d):
+    """Brute force: Eq. (4) in the layout above, one einsum per (t, q, w) over (kz, E, a, s, i, j) and the orbital
+    indices of the trace; the diagonal slot sums the bond slots."""
+    x = make_inputs(d, seed=21)
+    Pl, Pg = run(x.nbr, x.dH, x.G_less, x.G_greater, d.Nqz, d.Nw)
+    A, nbr = x.dH.numpy(), x.nbr.numpy()
+    Gs = (x.G_less.numpy(), x.G_greater.numpy())
+    k = np.arange(d.Nkz)
+    for t, P in enumerate((Pl, Pg)):
+        ref = np.zeros_like(P)
+        for q in range(d.Nqz):
+            for w in range(d.Nw):
+                nE = d.NE - (w + 1)  # energies E with E + (w + 1) inside the grid
+                X = Gs[t][(k + q) % d.Nkz][:, w + 1:w + 1 + nE]     # G^t_aa(E + w + 1, k + q)  [k, E, a, n, p]
+                Y = Gs[1 - t][:, :nE][:, :, nbr]                      # G^t'_bb(E, k)             [k, E, a, s, r, m]
+                bond = -1j * SCALE * np.einsum("asinm,kEanp,asjpr,kEasrm->asij", A.conj(), X, A, Y, optimize=True)
+                ref[q, w, :, :d.NB] = bond
+                ref[q, w, :, d.NB] = bond.sum(axis=1)
+        assert normwise(P, ref) < 1e-13
