@@ -146,7 +146,8 @@ SSE_API size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
  * for atoms in range (all E, kz) and untouched elsewhere.
  * Host checks: non-null, 16-byte aligned complex arrays (4-byte nbr),
  * NA,NB,NE,Nkz,Nqz,Nw >= 1, 1 <= Norb <= 16, Nqz <= Nkz, Nw < NE,
- * 0 <= a_begin <= a_end <= NA, NA <= 32767, finite scale, known mode and flags. */
+ * 0 <= a_begin <= a_end <= NA, NA <= 32767, finite scale, known mode and flags;
+ * in modes FP64_FFT and FP32_FFT also the size limits stated with the modes. */
 SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
                   const double* D_greater, const double* G_less, const double* G_greater, double scale, int mode,
                   uint32_t flags, double* S_less, double* S_greater, void* workspace, size_t ws_bytes,
