@@ -399,3 +399,27 @@ def test_pi_half_spectrum_mirror_relation():
             Ch[..., i, j] = np.trace(A[i].conj().T @ X[:, :, a] @ A[j] @ Yneg, axis1=-2, axis2=-1)
     mirrored = np.conj(np.swapaxes(Ch, -1, -2))[np.ix_(neg_k, neg_e)]
     assert np.abs(Ch - mirrored).max() <= 1e-13 * np.abs(Ch).max()
+
+
+def test_stage_index_split_by_multiply_high_is_exact():
+    """The E-transform's Stockham stages split the butterfly index j = q * Ns + k with q = umulhi(j, floor(2^32/Ns)+1)
+    when Ns is not a power of two. For j, Ns < 2^16 the error of the multiplier, below j / 2^32 < 2^-16, never crosses
+    an integer (the fractional part of j / Ns is at most 1 - 1/Ns). Enumerated here for every stage of every 2^a 3^b
+    length below 2^16, stages in the plan's order (radix 4, then 2, then 3), j over the stage's L / R butterflies."""
+    lengths = sorted(2 ** a * 3 ** b for a in range(17) for b in range(11) if 2 <= 2 ** a * 3 ** b < 1 << 16)
+    checked = 0
+    for L in lengths:
+        radices, m = [], L
+        for r in (4, 2, 3):
+            while m % r == 0:
+                radices.append(r)
+                m //= r
+        ns = 1
+        for R in radices:
+            if ns & (ns - 1):  # not a power of two: the multiply-high path
+                mul = (1 << 32) // ns + 1
+                j = np.arange(L // R, dtype=np.uint64)
+                assert np.array_equal((j * np.uint64(mul)) >> np.uint64(32), j // np.uint64(ns)), (L, ns)
+                checked += 1
+            ns *= R
+    assert checked > 100
