@@ -5,11 +5,14 @@ One step = one sse_sigma_fwd call: Sigma^< and Sigma^> for every atom,
 energy and kz of the workload (default: the Si-FinFET-shaped problem,
 NA=1024, NB=4, Norb=10, NE=512, Nkz=Nqz=7, Nw=32), inputs resident in HBM.
 Default mode: FP64 through the convolution theorem (fp64_fft); the other
-modes (direct FP64, BF16X3, TF32) are timed on the same inputs in the
-"compare" object, with their error against this run's result. Prints one
-JSON line (rank 0).
+modes (direct FP64, BF16X3, TF32, FP32 transforms, and the transform modes
+with anti-Hermitian inputs) are timed on the same inputs in the "compare"
+object, with their error against this run's result; Pi (Eq. 4), the adjoint
+and the gradient in G follow in "pi" and "adjoint". Prints one JSON line
+(rank 0).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--mode fp64_fft|fp64|tf32|bf16x3]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload finfet|large|...]
+                  [--mode fp64_fft|fp32_fft|fp64|tf32|bf16x3] [--antihermitian]
 
 Metric: useful TFLOP/s of the paper-equivalent (regrouped, Sec. 5.1) flop
 count, plus (E,kz) points/s. Multi-GPU (torchrun): every rank solves its own
