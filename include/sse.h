@@ -70,6 +70,10 @@ typedef struct sse_dims {
  *            multiply by dH (Sec. 4.4 adapted to TF32).
  *   BF16X3 : like TF32 but each operand split into bf16 hi + lo parts and the
  *            three products hi*hi + hi*lo + lo*hi accumulated in FP32.
+ *            TF32 and BF16X3 need Norb <= 10 and a weight table of 2 Nw taps
+ *            per qz in shared memory: Nw <= 286 (TF32) or 194 (BF16X3) at
+ *            Norb = 10, more for smaller blocks. sse_sigma_fwd only; beyond
+ *            these limits the host checks return SSE_ERR_UNSUPPORTED.
  *   FP64_FFT : IEEE double throughout, evaluated with the convolution theorem:
  *            Eq. (3) is, per bond, a convolution of G^t_b with the phonon
  *            weights over (E, kz) -- cyclic in kz, linear in E -- so G is
@@ -147,7 +151,7 @@ SSE_API size_t sse_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
  * Host checks: non-null, 16-byte aligned complex arrays (4-byte nbr),
  * NA,NB,NE,Nkz,Nqz,Nw >= 1, 1 <= Norb <= 16, Nqz <= Nkz, Nw < NE,
  * 0 <= a_begin <= a_end <= NA, NA <= 32767, finite scale, known mode and flags;
- * in modes FP64_FFT and FP32_FFT also the size limits stated with the modes. */
+ * in modes TF32, BF16X3, FP64_FFT and FP32_FFT also the size limits stated with the modes. */
 SSE_API int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double* dH, const double* D_less,
                   const double* D_greater, const double* G_less, const double* G_greater, double scale, int mode,
                   uint32_t flags, double* S_less, double* S_greater, void* workspace, size_t ws_bytes,

@@ -38,13 +38,15 @@ bool valid_mode(int mode) {
 bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
 
 // The kernels' own limits for these sizes in this mode (transform length, kz DFT size, shared memory of the
-// configurations): host-only functions of the sizes, tested before any device work. The direct FP64 and
-// tensor-core kernels choose configurations that fit; their drivers keep their own checks.
+// configurations, Norb of the tensor-core epilogue): host-only functions of the sizes, tested before any device
+// work. The direct FP64 kernels choose configurations that fit; their drivers keep their own checks.
 enum class Op { Fwd, Bwd, BwdG, Pi };
 bool op_supported(const sse_dims& d, int mode, Op op) {
     const bool fp32 = mode == SSE_MODE_FP32_FFT;
     switch (op) {
-        case Op::Fwd: return (mode != SSE_MODE_FP64_FFT && !fp32) || sse::spectral_fwd_supported(d, fp32);
+        case Op::Fwd:
+            if (mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3) return sse::mixed_supported(d, mode);
+            return mode == SSE_MODE_FP64 || sse::spectral_fwd_supported(d, fp32);
         case Op::Bwd: return mode == SSE_MODE_FP64 || sse::spectral_bwd_supported(d);
         case Op::BwdG: return sse::spectral_bwd_g_supported(d, fp32);  // transforms in every mode it takes
         case Op::Pi: return sse::spectral_pi_supported(d);              // limits of the FP64 and FP32 kernels

@@ -61,6 +61,7 @@ cudaError_t fp64_bwd(const Problem& p, const double2* gS_less, const double2* gS
 
 // Mixed-precision forward (sse_mixed.cu).
 size_t mixed_fwd_workspace(const sse_dims& d, int mode);
+bool mixed_supported(const sse_dims& d, int mode);  // host-only limits: Norb, shared memory, grid
 cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status,
                       void* ws, size_t ws_bytes, cudaStream_t st);
 

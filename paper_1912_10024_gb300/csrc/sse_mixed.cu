@@ -921,13 +921,18 @@ size_t mixed_fwd_workspace(const sse_dims& d, int mode) {
     return ws_layout(d, make_cfg(d, mode)).total;
 }
 
+bool mixed_supported(const sse_dims& d, int mode) {
+    if (d.Norb > kMaxNorb) return false;  // the epilogue keeps 6 Norb accumulator columns in registers
+    const MixCfg c = make_cfg(d, mode);
+    if (c.tg < 1 || c.smem > 227 * 1024) return false;  // the weight rows of 2 Nw taps per qz buffer grow with Nw
+    return (long long)((c.wE + c.TE - 1) / c.TE) * d.Nkz * 2 * (d.a_end - d.a_begin) <= 0x7fffffffLL;
+}
+
 cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                       size_t ws_bytes, cudaStream_t st) {
-    if (p.d.Norb > kMaxNorb) return cudaErrorNotSupported;
+    if (!mixed_supported(p.d, mode)) return cudaErrorNotSupported;
     const MixCfg c = make_cfg(p.d, mode);
-    if (c.smem > 227 * 1024 || ws_bytes < ws_layout(p.d, c).total) return cudaErrorNotSupported;
-    if ((long long)((c.wE + c.TE - 1) / c.TE) * p.d.Nkz * 2 * (p.d.a_end - p.d.a_begin) > 0x7fffffffLL)
-        return cudaErrorNotSupported;
+    if (ws_bytes < ws_layout(p.d, c).total) return cudaErrorNotSupported;
     if (mode == SSE_MODE_BF16X3) return launch<SSE_MODE_BF16X3>(p, c, S_less, S_greater, status, ws, st);
     return launch<SSE_MODE_TF32>(p, c, S_less, S_greater, status, ws, st);
 }

@@ -222,3 +222,16 @@ def test_direct_fp64_adjoint_has_no_transform_limits():
     for d in (B.sse_dims(16, 17, 16, 64, 4, 1, 4, 0, 16), B.sse_dims(16, 4, 10, 64, 17, 1, 4, 0, 16),
               B.sse_dims(16, 4, 10, 6000, 4, 1, 32, 0, 16)):
         assert bwd(d, B.SSE_MODE_FP64) == 6
+
+
+@pytest.mark.parametrize("mode,nw_max", [(B.SSE_MODE_TF32, 286), (B.SSE_MODE_BF16X3, 194)])
+def test_tensor_core_mode_limits_are_checked_on_host(mode, nw_max):
+    """The tcgen05 forward keeps 6 Norb accumulator columns in epilogue registers (Norb <= 10) and the weight rows of
+    2 Nw taps per qz in shared memory: sizes beyond are SSE_ERR_UNSUPPORTED before any device work (a 16-byte
+    workspace makes every size inside the limits stop at SSE_ERR_WORKSPACE instead)."""
+    def fwd(d):
+        return call_fwd(d, mode=mode, ws_bytes=16)
+    assert fwd(B.sse_dims(16, 4, 10, 512, 4, 1, 4, 0, 16)) == 6
+    assert fwd(B.sse_dims(16, 4, 11, 512, 4, 1, 4, 0, 16)) == 2
+    assert fwd(B.sse_dims(16, 4, 10, 4096, 4, 1, nw_max, 0, 16)) == 6
+    assert fwd(B.sse_dims(16, 4, 10, 4096, 4, 1, nw_max + 1, 0, 16)) == 2
