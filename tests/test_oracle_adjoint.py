@@ -99,3 +99,24 @@ def test_atom_range_gradients(problem):
     np.testing.assert_array_equal(p[0][1:3], g_dH[1:3])
     np.testing.assert_array_equal(p[1][:, :, 1:3], g_Dl[:, :, 1:3])
     assert np.count_nonzero(p[0][3:]) == 0 and np.count_nonzero(p[2][:, :, :1]) == 0
+
+
+@pytest.mark.parametrize("d", [
+    Dims(NA=4, NB=1, Norb=1, NE=6, Nkz=1, Nqz=1, Nw=5),     # scalar blocks, one kz, Nw = NE - 1
+    Dims(NA=7, NB=3, Norb=5, NE=11, Nkz=4, Nqz=2, Nw=3),    # Nqz < Nkz, ragged sizes
+    Dims(NA=3, NB=2, Norb=2, NE=2, Nkz=5, Nqz=5, Nw=1),     # the shortest energy grid
+], ids=["scalar_all_lags", "ragged", "two_energies"])
+def test_euler_identities_on_edge_shapes(d):
+    """L is linear in (D^<, D^>) jointly, linear in (G^<, G^>) jointly and a Hermitian quadratic form in dH, so
+    Euler's theorem for homogeneous functions fixes L = Re<g_D, D> = Re<g_G, G> = Re<g_dH, dH> / 2 exactly: every
+    gradient entry weighted by its own input, on shapes at the edges of the index ranges."""
+    inp = make_inputs(d, seed=77)
+    W, V = (x.numpy() for x in make_upstream(d, seed=78))
+    args = (inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE)
+    g_dH, g_Dl, g_Dg = oracle.sigma_grad(*args, W, V)
+    g_Gl, g_Gg = oracle.sigma_grad_G(inp.nbr, inp.dH, inp.D_less, inp.D_greater, SCALE, W, V)
+    L = loss(inp, W, V)
+    dot = lambda g, x: float(np.real(np.vdot(g, x.numpy())))  # noqa: E731
+    for got in (dot(g_Dl, inp.D_less) + dot(g_Dg, inp.D_greater), dot(g_Gl, inp.G_less) + dot(g_Gg, inp.G_greater),
+                dot(g_dH, inp.dH) / 2):
+        assert abs(got - L) <= 1e-12 * abs(L), (got, L)
