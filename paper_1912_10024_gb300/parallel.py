@@ -105,6 +105,32 @@ def local_problem(nbr: torch.Tensor, a0: int, a1: int, G_owned: Sequence[torch.T
     return nbr_l.to(dH_owned.device), dH_l, Ds[0], Ds[1], Gs[0], Gs[1]
 
 
+def sigma_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, D_owned: Sequence[torch.Tensor],
+                       G_owned: Sequence[torch.Tensor], NA: int, scale: float, compute=None, group=None, **kw):
+    """Sigma^<, Sigma^> of this rank's atoms [a0, a1) with the one exchange step of the atom tiling.
+
+    nbr: the global neighbour list [NA, NB] (every rank holds it); dH_owned [a1-a0, NB, 3, Norb, Norb],
+    D_owned = (D^<, D^>) [Nqz, Nw, a1-a0, NB, 3, 3] and G_owned = (G^<, G^>) [Nkz, NE, a1-a0, Norb, Norb]: the
+    rank's slices. The halo G blocks are fetched (``exchange_halo``), the local problem is built
+    (``local_problem``) and ``compute`` evaluates Sigma of its first a1-a0 atoms; ``compute`` takes
+    (G_less, G_greater, dH, D_less, D_greater, nbr, scale=..., atoms=..., **kw) and returns the pair of full
+    local outputs, by default the library call ``binding.sigma`` (CUDA tensors; ``kw`` passes mode and flags).
+    Returns the owned slices [Nkz, NE, a1-a0, Norb, Norb]; no reduction follows.
+    """
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    a0, a1 = atom_range(NA, world, rank)
+    halo = exchange_halo(G_owned, nbr, NA, group)  # collective: every rank takes part
+    if a1 == a0:  # more ranks than atoms: nothing owned
+        return G_owned[0][:, :, :0].clone(), G_owned[1][:, :, :0].clone()
+    nbr_l, dH_l, Dl, Dg, Gl, Gg = local_problem(nbr, a0, a1, G_owned, halo, dH_owned, D_owned)
+    if compute is None:
+        from . import binding
+        compute = binding.sigma
+    Sl, Sg = compute(Gl, Gg, dH_l, Dl, Dg, nbr_l, scale=scale, atoms=(0, a1 - a0), **kw)
+    return Sl[:, :, :a1 - a0], Sg[:, :, :a1 - a0]
+
+
 def reduce_halo_grad(gG_local: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int,
                      group=None) -> List[torch.Tensor]:
     """The exchange step of the gradient with respect to G: the reverse of ``exchange_halo``.

@@ -104,6 +104,46 @@ def test_three_ranks_uneven_tiles():
     assert _run_grad_g(d, 3, seed=12, nbr=nbr)
 
 
+def _composed_worker(rank, world, port, dims, seed, nbr, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed, nbr=nbr)
+        a0, a1 = P.atom_range(dims.NA, world, rank)
+
+        def on_cpu(Gl, Gg, dH, Dl, Dg, nbr_l, scale, atoms):  # the oracle in place of the library call
+            return tuple(torch.from_numpy(x) for x in oracle.sigma(nbr_l, dH, Dl, Dg, Gl, Gg, scale, a_range=atoms,
+                                                                   nthreads=2))
+
+        Sl, Sg = P.sigma_atom_sharded(inp.nbr, inp.dH[a0:a1], (inp.D_less[:, :, a0:a1], inp.D_greater[:, :, a0:a1]),
+                                      (inp.G_less[:, :, a0:a1].clone(), inp.G_greater[:, :, a0:a1].clone()),
+                                      dims.NA, SCALE, compute=on_cpu)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (a0, a1, Sl.contiguous(), Sg.contiguous()))
+        if rank == 0:
+            full = oracle.sigma(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                                nthreads=2)
+            q.put(all(np.array_equal(sl.numpy(), full[0][:, :, b0:b1]) and
+                      np.array_equal(sg.numpy(), full[1][:, :, b0:b1]) for b0, b1, sl, sg in gathered))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_composed_sharded_sigma():
+    """parallel.sigma_atom_sharded (exchange, local problem, evaluation of the owned atoms) with the oracle as the
+    evaluation: the gathered shards equal the unsharded oracle bit for bit, at world 3 on 16 atoms (uneven tiles,
+    halos with several owners) and on 2 atoms (one rank owns nothing but still takes part in the exchange)."""
+    ctx = mp.get_context("spawn")
+    for dims, world, nbr in ((Dims(NA=16, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2), 3, diamond_neighbours(1, 1, 2)),
+                             (Dims(NA=2, NB=1, Norb=2, NE=6, Nkz=2, Nqz=1, Nw=2), 3, None)):
+        q = ctx.SimpleQueue()
+        mp.start_processes(_composed_worker, args=(world, _free_port(), dims, 13, nbr, q), nprocs=world, join=True,
+                           start_method="spawn")
+        assert q.get()
+
+
 def test_atom_ranges_partition():
     for NA in (1, 7, 16, 1024):
         for world in (1, 2, 3, 8):
