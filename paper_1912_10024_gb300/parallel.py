@@ -77,6 +77,19 @@ def exchange_halo(G_owned: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int,
     return recv
 
 
+def _local_neighbours(nbr: torch.Tensor, a0: int, a1: int, halo: Sequence[int]) -> torch.Tensor:
+    """Neighbour list [a1-a0+len(halo), NB] (CPU, int32) of the local numbering: atoms [a0, a1) first, then the halo
+    atoms in the given order; halo atoms point at themselves (they get zero dH and D)."""
+    order = list(range(a0, a1)) + list(halo)
+    index = {b: i for i, b in enumerate(order)}
+    NB = nbr.shape[1]
+    nbr_l = torch.arange(len(order), dtype=torch.int32).unsqueeze(1).repeat(1, NB)
+    if a1 > a0:
+        nbr_l[:a1 - a0] = torch.tensor([[index[int(b)] for b in row] for row in nbr[a0:a1].tolist()],
+                                       dtype=torch.int32)
+    return nbr_l
+
+
 def local_problem(nbr: torch.Tensor, a0: int, a1: int, G_owned: Sequence[torch.Tensor],
                   halo: Dict[int, List[torch.Tensor]], dH_owned: torch.Tensor, D_owned: Sequence[torch.Tensor]):
     """Rank-local problem: atoms [a0, a1) first, then the halo atoms.
@@ -85,12 +98,8 @@ def local_problem(nbr: torch.Tensor, a0: int, a1: int, G_owned: Sequence[torch.T
     G_greater_local); Sigma of local atoms [0, a1-a0) equals Sigma of global
     atoms [a0, a1). Halo atoms get zero dH/D and point at themselves.
     """
-    order = list(range(a0, a1)) + sorted(halo)
-    index = {b: i for i, b in enumerate(order)}
-    n_own, n_loc = a1 - a0, len(order)
-    NB = nbr.shape[1]
-    nbr_l = torch.arange(n_loc, dtype=torch.int32).unsqueeze(1).repeat(1, NB)
-    nbr_l[:n_own] = torch.tensor([[index[int(b)] for b in row] for row in nbr[a0:a1].tolist()], dtype=torch.int32)
+    n_own, n_loc = a1 - a0, a1 - a0 + len(halo)
+    nbr_l = _local_neighbours(nbr, a0, a1, sorted(halo))
     Gs = []
     for t, G in enumerate(G_owned):
         blocks = [G] + [halo[b][t].unsqueeze(2) for b in sorted(halo)]
@@ -173,6 +182,46 @@ def reduce_halo_grad(gG_local: Sequence[torch.Tensor], nbr: torch.Tensor, NA: in
         for t, buf in enumerate(bufs):
             out[t][:, :, b - a0] += buf
     return out
+
+
+def sigma_grad_G_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, D_owned: Sequence[torch.Tensor],
+                              gS_owned: Sequence[torch.Tensor], NA: int, scale: float, compute=None, group=None,
+                              **kw) -> List[torch.Tensor]:
+    """Gradient with respect to this rank's G^<, G^> blocks of L = sum_t Re tr(gS^t^H Sigma^t) summed over every
+    rank's atoms, with the atom tiling.
+
+    gS_owned = (gS^<, gS^>) [Nkz, NE, a1-a0, Norb, Norb]: the upstream gradient of the owned atoms' Sigma. The rank
+    evaluates the gradient of its own bonds over its local atoms (owned, then halo; Sigma is linear in G, so G itself
+    is not needed) with ``compute`` -- by default the library call ``binding.sigma_grad_G``, which takes
+    (dH, D_less, D_greater, nbr, gS_less, gS_greater, scale=..., **kw) -- and ``reduce_halo_grad`` returns the halo
+    blocks to their owners. Returns the owned slices [Nkz, NE, a1-a0, Norb, Norb].
+    """
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    a0, a1 = atom_range(NA, world, rank)
+    halo = halo_atoms(nbr, a0, a1)
+    n_own, n_loc = a1 - a0, a1 - a0 + len(halo)
+    dev = gS_owned[0].device
+    if n_loc == 0:  # nothing owned: only the collective of the reduction
+        return reduce_halo_grad([g.clone() for g in gS_owned], nbr, NA, group)
+    nbr_l = _local_neighbours(nbr, a0, a1, halo).to(dev)
+    dH_l = torch.zeros((n_loc,) + tuple(dH_owned.shape[1:]), dtype=dH_owned.dtype, device=dev)
+    dH_l[:n_own] = dH_owned
+    Ds = []
+    for D in D_owned:
+        Dl = torch.zeros(D.shape[:2] + (n_loc,) + D.shape[3:], dtype=D.dtype, device=dev)
+        Dl[:, :, :n_own] = D
+        Ds.append(Dl)
+    gS = []
+    for g in gS_owned:
+        x = torch.zeros(g.shape[:2] + (n_loc,) + g.shape[3:], dtype=g.dtype, device=dev)
+        x[:, :, :n_own] = g
+        gS.append(x)
+    if compute is None:
+        from . import binding
+        compute = binding.sigma_grad_G
+    gG = compute(dH_l, Ds[0], Ds[1], nbr_l, gS[0], gS[1], scale=scale, **kw)
+    return reduce_halo_grad(list(gG), nbr, NA, group)
 
 
 # ---------------------------------------------------------------------------

@@ -1,5 +1,6 @@
-"""The composed atom-sharded call on the GPU: parallel.sigma_atom_sharded with its default evaluation (the library
-call) on a one-rank process group equals the direct library call bit for bit (the local problem is the global one)."""
+"""The composed atom-sharded calls on the GPU: parallel.sigma_atom_sharded and parallel.sigma_grad_G_atom_sharded
+with their default evaluation (the library calls) on a one-rank process group equal the direct library calls bit for
+bit (the local problem is the global one)."""
 import math
 import socket
 
@@ -9,7 +10,7 @@ import torch.distributed as dist
 
 from paper_1912_10024_gb300 import binding as B
 from paper_1912_10024_gb300 import parallel as P
-from paper_1912_10024_gb300.inputs import Dims, diamond_neighbours, make_inputs
+from paper_1912_10024_gb300.inputs import Dims, diamond_neighbours, make_inputs, make_upstream
 
 pytestmark = pytest.mark.gpu
 SCALE = 1.0 / (2.0 * math.pi)
@@ -27,5 +28,10 @@ def test_single_rank_equals_the_library_call():
                                       mode="fp64_fft")
         Rl, Rg = B.sigma(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, scale=SCALE, mode="fp64_fft")
         assert torch.equal(Sl, Rl) and torch.equal(Sg, Rg)
+        W, V = make_upstream(d, seed=82, device="cuda")
+        gl, gg = P.sigma_grad_G_atom_sharded(g.nbr, g.dH, (g.D_less, g.D_greater), (W, V), d.NA, SCALE,
+                                             mode="fp64_fft")
+        rl, rg = B.sigma_grad_G(g.dH, g.D_less, g.D_greater, g.nbr, W, V, scale=SCALE, mode="fp64_fft")
+        assert torch.equal(gl, rl) and torch.equal(gg, rg)
     finally:
         dist.destroy_process_group()

@@ -144,6 +144,51 @@ def test_composed_sharded_sigma():
         assert q.get()
 
 
+def _composed_grad_g_worker(rank, world, port, dims, seed, nbr, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed, nbr=nbr)
+        W, V = make_upstream(dims, seed=seed + 1)
+        a0, a1 = P.atom_range(dims.NA, world, rank)
+
+        def on_cpu(dH, Dl, Dg, nbr_l, gl, gg, scale):  # the oracle in place of the library call
+            return tuple(torch.from_numpy(x) for x in oracle.sigma_grad_G(nbr_l, dH, Dl, Dg, scale, gl, gg,
+                                                                          nthreads=2))
+
+        owned = P.sigma_grad_G_atom_sharded(inp.nbr, inp.dH[a0:a1], (inp.D_less[:, :, a0:a1],
+                                                                       inp.D_greater[:, :, a0:a1]),
+                                            (W[:, :, a0:a1], V[:, :, a0:a1]), dims.NA, SCALE, compute=on_cpu)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (a0, a1, [t.contiguous() for t in owned]))
+        if rank == 0:
+            full = oracle.sigma_grad_G(inp.nbr, inp.dH, inp.D_less, inp.D_greater, SCALE, W, V, nthreads=2)
+            ok = True
+            for (b0, b1, sh) in gathered:
+                for t in range(2):
+                    ref = full[t][:, :, b0:b1]
+                    ok &= sh[t].shape == ref.shape
+                    if b1 > b0:
+                        ok &= bool(np.abs(sh[t].numpy() - ref).max() <= 1e-13 * np.abs(full[t]).max())
+            q.put(ok)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_composed_sharded_gradient_in_G():
+    """parallel.sigma_grad_G_atom_sharded with the oracle as the evaluation equals the unsharded oracle gradient up
+    to the order of the additions, at world 3 on 16 atoms and on 2 atoms (one rank owns nothing)."""
+    ctx = mp.get_context("spawn")
+    for dims, world, nbr in ((Dims(NA=16, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2), 3, diamond_neighbours(1, 1, 2)),
+                             (Dims(NA=2, NB=1, Norb=2, NE=6, Nkz=2, Nqz=1, Nw=2), 3, None)):
+        q = ctx.SimpleQueue()
+        mp.start_processes(_composed_grad_g_worker, args=(world, _free_port(), dims, 14, nbr, q), nprocs=world,
+                           join=True, start_method="spawn")
+        assert q.get()
+
+
 def test_atom_ranges_partition():
     for NA in (1, 7, 16, 1024):
         for world in (1, 2, 3, 8):
