@@ -278,6 +278,31 @@ def exchange_energy_halo(G_window: Sequence[torch.Tensor], NE: int, Nw: int, gro
     return e0, out
 
 
+def sigma_energy_sharded(nbr: torch.Tensor, dH: torch.Tensor, D: Sequence[torch.Tensor], G_window: Sequence[torch.Tensor],
+                         NE: int, scale: float, compute=None, group=None, **kw):
+    """Sigma^<, Sigma^> of every atom on this rank's energy window [E0, E1), from its rows of G alone plus the one
+    exchange of the +-Nw energy halo.
+
+    G_window = (G^<, G^>) [Nkz, E1-E0, NA, Norb, Norb]: the rank's rows; nbr, dH and D = (D^<, D^>) whole (they do
+    not depend on E). ``compute`` evaluates Sigma on the extended window as a problem of its own (energies outside
+    it contribute zero, which is exact on [E0, E1)); it takes (G_less, G_greater, dH, D_less, D_greater, nbr,
+    scale=..., **kw) and defaults to the library call ``binding.sigma``. Returns Sigma's rows [Nkz, E1-E0, NA, Norb,
+    Norb]."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    E0, E1 = energy_range(NE, world, rank)
+    Nw = D[0].shape[1]
+    e0, (Gl, Gg) = exchange_energy_halo(G_window, NE, Nw, group)  # collective: every rank takes part
+    if E1 == E0:
+        return G_window[0][:, :0].clone(), G_window[1][:, :0].clone()
+    # the extended window has at least Nw + 1 rows (NE > Nw and E1 > E0), so it is a valid problem of its own
+    if compute is None:
+        from . import binding
+        compute = binding.sigma
+    Sl, Sg = compute(Gl.contiguous(), Gg.contiguous(), dH, D[0], D[1], nbr, scale=scale, **kw)
+    return Sl[:, E0 - e0:E1 - e0], Sg[:, E0 - e0:E1 - e0]
+
+
 def reduce_in_rank_order(x: torch.Tensor, group=None) -> torch.Tensor:
     """Sum of ``x`` over the ranks, added in rank order on every rank (deterministic): the reduction that gradients
     summed over energies (dH, D) need when the energies are split."""

@@ -1,6 +1,6 @@
-"""The composed atom-sharded calls on the GPU: parallel.sigma_atom_sharded and parallel.sigma_grad_G_atom_sharded
-with their default evaluation (the library calls) on a one-rank process group equal the direct library calls bit for
-bit (the local problem is the global one)."""
+"""The composed sharded calls on the GPU: parallel.sigma_atom_sharded, sigma_grad_G_atom_sharded and
+sigma_energy_sharded with their default evaluation (the library calls) on a one-rank process group equal the direct
+library calls bit for bit (the local problem is the global one)."""
 import math
 import socket
 
@@ -33,5 +33,8 @@ def test_single_rank_equals_the_library_call():
                                              mode="fp64_fft")
         rl, rg = B.sigma_grad_G(g.dH, g.D_less, g.D_greater, g.nbr, W, V, scale=SCALE, mode="fp64_fft")
         assert torch.equal(gl, rl) and torch.equal(gg, rg)
+        El, Eg = P.sigma_energy_sharded(g.nbr, g.dH, (g.D_less, g.D_greater), (g.G_less, g.G_greater), d.NE, SCALE,
+                                        mode="fp64_fft")
+        assert torch.equal(El, Rl) and torch.equal(Eg, Rg)
     finally:
         dist.destroy_process_group()

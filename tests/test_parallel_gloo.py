@@ -189,6 +189,43 @@ def test_composed_sharded_gradient_in_G():
         assert q.get()
 
 
+def _composed_energy_worker(rank, world, port, dims, seed, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed)
+        E0, E1 = P.energy_range(dims.NE, world, rank)
+
+        def on_cpu(Gl, Gg, dH, Dl, Dg, nbr, scale):  # the oracle in place of the library call
+            return tuple(torch.from_numpy(x) for x in oracle.sigma(nbr, dH, Dl, Dg, Gl, Gg, scale, nthreads=2))
+
+        Sl, Sg = P.sigma_energy_sharded(inp.nbr, inp.dH, (inp.D_less, inp.D_greater),
+                                        (inp.G_less[:, E0:E1].clone(), inp.G_greater[:, E0:E1].clone()), dims.NE,
+                                        SCALE, compute=on_cpu)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (E0, E1, Sl.contiguous(), Sg.contiguous()))
+        if rank == 0:
+            full = oracle.sigma(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                                nthreads=2)
+            q.put(all(np.array_equal(sl.numpy(), full[0][:, b0:b1]) and np.array_equal(sg.numpy(), full[1][:, b0:b1])
+                      for b0, b1, sl, sg in gathered))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_composed_energy_sharded_sigma():
+    """parallel.sigma_energy_sharded with the oracle as the evaluation: each rank's rows equal the unsharded oracle
+    bit for bit, with windows longer than Nw and shorter than Nw (the halo spans several ranks)."""
+    ctx = mp.get_context("spawn")
+    for dims, world in ((TINY, 3), (Dims(NA=6, NB=2, Norb=2, NE=12, Nkz=2, Nqz=2, Nw=5), 4)):
+        q = ctx.SimpleQueue()
+        mp.start_processes(_composed_energy_worker, args=(world, _free_port(), dims, 15, q), nprocs=world, join=True,
+                           start_method="spawn")
+        assert q.get()
+
+
 def test_atom_ranges_partition():
     for NA in (1, 7, 16, 1024):
         for world in (1, 2, 3, 8):
