@@ -303,6 +303,36 @@ def sigma_energy_sharded(nbr: torch.Tensor, dH: torch.Tensor, D: Sequence[torch.
     return Sl[:, E0 - e0:E1 - e0], Sg[:, E0 - e0:E1 - e0]
 
 
+def sigma_grad_energy_sharded(nbr: torch.Tensor, dH: torch.Tensor, D: Sequence[torch.Tensor],
+                              G_window: Sequence[torch.Tensor], gS_window: Sequence[torch.Tensor], NE: int,
+                              scale: float, compute=None, group=None, **kw) -> List[torch.Tensor]:
+    """Gradients (g_dH, g_D^<, g_D^>) of L = sum_t Re tr(gS^t^H Sigma^t) over all energies, with the energy tiling.
+
+    G_window and gS_window: this rank's rows [Nkz, E1-E0, NA, Norb, Norb] of G and of the upstream gradient. The rank
+    evaluates the gradient of its own rows' loss on its extended window (upstream zero on the halo rows) with
+    ``compute`` -- by default ``binding.sigma_grad``, which takes (G_less, G_greater, dH, D_less, D_greater, nbr,
+    gS_less, gS_greater, scale=..., **kw) -- and the sums over energies are completed across the ranks in rank order.
+    Every rank returns the full gradients."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    E0, E1 = energy_range(NE, world, rank)
+    Nw = D[0].shape[1]
+    e0, (Gl, Gg) = exchange_energy_halo(G_window, NE, Nw, group)
+    if E1 > E0:
+        gS = []
+        for g in gS_window:
+            x = torch.zeros_like(Gl)
+            x[:, E0 - e0:E1 - e0] = g
+            gS.append(x)
+        if compute is None:
+            from . import binding
+            compute = binding.sigma_grad
+        parts = compute(Gl.contiguous(), Gg.contiguous(), dH, D[0], D[1], nbr, gS[0], gS[1], scale=scale, **kw)
+    else:  # nothing owned: zero contributions to the sums
+        parts = (torch.zeros_like(dH), torch.zeros_like(D[0]), torch.zeros_like(D[1]))
+    return [reduce_in_rank_order(p, group) for p in parts]
+
+
 def reduce_in_rank_order(x: torch.Tensor, group=None) -> torch.Tensor:
     """Sum of ``x`` over the ranks, added in rank order on every rank (deterministic): the reduction that gradients
     summed over energies (dH, D) need when the energies are split."""

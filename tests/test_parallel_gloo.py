@@ -215,6 +215,46 @@ def _composed_energy_worker(rank, world, port, dims, seed, q):
         dist.destroy_process_group()
 
 
+def _composed_energy_grad_worker(rank, world, port, dims, seed, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed)
+        W, V = make_upstream(dims, seed=seed + 1)
+        E0, E1 = P.energy_range(dims.NE, world, rank)
+
+        def on_cpu(Gl, Gg, dH, Dl, Dg, nbr, gl, gg, scale):  # the oracle in place of the library call
+            return tuple(torch.from_numpy(x) for x in oracle.sigma_grad(nbr, dH, Dl, Dg, Gl, Gg, scale, gl, gg,
+                                                                        nthreads=2))
+
+        grads = P.sigma_grad_energy_sharded(inp.nbr, inp.dH, (inp.D_less, inp.D_greater),
+                                            (inp.G_less[:, E0:E1].clone(), inp.G_greater[:, E0:E1].clone()),
+                                            (W[:, E0:E1], V[:, E0:E1]), dims.NE, SCALE, compute=on_cpu)
+        ref = oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, W, V,
+                                nthreads=2)
+        ok = all(bool(np.abs(g.numpy() - r).max() <= 1e-13 * np.abs(r).max()) for g, r in zip(grads, ref))
+        oks = [None] * world
+        dist.all_gather_object(oks, ok)
+        if rank == 0:
+            q.put(all(oks))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_composed_energy_sharded_gradients():
+    """parallel.sigma_grad_energy_sharded with the oracle as the evaluation: every rank's gradients with respect to
+    dH, D^< and D^> equal the unsharded oracle's up to the order of the additions, also with more ranks than
+    energies (a rank owns nothing)."""
+    ctx = mp.get_context("spawn")
+    for dims, world in ((TINY, 3), (Dims(NA=4, NB=2, Norb=2, NE=3, Nkz=2, Nqz=1, Nw=2), 4)):
+        q = ctx.SimpleQueue()
+        mp.start_processes(_composed_energy_grad_worker, args=(world, _free_port(), dims, 16, q), nprocs=world,
+                           join=True, start_method="spawn")
+        assert q.get()
+
+
 def test_composed_energy_sharded_sigma():
     """parallel.sigma_energy_sharded with the oracle as the evaluation: each rank's rows equal the unsharded oracle
     bit for bit, with windows longer than Nw and shorter than Nw (the halo spans several ranks)."""
