@@ -140,6 +140,29 @@ def sigma_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, D_owned: Seque
     return Sl[:, :, :a1 - a0], Sg[:, :, :a1 - a0]
 
 
+def pi_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, G_owned: Sequence[torch.Tensor], NA: int, Nqz: int,
+                    Nw: int, scale: float, compute=None, group=None, **kw):
+    """Pi^<, Pi^> of Eq. (4) for this rank's atoms [a0, a1): the same halo as Sigma (the G blocks of the neighbours),
+    one exchange, the local problem and ``compute`` on its first a1-a0 atoms. ``compute`` takes (G_less, G_greater,
+    dH, nbr, Nqz, Nw, scale=..., atoms=..., **kw) and defaults to the library call ``binding.pi``. Returns the owned
+    rows [Nqz, Nw, a1-a0, NB+1, 3, 3]."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    a0, a1 = atom_range(NA, world, rank)
+    halo = exchange_halo(G_owned, nbr, NA, group)  # collective: every rank takes part
+    NB = nbr.shape[1]
+    if a1 == a0:
+        empty = torch.zeros((Nqz, Nw, 0, NB + 1, 3, 3), dtype=G_owned[0].dtype, device=G_owned[0].device)
+        return empty, empty.clone()
+    D0 = dH_owned.new_zeros((Nqz, Nw, a1 - a0, NB, 3, 3))  # placeholders: Pi does not read D
+    nbr_l, dH_l, _, _, Gl, Gg = local_problem(nbr, a0, a1, G_owned, halo, dH_owned, (D0, D0))
+    if compute is None:
+        from . import binding
+        compute = binding.pi
+    Pl, Pg = compute(Gl, Gg, dH_l, nbr_l, Nqz, Nw, scale=scale, atoms=(0, a1 - a0), **kw)
+    return Pl[:, :, :a1 - a0], Pg[:, :, :a1 - a0]
+
+
 def reduce_halo_grad(gG_local: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int,
                      group=None) -> List[torch.Tensor]:
     """The exchange step of the gradient with respect to G: the reverse of ``exchange_halo``.

@@ -144,6 +144,44 @@ def test_composed_sharded_sigma():
         assert q.get()
 
 
+def _composed_pi_worker(rank, world, port, dims, seed, nbr, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed, nbr=nbr)
+        a0, a1 = P.atom_range(dims.NA, world, rank)
+
+        def on_cpu(Gl, Gg, dH, nbr_l, Nqz, Nw, scale, atoms):  # the oracle in place of the library call
+            return tuple(torch.from_numpy(x) for x in oracle.pi(nbr_l, dH, Gl, Gg, scale, Nqz, Nw, a_range=atoms,
+                                                                nthreads=2))
+
+        Pl, Pg = P.pi_atom_sharded(inp.nbr, inp.dH[a0:a1], (inp.G_less[:, :, a0:a1].clone(),
+                                                            inp.G_greater[:, :, a0:a1].clone()),
+                                   dims.NA, dims.Nqz, dims.Nw, SCALE, compute=on_cpu)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (a0, a1, Pl.contiguous(), Pg.contiguous()))
+        if rank == 0:
+            full = oracle.pi(inp.nbr, inp.dH, inp.G_less, inp.G_greater, SCALE, dims.Nqz, dims.Nw, nthreads=2)
+            q.put(all(pl.shape == full[0][:, :, b0:b1].shape and np.array_equal(pl.numpy(), full[0][:, :, b0:b1])
+                      and np.array_equal(pg.numpy(), full[1][:, :, b0:b1]) for b0, b1, pl, pg in gathered))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_composed_sharded_pi():
+    """parallel.pi_atom_sharded with the oracle as the evaluation: the gathered rows of Pi (Eq. 4) equal the
+    unsharded oracle bit for bit at world 3, with halos of several owners and with a rank that owns nothing."""
+    ctx = mp.get_context("spawn")
+    for dims, world, nbr in ((Dims(NA=16, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2), 3, diamond_neighbours(1, 1, 2)),
+                             (Dims(NA=2, NB=1, Norb=2, NE=6, Nkz=2, Nqz=1, Nw=2), 3, None)):
+        q = ctx.SimpleQueue()
+        mp.start_processes(_composed_pi_worker, args=(world, _free_port(), dims, 17, nbr, q), nprocs=world,
+                           join=True, start_method="spawn")
+        assert q.get()
+
+
 def _composed_grad_g_worker(rank, world, port, dims, seed, nbr, q):
     import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
