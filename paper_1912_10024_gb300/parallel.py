@@ -140,6 +140,33 @@ def sigma_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, D_owned: Seque
     return Sl[:, :, :a1 - a0], Sg[:, :, :a1 - a0]
 
 
+def sigma_grad_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, D_owned: Sequence[torch.Tensor],
+                            G_owned: Sequence[torch.Tensor], gS_owned: Sequence[torch.Tensor], NA: int, scale: float,
+                            compute=None, group=None, **kw):
+    """Gradients of L = sum_t Re tr(gS^t^H Sigma^t) with respect to this rank's dH and D^<, D^> rows: owned per atom,
+    so after the halo exchange of G no reduction follows. gS_owned = (gS^<, gS^>) [Nkz, NE, a1-a0, Norb, Norb].
+    ``compute`` takes (G_less, G_greater, dH, D_less, D_greater, nbr, gS_less, gS_greater, scale=..., atoms=..., **kw)
+    and defaults to ``binding.sigma_grad``. Returns (g_dH [a1-a0, ...], g_D^< and g_D^> [Nqz, Nw, a1-a0, ...])."""
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    a0, a1 = atom_range(NA, world, rank)
+    halo = exchange_halo(G_owned, nbr, NA, group)  # collective: every rank takes part
+    n_own = a1 - a0
+    if n_own == 0:
+        return dH_owned.clone(), D_owned[0].clone(), D_owned[1].clone()
+    nbr_l, dH_l, Dl, Dg, Gl, Gg = local_problem(nbr, a0, a1, G_owned, halo, dH_owned, D_owned)
+    gS = []
+    for g in gS_owned:
+        x = torch.zeros_like(Gl)
+        x[:, :, :n_own] = g
+        gS.append(x)
+    if compute is None:
+        from . import binding
+        compute = binding.sigma_grad
+    g_dH, g_Dl, g_Dg = compute(Gl, Gg, dH_l, Dl, Dg, nbr_l, gS[0], gS[1], scale=scale, atoms=(0, n_own), **kw)
+    return g_dH[:n_own], g_Dl[:, :, :n_own], g_Dg[:, :, :n_own]
+
+
 def pi_atom_sharded(nbr: torch.Tensor, dH_owned: torch.Tensor, G_owned: Sequence[torch.Tensor], NA: int, Nqz: int,
                     Nw: int, scale: float, compute=None, group=None, **kw):
     """Pi^<, Pi^> of Eq. (4) for this rank's atoms [a0, a1): the same halo as Sigma (the G blocks of the neighbours),

@@ -1,5 +1,5 @@
-"""The composed sharded calls on the GPU: parallel.sigma_atom_sharded, sigma_grad_G_atom_sharded, pi_atom_sharded and
-sigma_energy_sharded with their default evaluation (the library calls) on a one-rank process group equal the direct
+"""The composed sharded calls on the GPU: parallel.sigma_atom_sharded, sigma_grad_atom_sharded,
+sigma_grad_G_atom_sharded, pi_atom_sharded and sigma_energy_sharded with their default evaluation (the library calls) on a one-rank process group equal the direct
 library calls bit for bit (the local problem is the global one)."""
 import math
 import socket
@@ -33,6 +33,10 @@ def test_single_rank_equals_the_library_call():
                                              mode="fp64_fft")
         rl, rg = B.sigma_grad_G(g.dH, g.D_less, g.D_greater, g.nbr, W, V, scale=SCALE, mode="fp64_fft")
         assert torch.equal(gl, rl) and torch.equal(gg, rg)
+        ga = P.sigma_grad_atom_sharded(g.nbr, g.dH, (g.D_less, g.D_greater), (g.G_less, g.G_greater), (W, V), d.NA,
+                                       SCALE)
+        gr = B.sigma_grad(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, W, V, scale=SCALE)
+        assert all(torch.equal(x, y) for x, y in zip(ga, gr))
         Pl, Pg = P.pi_atom_sharded(g.nbr, g.dH, (g.G_less, g.G_greater), d.NA, d.Nqz, d.Nw, SCALE)
         Ql, Qg = B.pi(g.G_less, g.G_greater, g.dH, g.nbr, d.Nqz, d.Nw, scale=SCALE)
         assert torch.equal(Pl, Ql) and torch.equal(Pg, Qg)

@@ -144,6 +144,50 @@ def test_composed_sharded_sigma():
         assert q.get()
 
 
+def _composed_adjoint_worker(rank, world, port, dims, seed, nbr, q):
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        inp = make_inputs(dims, seed=seed, nbr=nbr)
+        W, V = make_upstream(dims, seed=seed + 1)
+        a0, a1 = P.atom_range(dims.NA, world, rank)
+
+        def on_cpu(Gl, Gg, dH, Dl, Dg, nbr_l, gl, gg, scale, atoms):  # the oracle in place of the library call
+            return tuple(torch.from_numpy(x) for x in oracle.sigma_grad(nbr_l, dH, Dl, Dg, Gl, Gg, scale, gl, gg,
+                                                                        a_range=atoms, nthreads=2))
+
+        g = P.sigma_grad_atom_sharded(inp.nbr, inp.dH[a0:a1], (inp.D_less[:, :, a0:a1], inp.D_greater[:, :, a0:a1]),
+                                      (inp.G_less[:, :, a0:a1].clone(), inp.G_greater[:, :, a0:a1].clone()),
+                                      (W[:, :, a0:a1], V[:, :, a0:a1]), dims.NA, SCALE, compute=on_cpu)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (a0, a1, [t.contiguous() for t in g]))
+        if rank == 0:
+            full = oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE,
+                                     W, V, nthreads=2)
+            ok = True
+            for b0, b1, sh in gathered:
+                ok &= np.array_equal(sh[0].numpy(), full[0][b0:b1])
+                for t in (1, 2):
+                    ok &= np.array_equal(sh[t].numpy(), full[t][:, :, b0:b1])
+            q.put(ok)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_composed_sharded_adjoint():
+    """parallel.sigma_grad_atom_sharded with the oracle as the evaluation: the gathered dH and D gradient rows equal
+    the unsharded oracle's bit for bit (owned per atom, no reduction), at world 3 with a rank that owns nothing."""
+    ctx = mp.get_context("spawn")
+    for dims, world, nbr in ((Dims(NA=16, NB=4, Norb=2, NE=9, Nkz=2, Nqz=2, Nw=2), 3, diamond_neighbours(1, 1, 2)),
+                             (Dims(NA=2, NB=1, Norb=2, NE=6, Nkz=2, Nqz=1, Nw=2), 3, None)):
+        q = ctx.SimpleQueue()
+        mp.start_processes(_composed_adjoint_worker, args=(world, _free_port(), dims, 18, nbr, q), nprocs=world,
+                           join=True, start_method="spawn")
+        assert q.get()
+
+
 def _composed_pi_worker(rank, world, port, dims, seed, nbr, q):
     import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
