@@ -1,4 +1,4 @@
-"""Atom-tile and energy-window sharding of Eq. (3) across ranks with halo exchanges of G.
+"""Atom-tile and energy-window sharding of Eqs. (3) and (4) across ranks with halo exchanges of G.
 
 The communication-avoiding decomposition of Sec. 4.2 tiles the atoms of the
 device: a rank that owns atoms [a0, a1) computes Sigma_a for exactly those
@@ -7,12 +7,22 @@ its atoms that other ranks own (the "+N_b atom halo"). One exchange step
 brings those blocks in; Sigma, Pi and the gradients with respect to dH and D
 need no reduction afterwards. The gradient with respect to G does: a rank's
 bonds also reach the G blocks of its halo atoms, so ``reduce_halo_grad`` sends
-those contributions back to their owners.
+those contributions back to their owners. The other axis tiles the energies:
+a rank that owns [E0, E1) needs the Nw rows of G on each side (the "+2 N_w
+energy halo"); the gradients with respect to dH and D, sums over energies, are
+then reduced across the ranks.
+
+The primitives (``exchange_halo``, ``local_problem``, ``reduce_halo_grad``,
+``exchange_energy_halo``, ``reduce_in_rank_order``) are composed into one call
+per operation: ``sigma_atom_sharded``, ``sigma_grad_atom_sharded``,
+``sigma_grad_G_atom_sharded``, ``pi_atom_sharded``, ``sigma_energy_sharded``
+and ``sigma_grad_energy_sharded``; each evaluates its local problem with the
+library call (or a ``compute`` the caller passes).
 
 On one GPU the shard primitive is sse_sigma_fwd's atom range; across GPUs the
-exchange below runs over torch.distributed (NCCL for CUDA tensors, gloo for
-CPU tensors). Every transfer is a point-to-point send/recv of whole
-[Nkz, NE, Norb, Norb] blocks; nothing else crosses ranks.
+exchanges run over torch.distributed (NCCL for CUDA tensors, gloo for CPU
+tensors): point-to-point sends of whole G blocks or energy rows, plus the
+rank-order gather of the energy-summed gradients.
 """
 from __future__ import annotations
 
