@@ -210,12 +210,21 @@ def gpu_local_cpus(dev):
         return None
 
 
-def load_peaks():
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks(path=None):
+    """Measured copy bandwidth and bf16 GEMM rates of this GPU model; the earlier GB300 measurement for any figure
+    the file lacks (or for all of them, without a readable file), with the source saying which."""
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+        with open(path or os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            measured = json.load(f)
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+    peaks = dict(FALLBACK_PEAKS)
+    usable = {k: float(v) for k, v in measured.items() if k in FALLBACK_PEAKS and isinstance(v, (int, float)) and v > 0}
+    peaks.update(usable)
+    return peaks, "measured" if len(usable) == len(FALLBACK_PEAKS) else "measured, partly fallback"
 
 
 class ClockSampler:

@@ -91,3 +91,22 @@ def test_reference_arm_other_ranks_exit_without_work():
                        capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_peaks_fall_back_per_figure(tmp_path):
+    """The roofline denominators: the measured file's figures where present, the earlier GB300 measurement where a
+    figure (or the whole file) is missing, and the source says which."""
+    full = tmp_path / "full.json"
+    full.write_text(json.dumps({"hbm_gbs": 6793.4, "bf16_tflops": 1897.2, "bf16_tflops_sustained": 1714.1,
+                                "gpu_name": "x"}))
+    peaks, src = bench.load_peaks(str(full))
+    assert src == "measured" and peaks["hbm_gbs"] == 6793.4 and peaks["bf16_tflops_sustained"] == 1714.1
+    part = tmp_path / "part.json"
+    part.write_text(json.dumps({"hbm_gbs": 7000.0, "bf16_tflops": "n/a"}))
+    peaks, src = bench.load_peaks(str(part))
+    assert src == "measured, partly fallback" and peaks["hbm_gbs"] == 7000.0
+    assert peaks["bf16_tflops"] == bench.FALLBACK_PEAKS["bf16_tflops"]
+    bad = tmp_path / "bad.json"
+    bad.write_text("{not json")
+    assert bench.load_peaks(str(bad)) == (bench.FALLBACK_PEAKS, "fallback")
+    assert bench.load_peaks(str(tmp_path / "missing.json"))[1] == "fallback"
