@@ -227,6 +227,13 @@ def load_peaks(path=None):
     return peaks, "measured" if len(usable) == len(FALLBACK_PEAKS) else "measured, partly fallback"
 
 
+def smi_gpu_id(local: int) -> str:
+    """The GPU behind torch's device ``local`` as nvidia-smi names it: with CUDA_VISIBLE_DEVICES set, its entry number
+    ``local`` (an index or a UUID; nvidia-smi counts every GPU of the machine), else ``local`` itself."""
+    ids = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    return ids[local] if local < len(ids) else str(local)
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
 
@@ -234,12 +241,12 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index, self.proc, self.lines = index, None, []
+    def __init__(self, gpu: str):
+        self.gpu, self.proc, self.lines = gpu, None, []
 
     def __enter__(self):
         if shutil.which("nvidia-smi"):
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -275,8 +282,9 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "gpu": self.gpu}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "gpu": self.gpu}
 
 
 def cpu_baseline(d, seconds: float, inp=None, seed: int = 0):
@@ -392,7 +400,7 @@ def main():
     barrier()
     torch.cuda.synchronize(dev)
     B.sse_profile_read()  # drop anything recorded before the timed region
-    with ClockSampler(local) as clk:
+    with ClockSampler(smi_gpu_id(local)) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)

@@ -110,3 +110,18 @@ def test_peaks_fall_back_per_figure(tmp_path):
     bad.write_text("{not json")
     assert bench.load_peaks(str(bad)) == (bench.FALLBACK_PEAKS, "fallback")
     assert bench.load_peaks(str(tmp_path / "missing.json"))[1] == "fallback"
+
+
+def test_clock_samples_come_from_the_gpu_torch_uses(monkeypatch):
+    """nvidia-smi numbers every GPU of the machine; torch numbers the visible ones: the sampler maps one to the
+    other through CUDA_VISIBLE_DEVICES (indices or UUIDs)."""
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "5,2")
+    assert bench.smi_gpu_id(0) == "5" and bench.smi_gpu_id(1) == "2"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-1234abcd")
+    assert bench.smi_gpu_id(0) == "GPU-1234abcd"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.smi_gpu_id(3) == "3"
+    clk = bench.ClockSampler("7")
+    clk.lines = ["1965, 2070, 900.1, Not Active, Not Active, Not Active, Active", "garbage"]
+    out = clk.summary()
+    assert out == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 1, "gpu": "7"}
