@@ -7,7 +7,6 @@ checked with the GPU forward on random dG.
 """
 import math
 
-import numpy as np
 import pytest
 import torch
 

@@ -6,7 +6,6 @@ the stated FP32_FFT bound below for the mixed adjoint.
 """
 import math
 
-import numpy as np
 import pytest
 
 import oracle
