@@ -30,7 +30,7 @@ PiCfg make_pi_cfg(const sse_dims& d, size_t nfreq) {
     c.smem = a16(c.off_self + c.F * 9 * 16);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
-    size_t chunks = (want + 2 * nA - 1) / (2 * nA ? 2 * nA : 1);
+    size_t chunks = (want + 2 * nA - 1) / (nA ? 2 * nA : 1);
     if (chunks < 1) chunks = 1;
     size_t fc = (nfreq + chunks - 1) / chunks;
     fc = ((fc + c.F - 1) / c.F) * c.F;
@@ -206,7 +206,7 @@ Pi32Cfg make_pi32_cfg(const sse_dims& d, size_t nfreq) {
     c.smem = a16(c.off_self + c.F * 9 * 8);
     const size_t nA = (size_t)(d.a_end - d.a_begin);
     size_t want = (size_t)152 * 2 * 8;
-    size_t chunks = (want + 2 * nA - 1) / (2 * nA ? 2 * nA : 1);
+    size_t chunks = (want + 2 * nA - 1) / (nA ? 2 * nA : 1);
     if (chunks < 1) chunks = 1;
     size_t fc = (nfreq + chunks - 1) / chunks;
     fc = ((fc + c.F - 1) / c.F) * c.F;
