@@ -17,6 +17,11 @@ structure stand in for them:
   X re/im ~ N(0, 0.01^2) -- exactly anti-Hermitian 3x3 blocks.
 * nbr      : int32 [NA, NB] neighbour list (ring or diamond lattice).
 
+With ``general=True`` G^<, G^> are plain complex blocks (re/im ~ N(0, 1/Norb))
+and D^<, D^> plain complex 3x3 blocks (re/im ~ N(0, 0.01^2)), with no
+symmetry at all: these are the inputs on which a kernel that used G^H = -G or
+D^H = -D without being told so would give a different Sigma.
+
 Draw order is G^<, G^>, dH, D^<, D^> from one torch.Generator seeded with
 `seed` on the requested device. The same bytes feed the GPU path and the
 oracle: whoever generated them copies them to the other side.
@@ -159,16 +164,30 @@ class Inputs:
                                                           self.G_less, self.G_greater)))
 
 
-def make_inputs(dims: Dims, seed: int = 0, device="cpu", nbr: Optional[torch.Tensor] = None) -> Inputs:
-    """Seeded synthetic inputs (draw order G^<, G^>, dH, D^<, D^>)."""
+def make_inputs(dims: Dims, seed: int = 0, device="cpu", nbr: Optional[torch.Tensor] = None,
+                general: bool = False) -> Inputs:
+    """Seeded synthetic inputs (draw order G^<, G^>, dH, D^<, D^>).
+
+    general=False: anti-Hermitian G and D blocks (lesser/greater functions);
+    general=True: the same draw order with no symmetry in G or D.
+    """
     device = torch.device(device)
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
-    G_less = _anti_hermitian_gram(dims.g_shape(), +1.0, gen, device)
-    G_greater = _anti_hermitian_gram(dims.g_shape(), -1.0, gen, device)
+    if general:
+        g_std = 1.0 / math.sqrt(dims.Norb)
+        G_less = _cnormal(dims.g_shape(), g_std, gen, device)
+        G_greater = _cnormal(dims.g_shape(), g_std, gen, device)
+    else:
+        G_less = _anti_hermitian_gram(dims.g_shape(), +1.0, gen, device)
+        G_greater = _anti_hermitian_gram(dims.g_shape(), -1.0, gen, device)
     dH = _cnormal(dims.dh_shape(), 0.1, gen, device)
-    D_less = _anti_hermitian_3x3(dims.d_shape(), 0.01, gen, device)
-    D_greater = _anti_hermitian_3x3(dims.d_shape(), 0.01, gen, device)
+    if general:
+        D_less = _cnormal(dims.d_shape(), 0.01, gen, device)
+        D_greater = _cnormal(dims.d_shape(), 0.01, gen, device)
+    else:
+        D_less = _anti_hermitian_3x3(dims.d_shape(), 0.01, gen, device)
+        D_greater = _anti_hermitian_3x3(dims.d_shape(), 0.01, gen, device)
     if nbr is None:
         nbr = default_neighbours(dims)
     return Inputs(dims, nbr.to(device=device, dtype=torch.int32).contiguous(), dH, D_less, D_greater,

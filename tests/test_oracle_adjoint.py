@@ -22,16 +22,16 @@ def loss(inp, W, V):
     return float(np.real(np.vdot(W, Sl)) + np.real(np.vdot(V, Sg)))
 
 
-def make_problem():
-    inp = make_inputs(D, seed=21, nbr=ring_neighbours(D.NA, D.NB))
+def make_problem(general=False):
+    inp = make_inputs(D, seed=21, nbr=ring_neighbours(D.NA, D.NB), general=general)
     W, V = (x.numpy() for x in make_upstream(D, seed=22))
     g = oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, W, V)
     return inp, W, V, g
 
 
-@pytest.fixture(scope="module")
-def problem():
-    return make_problem()
+@pytest.fixture(scope="module", params=[False, True], ids=["antihermitian", "general"])
+def problem(request):
+    return make_problem(request.param)
 
 
 def test_gradient_central_differences(problem):
@@ -68,7 +68,8 @@ def test_dot_product_in_D(problem):
     dg = rng.standard_normal(g_Dg.shape) + 1j * rng.standard_normal(g_Dg.shape)
     l0 = loss(inp, W, V)
     import torch
-    inp2 = make_inputs(D, seed=21, nbr=ring_neighbours(D.NA, D.NB))
+    import copy
+    inp2 = copy.copy(inp)  # same G, dH and neighbours
     inp2.D_less = inp.D_less + torch.from_numpy(dl)
     inp2.D_greater = inp.D_greater + torch.from_numpy(dg)
     l1 = loss(inp2, W, V)
@@ -106,11 +107,12 @@ def test_atom_range_gradients(problem):
     Dims(NA=7, NB=3, Norb=5, NE=11, Nkz=4, Nqz=2, Nw=3),    # Nqz < Nkz, ragged sizes
     Dims(NA=3, NB=2, Norb=2, NE=2, Nkz=5, Nqz=5, Nw=1),     # the shortest energy grid
 ], ids=["scalar_all_lags", "ragged", "two_energies"])
-def test_euler_identities_on_edge_shapes(d):
+@pytest.mark.parametrize("general", [False, True], ids=["antihermitian", "general"])
+def test_euler_identities_on_edge_shapes(d, general):
     """L is linear in (D^<, D^>) jointly, linear in (G^<, G^>) jointly and a Hermitian quadratic form in dH, so
     Euler's theorem for homogeneous functions fixes L = Re<g_D, D> = Re<g_G, G> = Re<g_dH, dH> / 2 exactly: every
     gradient entry weighted by its own input, on shapes at the edges of the index ranges."""
-    inp = make_inputs(d, seed=77)
+    inp = make_inputs(d, seed=77, general=general)
     W, V = (x.numpy() for x in make_upstream(d, seed=78))
     args = (inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE)
     g_dH, g_Dl, g_Dg = oracle.sigma_grad(*args, W, V)

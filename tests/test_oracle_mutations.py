@@ -35,6 +35,11 @@ FWD = [
      "J.c = scale;\n    J.n_out = 2LL * (d->a_end"),
     ("neighbour G replaced by own atom", "const cplx* Gp = J->G[t] + off_G(d, kp, Ep, b);\n                    const cplx* Dc = J->D[tau]",
      "const cplx* Gp = J->G[t] + off_G(d, kp, Ep, a);\n                    const cplx* Dc = J->D[tau]"),
+    # the two below change nothing for anti-Hermitian G and D blocks (the delta-response and closed-form pins,
+    # whose inputs are not anti-Hermitian, and the general-input einsum catch them)
+    ("G taken as -G^H", "mm(n, J->dH + off_dH(d, a, s, i), Gp, P); /* dH_i(a,b) G_bb */",
+     "mm_bh(n, J->dH + off_dH(d, a, s, i), Gp, P); for (int e = 0; e < nn; ++e) P[e] = -P[e];"),
+    ("weight taken as -D^H", "const cplx dij = Dc[i * 3 + j];", "const cplx dij = -conj(Dc[j * 3 + i]);"),
     ("edge terms wrapped instead of dropped",
      "const int Ep = E - sigma * (w + 1);\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out",
      "const int Ep = ((E - sigma * (w + 1)) % d->NE + d->NE) % d->NE;\n                    if (Ep < 0 || Ep >= d->NE) continue; /* out"),
@@ -45,6 +50,9 @@ BWD = [
     ("grad dH left term not conjugated", "const cplx f = conj(J->c * Dc[m * 3 + j]);", "const cplx f = J->c * Dc[m * 3 + j];"),
     ("grad dH left term misses G^H", "mm_bh(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */",
      "mm(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */"),
+    # changes nothing for anti-Hermitian G: only the problem with general G and D catches it
+    ("grad dH left term takes G^H as -G", "mm_bh(n, T, Gp, AG + (size_t)j * nn);  /* W dH_j G^H */",
+     "mm(n, T, Gp, AG + (size_t)j * nn); for (int e = 0; e < nn; ++e) AG[(size_t)j * nn + e] = -AG[(size_t)j * nn + e];"),
 ]
 DCOMB = [
     ("own slot instead of the reverse slot", "const cplx* Dba = raw[t] + off_raw(d, q, w, b, sr);",
@@ -129,15 +137,17 @@ def _fwd_pins():
     yield pins.test_anti_hermitian
     yield pins.test_sesquilinear_in_dH
     yield pins.test_term_count_matches_paper_flop_model
+    yield lambda: pins.test_literal_einsum(pins.Dims(NA=7, NB=3, Norb=5, NE=11, Nkz=4, Nqz=2, Nw=3), True)
 
 
 def _bwd_pins():
-    def run():
-        problem = adj.make_problem()
+    def run(general):
+        problem = adj.make_problem(general)
         adj.test_gradient_central_differences(problem)
         adj.test_dot_product_in_D(problem)
         adj.test_dot_product_in_dH(problem)
-    yield run
+    yield lambda: run(False)
+    yield lambda: run(True)
 
 
 def _build(tmp_path, old, new):

@@ -255,10 +255,12 @@ def test_term_count_matches_paper_flop_model():
     Dims(NA=7, NB=3, Norb=5, NE=11, Nkz=4, Nqz=2, Nw=3),  # Nqz < Nkz, odd orbitals, ragged everything
     Dims(NA=4, NB=2, Norb=2, NE=2, Nkz=5, Nqz=5, Nw=1),   # the shortest energy grid
 ], ids=["tiny", "scalar_all_lags", "ragged_nqz_lt_nkz", "two_energies"])
-def test_literal_einsum(d):
+@pytest.mark.parametrize("general", [False, True], ids=["antihermitian", "general"])
+def test_literal_einsum(d, general):
     """Eq. (3) written out as one einsum per (E, w, sigma) term over the whole (kz, qz, a, s, i, j) index space, on
-    shapes that reach its edge cases."""
-    inp = make_inputs(d, seed=0)
+    shapes that reach its edge cases; with anti-Hermitian inputs and with G, D of no symmetry (where G^H and -G,
+    D^H and -D differ, so the oracle may use neither in their place)."""
+    inp = make_inputs(d, seed=0, general=general)
     Sl, Sg = run(inp)
     nbr = inp.nbr.numpy()
     A = inp.dH.numpy()
