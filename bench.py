@@ -144,8 +144,6 @@ def mixed_tensor_flops(d, mode: str) -> float:
     return 2.0 * 128 * npad * kpad * taps * d.Nqz * d.NB * d.Nkz * 2 * d.NA
 
 
-# DRAM bytes (read + write) per unit of work measured by ncu for the transform-path kernels
-# (profiles/spec_*_adjoint_ncu_full.md), valid for the kernel source they were taken on.
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit from one ncu capture at the adjoint workload,
 # with the sha256 prefix of the captured kernel's own source text: the figure is dropped (None) once that kernel
 # has changed.
@@ -313,12 +311,13 @@ def cpu_baseline(d, seconds: float, inp=None, seed: int = 0):
                       f"all kz, Sigma^< and Sigma^>; FP64 C loops (pthreads)"}
 
 
-def bench_config(args, d):
-    """The workload description shared by both arms."""
+def bench_config(args, d, world=1):
+    """The workload description shared by both arms (the same keys and values for the same arguments)."""
     g_bytes = 2 * d.Nkz * d.NE * d.NA * d.Norb * d.Norb * 16
     return {"workload": args.workload, **d.__dict__, "mode": args.mode,
             "antihermitian_inputs_flag": bool(getattr(args, "antihermitian", False)),
-            "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (g_bytes / 1e9)}
+            "l2": "inputs larger than L2 (G^<,G^> %.1f GB)" % (g_bytes / 1e9),
+            "parallelism": f"{world} rank(s), one independent problem of this size each"}
 
 
 def run_reference(args, d, rank, world):
@@ -334,7 +333,7 @@ def run_reference(args, d, rank, world):
     out = {"impl": "reference", "metric": "SSE useful TFLOP/s (Eq. 3, paper-equivalent flops)", "value": v,
            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": bench_config(args, d),
+           "config": bench_config(args, d, world),
            "cpu_baseline": {**cb, "value": v},
            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -722,12 +721,12 @@ def main():
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sigma_fp64_fwd_kernel",
                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2070 MHz (DFMA probe: 1.25)"}
         elif args.mode == "fp32_fft":
-            ks, n = kernel_s("spec_prod_kernel")
+            ks, n = kernel_s("spec_prod32_kernel")
             achieved = spectral_prod32_flops(d, args.antihermitian) / ks / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_PEAK_TFLOPS,
                     "traffic": ncu_traffic("spec_prod32_kernel", d.NA * freq_count(d, args.antihermitian)),
-                    "kernel": "spec_prod_kernel",
+                    "kernel": "spec_prod32_kernel",
                     "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2070 MHz (FFMA probe: 73)"}
         elif args.mode == "fp64_fft":
             ks, n = kernel_s("spec_prod_kernel")
@@ -758,8 +757,7 @@ def main():
                "dtype": {"fp64": "f64", "fp64_fft": "f64", "fp32_fft": "f32", "tf32": "tf32+f64",
                          "bf16x3": "bf16x3+f64"}[args.mode],
                "data": "synthetic (seeded; Si-FinFET-shaped)",
-               "config": {**bench_config(args, d),
-                          "parallelism": f"{world} rank(s), one independent problem of this size each"},
+               "config": bench_config(args, d, world),
                "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
                "gpu_launches": sum(v[1] for v in kernels.values())}
         if compare:

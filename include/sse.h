@@ -276,8 +276,12 @@ SSE_API int sse_dcomb_bwd(const sse_dims* d, const int32_t* nbr, const double* g
  *   SSE_STATIC_SCRATCH_BYTES are rejected with SSE_ERR_WORKSPACE before any device work
  *   (the array holds e.g. NA*NB*Nkz*6*Norb^2*16 bytes of partials + 256: NA=256, NB=4,
  *   Norb=10, Nkz=5 fits; NA=1024, Nkz=7 does not).
- * - The first call on a device looks up the array's device address on that device
- *   (the current device); make that first call before any stream capture.
+ * - Argument checks and status codes are those of sse_sigma_bwd: a valid mode other than
+ *   SSE_MODE_FP64, or sizes the kernels are not built for, give SSE_ERR_UNSUPPORTED.
+ * - Every call looks up the array's device address on the current device (a host-side
+ *   query), so a device reset between calls is harmless. The first call on a device may
+ *   load the library's device code there: make it before any stream capture.
+ * - SSE_FLAG_PROFILE records kernel times as in sse_sigma_bwd.
  * - All calls share the one array and it keeps the last call's contents; the status
  *   word is cleared by each call. Calls that overlap on the GPU (different streams,
  *   different host threads) race on the array: order them on one stream. */

@@ -75,8 +75,11 @@ int finish(cudaError_t launch, unsigned* status, uint32_t flags, cudaStream_t st
     return SSE_OK;
 }
 
-int common_checks(const sse_dims* d, const int32_t* nbr, const double* dH, const double* Dl, const double* Dg,
-                  const double* Gl, const double* Gg, double scale, int mode, uint32_t flags) {
+}  // namespace
+
+namespace sse {
+int abi_common_checks(const sse_dims* d, const int32_t* nbr, const double* dH, const double* Dl, const double* Dg,
+                      const double* Gl, const double* Gg, double scale, int mode, uint32_t flags) {
     if (!valid_dims(d) || !valid_mode(mode) || !valid_flags(flags)) return SSE_ERR_INVALID_ARG;
     if (!isfinite(scale)) return SSE_ERR_INVALID_ARG;
     if (!nbr || !dH || !Dl || !Dg || !Gl || !Gg) return SSE_ERR_INVALID_ARG;
@@ -86,6 +89,10 @@ int common_checks(const sse_dims* d, const int32_t* nbr, const double* dH, const
     if (!supported_dims(d)) return SSE_ERR_UNSUPPORTED;
     return SSE_OK;
 }
+}  // namespace sse
+
+namespace {
+using sse::abi_common_checks;
 
 sse::Problem make_problem(const sse_dims* d, const int32_t* nbr, const double* dH, const double* Dl,
                           const double* Dg, const double* Gl, const double* Gg, double scale, uint32_t flags) {
@@ -132,7 +139,7 @@ extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double
                              int mode, uint32_t flags, double* S_less, double* S_greater, void* workspace,
                              size_t ws_bytes, void* stream) {
     sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
-    int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    int rc = abi_common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
     if (!op_supported(*d, mode, Op::Fwd)) return SSE_ERR_UNSUPPORTED;
@@ -161,7 +168,7 @@ extern "C" int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double
                              double* g_dH, double* g_D_less, double* g_D_greater, void* workspace, size_t ws_bytes,
                              void* stream) {
     sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
-    int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    int rc = abi_common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!gS_less || !gS_greater || !g_dH || !g_D_less || !g_D_greater) return SSE_ERR_INVALID_ARG;
     if (!aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_dH, 16) || !aligned(g_D_less, 16) ||
@@ -355,7 +362,7 @@ extern "C" int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const d
                                   double scale, int mode, uint32_t flags, double* S_less, double* S_greater,
                                   void* device_buf, size_t buf_bytes, void* stream, void* copy_stream) {
     sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
-    int rc = common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    int rc = abi_common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
     if (rc != SSE_OK) return rc;
     if (!S_less || !S_greater || !aligned(S_less, 16) || !aligned(S_greater, 16)) return SSE_ERR_INVALID_ARG;
     if (!op_supported(*d, mode, Op::Fwd)) return SSE_ERR_UNSUPPORTED;

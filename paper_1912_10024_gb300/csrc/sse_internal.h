@@ -45,6 +45,12 @@ void prof_end(cudaStream_t st);
         ::sse::prof_end(st);          \
     } while (0)
 
+// Argument checks shared by sse_sigma_fwd, sse_sigma_bwd and sse_sigma_bwd_static (sse_abi.cu): sizes, mode,
+// flags, scale and the input pointers. SSE_ERR_INVALID_ARG for invalid values, SSE_ERR_UNSUPPORTED for valid sizes
+// the kernels are not built for, SSE_OK otherwise. Host only.
+int abi_common_checks(const sse_dims* d, const int32_t* nbr, const double* dH, const double* Dl, const double* Dg,
+                      const double* Gl, const double* Gg, double scale, int mode, uint32_t flags);
+
 // Workspace layout: [0, 256) status word + padding; the rest per mode.
 constexpr size_t kStatusBytes = 256;
 

@@ -448,7 +448,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
         // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
         if (tiled) {
             const size_t gy = (fm.count + pc32.fchunk - 1) / pc32.fchunk;
-            SSE_TIMED("spec_prod_kernel", st,
+            SSE_TIMED("spec_prod32_kernel", st,
                       spec_prod32_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc32.threads, pc32.smem, st>>>(
                           pc32, d, fm, p.nbr, p.dH, reinterpret_cast<const float2*>(Gh),
                           reinterpret_cast<const float2*>(Kh), reinterpret_cast<float2*>(Sh), p.scale, status));

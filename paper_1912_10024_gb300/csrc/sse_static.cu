@@ -13,8 +13,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "sse.h"
 #include "sse_internal.h"
 
@@ -22,26 +20,16 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_scratch[SSE_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (looked up once per device).
-// In host code `g_scratch` names a host-side stand-in, never the device memory,
-// so the address must come from cudaGetSymbolAddress with the device current.
+// Device address of g_scratch on the current device. In host code `g_scratch` names a host-side stand-in,
+// never the device memory, so the address must come from cudaGetSymbolAddress with the device current. It is
+// looked up on every call (a host-side query that allocates nothing): an address cached across calls would go
+// stale if the process reset the device or re-created its primary context, which reloads the library's device
+// code at another address.
 cudaError_t scratch_on_current_device(void** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -54,21 +42,20 @@ extern "C" int sse_sigma_bwd_static(const sse_dims* d, const int32_t* nbr, const
                                     double scale, int mode, uint32_t flags, const double* gS_less,
                                     const double* gS_greater, double* g_dH, double* g_D_less, double* g_D_greater,
                                     void* stream) {
-    // Same argument checks as sse_sigma_bwd, made before anything touches the device:
-    // the workspace query returns 0 for invalid or unsupported sizes, modes and flags.
-    if (!d || (mode != SSE_MODE_FP64 && mode != SSE_MODE_TF32 && mode != SSE_MODE_BF16X3)) return SSE_ERR_INVALID_ARG;
-    const size_t need = sse_workspace_bytes(d, SSE_MODE_FP64, flags);
-    if (need == 0) return SSE_ERR_INVALID_ARG;
+    sse::ProfScope prof_scope((flags & SSE_FLAG_PROFILE) != 0);
+    // The checks of sse_sigma_bwd and the same status codes, all before anything touches the device: invalid
+    // arguments give SSE_ERR_INVALID_ARG; valid modes other than FP64 and valid sizes the kernels are not built for
+    // give SSE_ERR_UNSUPPORTED; problems whose scratch exceeds the static array give SSE_ERR_WORKSPACE.
+    const int rc = sse::abi_common_checks(d, nbr, dH, D_less, D_greater, G_less, G_greater, scale, mode, flags);
+    if (rc != SSE_OK) return rc;
+    if (!gS_less || !gS_greater || !g_dH || !g_D_less || !g_D_greater) return SSE_ERR_INVALID_ARG;
+    if (!aligned(gS_less, 16) || !aligned(gS_greater, 16) || !aligned(g_dH, 16) || !aligned(g_D_less, 16) ||
+        !aligned(g_D_greater, 16))
+        return SSE_ERR_INVALID_ARG;
     if (mode != SSE_MODE_FP64) return SSE_ERR_UNSUPPORTED;
-    if (!nbr || !dH || !D_less || !D_greater || !G_less || !G_greater || !gS_less || !gS_greater || !g_dH ||
-        !g_D_less || !g_D_greater)
-        return SSE_ERR_INVALID_ARG;
-    if (!aligned(nbr, 4) || !aligned(dH, 16) || !aligned(D_less, 16) || !aligned(D_greater, 16) ||
-        !aligned(G_less, 16) || !aligned(G_greater, 16) || !aligned(gS_less, 16) || !aligned(gS_greater, 16) ||
-        !aligned(g_dH, 16) || !aligned(g_D_less, 16) || !aligned(g_D_greater, 16))
-        return SSE_ERR_INVALID_ARG;
-    if (scale != scale || scale - scale != 0.0) return SSE_ERR_INVALID_ARG;  // NaN or infinite
-    if (need > SSE_STATIC_SCRATCH_BYTES) return SSE_ERR_WORKSPACE;          // problem too large for the array
+    const size_t need = sse_workspace_bytes(d, SSE_MODE_FP64, flags);  // nonzero: the checks above passed
+    if (need == 0) return SSE_ERR_UNSUPPORTED;
+    if (need > SSE_STATIC_SCRATCH_BYTES) return SSE_ERR_WORKSPACE;  // problem too large for the array
     if (d->a_begin == d->a_end) return SSE_OK;
 
     void* scratch = nullptr;

@@ -235,3 +235,29 @@ def test_tensor_core_mode_limits_are_checked_on_host(mode, nw_max):
     assert fwd(B.sse_dims(16, 4, 11, 512, 4, 1, 4, 0, 16)) == 2
     assert fwd(B.sse_dims(16, 4, 10, 4096, 4, 1, nw_max, 0, 16)) == 6
     assert fwd(B.sse_dims(16, 4, 10, 4096, 4, 1, nw_max + 1, 0, 16)) == 2
+
+
+def test_static_entry_point_status_codes_match_sse_sigma_bwd():
+    """sse_sigma_bwd_static returns sse_sigma_bwd's status codes, all decided on the host: unsupported valid modes
+    and sizes give SSE_ERR_UNSUPPORTED, invalid arguments SSE_ERR_INVALID_ARG, problems too large for the static
+    array SSE_ERR_WORKSPACE. The fake pointers are never dereferenced."""
+    fake = 1 << 20
+    scale = 0.159
+
+    def call(d, mode, ptr=fake):
+        return B.sse_sigma_bwd_static(d, ptr, fake, fake, fake, fake, fake, scale, mode, 0, fake, fake, fake, fake,
+                                      fake, 0)
+
+    d = good_dims()
+    for mode in (B.SSE_MODE_TF32, B.SSE_MODE_BF16X3, B.SSE_MODE_FP64_FFT, B.SSE_MODE_FP32_FFT):
+        assert call(d, mode) == 2, mode
+    assert call(d, 7) == 1
+    assert call(d, B.SSE_MODE_FP64, ptr=0) == 1
+    wide = good_dims()
+    wide.Norb = 17
+    assert call(wide, B.SSE_MODE_FP64) == 2
+    bad = good_dims()
+    bad.Nqz = 4
+    assert call(bad, B.SSE_MODE_FP64) == 1
+    big = B.sse_dims(1024, 4, 10, 512, 7, 7, 32, 0, 1024)
+    assert call(big, B.SSE_MODE_FP64) == 6

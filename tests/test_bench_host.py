@@ -1,6 +1,7 @@
 """Host-side checks of bench.py (no GPU): the flop counts and frequency counts it reports are recomputed by
 brute-force enumeration, the kernel-source hashes resolve, and the reference arm (the FP64 oracle timed on the
 host cores) prints one JSON line with the contract's keys."""
+import argparse
 import json
 import os
 import subprocess
@@ -81,6 +82,9 @@ def test_reference_arm_prints_the_contract_line():
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
     assert out["config"]["workload"] == "tiny"
+    # the GPU arm's config for the same arguments: same keys, same values
+    args = argparse.Namespace(workload="tiny", mode=out["config"]["mode"], antihermitian=False)
+    assert out["config"] == bench.bench_config(args, TINY, 1)
 
 
 def test_reference_arm_other_ranks_exit_without_work():

@@ -10,6 +10,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("mode,kernel,launches", [("fp64", "sigma_fp64_fwd_kernel", 1),
                                                   ("fp64_fft", "spec_prod_kernel", 2),
+                                                  ("fp32_fft", "spec_prod32_kernel", 2),
                                                   ("bf16x3", "sigma_mixed_kernel", 1)])
 def test_profile_records_kernels_and_changes_nothing(mode, kernel, launches):
     g = make_inputs(TINY, seed=9).to("cuda")
