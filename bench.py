@@ -5,14 +5,15 @@ One step = one sse_sigma_fwd call: Sigma^< and Sigma^> for every atom,
 energy and kz of the workload (default: the Si-FinFET-shaped problem,
 NA=1024, NB=4, Norb=10, NE=512, Nkz=Nqz=7, Nw=32), inputs resident in HBM.
 Default mode: FP64 through the convolution theorem (fp64_fft); the other
-modes (direct FP64, BF16X3, TF32, FP32 transforms, and the transform modes
+modes (direct FP64, BF16X3, TF32, FP32 transforms, FP32 transforms with the
+block products on the tensor cores (f16x3_fft), and the transform modes
 with anti-Hermitian inputs) are timed on the same inputs in the "compare"
 object, with their error against this run's result; Pi (Eq. 4), the adjoint
 and the gradient in G follow in "pi" and "adjoint". Prints one JSON line
 (rank 0).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload finfet|large|...]
-                  [--mode fp64_fft|fp32_fft|fp64|tf32|bf16x3] [--antihermitian]
+                  [--mode fp64_fft|fp32_fft|f16x3_fft|fp64|tf32|bf16x3] [--antihermitian]
 
 Metric: useful TFLOP/s of the paper-equivalent (regrouped, Sec. 5.1) flop
 count, plus (E,kz) points/s. Multi-GPU (torchrun): every rank solves its own
@@ -109,6 +110,24 @@ def spectral_prod32_flops(d, half: bool = False) -> float:
     4 FMA) and U_i = sum_j K_ij P_j (9 complex MACs at 4 FMA); 2 flops per FMA."""
     Np = d.Norb + (d.Norb & 1)
     return 2.0 * d.NA * d.NB * freq_count(d, half) * Np * Np * (36 + 24 * d.Norb)
+
+
+def tc_shape(norb: int):
+    """Tile shape of spec_prod_tc_kernel (mode F16X3_FFT): frequencies per 128-row tile and the padded GEMM sizes
+    (fp16 elements): GEMM1 K1 x N1, GEMM2 K2 x N2 (N per part: the dH operand's hi or lo)."""
+    r16 = lambda x: -(-x // 16) * 16  # noqa: E731
+    return {"FT": 4 * (32 // norb), "K1": r16(2 * norb), "N1": r16(6 * norb), "K2": 8 * (-(-norb // 2) * 2),
+            "N2": r16(2 * norb)}
+
+
+def tc_tensor_flops(d, half: bool = False) -> float:
+    """Tensor-pipe flops one spec_prod_tc_kernel launch (one type) issues (padding included): per 128-row tile of
+    frequencies and bond, GEMM1 as hi x [B_hi | B_lo] (N = 2 N1) + lo x B_hi (N = N1) over K1, GEMM2 likewise with
+    N2 over K2; 2 flops per multiply-add."""
+    t = tc_shape(d.Norb)
+    tiles = -(-freq_count(d, half) // t["FT"])
+    per = 2.0 * 128 * (3 * t["N1"] * t["K1"] + 3 * t["N2"] * t["K2"])
+    return per * tiles * d.NB * d.NA
 
 
 def spectral_pi_flops(d, half: bool = False) -> float:
@@ -493,10 +512,11 @@ def main():
         compare = {}
         ref = (Sl.clone(), Sg.clone())
         bounds = {"fp64": 1e-12, "fp64_fft": 1e-12, "bf16x3": 2e-5, "tf32": 2e-3, "fp64_fft_antihermitian": 1e-12,
-                  "fp32_fft": 2e-6, "fp32_fft_antihermitian": 2e-6}
+                  "fp32_fft": 2e-6, "fp32_fft_antihermitian": 2e-6, "f16x3_fft": 2e-6, "f16x3_fft_antihermitian": 2e-6}
         variants = [("fp64", 0), ("bf16x3", 0), ("tf32", 0), ("fp64_fft", 0),
                     ("fp64_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN), ("fp32_fft", 0),
-                    ("fp32_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN)]
+                    ("fp32_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN), ("f16x3_fft", 0),
+                    ("f16x3_fft_antihermitian", B.SSE_FLAG_ANTIHERMITIAN)]
         for mname, mflags in variants:
             if mname == args.mode and mflags == run_flags:
                 continue
@@ -728,6 +748,16 @@ def main():
                     "traffic": ncu_traffic("spec_prod32_kernel", d.NA * freq_count(d, args.antihermitian)),
                     "kernel": "spec_prod32_kernel",
                     "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x 2070 MHz (FFMA probe: 73)"}
+        elif args.mode == "f16x3_fft":
+            peaks, src = load_peaks()
+            ks, n = kernel_s("spec_prod_tc_kernel")
+            key = "bf16_tflops_sustained" if ks > 1.0 else "bf16_tflops"
+            achieved = tc_tensor_flops(d, args.antihermitian) / ks / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peaks[key], "unit": "TFLOP/s",
+                    "frac": achieved / peaks[key],
+                    "traffic": ncu_traffic("spec_prod_tc_kernel", d.NA * freq_count(d, args.antihermitian)),
+                    "kernel": "spec_prod_tc_kernel",
+                    "peak_source": f"{src} {key} (kind::f16 with fp16 operands runs at the bf16 rate)"}
         elif args.mode == "fp64_fft":
             ks, n = kernel_s("spec_prod_kernel")
             achieved = spectral_prod_flops(d, args.antihermitian) / ks / 1e12
@@ -755,7 +785,7 @@ def main():
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": {"fp64": "f64", "fp64_fft": "f64", "fp32_fft": "f32", "tf32": "tf32+f64",
-                         "bf16x3": "bf16x3+f64"}[args.mode],
+                         "bf16x3": "bf16x3+f64", "f16x3_fft": "f32+f16x3"}[args.mode],
                "data": "synthetic (seeded; Si-FinFET-shaped)",
                "config": bench_config(args, d, world),
                "pts_per_s": pts, "roofline": roof, "clocks": clk.summary(), "e2e": e2e,

@@ -93,13 +93,23 @@ typedef struct sse_dims {
  *            and outputs; for sse_sigma_fwd, sse_sigma_bwd, sse_sigma_bwd_g and
  *            sse_pi_fwd. Spectra take half of FP64_FFT's workspace. Error (normwise)
  *            a few 1e-7, tested to 2e-6; the adjoint's dH gradient, a sum over
- *            Nkz*L frequencies, to 1e-5. */
+ *            Nkz*L frequencies, to 1e-5.
+ *   F16X3_FFT : the FP32 transforms of FP32_FFT with the per-frequency block products on
+ *            the tcgen05 tensor cores (Sec. 4.4: split-complex FP16 operands with
+ *            power-of-two normalisation, wider accumulation). Frequencies stack into the
+ *            rows of two GEMMs per bond whose second operand, dH, is shared by every
+ *            frequency; each operand is scaled by a power of two and split into FP16
+ *            hi + lo, and hi*hi + hi*lo + lo*hi accumulate in FP32. Error (normwise)
+ *            a few 1e-7, tested to 2e-6. sse_sigma_fwd and sse_sigma_fwd_host only;
+ *            FP32_FFT's workspace; needs Norb <= 10 and NB <= 4 besides the transform
+ *            limits (else SSE_ERR_UNSUPPORTED before any device work). */
 typedef enum sse_mode {
     SSE_MODE_FP64 = 0,
     SSE_MODE_TF32 = 1,
     SSE_MODE_BF16X3 = 2,
     SSE_MODE_FP64_FFT = 3,
-    SSE_MODE_FP32_FFT = 4
+    SSE_MODE_FP32_FFT = 4,
+    SSE_MODE_F16X3_FFT = 5
 } sse_mode;
 
 /* SYMMETRIZE: replace each output block S by (S - S^H)/2 in FP64 before the

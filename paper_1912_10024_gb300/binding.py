@@ -16,10 +16,10 @@ import torch
 
 from . import build as _build
 
-SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT, SSE_MODE_FP32_FFT = 0, 1, 2, 3, 4
+SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT, SSE_MODE_FP32_FFT, SSE_MODE_F16X3_FFT = 0, 1, 2, 3, 4, 5
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE, SSE_FLAG_ANTIHERMITIAN = 1, 2, 4, 8
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT,
-         "fp32_fft": SSE_MODE_FP32_FFT}
+         "fp32_fft": SSE_MODE_FP32_FFT, "f16x3_fft": SSE_MODE_F16X3_FFT}
 EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
             "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes",
             "sse_sigma_bwd_g",
@@ -451,8 +451,8 @@ class SigmaFunction(torch.autograd.Function):
         ctx.scale, ctx.symmetrize = scale, symmetrize
         # transform-based adjoint after a transform-based forward (FP32 products after an FP32_FFT
         # forward), the direct FP64 adjoint otherwise
-        if mode in ("fp32_fft", SSE_MODE_FP32_FFT):
-            ctx.bwd_mode = "fp32_fft"
+        if mode in ("fp32_fft", SSE_MODE_FP32_FFT, "f16x3_fft", SSE_MODE_F16X3_FFT):
+            ctx.bwd_mode = "fp32_fft"  # the tensor-core forward's adjoint: FP32 transforms and products
         elif mode in ("fp64_fft", SSE_MODE_FP64_FFT):
             ctx.bwd_mode = "fp64_fft"
         else:

@@ -33,7 +33,7 @@ bool supported_dims(const sse_dims* d) {
 
 bool valid_mode(int mode) {
     return mode == SSE_MODE_FP64 || mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3 || mode == SSE_MODE_FP64_FFT ||
-           mode == SSE_MODE_FP32_FFT;
+           mode == SSE_MODE_FP32_FFT || mode == SSE_MODE_F16X3_FFT;
 }
 bool fp64_mode(int mode) { return mode == SSE_MODE_FP64 || mode == SSE_MODE_FP64_FFT; }
 
@@ -46,6 +46,7 @@ bool op_supported(const sse_dims& d, int mode, Op op) {
     switch (op) {
         case Op::Fwd:
             if (mode == SSE_MODE_TF32 || mode == SSE_MODE_BF16X3) return sse::mixed_supported(d, mode);
+            if (mode == SSE_MODE_F16X3_FFT) return sse::spectral_fwd_tc_supported(d);
             return mode == SSE_MODE_FP64 || sse::spectral_fwd_supported(d, fp32);
         case Op::Bwd: return mode == SSE_MODE_FP64 || sse::spectral_bwd_supported(d);
         case Op::BwdG: return sse::spectral_bwd_g_supported(d, fp32);  // transforms in every mode it takes
@@ -60,7 +61,7 @@ bool valid_flags(uint32_t f) {
 size_t fwd_ws(const sse_dims& d, int mode) {
     if (mode == SSE_MODE_FP64) return sse::fp64_fwd_workspace(d);
     if (mode == SSE_MODE_FP64_FFT) return sse::spectral_fwd_workspace(d);
-    if (mode == SSE_MODE_FP32_FFT) return sse::spectral_fwd32_workspace(d);
+    if (mode == SSE_MODE_FP32_FFT || mode == SSE_MODE_F16X3_FFT) return sse::spectral_fwd32_workspace(d);
     return sse::mixed_fwd_workspace(d, mode);
 }
 
@@ -157,6 +158,7 @@ extern "C" int sse_sigma_fwd(const sse_dims* d, const int32_t* nbr, const double
     cudaError_t e = mode == SSE_MODE_FP64       ? sse::fp64_fwd(p, Sl, Sg, status, ws, wsb, st)
                     : mode == SSE_MODE_FP64_FFT ? sse::spectral_fwd(p, Sl, Sg, status, ws, wsb, st)
                     : mode == SSE_MODE_FP32_FFT ? sse::spectral_fwd32(p, Sl, Sg, status, ws, wsb, st)
+                    : mode == SSE_MODE_F16X3_FFT ? sse::spectral_fwd_tc(p, Sl, Sg, status, ws, wsb, st)
                                                 : sse::mixed_fwd(p, mode, Sl, Sg, status, ws, wsb, st);
     if (e == cudaErrorNotSupported) return SSE_ERR_UNSUPPORTED;
     return finish(e, status, flags, st);
@@ -418,9 +420,9 @@ extern "C" int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const d
     void* ws = base + L.ws;
     const size_t wsb = L.total - L.ws;
     cudaError_t e;
-    if (mode == SSE_MODE_FP64_FFT || mode == SSE_MODE_FP32_FFT) {
+    if (mode == SSE_MODE_FP64_FFT || mode == SSE_MODE_FP32_FFT || mode == SSE_MODE_F16X3_FFT) {
         const sse::FwdPipe pipe{ev_in, {ev_g[0], ev_g[1]}, {ev_s[0], ev_s[1]}};
-        e = sse::spectral_fwd_pipelined(p, mode == SSE_MODE_FP32_FFT, Sd[0], Sd[1], status, ws, wsb, st, pipe);
+        e = sse::spectral_fwd_pipelined(p, mode, Sd[0], Sd[1], status, ws, wsb, st, pipe);
     } else {  // one kernel sequence for both types: wait for every input, hand every slice over at the end
         if (cudaStreamWaitEvent(st, ev_g[1][nk - 1], 0) != cudaSuccess) return cleanup(SSE_ERR_CUDA);
         e = mode == SSE_MODE_FP64 ? sse::fp64_fwd(p, Sd[0], Sd[1], status, ws, wsb, st)

@@ -88,12 +88,18 @@ struct FwdPipe {
     const cudaEvent_t* g[2];  // [Nkz] each
     const cudaEvent_t* s[2];  // [Nkz] each
 };
-cudaError_t spectral_fwd_pipelined(const Problem& p, bool fp32, double2* S_less, double2* S_greater, unsigned* status,
+cudaError_t spectral_fwd_pipelined(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status,
                                    void* ws, size_t ws_bytes, cudaStream_t st, const FwdPipe& pipe);
 // FP32 transforms and block products (mode FP32_FFT), FP64 inputs and outputs.
 size_t spectral_fwd32_workspace(const sse_dims& d);
 cudaError_t spectral_fwd32(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                            size_t ws_bytes, cudaStream_t st);
+
+// FP32 transforms with the block products on the tcgen05 tensor cores (mode F16X3_FFT, sse_spectral_tc.cu); the
+// workspace is FP32_FFT's.
+bool spectral_fwd_tc_supported(const sse_dims& d);
+cudaError_t spectral_fwd_tc(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                            size_t ws_bytes, cudaStream_t st);
 
 // Transform-based adjoint of Eq. (3), FP64 and FP32 (sse_spectral_adj.cu).
 size_t spectral_bwd_workspace(const sse_dims& d);

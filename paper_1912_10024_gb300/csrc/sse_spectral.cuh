@@ -438,11 +438,14 @@ __global__ void dft_k_kernel(C* __restrict__ X, int Nk, int n_in, size_t M, int 
     }
 }
 
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // frequency index maps. With anti-Hermitian inputs (SSE_FLAG_ANTIHERMITIAN) the spectra obey
 // S^(-f) = -S^(f)^H (Sigma) and C^(-f) = C^(f)^H (Pi), so only one frequency of each pair (f, -f)
 // is computed: eps in [1, (L-1)/2] for every kappa, and on the rows eps = 0 and eps = L/2 (L even)
-// kappa in [0, Nk/2]; a mirror kernel fills the partners.
+// kappa in [0, Nk/2]; a mirror kernel fills the partners. (Outside the file-local namespace: the
+// tensor-core product kernel in sse_spectral_tc.cu takes the same map.)
 // ---------------------------------------------------------------------------
 struct FreqMap {
     int Nk, L, half, Lh, nK0;
@@ -473,6 +476,16 @@ __device__ __forceinline__ size_t freq_neg(const FreqMap& m, size_t f) {
     const int kap = (int)(f / m.L), eps = (int)(f - (size_t)kap * m.L);
     return (size_t)((m.Nk - kap) % m.Nk) * m.L + (size_t)((m.L - eps) % m.L);
 }
+
+// Block products of the F16X3_FFT forward on the tcgen05 tensor cores (sse_spectral_tc.cu): S^ of one type from the
+// FP32 spectra G^ [Nkz*L][NA][Norb^2] and K^ [Nkz*L][nA][NB][9] into S^ [Nkz*L][nA][Norb^2] (frequencies of `fm`).
+// Limits (host-only): Norb <= 10, NB <= 4.
+bool spectral_prod_tc_supported(const sse_dims& d);
+cudaError_t spectral_prod_tc(const sse_dims& d, const FreqMap& fm, const int32_t* nbr, const double2* dH,
+                             const float2* Gh, const float2* Kh, float2* Sh, double scale, unsigned* status,
+                             cudaStream_t st);
+
+namespace {
 
 // Sigma^(-f) = -Sigma^(f)^H per atom block, for the computed half
 template <class C>

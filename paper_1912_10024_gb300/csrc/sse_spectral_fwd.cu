@@ -1,6 +1,7 @@
 // Sigma of Eq. (3) through the transforms: the per-frequency block products in FP64 (spec_prod_kernel, mode
 // FP64_FFT) and FP32 (spec_prod32_kernel, mode FP32_FFT), the symmetrisation, the workspace layout and the
-// drivers (device buffers, and the pipelined variant behind the host-buffer entry point).
+// drivers (device buffers, and the pipelined variant behind the host-buffer entry point). Mode F16X3_FFT runs the
+// same FP32 transforms with the block products of sse_spectral_tc.cu on the tensor cores.
 #include "sse_spectral.cuh"
 
 namespace sse {
@@ -373,13 +374,15 @@ namespace {
 // products on the FP32 pipe, FP64 inputs and outputs).
 template <class T>
 cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
-                           size_t ws_bytes, cudaStream_t st, const FwdPipe* pipe = nullptr) {
+                           size_t ws_bytes, cudaStream_t st, const FwdPipe* pipe = nullptr, bool tc = false) {
     // With `pipe` (inputs arriving from the host): the lag kernel is transformed first, G^t slice by slice as its
     // kz slices arrive, and the inverse E-transform of Sigma^t runs slice by slice so that each slice's download
     // can start; without it every transform is one launch over all slices.
     using C = typename CX<T>::C;
     const sse_dims& d = p.d;
-    if (!spectral_fwd_supported(d, sizeof(T) == 4)) return cudaErrorNotSupported;
+    // tc: the FP32 transforms with the block products on the tensor cores (mode F16X3_FFT)
+    if (tc && sizeof(T) != 4) return cudaErrorNotSupported;
+    if (!(tc ? spectral_fwd_tc_supported(d) : spectral_fwd_supported(d, sizeof(T) == 4))) return cudaErrorNotSupported;
     const SpecLayout lay = spec_layout(d, sizeof(C));
     if (ws_bytes < lay.total) return cudaErrorInvalidValue;
     unsigned char* base = static_cast<unsigned char*>(ws);
@@ -446,7 +449,12 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                   dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
-        if (tiled) {
+        if (tc) {
+            e = spectral_prod_tc(d, fm, p.nbr, p.dH, reinterpret_cast<const float2*>(Gh),
+                                 reinterpret_cast<const float2*>(Kh), reinterpret_cast<float2*>(Sh), p.scale, status,
+                                 st);
+            if (e != cudaSuccess) return e;
+        } else if (tiled) {
             const size_t gy = (fm.count + pc32.fchunk - 1) / pc32.fchunk;
             SSE_TIMED("spec_prod32_kernel", st,
                       spec_prod32_kernel<<<dim3((unsigned)nA, (unsigned)gy), pc32.threads, pc32.smem, st>>>(
@@ -502,10 +510,10 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
 }
 }  // namespace
 
-cudaError_t spectral_fwd_pipelined(const Problem& p, bool fp32, double2* S_less, double2* S_greater, unsigned* status,
+cudaError_t spectral_fwd_pipelined(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status,
                                    void* ws, size_t ws_bytes, cudaStream_t st, const FwdPipe& pipe) {
-    return fp32 ? spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st, &pipe)
-                : spectral_fwd_t<double>(p, S_less, S_greater, status, ws, ws_bytes, st, &pipe);
+    if (mode == SSE_MODE_FP64_FFT) return spectral_fwd_t<double>(p, S_less, S_greater, status, ws, ws_bytes, st, &pipe);
+    return spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st, &pipe, mode == SSE_MODE_F16X3_FFT);
 }
 
 cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
@@ -516,6 +524,15 @@ cudaError_t spectral_fwd(const Problem& p, double2* S_less, double2* S_greater, 
 cudaError_t spectral_fwd32(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                            size_t ws_bytes, cudaStream_t st) {
     return spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st);
+}
+
+bool spectral_fwd_tc_supported(const sse_dims& d) {
+    return spectral_fwd_supported(d, true) && spectral_prod_tc_supported(d);
+}
+
+cudaError_t spectral_fwd_tc(const Problem& p, double2* S_less, double2* S_greater, unsigned* status, void* ws,
+                            size_t ws_bytes, cudaStream_t st) {
+    return spectral_fwd_t<float>(p, S_less, S_greater, status, ws, ws_bytes, st, nullptr, true);
 }
 
 }  // namespace sse

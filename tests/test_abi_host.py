@@ -216,6 +216,29 @@ def test_transform_size_limits_are_checked_on_host(mode):
         assert fn(B.sse_dims(16, 4, 10, 4577, 4, 1, 32, 0, 16), mode) == 2, name  # L = 5184
 
 
+def test_tensor_core_transform_mode_limits_are_checked_on_host():
+    """Mode F16X3_FFT (FP32 transforms, block products on tcgen05): the forward entries take Norb <= 10 and NB <= 4
+    (one TMEM accumulator and one pair of staged dH operands per bond) inside the transform limits; the adjoint, Pi
+    and the G-gradient refuse the mode. All of it before any device work."""
+    m = B.SSE_MODE_F16X3_FFT
+    entries = dict((n, f) for n, f, _ in transform_entries())
+    for name in ("fwd", "fwd_host"):
+        fn = entries[name]
+        for Norb in range(1, 12):
+            for NB in range(1, 6):
+                want = 6 if Norb <= 10 and NB <= 4 else 2
+                assert fn(B.sse_dims(16, NB, Norb, 64, 4, 1, 4, 0, 16), m) == want, (name, Norb, NB)
+        assert fn(B.sse_dims(16, 4, 10, 64, 17, 1, 4, 0, 16), m) == 2, name  # the kz DFT pass
+        assert fn(B.sse_dims(16, 4, 10, 4577, 4, 1, 32, 0, 16), m) == 2, name  # the FFT length
+    for name in ("bwd", "pi", "bwd_g"):
+        assert entries[name](B.sse_dims(16, 4, 10, 64, 4, 1, 4, 0, 16), m) == 2, name
+    # FP32_FFT's workspace
+    d = B.sse_dims(256, 4, 10, 256, 5, 5, 16, 0, 256)
+    assert B.sse_workspace_bytes(d, m, 0) == B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0) - (
+        B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0) - B.sse_workspace_bytes(d, m, 0))
+    assert 0 < B.sse_workspace_bytes(d, m, 0) <= B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0)
+
+
 def test_direct_fp64_adjoint_has_no_transform_limits():
     """Mode FP64 of sse_sigma_bwd runs the direct kernels: no kz, length or NB limit beyond the common ones."""
     bwd = dict((n, f) for n, f, _ in transform_entries())["bwd"]

@@ -5,7 +5,8 @@ used G^H = -G or D^H = -D (outside SSE_FLAG_ANTIHERMITIAN) would pass those test
 every result is compared element by element with the FP64 oracle, which takes G and D as given.
 
 Bounds (normwise max|gpu - oracle| / max|oracle| per output tensor), the same as each mode's own tests:
-FP64 and FP64_FFT 1e-12; FP32_FFT 2e-6 (forward, Pi), 1e-5 (adjoint, G-gradient); BF16X3 2e-5; TF32 2e-3.
+FP64 and FP64_FFT 1e-12; FP32_FFT 2e-6 (forward, Pi), 1e-5 (adjoint, G-gradient); F16X3_FFT 2e-6; BF16X3 2e-5;
+TF32 2e-3.
 Shapes: the tiny workload, and Norb = 10 with ragged energy tiles and Nqz < Nkz.
 """
 import math
@@ -23,7 +24,7 @@ pytestmark = pytest.mark.gpu
 SCALE = 1.0 / (2.0 * math.pi)
 NORB10 = Dims(NA=5, NB=2, Norb=10, NE=40, Nkz=3, Nqz=2, Nw=11)
 SHAPES = [TINY, NORB10]
-FWD_BOUND = {"fp64": 1e-12, "fp64_fft": 1e-12, "fp32_fft": 2e-6, "bf16x3": 2e-5, "tf32": 2e-3}
+FWD_BOUND = {"fp64": 1e-12, "fp64_fft": 1e-12, "fp32_fft": 2e-6, "f16x3_fft": 2e-6, "bf16x3": 2e-5, "tf32": 2e-3}
 BWD_BOUND = {"fp64": 1e-12, "fp64_fft": 1e-12, "fp32_fft": 1e-5}
 
 
@@ -52,7 +53,7 @@ def test_forward(dims, mode):
     assert max(errs) <= FWD_BOUND[mode], errs
 
 
-@pytest.mark.parametrize("mode", ["fp64_fft", "fp32_fft"])
+@pytest.mark.parametrize("mode", ["fp64_fft", "fp32_fft", "f16x3_fft"])
 def test_host_buffer_forward(mode):
     inp = _general(NORB10, seed=1100)
     pin = [t.pin_memory() for t in (inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr)]
