@@ -15,11 +15,11 @@
 // A 128-row tile holds four 32-row groups of FG = 32 / Norb frequencies each (12 frequencies at Norb = 10), so that
 // every frequency's rows lie in one warp's TMEM lane quarter.
 //
-// Precision: every operand x is scaled by a power of two (per 32-row group for the frequency-stacked operands, per
-// bond for dH; exact, undone in the epilogue) and split into FP16 hi = fp16(x), lo = fp16(x - hi); each GEMM runs
-// as hi x [B_hi | B_lo] (one MMA with N doubled) + lo x B_hi, so one FP32 accumulation holds hi*hi + lo*hi and
-// another hi*lo (lo*lo, ~2^-22 relative, is dropped). The result carries about 22 significant bits, the level of
-// the FP32 transforms around it.
+// Precision: every operand x is scaled by a power of two (per 32-row group, or per warp, for the frequency-stacked
+// operands, per bond for dH; exact, undone in the epilogue) and split into FP16 hi = fp16(x), lo = fp16(x - hi).
+// GEMM1 accumulates hi*B_hi + lo*B_hi + hi*B_lo in one FP32 accumulator; GEMM2 runs as hi x [B_hi | B_lo] (one MMA
+// with N doubled) + lo x B_hi, two accumulators that the epilogue adds. lo*lo (~2^-22 relative) is dropped; the
+// result carries about 22 significant bits, the level of the FP32 transforms around it.
 //
 // Roles (one persistent CTA per SM, 13 warps):
 //   warps 0-7   epilogue: two warps per TMEM lane quarter, each half of the columns. Per bond: P from TMEM, the
@@ -47,6 +47,7 @@ constexpr int kTcProd0 = kTcEpiWarps * 32;  // first producer thread
 constexpr int kTcMaxNB = 4;                 // GEMM2 accumulators: one TMEM slot per bond
 constexpr int kTcTilesPerItem = 8;          // frequency tiles per work item (the dH operands are staged per item)
 constexpr int kTcExpTarget = 13;            // scaled operands have max |x| in [2^13, 2^14): FP16 holds up to 65504
+constexpr int kTcRaw = 3;                   // raw stages: the producers copy up to two units ahead (cp.async)
 
 template <int NORB>
 struct TcShape {
@@ -54,6 +55,9 @@ struct TcShape {
     static constexpr int FT = 4 * FG;                       // frequencies per 128-row tile
     static constexpr int R = FG * NORB;                     // used rows per group
     static constexpr int CD = (NORB + 3) / 4;               // 16-B chunks of one G^ row (4 complex each)
+    static constexpr int KPL = (FG * 9 + 31) / 32;          // K^ entries per producer lane (group of FG frequencies)
+    static constexpr int RAW_G = FG * NORB * NORB + FG * 9;  // float2 per group and raw stage: G^ blocks, then K^
+    static constexpr int RAW_STAGE = 4 * RAW_G * 8;          // bytes per raw stage (four groups)
     static constexpr int K1 = (2 * NORB + 15) / 16 * 16;    // GEMM1 K (fp16 elements)
     static constexpr int C1 = K1 / 8;                       // 16-B K chunks of GEMM1's operands
     static constexpr int N1 = (6 * NORB + 15) / 16 * 16;    // GEMM1 N of one part (hi or lo of dH)
@@ -68,7 +72,7 @@ struct TcShape {
     static constexpr int A1_PLANE = C1 * LA1, A1_STAGE = 2 * A1_PLANE;
     static constexpr int A2_PLANE = C2 * LA2, A2_STAGE = 2 * A2_PLANE;
     static constexpr int B1_BOND = C1 * LB1, B2_BOND = C2 * LB2;
-    static constexpr int TM_P = 2 * N1;                     // TMEM columns per P buffer (two)
+    static constexpr int TM_P = N1;                         // TMEM columns per P buffer (two)
     static constexpr int TM_O = 2 * N2;                     // TMEM columns per bond accumulator
 };
 
@@ -78,7 +82,7 @@ enum { BA1F = 0, BA1E = 2, BPF = 4, BPE = 6, BA2F = 8, BA2E = 10, BXE = 12, BOF 
 
 struct TcCfg {
     int NB, nA, ntiles, ngroups, nitems;
-    int off_A1, off_A2, off_B1, off_B2, off_bar, off_x, smem, tmem_cols;
+    int off_A1, off_A2, off_B1, off_B2, off_K, off_raw, off_bar, off_x, smem, tmem_cols;
 };
 
 template <int NORB>
@@ -94,11 +98,13 @@ TcCfg make_tc_cfg(const sse_dims& d, size_t nfreq) {
     c.off_A2 = c.off_A1 + 2 * S::A1_STAGE;
     c.off_B1 = c.off_A2 + 2 * S::A2_STAGE;
     c.off_B2 = c.off_B1 + d.NB * S::B1_BOND;
-    c.off_bar = c.off_B2 + d.NB * S::B2_BOND;
+    c.off_K = c.off_B2 + d.NB * S::B2_BOND;  // K^ of the tile's frequencies, two stages: [2][FT][9] float2
+    c.off_raw = c.off_K + 2 * S::FT * 9 * 8;  // raw FP32 G^ and K^ of the next units: [kTcRaw][4][RAW_G] float2
+    c.off_bar = c.off_raw + kTcRaw * S::RAW_STAGE;
     c.off_x = c.off_bar + kTcBars * 8;
-    // exchange area: exponent ring [2][8] int, bond exponents [16] int, producer maxima [4] float,
-    // epilogue pair maxima [2][4][2] float, TMEM base, abort flag
-    c.smem = c.off_x + (16 + 16 + 4 + 16 + 2) * 4;
+    // exchange area: exponent ring [2][8] int, bond exponents [16] int, producer maxima [2][4][4] float,
+    // GEMM2 operand exponents [2][4][4][2] int, TMEM base, abort flag
+    c.smem = c.off_x + (16 + 16 + 32 + 64 + 2) * 4;
     const int cols = 2 * S::TM_P + d.NB * S::TM_O;
     c.tmem_cols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
     return c;
@@ -153,17 +159,25 @@ __device__ __forceinline__ float warp_max_abs(float m) {  // max over the warp o
     return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m)));
 }
 
-// Exponent e that brings max |x| into [2^13, 2^14); 0 for an all-zero (or non-finite) group.
+// Exponent e that brings max |x| into [2^13, 2^14) (m = max |x| >= 0, read from its bits: floor(log2 m) is the
+// unbiased exponent of a normal float, 31 - clz - 149 of a subnormal); 0 for an all-zero or non-finite group.
 __device__ __forceinline__ int scale_exp(float m) {
-    if (!(m > 0.f) || !isfinite(m)) return 0;
-    return kTcExpTarget - floor_log2(m);
+    const uint32_t b = __float_as_uint(m);
+    const int ex = (int)(b >> 23);
+    if (b == 0u || ex >= 255) return 0;
+    const int lg = ex > 0 ? ex - 127 : (31 - __clz((int)b)) - 149;
+    return kTcExpTarget - lg;
 }
-// x * 2^e for |e| <= 252 (two exact power-of-two factors, each a normal float).
-__device__ __forceinline__ float mul_pow2(float x, int e) {
+// 2^e as two normal floats (a * b == 2^e exactly for |e| <= 252): computed once per scale, two FMULs per value.
+struct Pow2 {
+    float a, b;
+};
+__device__ __forceinline__ Pow2 pow2_factors(int e) {
     const int e1 = max(-126, min(127, e));
     const int e2 = max(-126, min(127, e - e1));
-    return x * __int_as_float((e1 + 127) << 23) * __int_as_float((e2 + 127) << 23);
+    return {__int_as_float((e1 + 127) << 23), __int_as_float((e2 + 127) << 23)};
 }
+__device__ __forceinline__ float scaled(float x, Pow2 f) { return x * f.a * f.b; }
 
 // (a, b) -> packed fp16 pairs hi = fp16(.), lo = fp16(. - hi); element a in the low half (the lower K index).
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
@@ -177,6 +191,14 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
+// 8-byte asynchronous copy global -> shared; with pred false the destination is zero-filled (nothing is read).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool pred) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(pred ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void st_shared_b32(uint32_t addr, uint32_t x) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(x) : "memory");
 }
@@ -196,9 +218,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     auto B_ = [&](int i) { return bars + 8u * (uint32_t)i; };
     int* xr = reinterpret_cast<int*>(smem + c.off_x);           // [2][8]: e1 of the four groups, eH of the bond
     int* ehs = xr + 16;                                          // [16] bond exponents of the current item
-    float* pmax = reinterpret_cast<float*>(ehs + 16);            // [4] producer warp maxima
-    float* xmax = pmax + 4;                                      // [2][4][2] epilogue pair maxima
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xmax + 16);
+    float* pmax = reinterpret_cast<float*>(ehs + 16);            // [2 items][4 warps][4 bonds] producer maxima
+    int* e2s = reinterpret_cast<int*>(pmax + 32);                // [2 tiles][4 bonds][4 groups][2 halves] GEMM2 A scales
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(e2s + 64);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int NB = c.NB, nA = c.nA;
 
@@ -235,44 +257,158 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp >= kTcEpiWarps && warp < kTcMmaWarp) {
         // ------------------------------------------------------------------ producers
         const int g = warp - kTcEpiWarps, pt = tid - kTcProd0;
+        float2* ks = reinterpret_cast<float2*>(smem + c.off_K);  // [2][FT][9]
         uint32_t u = 0;
         int nitem = 0;
+        // One unit (tile, bond) of this warp's row group: the G^ blocks of the group's FG frequencies and their K^
+        // entries, copied raw (FP32) into a ring of kTcRaw stages up to two units ahead of their use.
+        int bnb[kTcMaxNB] = {-1, -1, -1, -1};  // the item's neighbours (loaded once per item)
+        const float2* raw = reinterpret_cast<const float2*>(smem + c.off_raw);
+        auto issue_unit = [&](int la, int tile, int s, int rs) {
+            int b = bnb[0];
+#pragma unroll
+            for (int t4 = 1; t4 < kTcMaxNB; ++t4)
+                if (t4 == s) b = bnb[t4];
+            const bool bok = b >= 0 && b < d.NA;
+            // lane l < FG: the frequency of the group's l-th row block (shared by shuffles below)
+            const size_t fi_l = (size_t)tile * S::FT + g * S::FG + lane;
+            const bool ok_l = bok && lane < S::FG && fi_l < fm.count;
+            const unsigned long long f_l = ok_l ? (unsigned long long)freq_of(fm, fi_l) : ~0ull;
+            const uint32_t dst = sbase + (uint32_t)(c.off_raw + rs * S::RAW_STAGE + g * S::RAW_G * 8);
+#pragma unroll
+            for (int it = 0; it < (S::FG * nel + 31) / 32; ++it) {
+                const int idx = lane + 32 * it, fl = idx / nel, e = idx - fl * nel;
+                const unsigned long long f = __shfl_sync(0xffffffffu, f_l, fl < S::FG ? fl : 0);
+                const bool ok = idx < S::FG * nel && f != ~0ull;
+                if (idx < S::FG * nel)
+                    cp_async8(dst + (uint32_t)idx * 8, ok ? Ghat + ((size_t)f * d.NA + b) * nel + e : Ghat, ok);
+            }
+#pragma unroll
+            for (int it = 0; it < S::KPL; ++it) {
+                const int idx = lane + 32 * it, fl = idx / 9, ij = idx - fl * 9;
+                const unsigned long long f = __shfl_sync(0xffffffffu, f_l, fl < S::FG ? fl : 0);
+                const bool ok = idx < S::FG * 9 && f != ~0ull;
+                if (idx < S::FG * 9)
+                    cp_async8(dst + (uint32_t)(S::FG * nel + idx) * 8,
+                              ok ? Khat + (((size_t)f * nA + la) * NB + s) * 9 + ij : Khat, ok);
+            }
+            cp_async_commit();
+            if (!bok && pt == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
+        };
+        auto produce = [&](int s, int rs) {
+            const int st = (int)(u & 1);
+            const uint32_t par = ((u >> 1) & 1) ^ 1;
+            wait_or_abort(B_(BA1E + st), par, abort_flag, status);  // GEMM1 has read the stage
+            wait_or_abort(B_(BXE + st), par, abort_flag, status);   // the epilogue has read its exponents and K^
+            const float2* rg = raw + (size_t)rs * (S::RAW_STAGE / 8) + g * S::RAW_G;
+            float v[S::CD][8];
+            float m = 0.f;
+#pragma unroll
+            for (int it = 0; it < S::CD; ++it) {
+                const int task = lane + 32 * it;
+                const int ch = task / S::R, row = task - ch * S::R;
+                const int fp = row / NORB, mr = row - fp * NORB;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int l = 4 * ch + q;
+                    float2 x = make_float2(0.f, 0.f);
+                    if (ch < S::CD && l < NORB) x = rg[fp * nel + mr * NORB + l];
+                    v[it][2 * q] = x.x;
+                    v[it][2 * q + 1] = x.y;
+                    m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+                }
+            }
+            const int e1 = scale_exp(warp_max_abs(m));
+            const Pow2 f1 = pow2_factors(e1);
+            const uint32_t a1 = sbase + (uint32_t)(c.off_A1 + st * S::A1_STAGE);
+#pragma unroll
+            for (int it = 0; it < S::CD; ++it) {
+                const int task = lane + 32 * it;
+                const int ch = task / S::R, row = task - ch * S::R;
+                if (ch < S::CD) {
+                    uint32_t h[4], lo[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        split2(scaled(v[it][2 * q], f1), scaled(v[it][2 * q + 1], f1), h[q], lo[q]);
+                    const uint32_t o = a1 + (uint32_t)ch * S::LA1 + (uint32_t)(32 * g + row) * 16;
+                    st_shared_v4(o, h[0], h[1], h[2], h[3]);
+                    st_shared_v4(o + S::A1_PLANE, lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < S::KPL; ++r) {
+                const int idx = lane + 32 * r;
+                if (idx < S::FG * 9) ks[(st * S::FT + g * S::FG) * 9 + idx] = rg[S::FG * nel + idx];
+            }
+            if (lane == 0) xr[st * 8 + g] = e1;
+            if (pt == 0) xr[st * 8 + 4] = ehs[s];
+            fence_async_smem();
+            mbar_arrive(B_(BA1F + st));
+            ++u;
+        };
+        uint32_t ru = 0;  // units copied into the raw ring
         for (int item = blockIdx.x; item < c.nitems; item += gridDim.x, ++nitem) {
             const int la = item % nA, tg = item / nA;
             const int a = d.a_begin + la;
-            // dH operands of every bond of the atom, once the MMAs of the previous item are done with them
-            if (nitem > 0) wait_or_abort(B_(BBE), (nitem - 1) & 1, abort_flag, status);
-            for (int s = 0; s < NB; ++s) {
-                const double2* A = dH + ((size_t)a * NB + s) * 3 * nel;
-                float m = 0.f;
-                for (int i = pt; i < 3 * nel; i += kTcProdWarps * 32) {
-                    const double2 v = A[i];
-                    m = fmaxf(m, fmaxf(fabsf((float)v.x), fabsf((float)v.y)));
+            const int j0 = tg * kTcTilesPerItem, j1 = min(j0 + kTcTilesPerItem, c.ntiles);
+            const int units = (j1 - j0) * NB;
+#pragma unroll
+            for (int t4 = 0; t4 < kTcMaxNB; ++t4) bnb[t4] = t4 < NB ? nbr[(size_t)a * NB + t4] : -1;
+            const uint32_t r0 = ru;  // raw slot of the item's first unit
+            for (int v = 0; v < 2 && v < units; ++v, ++ru)  // in flight during the dH staging below
+                issue_unit(la, j0 + v / NB, v % NB, (int)(ru % kTcRaw));
+            // dH operands of every bond of the atom (all loads issued at once), once the MMAs of the previous item
+            // are done with them
+            constexpr int RPT = (3 * nel + kTcProdWarps * 32 - 1) / (kTcProdWarps * 32);
+            double2 hv[kTcMaxNB][RPT];
+            float hm[kTcMaxNB];
+#pragma unroll
+            for (int t4 = 0; t4 < kTcMaxNB; ++t4) {
+                hm[t4] = 0.f;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int i = pt + r * kTcProdWarps * 32;
+                    hv[t4][r] = (t4 < NB && i < 3 * nel) ? dH[((size_t)a * NB + t4) * 3 * nel + i]
+                                                          : make_double2(0.0, 0.0);
                 }
-                m = warp_max_abs(m);
-                if (lane == 0) pmax[g] = m;
-                named_bar(2, kTcProdWarps * 32);
-                m = fmaxf(fmaxf(pmax[0], pmax[1]), fmaxf(pmax[2], pmax[3]));
-                const int eH = scale_exp(m);
-                if (pt == 0) ehs[s] = eH;
-                named_bar(2, kTcProdWarps * 32);  // pmax is free again
-                const uint32_t b1 = sbase + (uint32_t)(c.off_B1 + s * S::B1_BOND);
-                const uint32_t b2 = sbase + (uint32_t)(c.off_B2 + s * S::B2_BOND);
-                for (int i = pt; i < 3 * nel; i += kTcProdWarps * 32) {
+            }
+#pragma unroll
+            for (int t4 = 0; t4 < kTcMaxNB; ++t4) {
+#pragma unroll
+                for (int r = 0; r < RPT; ++r)
+                    hm[t4] = fmaxf(hm[t4], fmaxf(fabsf((float)hv[t4][r].x), fabsf((float)hv[t4][r].y)));
+                hm[t4] = warp_max_abs(hm[t4]);
+                if (lane == 0) pmax[((nitem & 1) * 4 + g) * 4 + t4] = hm[t4];  // two item buffers, no reuse race
+            }
+            if (nitem > 0) wait_or_abort(B_(BBE), (nitem - 1) & 1, abort_flag, status);
+            named_bar(2, kTcProdWarps * 32);  // the four warps' maxima are in place
+#pragma unroll
+            for (int t4 = 0; t4 < kTcMaxNB; ++t4) {
+                if (t4 >= NB) break;
+                const float* pm = pmax + (nitem & 1) * 16 + t4;
+                const int eH = scale_exp(fmaxf(fmaxf(pm[0], pm[4]), fmaxf(pm[8], pm[12])));
+                if (pt == 0) ehs[t4] = eH;
+                const Pow2 fH = pow2_factors(eH);
+                const uint32_t b1 = sbase + (uint32_t)(c.off_B1 + t4 * S::B1_BOND);
+                const uint32_t b2 = sbase + (uint32_t)(c.off_B2 + t4 * S::B2_BOND);
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int i = pt + r * kTcProdWarps * 32;
+                    if (i >= 3 * nel) break;
                     const int j = i / nel, e = i - j * nel, n = e / NORB, l = e - n * NORB;
-                    const double2 v = A[i];  // dH_j[n][l]
-                    const float hr = mul_pow2((float)v.x, eH), hi = mul_pow2((float)v.y, eH);
+                    const double2 v = hv[t4][r];  // dH_j[n][l]
+                    const float hr = scaled((float)v.x, fH), hi = scaled((float)v.y, fH);
                     uint32_t h0, l0, h1, l1;
                     // GEMM1 B = dH_j^H in the real embedding: column (j, n, re) holds (Hr, Hi) at K = (l, re/im),
                     // column (j, n, im) holds (-Hi, Hr); hi rows first, lo rows after N1
-                    const int r = j * 2 * NORB + 2 * n;
+                    const int rr = j * 2 * NORB + 2 * n;
                     const uint32_t k1 = (uint32_t)((2 * l) >> 3) * S::LB1 + (uint32_t)((2 * l) & 7) * 2;
                     split2(hr, hi, h0, l0);
                     split2(-hi, hr, h1, l1);
-                    st_shared_b32(b1 + k1 + (uint32_t)r * 16, h0);
-                    st_shared_b32(b1 + k1 + (uint32_t)(r + 1) * 16, h1);
-                    st_shared_b32(b1 + k1 + (uint32_t)(S::N1 + r) * 16, l0);
-                    st_shared_b32(b1 + k1 + (uint32_t)(S::N1 + r + 1) * 16, l1);
+                    st_shared_b32(b1 + k1 + (uint32_t)rr * 16, h0);
+                    st_shared_b32(b1 + k1 + (uint32_t)(rr + 1) * 16, h1);
+                    st_shared_b32(b1 + k1 + (uint32_t)(S::N1 + rr) * 16, l0);
+                    st_shared_b32(b1 + k1 + (uint32_t)(S::N1 + rr + 1) * 16, l1);
                     // GEMM2 B = dH_i^T: the entry dH_i[m'][m] (i = j, m' = n, m = l) sits at K = (m, i, re/im) of
                     // column (m', re) as (Hr, -Hi) and of column (m', im) as (Hi, Hr)
                     const uint32_t k2 = (uint32_t)l * S::LB2 + (uint32_t)(2 * j) * 2;
@@ -286,67 +422,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             fence_async_smem();
             mbar_arrive(B_(BBF));
-            named_bar(2, kTcProdWarps * 32);  // ehs written
-            const int j0 = tg * kTcTilesPerItem, j1 = min(j0 + kTcTilesPerItem, c.ntiles);
-            for (int tile = j0; tile < j1; ++tile) {
-                for (int s = 0; s < NB; ++s, ++u) {
-                    const int st = (int)(u & 1);
-                    const uint32_t par = ((u >> 1) & 1) ^ 1;
-                    wait_or_abort(B_(BA1E + st), par, abort_flag, status);  // GEMM1 has read the stage
-                    wait_or_abort(B_(BXE + st), par, abort_flag, status);   // the epilogue has read its exponents
-                    const int b = nbr[(size_t)a * NB + s];
-                    const bool bok = b >= 0 && b < d.NA;
-                    if (!bok && pt == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
-                    // this warp's group: rows (f', m) for FG frequencies, chunks of 4 complex along l
-                    float v[S::CD][8];
-                    float m = 0.f;
-#pragma unroll
-                    for (int it = 0; it < S::CD; ++it) {
-                        const int task = lane + 32 * it;
-                        const int ch = task / S::R, row = task - ch * S::R;
-                        const int fp = row / NORB, mr = row - fp * NORB;
-                        const size_t fi = (size_t)tile * S::FT + g * S::FG + fp;
-                        const bool ok = bok && ch < S::CD && fi < fm.count;
-                        const float2* src = ok ? Ghat + (freq_of(fm, fi) * d.NA + b) * nel + mr * NORB : Ghat;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int l = 4 * ch + q;
-                            float2 x = make_float2(0.f, 0.f);
-                            if (ok && l < NORB) x = src[l];
-                            v[it][2 * q] = x.x;
-                            v[it][2 * q + 1] = x.y;
-                            m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
-                        }
-                    }
-                    const int e1 = scale_exp(warp_max_abs(m));
-                    const uint32_t a1 = sbase + (uint32_t)(c.off_A1 + st * S::A1_STAGE);
-#pragma unroll
-                    for (int it = 0; it < S::CD; ++it) {
-                        const int task = lane + 32 * it;
-                        const int ch = task / S::R, row = task - ch * S::R;
-                        if (ch < S::CD) {
-                            uint32_t h[4], lo[4];
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                split2(mul_pow2(v[it][2 * q], e1), mul_pow2(v[it][2 * q + 1], e1), h[q], lo[q]);
-                            const uint32_t o = a1 + (uint32_t)ch * S::LA1 + (uint32_t)(32 * g + row) * 16;
-                            st_shared_v4(o, h[0], h[1], h[2], h[3]);
-                            st_shared_v4(o + S::A1_PLANE, lo[0], lo[1], lo[2], lo[3]);
-                        }
-                    }
-                    if (lane == 0) xr[st * 8 + g] = e1;
-                    if (pt == 0) xr[st * 8 + 4] = ehs[s];
-                    fence_async_smem();
-                    mbar_arrive(B_(BA1F + st));
+            for (int v = 0; v < units; ++v) {
+                if (v + 2 < units) {
+                    issue_unit(la, j0 + (v + 2) / NB, (v + 2) % NB, (int)(ru % kTcRaw));
+                    ++ru;
+                    cp_async_wait<2>();  // this unit's copies are done (the two after it may be in flight)
+                } else if (v + 1 < units) {
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
+                __syncwarp();  // every lane's copies are visible to the warp
+                produce(v % NB, (int)((r0 + v) % kTcRaw));
             }
-            named_bar(2, kTcProdWarps * 32);  // every producer is done with ehs before the next item rewrites it
         }
     } else if (warp == kTcMmaWarp) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t id1w = tc_idesc_f16(2 * S::N1), id1 = tc_idesc_f16(S::N1);
+            const uint32_t id1 = tc_idesc_f16(S::N1);
             const uint32_t id2w = tc_idesc_f16(2 * S::N2), id2 = tc_idesc_f16(S::N2);
+            // descriptors of the buffer bases; an operand at byte offset o from its base has descriptor base + o/16
+            // (the start-address field holds address/16, and every address stays below 256 KB)
+            const uint64_t dA1 = smem_desc(sbase + (uint32_t)c.off_A1, S::LA1, 128);
+            const uint64_t dA2 = smem_desc(sbase + (uint32_t)c.off_A2, S::LA2, 128);
+            const uint64_t dB1 = smem_desc(sbase + (uint32_t)c.off_B1, S::LB1, 128);
+            const uint64_t dB2 = smem_desc(sbase + (uint32_t)c.off_B2, S::LB2, 128);
             uint32_t u1 = 0, u2 = 0;  // units issued to GEMM1 / GEMM2
             int nitem = 0;
             auto gemm1 = [&](int s) {
@@ -356,16 +456,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
                 if (!*abort_flag) {
                     const uint32_t dP = tmem + (uint32_t)(st * S::TM_P);
-                    const uint32_t ah = sbase + (uint32_t)(c.off_A1 + st * S::A1_STAGE), al = ah + S::A1_PLANE;
-                    const uint32_t b = sbase + (uint32_t)(c.off_B1 + s * S::B1_BOND);
+                    const uint64_t ah = dA1 + (uint64_t)((st * S::A1_STAGE) >> 4), al = ah + (S::A1_PLANE >> 4);
+                    const uint64_t b = dB1 + (uint64_t)((s * S::B1_BOND) >> 4);
+                    // one accumulator: hi*B_hi + lo*B_hi + hi*B_lo (B_lo = the rows after N1 of each chunk plane)
 #pragma unroll
-                    for (int kc = 0; kc < S::K1 / 16; ++kc)
-                        umma_f16(dP, smem_desc(ah + 2 * kc * S::LA1, S::LA1, 128), smem_desc(b + 2 * kc * S::LB1, S::LB1, 128),
-                                 id1w, kc > 0);
-#pragma unroll
-                    for (int kc = 0; kc < S::K1 / 16; ++kc)
-                        umma_f16(dP, smem_desc(al + 2 * kc * S::LA1, S::LA1, 128), smem_desc(b + 2 * kc * S::LB1, S::LB1, 128),
-                                 id1, 1);
+                    for (int kc = 0; kc < S::K1 / 16; ++kc) {
+                        const uint64_t bh = b + (uint64_t)((2 * kc * S::LB1) >> 4), bl = bh + (uint64_t)S::N1;
+                        const uint64_t kofs = (uint64_t)((2 * kc * S::LA1) >> 4);
+                        umma_f16(dP, ah + kofs, bh, id1, kc > 0);
+                        umma_f16(dP, al + kofs, bh, id1, 1);
+                        umma_f16(dP, ah + kofs, bl, id1, 1);
+                    }
                 }
                 umma_commit(B_(BA1E + st));
                 umma_commit(B_(BPF + st));
@@ -377,16 +478,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
                 if (!*abort_flag) {
                     const uint32_t dO = tmem + (uint32_t)(2 * S::TM_P + s * S::TM_O);
-                    const uint32_t ah = sbase + (uint32_t)(c.off_A2 + st * S::A2_STAGE), al = ah + S::A2_PLANE;
-                    const uint32_t b = sbase + (uint32_t)(c.off_B2 + s * S::B2_BOND);
+                    const uint64_t ah = dA2 + (uint64_t)((st * S::A2_STAGE) >> 4), al = ah + (S::A2_PLANE >> 4);
+                    const uint64_t b = dB2 + (uint64_t)((s * S::B2_BOND) >> 4);
 #pragma unroll
                     for (int kc = 0; kc < S::K2 / 16; ++kc)
-                        umma_f16(dO, smem_desc(ah + 2 * kc * S::LA2, S::LA2, 128), smem_desc(b + 2 * kc * S::LB2, S::LB2, 128),
-                                 id2w, kc > 0);
+                        umma_f16(dO, ah + (uint64_t)((2 * kc * S::LA2) >> 4), b + (uint64_t)((2 * kc * S::LB2) >> 4), id2w,
+                                 kc > 0);
 #pragma unroll
                     for (int kc = 0; kc < S::K2 / 16; ++kc)
-                        umma_f16(dO, smem_desc(al + 2 * kc * S::LA2, S::LA2, 128), smem_desc(b + 2 * kc * S::LB2, S::LB2, 128),
-                                 id2, 1);
+                        umma_f16(dO, al + (uint64_t)((2 * kc * S::LA2) >> 4), b + (uint64_t)((2 * kc * S::LB2) >> 4), id2, 1);
                 }
                 umma_commit(B_(BA2E + st));
                 ++u2;
@@ -412,6 +512,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else {
         // ------------------------------------------------------------------ epilogue
         const int q = warp & 3, h = warp >> 2;  // TMEM lane quarter (= row group), column half
+        const float2* ks = reinterpret_cast<const float2*>(smem + c.off_K);
         const int fp = lane / NORB, mr = lane - fp * NORB;
         const bool row_ok = fp < S::FG;
         const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
@@ -424,19 +525,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const size_t fi = (size_t)tile * S::FT + q * S::FG + fp;
                 const bool fok = row_ok && fi < fm.count;
                 const size_t f = fok ? freq_of(fm, fi) : 0;
-                int etot[kTcMaxNB] = {0, 0, 0, 0};  // per bond: the exponent that undoes the operand scales
+                int e12[kTcMaxNB] = {0, 0, 0, 0};  // per bond: the exponents of GEMM1's operands (G^, dH twice)
                 for (int s = 0; s < NB; ++s, ++u) {
                     const int st = (int)(u & 1);
                     const uint32_t par = (u >> 1) & 1;
                     // exponents of this unit (GEMM1's A scale of this row group, the bond's dH scale)
                     wait_or_abort(B_(BA1F + st), par, abort_flag, status);
                     const int e1 = xr[st * 8 + q], eH = xr[st * 8 + 4];
-                    mbar_arrive(B_(BXE + st));
-                    float2 k[9];
+                    float2 k[9];  // K^_ij of this row's frequency (staged by the producers; zero where not in range)
 #pragma unroll
                     for (int ij = 0; ij < 9; ++ij)
-                        k[ij] = fok ? Khat[((f * nA + la) * NB + s) * 9 + ij] : make_float2(0.f, 0.f);
-                    // P_j rows from TMEM (two parts: hi*B_hi + lo*B_hi, and hi*B_lo), U_i = sum_j K_ij P_j
+                        k[ij] = row_ok ? ks[(st * S::FT + q * S::FG + fp) * 9 + ij] : make_float2(0.f, 0.f);
+                    mbar_arrive(B_(BXE + st));
+                    // P_j rows from TMEM (all three loads, one wait), U_i = sum_j K_ij P_j
                     wait_or_abort(B_(BPF + st), par, abort_flag, status);
                     tc_fence_after();
                     float ur[3][S::NH], ui[3][S::NH];
@@ -444,16 +545,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int i = 0; i < 3; ++i)
 #pragma unroll
                         for (int nn = 0; nn < S::NH; ++nn) ur[i][nn] = ui[i][nn] = 0.f;
+                    float pv[3][2 * S::NH];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        tmem_ld_half<S::NH>(tq + (uint32_t)(st * S::TM_P + j * 2 * NORB + 2 * h * S::NH), pv[j]);
+                    tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
-                        float p1[2 * S::NH], p2[2 * S::NH];
-                        const uint32_t col = (uint32_t)(st * S::TM_P + j * 2 * NORB + 2 * h * S::NH);
-                        tmem_ld_half<S::NH>(tq + col, p1);
-                        tmem_ld_half<S::NH>(tq + col + S::N1, p2);
-                        tmem_wait_ld();
 #pragma unroll
                         for (int nn = 0; nn < S::NH; ++nn) {
-                            const float pr = p1[2 * nn] + p2[2 * nn], pim = p1[2 * nn + 1] + p2[2 * nn + 1];
+                            const float pr = pv[j][2 * nn], pim = pv[j][2 * nn + 1];
 #pragma unroll
                             for (int i = 0; i < 3; ++i) {
                                 const float2 kk = k[i * 3 + j];
@@ -464,17 +565,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     tc_fence_before();
                     mbar_arrive(B_(BPE + st));  // the P buffer may be overwritten
-                    // one scale for the row group: max over both column halves (the partner warp)
+                    // one scale per warp: the rows (f', n) of this half of the group; the final phase reads it back
                     float m = 0.f;
 #pragma unroll
                     for (int nn = 0; nn < S::NH; ++nn)
                         if (h * S::NH + nn < NORB)
 #pragma unroll
                             for (int i = 0; i < 3; ++i) m = fmaxf(m, fmaxf(fabsf(ur[i][nn]), fabsf(ui[i][nn])));
-                    m = warp_max_abs(m);
-                    if (lane == 0) xmax[(st * 4 + q) * 2 + h] = m;
-                    named_bar(3 + q, 64);
-                    const int e2 = scale_exp(fmaxf(xmax[(st * 4 + q) * 2], xmax[(st * 4 + q) * 2 + 1]));
+                    const int e2 = scale_exp(warp_max_abs(m));
+                    if (lane == 0) e2s[(((ntile & 1) * kTcMaxNB + s) * 4 + q) * 2 + h] = e2;
+                    const Pow2 f2 = pow2_factors(e2);
                     // U^T rows (f', n) into GEMM2's A operand: K chunk m holds (i, re/im) for i = 0..2, then 0, 0
                     wait_or_abort(B_(BA2E + st), par ^ 1, abort_flag, status);
                     if (row_ok) {
@@ -486,7 +586,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 uint32_t hw[3], lw[3];
 #pragma unroll
                                 for (int i = 0; i < 3; ++i)
-                                    split2(mul_pow2(ur[i][nn], e2), mul_pow2(ui[i][nn], e2), hw[i], lw[i]);
+                                    split2(scaled(ur[i][nn], f2), scaled(ui[i][nn], f2), hw[i], lw[i]);
                                 const uint32_t o = a2 + (uint32_t)(32 * q + fp * NORB + n) * 16;
                                 st_shared_v4(o, hw[0], hw[1], hw[2], 0u);
                                 st_shared_v4(o + S::A2_PLANE, lw[0], lw[1], lw[2], 0u);
@@ -497,17 +597,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     mbar_arrive(B_(BA2F + st));
 #pragma unroll
                     for (int t4 = 0; t4 < kTcMaxNB; ++t4)  // static register indices
-                        if (t4 == s) etot[t4] = e1 + 2 * eH + e2;
+                        if (t4 == s) e12[t4] = e1 + 2 * eH;
                 }
                 // S^(f)^T rows (f', n = mr): sum over bonds of the unscaled accumulators, times i*scale
+                named_bar(1, kTcEpiWarps * 32);  // every warp's GEMM2 operand exponents of this tile are in place
                 wait_or_abort(B_(BOF), ntile & 1, abort_flag, status);
                 tc_fence_after();
+                const int hrow = mr >= S::NH;  // the half (warp) that wrote this row (f', n = mr) of U^T
                 float accr[S::NH], acci[S::NH];
 #pragma unroll
                 for (int mm = 0; mm < S::NH; ++mm) accr[mm] = acci[mm] = 0.f;
 #pragma unroll
                 for (int s = 0; s < kTcMaxNB; ++s) {
                     if (s < NB) {
+                        const Pow2 unsc =  // undoes the operand scales of this bond
+                            pow2_factors(-(e12[s] + e2s[(((ntile & 1) * kTcMaxNB + s) * 4 + q) * 2 + hrow]));
                         float p1[2 * S::NH], p2[2 * S::NH];
                         const uint32_t col = (uint32_t)(2 * S::TM_P + s * S::TM_O + 2 * h * S::NH);
                         tmem_ld_half<S::NH>(tq + col, p1);
@@ -515,8 +619,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         tmem_wait_ld();
 #pragma unroll
                         for (int mm = 0; mm < S::NH; ++mm) {
-                            accr[mm] += mul_pow2(p1[2 * mm] + p2[2 * mm], -etot[s]);
-                            acci[mm] += mul_pow2(p1[2 * mm + 1] + p2[2 * mm + 1], -etot[s]);
+                            accr[mm] = fmaf((p1[2 * mm] + p2[2 * mm]) * unsc.a, unsc.b, accr[mm]);
+                            acci[mm] = fmaf((p1[2 * mm + 1] + p2[2 * mm + 1]) * unsc.a, unsc.b, acci[mm]);
                         }
                     }
                 }
