@@ -174,6 +174,7 @@ NCU_TRAFFIC = {
     "spec_adj32_kernel": (7533.4, "8e9f1b2f0231170c", "atom-frequency of one type"),
     "spec_pi32_kernel": (2121.4, "3f8eabc933beac4b", "type-atom-frequency"),
     "spec_gradg32_kernel": (1863.7, "aa646c7c1d04f57d", "atom-frequency of one type"),
+    "spec_prod_tc_kernel": (1861.1, "7cf062564120227b", "atom-frequency of one type"),
 }
 
 
