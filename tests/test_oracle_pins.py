@@ -305,3 +305,58 @@ def test_oracle_results_do_not_depend_on_the_thread_count():
             assert np.array_equal(a, b), name
     for a, b in zip(oracle.sigma_grad(*args, W, V, nthreads=1), oracle.sigma_grad(*args, W, V, nthreads=7)):
         assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+# --------------------------------------------------------------------------
+# reading R3 (absorption term) against the bosonic form
+# --------------------------------------------------------------------------
+
+def _bosonic_sigma(inp, d):
+    """Eq. (3) with the absorption weight in the bosonic form: for sigma = -1 the weight of type t is the other
+    type's combined weight transposed in (i, j) at -qz, Dc^{t'}_ji(w, -q) (from D^<_ab(-w, q) = D^>_ba(w, -q) and the
+    a <-> b symmetry of the bond combination). Needs the full qz grid (Nqz = Nkz)."""
+    nbr = inp.nbr.numpy()
+    A = inp.dH.numpy()
+    k = np.arange(d.Nkz)[:, None]
+    q = np.arange(d.Nqz)[None, :]
+    kp = (k - q) % d.Nkz
+    qneg = (-np.arange(d.Nqz)) % d.Nkz
+    c = 1j * SCALE
+    Ds = (inp.D_less.numpy(), inp.D_greater.numpy())
+    out = []
+    for t, G in enumerate((inp.G_less.numpy(), inp.G_greater.numpy())):
+        ref = np.zeros(d.g_shape(), dtype=np.complex128)
+        for E in range(d.NE):
+            for w in range(d.Nw):
+                for sigma in (+1, -1):
+                    Ep = E - sigma * (w + 1)
+                    if not 0 <= Ep < d.NE:
+                        continue
+                    if sigma == 1:
+                        Dt = Ds[t][:, w]
+                    else:
+                        Dt = np.swapaxes(Ds[1 - t][qneg, w], -1, -2)
+                    Gg = G[kp, Ep][:, :, nbr]
+                    ref[:, E] += c * np.einsum("qasij,asiml,kqaslp,asjnp->kamn", Dt, A, Gg, A.conj(), optimize=True)
+        out.append(ref)
+    return out
+
+
+def test_absorption_reading_vs_bosonic_form():
+    """The library's absorption weight Dc^{t'}_ij(w, qz) equals the bosonic form Dc^{t'}_ji(w, -qz) exactly when the
+    combined weights are reciprocal, Dc_ij(w, q) = Dc_ji(w, -q) (phonon functions of a time-reversal-symmetric
+    lattice); for weights that are not reciprocal the two readings differ, so the reading is a real choice."""
+    d = Dims(NA=5, NB=2, Norb=3, NE=9, Nkz=4, Nqz=4, Nw=3)
+    inp = make_inputs(d, seed=41, nbr=ring_neighbours(d.NA, d.NB), general=True)
+    qneg = (-np.arange(d.Nqz)) % d.Nkz
+    for name in ("D_less", "D_greater"):
+        X = getattr(inp, name).numpy()
+        recip = 0.5 * (X + np.swapaxes(X[qneg], -1, -2))  # Dc(q)_ij = Dc(-q)_ji
+        setattr(inp, name, torch.from_numpy(recip.copy()))
+    Sl, Sg = run(inp)
+    Bl, Bg = _bosonic_sigma(inp, d)
+    assert normwise(Sl, Bl) < 1e-13 and normwise(Sg, Bg) < 1e-13
+    general = make_inputs(d, seed=42, nbr=ring_neighbours(d.NA, d.NB), general=True)
+    Sl, Sg = run(general)
+    Bl, Bg = _bosonic_sigma(general, d)
+    assert normwise(Sl, Bl) > 1e-2 and normwise(Sg, Bg) > 1e-2
