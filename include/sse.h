@@ -301,6 +301,19 @@ SSE_API int sse_sigma_bwd_static(const sse_dims* d, const int32_t* nbr, const do
                                  const double* gS_greater, double* g_dH, double* g_D_less, double* g_D_greater,
                                  void* stream);
 
+/* Test hook of the bounded device waits (the paper has no counterpart). The next
+ * sse_sigma_fwd call in mode TF32 or BF16X3 (and only that call) issues none of the
+ * shared-memory window loads of work item `item` of its first energy window -- a
+ * work item is (128-row energy tile, kz, type, atom), tile fastest, so item 0 is the first
+ * tile of atom a_begin -- and bounds each pipeline wait by `wait_polls` mbarrier polls.
+ * The waits that depend on the withheld loads run out, the kernel stops issuing work,
+ * still waits (with the full limit) for the loads and matrix products it did issue,
+ * and the call reports SSE_ERR_TIMEOUT when made with SSE_FLAG_CHECK. No device fault is
+ * involved; the outputs of that call are unspecified and later calls are unaffected.
+ * item < 0 disarms the hook. Returns SSE_ERR_INVALID_ARG for item >= 0 with
+ * wait_polls = 0, else SSE_OK. Host memory only; not meant for concurrent use. */
+SSE_API int sse_test_withhold_window(int item, uint32_t wait_polls);
+
 /* Device time of one kernel over the calls recorded with SSE_FLAG_PROFILE. */
 typedef struct sse_profile_entry {
     const char* name; /* static string, e.g. "sigma_fp64_fwd_kernel"      */

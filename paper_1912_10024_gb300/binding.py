@@ -20,7 +20,8 @@ SSE_MODE_FP64, SSE_MODE_TF32, SSE_MODE_BF16X3, SSE_MODE_FP64_FFT, SSE_MODE_FP32_
 SSE_FLAG_SYMMETRIZE, SSE_FLAG_CHECK, SSE_FLAG_PROFILE, SSE_FLAG_ANTIHERMITIAN = 1, 2, 4, 8
 MODES = {"fp64": SSE_MODE_FP64, "tf32": SSE_MODE_TF32, "bf16x3": SSE_MODE_BF16X3, "fp64_fft": SSE_MODE_FP64_FFT,
          "fp32_fft": SSE_MODE_FP32_FFT, "f16x3_fft": SSE_MODE_F16X3_FFT}
-EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_dcomb_fwd",
+EXPORTED = ("sse_workspace_bytes", "sse_sigma_fwd", "sse_sigma_bwd", "sse_sigma_bwd_static", "sse_test_withhold_window",
+            "sse_dcomb_fwd",
             "sse_dcomb_bwd", "sse_pi_workspace_bytes", "sse_pi_fwd", "sse_sigma_bwd_g_workspace_bytes",
             "sse_sigma_bwd_g",
             "sse_sigma_fwd_host_bytes", "sse_sigma_fwd_host", "sse_profile_read", "sse_strerror")
@@ -84,6 +85,8 @@ def load() -> ctypes.CDLL:
             lib.sse_sigma_fwd_host.argtypes = [pd, vp, vp, vp, vp, vp, vp, f64, i32, u32, vp, vp, vp, ctypes.c_size_t,
                                                vp, vp]
             lib.sse_sigma_fwd_host.restype = i32
+            lib.sse_test_withhold_window.argtypes = [i32, u32]
+            lib.sse_test_withhold_window.restype = i32
             lib.sse_profile_read.argtypes = [ctypes.POINTER(sse_profile_entry), i32]
             lib.sse_profile_read.restype = i32
             _lib = lib
@@ -180,6 +183,11 @@ def sse_dcomb_bwd(d: sse_dims, nbr, gD_less, gD_greater, gDraw_less, gDraw_great
                   ws_bytes: int, stream=None) -> int:
     return int(load().sse_dcomb_bwd(ctypes.byref(d), _p(nbr), _p(gD_less), _p(gD_greater), _p(gDraw_less),
                                     _p(gDraw_greater), int(flags), _p(workspace), int(ws_bytes), _stream(stream)))
+
+
+def sse_test_withhold_window(item: int, wait_polls: int) -> int:
+    """Arm the test hook of the bounded device waits for the next TF32 / BF16X3 forward (see include/sse.h)."""
+    return load().sse_test_withhold_window(int(item), int(wait_polls))
 
 
 def sse_profile_read(max_entries: int = 64):

@@ -50,6 +50,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "sse_internal.h"
 #include "sse_tcgen05.cuh"
 
@@ -76,6 +78,8 @@ struct MixCfg {
     int tmem_cols, acc_stride, btile, tg;  // TMEM columns, offset of the 2nd accumulator, W tile bytes, taps per W stage
     int off_B, off_D, off_Ah, off_A64, off_Y, off_bar, smem;
     int nrows;                       // staged rows per slice for the largest window: min(NE, wE + 2 Nw) * Norb
+    int withhold_item;               // test hook: work item whose window loads are not issued (-1: none)
+    uint32_t wait_polls;             // polls before a pipeline wait gives up (the drains always wait the full limit)
 };
 
 MixCfg make_cfg(const sse_dims& d, int mode) {
@@ -114,6 +118,8 @@ MixCfg make_cfg(const sse_dims& d, int mode) {
         if (c.off_bar + 256 + 128 <= 227 * 1024 && c.tg * per_tile <= items * kRole) break;
     }
     c.smem = c.off_bar + 256 + 128;  // barriers and flags, + alignment slack of the dynamic base
+    c.withhold_item = -1;
+    c.wait_polls = kWaitIters;
     return c;
 }
 
@@ -362,8 +368,8 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                                 const int r0 = (it.E0 - win.Es) * N;  // staged row of the tile's first row
                                 const int start = sg == 0 ? r0 - (w0 + wn) * N : r0 + (w0 + 1) * N;
                                 const int st = (int)(wcnt & 1);
-                                wait_or_abort(B_(WE + st), ((wcnt >> 1) & 1) ^ 1, abort_flag, status);
-                                if (!*abort_flag) {
+                                wait_or_abort(B_(WE + st), ((wcnt >> 1) & 1) ^ 1, abort_flag, status, c.wait_polls);
+                                if (!*abort_flag && item != c.withhold_item) {
                                     const uint32_t dst = smem_u32(smem) + (uint32_t)st * win_bytes;
                                     mbar_expect_tx(B_(WF + st), win_bytes);
                                     for (int ch = 0; ch < c.nch; ++ch)
@@ -401,7 +407,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                     if (b < 0 || b >= d.NA) continue;
                     for (int q = 0; q < d.Nqz; ++q) {
                         const int ab = (int)(acnt & 1);
-                        wait_or_abort(B_(AE + ab), ((acnt >> 1) & 1) ^ 1, abort_flag, status);
+                        wait_or_abort(B_(AE + ab), ((acnt >> 1) & 1) ^ 1, abort_flag, status, c.wait_polls);
                         tc_fence_after();
                         const uint32_t dtm = tmem + (uint32_t)(ab * c.acc_stride);
                         uint32_t acc = 0;
@@ -410,12 +416,12 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                             for (int w0 = 0; w0 < wend; w0 += c.wc) {
                                 const int wn = min(c.wc, wend - w0);
                                 const int st = (int)(wcnt & 1);
-                                wait_or_abort(B_(WF + st), (wcnt >> 1) & 1, abort_flag, status);
+                                wait_or_abort(B_(WF + st), (wcnt >> 1) & 1, abort_flag, status, c.wait_polls);
                                 tc_fence_after();
                                 for (int g0 = 0; g0 < wn; g0 += c.tg) {
                                     const int ng = min(c.tg, wn - g0);
                                     const int bs = (int)(bcnt % kBStages);
-                                    wait_or_abort(B_(BF + bs), (bcnt / kBStages) & 1, abort_flag, status);
+                                    wait_or_abort(B_(BF + bs), (bcnt / kBStages) & 1, abort_flag, status, c.wait_polls);
                                     tc_fence_after();
                                     if (!*abort_flag) {
                                         for (int gi = 0; gi < ng; ++gi) {
@@ -529,7 +535,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                             for (int g0 = 0; g0 < wn; g0 += c.tg) {
                                 const int ng = min(c.tg, wn - g0);
                                 const int bs = (int)(bcnt % kBStages);
-                                wait_or_abort(B_(BE + bs), ((bcnt / kBStages) & 1) ^ 1, abort_flag, status);
+                                wait_or_abort(B_(BE + bs), ((bcnt / kBStages) & 1) ^ 1, abort_flag, status, c.wait_polls);
                                 unsigned char* stage = sB + (size_t)bs * c.tg * c.btile;
                                 const float2* Dst = sDq + ((size_t)sg * d.Nw + w0 + g0) * 9;
                                 if (MODE == SSE_MODE_BF16X3) {
@@ -687,7 +693,7 @@ sigma_mixed_kernel(const __grid_constant__ CUtensorMap tmap, Problem p, MixCfg c
                 for (int j = 0; j < kMaxCols; ++j) Yrow[j] = 0.0;
                 for (int q = 0; q < d.Nqz; ++q) {
                     const int ab = (int)(acnt & 1);
-                    wait_or_abort(B_(AF + ab), (acnt >> 1) & 1, abort_flag, status);
+                    wait_or_abort(B_(AF + ab), (acnt >> 1) & 1, abort_flag, status, c.wait_polls);
                     tc_fence_after();
                     const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * c.acc_stride);
 #pragma unroll
@@ -830,7 +836,9 @@ cudaError_t launch(const Problem& p, const MixCfg& c, double2* Sl, double2* Sg, 
             return cudaErrorInvalidValue;
         const long long nitems = (long long)win.ntiles * d.Nkz * 2 * nA;
         const int grid = (int)(nitems < nsm ? nitems : nsm);
-        SSE_TIMED("sigma_mixed_kernel", st, sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, c, win, gmax, ew, Sl, Sg, status));
+        MixCfg cw = c;  // the test hook withholds an item of the first energy window only
+        if (E0 > 0) cw.withhold_item = -1;
+        SSE_TIMED("sigma_mixed_kernel", st, sigma_mixed_kernel<MODE><<<grid, kThreads, c.smem, st>>>(map, p, cw, win, gmax, ew, Sl, Sg, status));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -850,13 +858,31 @@ bool mixed_supported(const sse_dims& d, int mode) {
     return (long long)((c.wE + c.TE - 1) / c.TE) * d.Nkz * 2 * (d.a_end - d.a_begin) <= 0x7fffffffLL;
 }
 
+namespace {
+// Test hook of the bounded waits (sse_test_withhold_window): armed by the host, consumed by the next forward call.
+std::atomic<int> g_withhold_item{-1};
+std::atomic<uint32_t> g_withhold_polls{0};
+}  // namespace
+
 cudaError_t mixed_fwd(const Problem& p, int mode, double2* S_less, double2* S_greater, unsigned* status, void* ws,
                       size_t ws_bytes, cudaStream_t st) {
     if (!mixed_supported(p.d, mode)) return cudaErrorNotSupported;
-    const MixCfg c = make_cfg(p.d, mode);
+    MixCfg c = make_cfg(p.d, mode);
+    const int hold = g_withhold_item.exchange(-1);
+    if (hold >= 0) {
+        c.withhold_item = hold;
+        c.wait_polls = g_withhold_polls.load();
+    }
     if (ws_bytes < ws_layout(p.d, c).total) return cudaErrorNotSupported;
     if (mode == SSE_MODE_BF16X3) return launch<SSE_MODE_BF16X3>(p, c, S_less, S_greater, status, ws, st);
     return launch<SSE_MODE_TF32>(p, c, S_less, S_greater, status, ws, st);
 }
 
 }  // namespace sse
+
+extern "C" int sse_test_withhold_window(int item, uint32_t wait_polls) {
+    if (item >= 0 && wait_polls == 0) return SSE_ERR_INVALID_ARG;
+    sse::g_withhold_polls.store(wait_polls);
+    sse::g_withhold_item.store(item < 0 ? -1 : item);
+    return SSE_OK;
+}

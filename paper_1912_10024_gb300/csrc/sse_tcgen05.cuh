@@ -78,9 +78,9 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 // Bounded wait; after any wait of the CTA has given up, waits return at once (results are then
 // discarded: the host reports SSE_ERR_TIMEOUT), so every role still runs its loops to the end.
 __device__ __forceinline__ void wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                              unsigned* status) {
+                                              unsigned* status, uint32_t limit = kWaitIters) {
     if (*abort_flag) return;
-    for (uint32_t it = 0; it < kWaitIters; ++it)
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return;
     *abort_flag = 1;
     atomicOr(status, DEV_TIMEOUT);

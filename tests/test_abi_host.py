@@ -284,3 +284,11 @@ def test_static_entry_point_status_codes_match_sse_sigma_bwd():
     assert call(bad, B.SSE_MODE_FP64) == 1
     big = B.sse_dims(1024, 4, 10, 512, 7, 7, 32, 0, 1024)
     assert call(big, B.SSE_MODE_FP64) == 6
+
+
+def test_withhold_window_hook_arguments():
+    """The bounded-wait test hook checks its arguments on the host and disarms with item < 0."""
+    assert B.sse_test_withhold_window(0, 0) == 1
+    assert B.sse_test_withhold_window(-1, 0) == 0
+    assert B.sse_test_withhold_window(3, 1 << 16) == 0
+    assert B.sse_test_withhold_window(-1, 0) == 0  # leave it disarmed

@@ -94,3 +94,24 @@ def test_finfet_bf16x3_sampled():
             errs.append(normwise(S[:, E0:E1, a].cpu().numpy(), O))
     print("finfet bf16x3 sampled errors", errs)
     assert max(errs) <= BOUND["bf16x3"]
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_timed_out_wait_is_reported_and_the_next_call_is_clean(mode):
+    """The bounded waits of the tensor-core kernel, made to run out without any device fault: the test hook withholds
+    the window loads of one work item, the waits that depend on them give up after a short poll limit, the kernel
+    drains the loads and matrix products it did issue and returns, and the call reports SSE_ERR_TIMEOUT. The next
+    call on the same stream matches the oracle."""
+    inp = make_inputs(TINY, seed=61)
+    g = inp.to("cuda")
+    args = (g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr)
+    assert B.sse_test_withhold_window(0, 1 << 18) == 0
+    with pytest.raises(B.SseError) as e:
+        B.sigma(*args, mode=mode, check=True)
+    assert e.value.status == 4  # SSE_ERR_TIMEOUT
+    torch.cuda.synchronize()  # the context is still usable
+    S = B.sigma(*args, mode=mode, check=True)  # the hook disarmed itself
+    O = oracle.sigma(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE)
+    assert max(normwise(s.cpu().numpy(), o) for s, o in zip(S, O)) <= BOUND[mode]
+    assert B.sse_test_withhold_window(0, 0) == 1  # invalid: no poll limit
+    assert B.sse_test_withhold_window(-1, 0) == 0  # disarm
