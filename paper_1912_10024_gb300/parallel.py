@@ -21,8 +21,8 @@ library call (or a ``compute`` the caller passes).
 
 On one GPU the shard primitive is sse_sigma_fwd's atom range; across GPUs the
 exchanges run over torch.distributed (NCCL for CUDA tensors, gloo for CPU
-tensors): point-to-point sends of whole G blocks or energy rows, plus the
-rank-order gather of the energy-summed gradients.
+tensors): one packed point-to-point message of G blocks (or energy rows) per peer, plus the
+rank-order chain that sums the energy-summed gradients.
 """
 from __future__ import annotations
 
@@ -66,24 +66,31 @@ def exchange_halo(G_owned: Sequence[torch.Tensor], nbr: torch.Tensor, NA: int,
     mine = halo_atoms(nbr, a0, a1)
     wants: List[List[int]] = [None] * world  # type: ignore[list-item]
     dist.all_gather_object(wants, mine, group=group)
-    ops, recv = [], {}
+    ntype = len(G_owned)
+    ops, pending = [], []
     for peer in range(world):
         if peer == rank:
             continue
-        # blocks the peer needs from me, in the peer's (sorted) order
-        give = [b for b in wants[peer] if a0 <= b < a1]
-        for b in give:
-            for G in G_owned:
-                ops.append(dist.P2POp(dist.isend, G[:, :, b - a0].contiguous(), peer, group))
-        for b in mine:
-            if owner(b, NA, world) == peer:
-                bufs = [torch.empty_like(G[:, :, 0]) for G in G_owned]
-                recv[b] = bufs
-                for buf in bufs:
-                    ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+        # one packed message per peer: the blocks it needs from me, in its (sorted) order, both types
+        give = [b - a0 for b in wants[peer] if a0 <= b < a1]
+        if give:
+            idx = torch.tensor(give, dtype=torch.long, device=G_owned[0].device)
+            send = torch.stack([G.index_select(2, idx) for G in G_owned])  # [types, Nkz, NE, len(give), ...]
+            ops.append(dist.P2POp(dist.isend, send, peer, group))
+        take = [b for b in mine if owner(b, NA, world) == peer]
+        if take:
+            G = G_owned[0]
+            buf = torch.empty((ntype, G.shape[0], G.shape[1], len(take)) + tuple(G.shape[3:]), dtype=G.dtype,
+                              device=G.device)
+            ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+            pending.append((take, buf))
     if ops:
         for req in dist.batch_isend_irecv(ops):
             req.wait()
+    recv: Dict[int, List[torch.Tensor]] = {}
+    for take, buf in pending:
+        for i, b in enumerate(take):
+            recv[b] = [buf[t, :, :, i] for t in range(ntype)]
     return recv
 
 
@@ -219,28 +226,33 @@ def reduce_halo_grad(gG_local: Sequence[torch.Tensor], nbr: torch.Tensor, NA: in
     halos: List[List[int]] = [None] * world  # type: ignore[list-item]
     dist.all_gather_object(halos, mine, group=group)
     out = [g[:, :, :n_own].clone() for g in gG_local]
+    ntype = len(gG_local)
     ops, recv = [], []
     for peer in range(world):
         if peer == rank:
             continue
-        # my halo blocks that the peer owns, in my (sorted) halo order
-        for idx, b in enumerate(mine):
-            if owner(b, NA, world) == peer:
-                for g in gG_local:
-                    ops.append(dist.P2POp(dist.isend, g[:, :, n_own + idx].contiguous(), peer, group))
+        # one packed message per peer: my halo blocks that it owns, in my (sorted) halo order, both types
+        give = [n_own + i for i, b in enumerate(mine) if owner(b, NA, world) == peer]
+        if give:
+            idx = torch.tensor(give, dtype=torch.long, device=gG_local[0].device)
+            ops.append(dist.P2POp(dist.isend, torch.stack([g.index_select(2, idx) for g in gG_local]), peer, group))
         # the peer's halo blocks that I own, in the peer's order
-        for b in halos[peer]:
-            if a0 <= b < a1:
-                bufs = [torch.empty_like(g[:, :, 0]) for g in gG_local]
-                recv.append((peer, b, bufs))
-                for buf in bufs:
-                    ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+        take = [b for b in halos[peer] if a0 <= b < a1]
+        if take:
+            g = gG_local[0]
+            buf = torch.empty((ntype, g.shape[0], g.shape[1], len(take)) + tuple(g.shape[3:]), dtype=g.dtype,
+                              device=g.device)
+            ops.append(dist.P2POp(dist.irecv, buf, peer, group))
+            recv.append((peer, take, buf))
     if ops:
         for req in dist.batch_isend_irecv(ops):
             req.wait()
-    for _peer, b, bufs in sorted(recv, key=lambda x: (x[0], x[1])):
-        for t, buf in enumerate(bufs):
-            out[t][:, :, b - a0] += buf
+    # added in (peer rank, atom) order: deterministic
+    adds = sorted(((peer, b, buf, i) for peer, take, buf in recv for i, b in enumerate(take)),
+                  key=lambda x: (x[0], x[1]))
+    for _peer, b, buf, i in adds:
+        for t in range(ntype):
+            out[t][:, :, b - a0] += buf[t, :, :, i]
     return out
 
 
@@ -394,12 +406,21 @@ def sigma_grad_energy_sharded(nbr: torch.Tensor, dH: torch.Tensor, D: Sequence[t
 
 
 def reduce_in_rank_order(x: torch.Tensor, group=None) -> torch.Tensor:
-    """Sum of ``x`` over the ranks, added in rank order on every rank (deterministic): the reduction that gradients
-    summed over energies (dH, D) need when the energies are split."""
+    """Sum of ``x`` over the ranks in rank order, (((x_0 + x_1) + x_2) + ...), returned on every rank (deterministic):
+    the reduction that gradients summed over energies (dH, D) need when the energies are split. A chain of
+    point-to-point messages (rank r adds its part to the partial sum of ranks < r and passes it on) and a broadcast
+    from the last rank: two buffers of x's size per rank, where gathering every rank's part would take world."""
     world = dist.get_world_size(group)
-    parts = [torch.empty_like(x) for _ in range(world)]
-    dist.all_gather(parts, x.contiguous(), group=group)
-    total = parts[0].clone()
-    for p in parts[1:]:
-        total += p
+    rank = dist.get_rank(group)
+    if world == 1:
+        return x.clone()
+    ranks = dist.get_process_group_ranks(group) if group is not None else list(range(world))
+    total = x.contiguous().clone()
+    if rank > 0:
+        prev = torch.empty_like(total)
+        dist.recv(prev, src=ranks[rank - 1], group=group)
+        total = prev.add_(total)  # partial sum of ranks < r, then x_r
+    if rank < world - 1:
+        dist.send(total, dst=ranks[rank + 1], group=group)
+    dist.broadcast(total, src=ranks[world - 1], group=group)
     return total
