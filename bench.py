@@ -384,6 +384,7 @@ def run_sharded(args, d, rank, world, local, dev):
     def step(profile=False):
         return P.sigma_atom_sharded(nbr, dH_own, D_own, G_own, d.NA, SCALE, mode=args.mode, profile=profile, **flags)
 
+    S = None
     for _ in range(args.warmup):
         S = step()
     del S

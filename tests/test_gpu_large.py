@@ -6,8 +6,9 @@ checked against the FP64 oracle on sampled blocks (grid edges, window
 boundaries, interior); the phonon self-energy Pi on a sampled atom; the
 FP64 adjoint on a subset of atoms checked against central differences of the
 FP64 forward; and the transform-based adjoint on a subset of atoms against
-the direct one. The FP32_FFT forward, Pi and adjoint are checked the same way
-to their stated bounds (2e-6, 2e-6, 1e-5).
+the direct one. The FP32_FFT forward, Pi and adjoint, and the F16X3_FFT
+(tensor-core) forward, are checked the same way to their stated bounds
+(2e-6, 2e-6, 1e-5, 2e-6).
 """
 import math
 
@@ -162,6 +163,25 @@ def test_large_fp32_fft_sampled(large):
         for S, O in ((Sl, Ol), (Sg, Og)):
             errs.append(normwise(S[:, E0:E1, a].cpu().numpy(), O))
     print("large fp32_fft sampled errors", errs)
+    assert max(errs) <= 2e-6
+    del Sl, Sg
+    torch.cuda.empty_cache()
+
+
+def test_large_f16x3_fft_sampled(large):
+    """F16X3_FFT forward (FP32 transforms, block products on the tensor cores) at the large sizes: sampled blocks
+    against the oracle to the mode's bound 2e-6."""
+    inp = large
+    args = (inp.G_less, inp.G_greater, inp.dH, inp.D_less, inp.D_greater, inp.nbr)
+    Sl, Sg = B.sigma(*args, mode="f16x3_fft", check=True)
+    torch.cuda.synchronize()
+    errs = []
+    for (a, E0, E1) in [(0, 0, 2), (4095, 1022, 1024), (2047, 511, 513), (1234, 300, 302)]:
+        Ol, Og = oracle_blocks(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, a,
+                               E0, E1)
+        for S, O in ((Sl, Ol), (Sg, Og)):
+            errs.append(normwise(S[:, E0:E1, a].cpu().numpy(), O))
+    print("large f16x3_fft sampled errors", errs)
     assert max(errs) <= 2e-6
     del Sl, Sg
     torch.cuda.empty_cache()
