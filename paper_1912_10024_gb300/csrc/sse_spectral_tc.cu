@@ -56,7 +56,9 @@ struct TcShape {
     static constexpr int R = FG * NORB;                     // used rows per group
     static constexpr int CD = (NORB + 3) / 4;               // 16-B chunks of one G^ row (4 complex each)
     static constexpr int KPL = (FG * 9 + 31) / 32;          // K^ entries per producer lane (group of FG frequencies)
-    static constexpr int RAW_G = FG * NORB * NORB + FG * 9;  // float2 per group and raw stage: G^ blocks, then K^
+    static constexpr int RAW_G = (FG * NORB * NORB + FG * 9 + 1) / 2 * 2;  // float2 per group and raw stage: G^ blocks,
+                                                                            // then K^ (even: 16-byte aligned groups)
+    static constexpr bool BULK = (NORB * NORB * 8) % 16 == 0;  // a G^ block is whole 16-byte units: one bulk copy
     static constexpr int RAW_STAGE = 4 * RAW_G * 8;          // bytes per raw stage (four groups)
     static constexpr int K1 = (2 * NORB + 15) / 16 * 16;    // GEMM1 K (fp16 elements)
     static constexpr int C1 = K1 / 8;                       // 16-B K chunks of GEMM1's operands
@@ -78,7 +80,8 @@ struct TcShape {
 
 // Barriers (8 B each) after the operand buffers.
 enum { BA1F = 0, BA1E = 2, BPF = 4, BPE = 6, BA2F = 8, BA2E = 10, BXE = 12, BOF = 14, BBF = 15, BBE = 16, BMD = 17,
-       kTcBars = 18 };
+       BRF = 18,  // raw ring: one barrier per (stage, group), completed by the bulk copies of the G^ blocks
+       kTcBars = 18 + 3 * 4 };
 
 struct TcCfg {
     int NB, nA, ntiles, ngroups, nitems;
@@ -191,6 +194,13 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
+// Bulk copy global -> shared through the TMA engine (16-byte aligned addresses, size a multiple of 16), completing
+// on an mbarrier's transaction count.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
 // 8-byte asynchronous copy global -> shared; with pred false the destination is zero-filled (nothing is read).
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool pred) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(pred ? 8 : 0) : "memory");
@@ -240,6 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_init(B_(BBF), kTcProdWarps * 32);
         mbar_init(B_(BBE), 1);
         mbar_init(B_(BMD), 1);
+        for (int i = 0; i < kTcRaw * 4; ++i) mbar_init(B_(BRF + i), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -264,7 +275,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // entries, copied raw (FP32) into a ring of kTcRaw stages up to two units ahead of their use.
         int bnb[kTcMaxNB] = {-1, -1, -1, -1};  // the item's neighbours (loaded once per item)
         const float2* raw = reinterpret_cast<const float2*>(smem + c.off_raw);
-        auto issue_unit = [&](int la, int tile, int s, int rs) {
+        uint32_t r_issued = 0, r_last = 0;  // raw slots with bulk copies issued; parity of the last use of each
+        auto issue_unit = [&](int la, int tile, int s, uint32_t rq) {
+            const int rs = (int)(rq % kTcRaw);
             int b = bnb[0];
 #pragma unroll
             for (int t4 = 1; t4 < kTcMaxNB; ++t4)
@@ -275,13 +288,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool ok_l = bok && lane < S::FG && fi_l < fm.count;
             const unsigned long long f_l = ok_l ? (unsigned long long)freq_of(fm, fi_l) : ~0ull;
             const uint32_t dst = sbase + (uint32_t)(c.off_raw + rs * S::RAW_STAGE + g * S::RAW_G * 8);
+            if (S::BULK) {
+                // one bulk copy of its frequency's G^ block per lane l < FG (blocks of invalid frequencies are not
+                // copied: the reader takes zeros for them)
+                const uint32_t rbar = B_(BRF + rs * 4 + g);
+                const unsigned vm = __ballot_sync(0xffffffffu, ok_l);
+                if (lane == 0) mbar_expect_tx(rbar, (uint32_t)__popc(vm) * (uint32_t)(nel * 8));
+                __syncwarp();
+                if (ok_l)
+                    bulk_copy(dst + (uint32_t)(lane * nel * 8), Ghat + ((size_t)f_l * d.NA + b) * nel,
+                              (uint32_t)(nel * 8), rbar);
+                r_issued |= 1u << rs;
+                r_last = (r_last & ~(1u << rs)) | (((rq / kTcRaw) & 1u) << rs);
+            } else {
 #pragma unroll
-            for (int it = 0; it < (S::FG * nel + 31) / 32; ++it) {
-                const int idx = lane + 32 * it, fl = idx / nel, e = idx - fl * nel;
-                const unsigned long long f = __shfl_sync(0xffffffffu, f_l, fl < S::FG ? fl : 0);
-                const bool ok = idx < S::FG * nel && f != ~0ull;
-                if (idx < S::FG * nel)
-                    cp_async8(dst + (uint32_t)idx * 8, ok ? Ghat + ((size_t)f * d.NA + b) * nel + e : Ghat, ok);
+                for (int it = 0; it < (S::FG * nel + 31) / 32; ++it) {
+                    const int idx = lane + 32 * it, fl = idx / nel, e = idx - fl * nel;
+                    const unsigned long long f = __shfl_sync(0xffffffffu, f_l, fl < S::FG ? fl : 0);
+                    const bool ok = idx < S::FG * nel && f != ~0ull;
+                    if (idx < S::FG * nel)
+                        cp_async8(dst + (uint32_t)idx * 8, ok ? Ghat + ((size_t)f * d.NA + b) * nel + e : Ghat, ok);
+                }
             }
 #pragma unroll
             for (int it = 0; it < S::KPL; ++it) {
@@ -295,11 +322,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             cp_async_commit();
             if (!bok && pt == 0) atomicOr(status, DEV_BAD_NEIGHBOUR);
         };
-        auto produce = [&](int s, int rs) {
+        auto produce = [&](int la, int tile, int s, uint32_t rq) {
+            const int rs = (int)(rq % kTcRaw);
             const int st = (int)(u & 1);
             const uint32_t par = ((u >> 1) & 1) ^ 1;
             wait_or_abort(B_(BA1E + st), par, abort_flag, status);  // GEMM1 has read the stage
             wait_or_abort(B_(BXE + st), par, abort_flag, status);   // the epilogue has read its exponents and K^
+            int b = bnb[0];
+#pragma unroll
+            for (int t4 = 1; t4 < kTcMaxNB; ++t4)
+                if (t4 == s) b = bnb[t4];
+            const bool bok = b >= 0 && b < d.NA;
+            if (S::BULK) wait_or_abort(B_(BRF + rs * 4 + g), (rq / kTcRaw) & 1u, abort_flag, status);
             const float2* rg = raw + (size_t)rs * (S::RAW_STAGE / 8) + g * S::RAW_G;
             float v[S::CD][8];
             float m = 0.f;
@@ -308,14 +342,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int task = lane + 32 * it;
                 const int ch = task / S::R, row = task - ch * S::R;
                 const int fp = row / NORB, mr = row - fp * NORB;
+                // blocks of frequencies out of range (or of a bad neighbour) were not copied: zeros
+                const bool ok = ch < S::CD && (!S::BULK || (bok && (size_t)tile * S::FT + g * S::FG + fp < fm.count));
+                if (S::BULK) {  // even Norb: rows are 16-byte aligned, pairs of complex entries as one load
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int l = 4 * ch + q;
-                    float2 x = make_float2(0.f, 0.f);
-                    if (ch < S::CD && l < NORB) x = rg[fp * nel + mr * NORB + l];
-                    v[it][2 * q] = x.x;
-                    v[it][2 * q + 1] = x.y;
-                    m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+                    for (int q = 0; q < 4; q += 2) {
+                        const int l = 4 * ch + q;
+                        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ok && l < NORB) x = *reinterpret_cast<const float4*>(rg + fp * nel + mr * NORB + l);
+                        v[it][2 * q] = x.x;
+                        v[it][2 * q + 1] = x.y;
+                        v[it][2 * q + 2] = x.z;
+                        v[it][2 * q + 3] = x.w;
+                        m = fmaxf(m, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int l = 4 * ch + q;
+                        float2 x = make_float2(0.f, 0.f);
+                        if (ok && l < NORB) x = rg[fp * nel + mr * NORB + l];
+                        v[it][2 * q] = x.x;
+                        v[it][2 * q + 1] = x.y;
+                        m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+                    }
                 }
             }
             const int e1 = scale_exp(warp_max_abs(m));
@@ -354,9 +404,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int units = (j1 - j0) * NB;
 #pragma unroll
             for (int t4 = 0; t4 < kTcMaxNB; ++t4) bnb[t4] = t4 < NB ? nbr[(size_t)a * NB + t4] : -1;
-            const uint32_t r0 = ru;  // raw slot of the item's first unit
+            const uint32_t r0 = ru;  // raw sequence number of the item's first unit
             for (int v = 0; v < 2 && v < units; ++v, ++ru)  // in flight during the dH staging below
-                issue_unit(la, j0 + v / NB, v % NB, (int)(ru % kTcRaw));
+                issue_unit(la, j0 + v / NB, v % NB, ru);
             // dH operands of every bond of the atom (all loads issued at once), once the MMAs of the previous item
             // are done with them
             constexpr int RPT = (3 * nel + kTcProdWarps * 32 - 1) / (kTcProdWarps * 32);
@@ -424,7 +474,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_arrive(B_(BBF));
             for (int v = 0; v < units; ++v) {
                 if (v + 2 < units) {
-                    issue_unit(la, j0 + (v + 2) / NB, (v + 2) % NB, (int)(ru % kTcRaw));
+                    issue_unit(la, j0 + (v + 2) / NB, (v + 2) % NB, ru);
                     ++ru;
                     cp_async_wait<2>();  // this unit's copies are done (the two after it may be in flight)
                 } else if (v + 1 < units) {
@@ -433,9 +483,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     cp_async_wait<0>();
                 }
                 __syncwarp();  // every lane's copies are visible to the warp
-                produce(v % NB, (int)((r0 + v) % kTcRaw));
+                produce(la, j0 + v / NB, v % NB, r0 + v);
             }
         }
+        // every bulk copy this warp issued has landed before the CTA releases its shared memory (after an abort the
+        // reads above may have skipped their waits)
+        if (S::BULK)
+            for (int rs = 0; rs < kTcRaw; ++rs)
+                if ((r_issued >> rs) & 1u) drain_wait(B_(BRF + rs * 4 + g), (r_last >> rs) & 1u, status);
+        cp_async_wait<0>();
     } else if (warp == kTcMmaWarp) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
