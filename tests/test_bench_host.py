@@ -32,6 +32,37 @@ def test_useful_flops_is_the_term_count(d):
     assert bench.useful_flops(d) == total
 
 
+@pytest.mark.parametrize("norb", [1, 3, 4, 7, 10])
+def test_tensor_core_tile_counts(norb):
+    """spec_prod_tc_kernel's issued and useful tensor work, enumerated per 128-row tile of frequencies and bond: FP16
+    MMAs of K = 16 over the padded K, N and all 128 rows, against the unpadded real GEMMs of the used rows."""
+    d = Dims(NA=3, NB=2, Norb=norb, NE=40, Nkz=3, Nqz=2, Nw=11)
+    t = bench.tc_shape(norb)
+    nfreq = bench.freq_count(d, False)
+    issued = useful = 0
+    for f0 in range(0, nfreq, t["FT"]):
+        rows = min(t["FT"], nfreq - f0) * norb
+        for _s in range(d.NB):
+            for _a in range(d.NA):
+                issued += 3 * (2 * 128 * t["N1"] * t["K1"] + 2 * 128 * t["N2"] * t["K2"])
+                useful += 3 * (2 * rows * (6 * norb) * (2 * norb) + 2 * rows * (2 * norb) * (6 * norb))
+    assert bench.tc_tensor_flops(d) == issued
+    assert bench.tc_useful_flops(d) == useful
+    assert t["K1"] >= 2 * norb and t["N1"] >= 6 * norb and t["K2"] >= 6 * norb and t["N2"] >= 2 * norb
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32"])
+def test_mixed_useful_work_is_within_the_issued_work(mode):
+    """Useful rows x K x N per in-range tap never exceeds the padded 128 x npad x kpad, and equals it where the
+    padding vanishes (Norb = 8: 16 energies fill 128 rows, 6 Norb = 48 fills N and K)."""
+    for d in (Dims(NA=2, NB=2, Norb=10, NE=50, Nkz=2, Nqz=2, Nw=7), Dims(NA=2, NB=1, Norb=8, NE=32, Nkz=1, Nqz=1, Nw=3)):
+        u, p = bench.mixed_useful_flops(d, mode), bench.mixed_tensor_flops(d, mode)
+        assert 0 < u <= p
+    d = Dims(NA=2, NB=1, Norb=8, NE=32, Nkz=1, Nqz=1, Nw=3)
+    if mode == "bf16x3":
+        assert bench.mixed_useful_flops(d, mode) == bench.mixed_tensor_flops(d, mode)
+
+
 def test_fft_length_is_the_smallest_2a3b():
     smooth = sorted(2 ** a * 3 ** b for a in range(14) for b in range(9))
     for NE in (1, 7, 32, 61, 256, 512, 1000, 1024):
