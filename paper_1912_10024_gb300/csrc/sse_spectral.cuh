@@ -642,3 +642,5 @@ cudaError_t launch_fft(const char* name, const FftPlan& p, const double2* tw, Lo
 
 }  // namespace
 }  // namespace sse
+
+#include "sse_fft32.cuh"

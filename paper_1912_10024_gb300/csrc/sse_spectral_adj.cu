@@ -984,7 +984,7 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
     double2* gD[2] = {g_D_less, g_D_greater};
     const int sym = (p.flags & SSE_FLAG_SYMMETRIZE) ? 1 : 0;
     for (int t = 0; t < 2; ++t) {
-        e = launch_fft("fft_e_kernel(W)", plan, tw,
+        e = launch_fft32("fft_e_kernel(W)", plan, tw,
                        LoadWT<C>{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
                        StoreSpecT<C>{Wh, L, wcols, L}, wcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
@@ -992,7 +992,7 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
                   dft_k_kernel<<<grid_for((size_t)L * wcols, 256), 256, 0, st>>>(Wh, d.Nkz, d.Nkz, (size_t)L * wcols,
                                                                                  0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
+        e = launch_fft32("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
                        gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(G)", st,
@@ -1000,7 +1000,7 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
                                                                                  0));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
+        e = launch_fft32("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(K)", st,
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols,
@@ -1023,7 +1023,7 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         StoreGDT<C> sg{gD[t], gD[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9,
                        p.scale / (double)nfreq, t, L};
-        e = launch_fft("fft_e_kernel(H)", plan, tw, LoadSpecConjT<C>{Hh, L, kcols}, sg, kcols, d.Nqz, st);
+        e = launch_fft32("fft_e_kernel(H)", plan, tw, LoadSpecConjT<C>{Hh, L, kcols}, sg, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
     }
     SSE_TIMED("spec_gdh_reduce_kernel", st,
@@ -1137,7 +1137,7 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
     const int sym = (p.flags & SSE_FLAG_SYMMETRIZE) ? 1 : 0;
     for (int t = 0; t < 2; ++t) {
         if (nA > 0) {
-            e = launch_fft("fft_e_kernel(W)", plan, tw,
+            e = launch_fft32("fft_e_kernel(W)", plan, tw,
                            LoadWT<C>{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
                            StoreSpecT<C>{Wh, L, wcols, L}, wcols, d.Nkz, st);
             if (e != cudaSuccess) return e;
@@ -1146,7 +1146,7 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
                                                                                      (size_t)L * wcols, 0));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-            e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
+            e = launch_fft32("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
             if (e != cudaSuccess) return e;
             SSE_TIMED("dft_k_kernel(K)", st,
                       dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz,
@@ -1170,7 +1170,7 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
                                                                                  1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
-        e = launch_fft("fft_e_kernel(R)", plan, tw, LoadSpecConjT<C>{Rh, L, gcols},
+        e = launch_fft32("fft_e_kernel(R)", plan, tw, LoadSpecConjT<C>{Rh, L, gcols},
                        StoreSigmaT<C>{gG[t], d.NE, gcols, 0, inv, d.NE}, gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
     }

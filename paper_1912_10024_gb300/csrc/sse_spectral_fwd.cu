@@ -427,7 +427,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
     for (int t = 0; t < 2; ++t) {
         // 1. lag kernel -> K^ (needs only D; with `pipe` it runs while G^t is still arriving)
         LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
-        e = launch_fft("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
+        e = launch_fft32("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(K)", st,
                   dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
@@ -436,12 +436,12 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
         if (pipe) {
             for (int k = 0; k < d.Nkz; ++k) {
                 if ((e = cudaStreamWaitEvent(st, pipe->g[t][k], 0)) != cudaSuccess) return e;
-                e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t] + (size_t)k * d.NE * gcols, d.NE, gcols},
+                e = launch_fft32("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t] + (size_t)k * d.NE * gcols, d.NE, gcols},
                                StoreSpecT<C>{Gh + (size_t)k * L * gcols, L, gcols, L}, gcols, 1, st);
                 if (e != cudaSuccess) return e;
             }
         } else {
-            e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols},
+            e = launch_fft32("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols},
                            StoreSpecT<C>{Gh, L, gcols, L}, gcols, d.Nkz, st);
             if (e != cudaSuccess) return e;
         }
@@ -483,7 +483,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
             dk.Nkz = 1;
             for (int k = 0; k < d.Nkz; ++k) {
                 double2* Sk = S[t] + (size_t)k * d.NE * d.NA * nel;
-                e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh + (size_t)k * L * scols, L, scols},
+                e = launch_fft32("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh + (size_t)k * L * scols, L, scols},
                                StoreSigmaT<C>{Sk, d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE},
                                scols, 1, st);
                 if (e != cudaSuccess) return e;
@@ -495,7 +495,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                 if ((e = cudaEventRecord(pipe->s[t][k], st)) != cudaSuccess) return e;
             }
         } else {
-            e = launch_fft("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh, L, scols},
+            e = launch_fft32("fft_e_kernel(S)", plan, tw, LoadSpecConjT<C>{Sh, L, scols},
                            StoreSigmaT<C>{S[t], d.NE, (size_t)d.NA * nel, (size_t)d.a_begin * nel, inv, d.NE}, scols,
                            d.Nkz, st);
             if (e != cudaSuccess) return e;

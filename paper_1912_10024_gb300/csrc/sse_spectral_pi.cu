@@ -475,7 +475,7 @@ cudaError_t spectral_pi_t(const sse_dims& d, const int32_t* nbr, const double2* 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const double2* G[2] = {G_less, G_greater};
     for (int t = 0; t < 2; ++t) {
-        e = launch_fft("fft_e_kernel(G)", plan, tw, LoadGT<C>{G[t], d.NE, gcols}, StoreSpecT<C>{Gh[t], L, gcols, L},
+        e = launch_fft32("fft_e_kernel(G)", plan, tw, LoadGT<C>{G[t], d.NE, gcols}, StoreSpecT<C>{Gh[t], L, gcols, L},
                        gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
         SSE_TIMED("dft_k_kernel(G)", st,
@@ -526,7 +526,7 @@ cudaError_t spectral_pi_t(const sse_dims& d, const int32_t* nbr, const double2* 
                   dft_k_kernel<<<grid_for((size_t)L * ccols, 256), 256, 0, st>>>(Ch[t], d.Nkz, d.Nkz,
                                                                                  (size_t)L * ccols, 1));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = launch_fft("fft_e_kernel(C)", plan, tw, LoadSpecConjT<C>{Ch[t], L, ccols},
+        e = launch_fft32("fft_e_kernel(C)", plan, tw, LoadSpecConjT<C>{Ch[t], L, ccols},
                        StorePiT<C>{P[t], d.Nw, d.NA, d.NB + 1, (size_t)d.a_begin * (d.NB + 1) * 9, inv_scale,
                                    d.Nw + 1},
                        ccols, d.Nqz, st);
