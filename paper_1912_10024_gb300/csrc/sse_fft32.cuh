@@ -264,5 +264,94 @@ cudaError_t launch_fft32(const char* name, const FftPlan& p, const double2* tw, 
     return launch_fft(name, p, tw, ld, sv, ncols, batches, st);
 }
 
+// kz-direction DFT with the grid size Nk as a template parameter (FP32 and FP64 spectra), in place on X[Nk][M]:
+// out[kappa] = sum_{k < n_in} x_k exp(-+2 pi i k kappa / Nk), one column m per thread, the column in registers and
+// the cosines and sines compile-time constants. Inputs k and Nk - k are paired (p = x_k + x_{Nk-k},
+// q = x_k - x_{Nk-k}) and so are outputs kappa and Nk - kappa: out[kappa] = C -+ i S, out[Nk - kappa] = C +- i S
+// with C = x_0 (+ (-1)^kappa x_{Nk/2}) + sum_k p_k cos(2 pi k kappa / Nk), S = sum_k q_k sin(2 pi k kappa / Nk).
+template <class C, int NK>
+__global__ void __launch_bounds__(256) dft_kz_kernel(C* __restrict__ X, int n_in, size_t M, int inverse) {
+    using R = typename CT<C>::R;
+    constexpr int H = (NK - 1) / 2;  // (k, NK - k) pairs
+    constexpr bool EVEN = NK % 2 == 0;
+    const R sgn = inverse ? (R)1 : (R)-1;
+    for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
+        C x[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) x[k] = k < n_in ? X[(size_t)k * M + m] : CT<C>::mk(0, 0);
+        C p[H + 1], q[H + 1];
+        C c0 = x[0];
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            p[k] = cadd(x[k], x[NK - k]);
+            q[k] = csub(x[k], x[NK - k]);
+            c0 = cadd(c0, p[k]);
+        }
+        const C xh = EVEN ? x[NK / 2] : CT<C>::mk(0, 0);
+        X[m] = cadd(c0, xh);
+        static_for<1, H + 1>([&](auto kc) {
+            constexpr int kap = decltype(kc)::value;
+            C Cs = x[0], Sn = CT<C>::mk(0, 0);
+            static_for<1, H + 1>([&](auto jc) {
+                constexpr int k = decltype(jc)::value;
+                constexpr CxCis w = cx_cis((long)k * kap, NK);
+                Cs.x = fma(p[k].x, (R)w.c, Cs.x);
+                Cs.y = fma(p[k].y, (R)w.c, Cs.y);
+                Sn.x = fma(q[k].x, (R)w.s, Sn.x);
+                Sn.y = fma(q[k].y, (R)w.s, Sn.y);
+            });
+            if constexpr (EVEN) {
+                constexpr R e = (kap & 1) ? (R)-1 : (R)1;
+                Cs.x = fma(e, xh.x, Cs.x);
+                Cs.y = fma(e, xh.y, Cs.y);
+            }
+            X[(size_t)kap * M + m] = CT<C>::mk(Cs.x - sgn * Sn.y, Cs.y + sgn * Sn.x);
+            X[(size_t)(NK - kap) * M + m] = CT<C>::mk(Cs.x + sgn * Sn.y, Cs.y - sgn * Sn.x);
+        });
+        if constexpr (EVEN && NK > 1) {  // kappa = NK/2: cos(pi k) = (-1)^k, sin = 0
+            C Cs = x[0];
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                const R e = (k & 1) ? (R)-1 : (R)1;
+                Cs.x = fma(e, p[k].x, Cs.x);
+                Cs.y = fma(e, p[k].y, Cs.y);
+            }
+            constexpr R e = ((NK / 2) & 1) ? (R)-1 : (R)1;
+            X[(size_t)(NK / 2) * M + m] = CT<C>::mk(fma(e, xh.x, Cs.x), fma(e, xh.y, Cs.y));
+        }
+    }
+}
+
+template <class C, int NK>
+cudaError_t launch_dft_kz_t(const char* name, C* X, int n_in, size_t M, int inverse, cudaStream_t st) {
+    SSE_TIMED(name, st, dft_kz_kernel<C, NK><<<grid_for(M, 256), 256, 0, st>>>(X, n_in, M, inverse));
+    return cudaGetLastError();
+}
+
+// the kz DFT of a spectrum: the compile-time kernel for Nk = 1 .. kMaxNk
+template <class C>
+cudaError_t launch_dft_k(const char* name, C* X, int Nk, int n_in, size_t M, int inverse, cudaStream_t st) {
+    if (M == 0) return cudaSuccess;
+    switch (Nk) {
+        case 1: return launch_dft_kz_t<C, 1>(name, X, n_in, M, inverse, st);
+        case 2: return launch_dft_kz_t<C, 2>(name, X, n_in, M, inverse, st);
+        case 3: return launch_dft_kz_t<C, 3>(name, X, n_in, M, inverse, st);
+        case 4: return launch_dft_kz_t<C, 4>(name, X, n_in, M, inverse, st);
+        case 5: return launch_dft_kz_t<C, 5>(name, X, n_in, M, inverse, st);
+        case 6: return launch_dft_kz_t<C, 6>(name, X, n_in, M, inverse, st);
+        case 7: return launch_dft_kz_t<C, 7>(name, X, n_in, M, inverse, st);
+        case 8: return launch_dft_kz_t<C, 8>(name, X, n_in, M, inverse, st);
+        case 9: return launch_dft_kz_t<C, 9>(name, X, n_in, M, inverse, st);
+        case 10: return launch_dft_kz_t<C, 10>(name, X, n_in, M, inverse, st);
+        case 11: return launch_dft_kz_t<C, 11>(name, X, n_in, M, inverse, st);
+        case 12: return launch_dft_kz_t<C, 12>(name, X, n_in, M, inverse, st);
+        case 13: return launch_dft_kz_t<C, 13>(name, X, n_in, M, inverse, st);
+        case 14: return launch_dft_kz_t<C, 14>(name, X, n_in, M, inverse, st);
+        case 15: return launch_dft_kz_t<C, 15>(name, X, n_in, M, inverse, st);
+        case 16: return launch_dft_kz_t<C, 16>(name, X, n_in, M, inverse, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 }  // namespace sse

@@ -375,69 +375,6 @@ __global__ void __launch_bounds__(kFftThreads) fft_e_kernel(FftPlan p, const dou
     }
 }
 
-// ---------------------------------------------------------------------------
-// kz-direction DFT, in place on X[Nk][M]: out[kappa] = sum_{k < n_in} in[k] exp(-+2 pi i k kappa / Nk).
-// Inputs k and Nk-k are paired (p = x_k + x_{Nk-k}, m = x_k - x_{Nk-k}) and so are outputs kappa and
-// Nk-kappa: out[kappa] = C -+ i S, out[Nk-kappa] = C +- i S with C = x_0 (+ (-1)^kappa x_{Nk/2}) +
-// sum_k p_k cos(2 pi k kappa / Nk), S = sum_k m_k sin(2 pi k kappa / Nk).
-// ---------------------------------------------------------------------------
-template <class C>
-__global__ void dft_k_kernel(C* __restrict__ X, int Nk, int n_in, size_t M, int inverse) {
-    using R = typename CT<C>::R;
-    __shared__ R cs[kMaxNk], sn[kMaxNk];
-    if (threadIdx.x < Nk) {
-        double s, c;
-        sincospi(2.0 * (double)threadIdx.x / (double)Nk, &s, &c);
-        cs[threadIdx.x] = (R)c;
-        sn[threadIdx.x] = (R)s;
-    }
-    __syncthreads();
-    const int half = (Nk - 1) / 2;  // number of (k, Nk-k) pairs
-    const bool even = (Nk % 2) == 0;
-    const R sgn = inverse ? (R)1 : (R)-1;  // out = C + sgn * i * S for kappa <= half
-    for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
-        C x[kMaxNk];
-        for (int k = 0; k < Nk; ++k) x[k] = k < n_in ? X[(size_t)k * M + m] : CT<C>::mk(0, 0);
-        C p[kMaxNk / 2 + 1], q[kMaxNk / 2 + 1];
-        C c0 = x[0];
-        for (int k = 1; k <= half; ++k) {
-            p[k] = cadd(x[k], x[Nk - k]);
-            q[k] = csub(x[k], x[Nk - k]);
-            c0 = cadd(c0, p[k]);
-        }
-        const C xh = even ? x[Nk / 2] : CT<C>::mk(0, 0);
-        X[m] = cadd(c0, xh);  // kappa = 0
-        for (int kap = 1; kap <= half; ++kap) {
-            C Cs = x[0], S = CT<C>::mk(0, 0);
-            for (int k = 1; k <= half; ++k) {
-                const int r = (k * kap) % Nk;
-                Cs.x = fma(p[k].x, cs[r], Cs.x);
-                Cs.y = fma(p[k].y, cs[r], Cs.y);
-                S.x = fma(q[k].x, sn[r], S.x);
-                S.y = fma(q[k].y, sn[r], S.y);
-            }
-            if (even) {
-                const R e = (kap & 1) ? (R)-1 : (R)1;
-                Cs.x = fma(e, xh.x, Cs.x);
-                Cs.y = fma(e, xh.y, Cs.y);
-            }
-            // i*S = (-S.y, S.x)
-            X[(size_t)kap * M + m] = CT<C>::mk(Cs.x - sgn * S.y, Cs.y + sgn * S.x);
-            X[(size_t)(Nk - kap) * M + m] = CT<C>::mk(Cs.x + sgn * S.y, Cs.y - sgn * S.x);
-        }
-        if (even && Nk > 1) {  // kappa = Nk/2: cos(pi k) = (-1)^k, sin = 0
-            C Cs = x[0];
-            for (int k = 1; k <= half; ++k) {
-                const R e = (k & 1) ? (R)-1 : (R)1;
-                Cs.x = fma(e, p[k].x, Cs.x);
-                Cs.y = fma(e, p[k].y, Cs.y);
-            }
-            const R e = ((Nk / 2) & 1) ? (R)-1 : (R)1;
-            X[(size_t)(Nk / 2) * M + m] = CT<C>::mk(fma(e, xh.x, Cs.x), fma(e, xh.y, Cs.y));
-        }
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------

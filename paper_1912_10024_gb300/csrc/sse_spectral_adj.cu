@@ -988,24 +988,15 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
                        LoadWT<C>{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
                        StoreSpecT<C>{Wh, L, wcols, L}, wcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(W)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * wcols, 256), 256, 0, st>>>(Wh, d.Nkz, d.Nkz, (size_t)L * wcols,
-                                                                                 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(W)", Wh, d.Nkz, d.Nkz, (size_t)L * wcols, 0, st)) != cudaSuccess) return e;
         e = launch_fft32("fft_e_kernel(G)", plan, tw, LoadGT<C>{p.G[t], d.NE, gcols}, StoreSpecT<C>{Gh, L, gcols, L},
                        gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(G)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols,
-                                                                                 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(G)", Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0, st)) != cudaSuccess) return e;
         LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
         e = launch_fft32("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(K)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols,
-                                                                                 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(K)", Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0, st)) != cudaSuccess) return e;
         if constexpr (fp32) {
             SSE_TIMED("spec_adj_kernel", st,
                       spec_adj32_kernel<<<dim3((unsigned)nA, (unsigned)ac32.nchunks), ac32.threads, ac32.smem, st>>>(
@@ -1017,10 +1008,7 @@ cudaError_t spectral_bwd_t(const Problem& p, const double2* gS_less, const doubl
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // grad D from H^t: emission lags -> D^t, absorption lags -> D^t'
-        SSE_TIMED("dft_k_kernel(H)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Hh, d.Nkz, d.Nkz, (size_t)L * kcols,
-                                                                                 1));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(H)", Hh, d.Nkz, d.Nkz, (size_t)L * kcols, 1, st)) != cudaSuccess) return e;
         StoreGDT<C> sg{gD[t], gD[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9,
                        p.scale / (double)nfreq, t, L};
         e = launch_fft32("fft_e_kernel(H)", plan, tw, LoadSpecConjT<C>{Hh, L, kcols}, sg, kcols, d.Nqz, st);
@@ -1141,17 +1129,11 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
                            LoadWT<C>{W[t], d.NE, d.Norb, (size_t)d.NA * nel, (size_t)d.a_begin * nel, sym},
                            StoreSpecT<C>{Wh, L, wcols, L}, wcols, d.Nkz, st);
             if (e != cudaSuccess) return e;
-            SSE_TIMED("dft_k_kernel(W)", st,
-                      dft_k_kernel<<<grid_for((size_t)L * wcols, 256), 256, 0, st>>>(Wh, d.Nkz, d.Nkz,
-                                                                                     (size_t)L * wcols, 0));
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = launch_dft_k("dft_kz_kernel(W)", Wh, d.Nkz, d.Nkz, (size_t)L * wcols, 0, st)) != cudaSuccess) return e;
             LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
             e = launch_fft32("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
             if (e != cudaSuccess) return e;
-            SSE_TIMED("dft_k_kernel(K)", st,
-                      dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz,
-                                                                                     (size_t)L * kcols, 0));
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = launch_dft_k("dft_kz_kernel(K)", Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0, st)) != cudaSuccess) return e;
         }
         if constexpr (fp32) {
             const size_t gy = (nfreq + gc.fchunk - 1) / gc.fchunk;
@@ -1165,10 +1147,7 @@ cudaError_t spectral_bwd_g_t(const Problem& p, const double2* gS_less, const dou
                           pc, d, offs, list, p.dH, Wh, Kh, Rh, L, p.scale));
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(R)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Rh, d.Nkz, d.Nkz, (size_t)L * gcols,
-                                                                                 1));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(R)", Rh, d.Nkz, d.Nkz, (size_t)L * gcols, 1, st)) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
         e = launch_fft32("fft_e_kernel(R)", plan, tw, LoadSpecConjT<C>{Rh, L, gcols},
                        StoreSigmaT<C>{gG[t], d.NE, gcols, 0, inv, d.NE}, gcols, d.Nkz, st);

@@ -429,9 +429,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
         LoadLagT<C> ll{p.D[t], p.D[1 - t], d.Nw, L, (size_t)d.NA * d.NB * 9, (size_t)d.a_begin * d.NB * 9};
         e = launch_fft32("fft_e_kernel(K)", plan, tw, ll, StoreSpecT<C>{Kh, L, kcols, L}, kcols, d.Nqz, st);
         if (e != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(K)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * kcols, 256), 256, 0, st>>>(Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(K)", Kh, d.Nkz, d.Nqz, (size_t)L * kcols, 0, st)) != cudaSuccess) return e;
         // 2. G^t -> G^ (E-transform per kz slice as the slices arrive, then the kz DFT)
         if (pipe) {
             for (int k = 0; k < d.Nkz; ++k) {
@@ -445,9 +443,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
                            StoreSpecT<C>{Gh, L, gcols, L}, gcols, d.Nkz, st);
             if (e != cudaSuccess) return e;
         }
-        SSE_TIMED("dft_k_kernel(G)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(G)", Gh, d.Nkz, d.Nkz, (size_t)L * gcols, 0, st)) != cudaSuccess) return e;
         // 3. block products (one frequency of each (f, -f) pair with anti-Hermitian inputs, then the mirror)
         if (tc) {
             e = spectral_prod_tc(d, fm, p.nbr, p.dH, reinterpret_cast<const float2*>(Gh),
@@ -473,9 +469,7 @@ cudaError_t spectral_fwd_t(const Problem& p, double2* S_less, double2* S_greater
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         // 4. inverse transforms into Sigma^t
-        SSE_TIMED("dft_k_kernel(S)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * scols, 256), 256, 0, st>>>(Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(S)", Sh, d.Nkz, d.Nkz, (size_t)L * scols, 1, st)) != cudaSuccess) return e;
         const double inv = 1.0 / ((double)d.Nkz * (double)L);
         const bool sym = (p.flags & SSE_FLAG_SYMMETRIZE) != 0;
         if (pipe) {  // slice by slice, each handed to its download as soon as it is written

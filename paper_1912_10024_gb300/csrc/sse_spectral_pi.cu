@@ -478,10 +478,7 @@ cudaError_t spectral_pi_t(const sse_dims& d, const int32_t* nbr, const double2* 
         e = launch_fft32("fft_e_kernel(G)", plan, tw, LoadGT<C>{G[t], d.NE, gcols}, StoreSpecT<C>{Gh[t], L, gcols, L},
                        gcols, d.Nkz, st);
         if (e != cudaSuccess) return e;
-        SSE_TIMED("dft_k_kernel(G)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * gcols, 256), 256, 0, st>>>(Gh[t], d.Nkz, d.Nkz,
-                                                                                 (size_t)L * gcols, 0));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(G)", Gh[t], d.Nkz, d.Nkz, (size_t)L * gcols, 0, st)) != cudaSuccess) return e;
     }
     const bool half = (flags & SSE_FLAG_ANTIHERMITIAN) != 0;
     const FreqMap fm = make_freq_map(d.Nkz, L, half);
@@ -522,10 +519,7 @@ cudaError_t spectral_pi_t(const sse_dims& d, const int32_t* nbr, const double2* 
     double2* P[2] = {P_less, P_greater};
     const double inv_scale = scale / ((double)d.Nkz * (double)L);
     for (int t = 0; t < 2; ++t) {
-        SSE_TIMED("dft_k_kernel(C)", st,
-                  dft_k_kernel<<<grid_for((size_t)L * ccols, 256), 256, 0, st>>>(Ch[t], d.Nkz, d.Nkz,
-                                                                                 (size_t)L * ccols, 1));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_dft_k("dft_kz_kernel(C)", Ch[t], d.Nkz, d.Nkz, (size_t)L * ccols, 1, st)) != cudaSuccess) return e;
         e = launch_fft32("fft_e_kernel(C)", plan, tw, LoadSpecConjT<C>{Ch[t], L, ccols},
                        StorePiT<C>{P[t], d.Nw, d.NA, d.NB + 1, (size_t)d.a_begin * (d.NB + 1) * 9, inv_scale,
                                    d.Nw + 1},
