@@ -5,13 +5,15 @@
 // place), and stores the frequencies in natural order. The lengths and the codelets are compile-time, so every index
 // inside a codelet is a constant; the radix-4/2/3 Stockham kernel fft_e_kernel keeps every other length and the FP64
 // transforms. Same loader and store interface. At the FinFET workload (L = 576) the transform of G takes 2.9 ms per
-// type against 3.8 ms for fft_e_kernel, the inverse transform into Sigma 2.3 ms against 3.2.
+// type against 3.8 ms for fft_e_kernel (2.6 ms with the prefetching variant below), the inverse transform into
+// Sigma 2.3 ms against 3.2.
 //
 // Included at the end of sse_spectral.cuh (it uses that file's loaders, stores, CT, launch_fft and SSE_TIMED).
 #pragma once
 
 #include <string.h>
 
+#include <algorithm>
 #include <type_traits>
 
 namespace sse {
@@ -234,6 +236,143 @@ cudaError_t launch_e4_t(const char* name, const double2* tw, Load ld, Store sv, 
     return cudaGetLastError();
 }
 
+// The same transform in a persistent CTA that copies the next tile into a raw staging buffer (cp.async, the
+// loader's own element type) while it transforms the current one, for loaders that read one global element per
+// (batch, row, column): the tile's loads are no longer a wait between the CTA's compute phases.
+constexpr int kE4pSmemMax = 113 * 1024;
+
+template <class T, class = void>
+struct HasRawSrc : std::false_type {};
+template <class T>
+struct HasRawSrc<T, std::void_t<typename T::Raw>> : std::true_type {};
+template <class T, bool = HasRawSrc<T>::value>
+struct HasRawSrcType {
+    using type = char;
+};
+template <class T>
+struct HasRawSrcType<T, true> {
+    using type = typename T::Raw;
+};
+
+// asynchronous copy of one 8- or 16-byte element global -> shared; with ok false the destination is zero-filled and
+// nothing is read
+template <int B>
+__device__ __forceinline__ void cp_async_elem(uint32_t dst, const void* src, bool ok) {
+    static_assert(B == 8 || B == 16, "8- or 16-byte elements");
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+
+template <int L1, int L2, class Load>
+size_t e4p_smem(const Load& ld) {
+    return (size_t)E4Shape<L1, L2>::SMEM + (size_t)ld.src_rows() * kE4Cols * sizeof(typename Load::Raw);
+}
+
+template <int L1, int L2, class Load, class Store>
+__global__ void __launch_bounds__(kE4Threads, 2)
+    fft_e4p_kernel(const double2* __restrict__ tw_g, Load ld, Store sv, size_t ncols, int gx, int ntiles) {
+    using S = E4Shape<L1, L2>;
+    using Raw = typename Load::Raw;
+    constexpr int CC = kE4Cols, L = S::L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* X = reinterpret_cast<float2*>(smem_raw);  // [L1][LP][CC]
+    float2* tw = X + S::SL;                          // [L]
+    Raw* raw = reinterpret_cast<Raw*>(tw + L);       // [rows][CC]: the next tile as stored (16-byte aligned: L even)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rows = ld.src_rows();
+    const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(raw);
+    auto issue = [&](int tile) {
+        const int batch = tile / gx;
+        const size_t col0 = (size_t)(tile % gx) * CC;
+        for (int i = tid; i < rows * CC; i += nt) {
+            const int c = i % CC, r = i / CC;
+            const bool ok = col0 + c < ncols;
+            cp_async_elem<(int)sizeof(Raw)>(raw_s + (uint32_t)(i * (int)sizeof(Raw)),
+                                           ld.src(ok ? batch : 0, ok ? r : 0, ok ? col0 + c : 0), ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int m = tid; m < L; m += nt) tw[m] = make_float2((float)tw_g[m].x, (float)tw_g[m].y);
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int batch = tile / gx;
+        const size_t col0 = (size_t)(tile % gx) * CC;
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();  // the raw tile has landed for every thread; the previous tile's store has read X
+        for (int i = tid; i < L * CC; i += nt) {
+            const int r = i / CC;
+            X[S::pos_in(r) * CC + i % CC] = r < rows ? Load::cvt(raw[i]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();  // the raw buffer is free
+        if (tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
+        for (int t = tid; t < CC * L2; t += nt) {
+            const int c = t % CC, n2 = t / CC;
+            float2* p = X + n2 * CC + c;
+            float2 x[L1];
+#pragma unroll
+            for (int n1 = 0; n1 < L1; ++n1) x[n1] = p[n1 * S::LP * CC];
+            RegDft<L1>::run(x);
+#pragma unroll
+            for (int k1 = 1; k1 < L1; ++k1) x[k1] = cmul(x[k1], tw[n2 * k1]);
+#pragma unroll
+            for (int k1 = 0; k1 < L1; ++k1) p[k1 * S::LP * CC] = x[k1];
+        }
+        __syncthreads();
+        for (int t = tid; t < CC * L1; t += nt) {
+            const int c = t % CC, k1 = t / CC;
+            float2* p = X + k1 * S::LP * CC + c;
+            float2 x[L2];
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) x[n2] = p[n2 * CC];
+            RegDft<L2>::run(x);
+#pragma unroll
+            for (int k2 = 0; k2 < L2; ++k2) p[k2 * CC] = x[k2];
+        }
+        __syncthreads();
+        for (int t = tid; t < sv.rows * CC; t += nt) {
+            const int c = t % CC, e = t / CC;
+            if (col0 + c < ncols) sv(batch, e, col0 + c, X[S::pos_out(e) * CC + c]);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int L1, int L2, class Load, class Store>
+cudaError_t launch_e4p_t(const char* name, const double2* tw, Load ld, Store sv, size_t ncols, int batches,
+                         cudaStream_t st) {
+    const size_t smem = e4p_smem<L1, L2>(ld);
+    auto kern = fft_e4p_kernel<L1, L2, Load, Store>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const size_t gx = (ncols + kE4Cols - 1) / kE4Cols;
+    if (gx == 0 || batches == 0) return cudaSuccess;
+    if (gx * (size_t)batches > 0x7fffffffu) return cudaErrorInvalidValue;
+    const int ntiles = (int)(gx * (size_t)batches);
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kE4Threads, smem)) != cudaSuccess) return e;
+    const int grid = std::min(ntiles, std::max(1, per_sm) * nsm);
+    SSE_TIMED(name, st, kern<<<grid, kE4Threads, smem, st>>>(tw, ld, sv, ncols, (int)gx, ntiles));
+    return cudaGetLastError();
+}
+
+// The prefetching kernel for FP64 input tiles (G: 16-byte elements, the larger share of the transform's traffic)
+// where the staging buffer fits; fft_e4_kernel otherwise. Measured at FinFET (L = 576), per step of two types: the
+// transform of G 5.81 -> 5.27 ms with the prefetch; the inverse transform into Sigma (FP32 spectrum in, 8-byte
+// elements) 4.62 -> 5.05 ms with it (two CTAs per SM instead of four), so it keeps fft_e4_kernel.
+template <int L1, int L2, class Load, class Store>
+cudaError_t launch_e4_any(const char* name, const double2* tw, Load ld, Store sv, size_t ncols, int batches,
+                          cudaStream_t st) {
+    if constexpr (HasRawSrc<Load>::value && sizeof(typename HasRawSrcType<Load>::type) == 16) {
+        if (e4p_smem<L1, L2>(ld) <= (size_t)kE4pSmemMax)
+            return launch_e4p_t<L1, L2>(name, tw, ld, sv, ncols, batches, st);
+    }
+    return launch_e4_t<L1, L2>(name, tw, ld, sv, ncols, batches, st);
+}
+
 // profile label of the register-codelet kernel for a transform the drivers name "fft_e_kernel(X)"
 inline const char* e4_label(const char* name) {
     static const char* const labels[][2] = {
@@ -253,11 +392,11 @@ cudaError_t launch_fft32(const char* name, const FftPlan& p, const double2* tw, 
                          int batches, cudaStream_t st) {
     if constexpr (std::is_same<typename Load::C, float2>::value) {
         switch (p.L) {
-            case 36: return launch_e4_t<6, 6>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 54: return launch_e4_t<6, 9>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 288: return launch_e4_t<16, 18>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 576: return launch_e4_t<24, 24>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 1152: return launch_e4_t<32, 36>(e4_label(name), tw, ld, sv, ncols, batches, st);
+            case 36: return launch_e4_any<6, 6>(e4_label(name), tw, ld, sv, ncols, batches, st);
+            case 54: return launch_e4_any<6, 9>(e4_label(name), tw, ld, sv, ncols, batches, st);
+            case 288: return launch_e4_any<16, 18>(e4_label(name), tw, ld, sv, ncols, batches, st);
+            case 576: return launch_e4_any<24, 24>(e4_label(name), tw, ld, sv, ncols, batches, st);
+            case 1152: return launch_e4_any<32, 36>(e4_label(name), tw, ld, sv, ncols, batches, st);
             default: break;
         }
     }

@@ -286,6 +286,11 @@ struct LoadGT {
         const double2 v = G[((size_t)k * NE + r) * ncols + col];
         return CT<C>::mk(v.x, v.y);
     }
+    // the same element for an asynchronous copy: rows below src_rows() are read raw from src() and converted
+    using Raw = double2;
+    __host__ __device__ int src_rows() const { return NE; }
+    __device__ const Raw* src(int k, int r, size_t col) const { return G + ((size_t)k * NE + r) * ncols + col; }
+    static __device__ C cvt(Raw v) { return CT<C>::mk(v.x, v.y); }
 };
 using LoadG = LoadGT<double2>;
 // lag kernel of one qz slice: row w+1 <- D^t(q,w), row L-(w+1) <- D^t'(q,w), else zero.
@@ -313,6 +318,10 @@ struct LoadSpecConjT {
     int L;
     size_t ncols;
     __device__ C operator()(int k, int r, size_t col) const { return cconj(X[((size_t)k * L + r) * ncols + col]); }
+    using Raw = C;
+    __host__ __device__ int src_rows() const { return L; }
+    __device__ const Raw* src(int k, int r, size_t col) const { return X + ((size_t)k * L + r) * ncols + col; }
+    static __device__ C cvt(Raw v) { return cconj(v); }
 };
 using LoadSpecConj = LoadSpecConjT<double2>;
 
