@@ -1,6 +1,7 @@
 // Shared machinery of the transform-based (convolution-theorem) evaluation of Eqs. (3) and (4) and of the
-// adjoint of Eq. (3): the E-direction FFT and kz DFT kernels with their loaders and stores, the frequency maps of
-// the half spectrum, complex helpers, the frequency-per-CTA picker and the FP64 product configuration. Included by
+// adjoint of Eq. (3): the E-direction FFT kernel with its loaders and stores, the frequency maps of the half
+// spectrum, complex helpers, the frequency-per-CTA picker and the FP64 product configuration; sse_fft32.cuh, included
+// at the end, adds the kz DFT and the FP32 E-transforms with register codelets. Included by
 // sse_spectral_fwd.cu (Sigma), sse_spectral_pi.cu (Pi) and sse_spectral_adj.cu (adjoint, gradient in G); each
 // translation unit gets its own copy of the internal-linkage kernels and helpers.
 //
@@ -41,13 +42,13 @@ namespace {
 
 // Transform CTAs: 512 threads and at most 100 KB of shared memory, two CTAs (32 warps) per SM; each thread keeps
 // 8 global loads in flight (the shape was chosen by timing 256/512/1024 threads and 8/12/16 loads). The FP64
-// transforms are bound by the FP64 pipe; the FP32 ones by instruction issue and by the FP64 -> FP32 conversions of
-// their inputs, which also run on the FP64 pipe.
+// transforms are bound by the FP64 pipe; the FP32 ones (lengths without a register-codelet kernel) by instruction
+// issue and the waits on their loads.
 constexpr int kFftThreads = 512;
 constexpr int kFftSmemBudget = 100 * 1024;
 constexpr int kFftLoadBatch = 8;
 constexpr int kMaxStages = 24;
-constexpr int kMaxNk = 16;  // kz grid sizes handled by the small DFT pass
+constexpr int kMaxNk = 16;  // kz grid sizes handled by the kz DFT pass (one kernel instantiation each)
 
 struct FftPlan {
     int L, C, nst;
