@@ -1,12 +1,12 @@
-// FP32 E-direction transforms with the DFT codelets in registers, for the transform lengths of the stated workloads
-// and of the small test shapes: each CTA transforms 8 adjacent columns of one batch, of length L = L1 * L2, as two
-// passes over a tile in shared memory (the four-step factorisation of the DFT: L2 DFTs of length L1 down the
-// stride-L2 rows, the twiddles exp(-2 pi i n2 k1 / L), then L1 DFTs of length L2 along contiguous rows, both in
-// place), and stores the frequencies in natural order. The lengths and the codelets are compile-time, so every index
+// Transform kernels with compile-time sizes. (1) FP32 E-direction transforms with the DFT codelets in registers,
+// for the transform lengths of the stated workloads and of the small test shapes: each CTA transforms 8 adjacent
+// columns of one batch, of length L = L1 * L2, as two passes over a tile in shared memory (the four-step
+// factorisation of the DFT: L2 DFTs of length L1 down the stride-L2 rows, the twiddles exp(-2 pi i n2 k1 / L), then
+// L1 DFTs of length L2 along contiguous rows, both in place), and stores the frequencies in natural order. Every index
 // inside a codelet is a constant; the radix-4/2/3 Stockham kernel fft_e_kernel keeps every other length and the FP64
 // transforms. Same loader and store interface. At the FinFET workload (L = 576) the transform of G takes 2.9 ms per
 // type against 3.8 ms for fft_e_kernel (2.6 ms with the prefetching variant below), the inverse transform into
-// Sigma 2.3 ms against 3.2.
+// Sigma 2.3 ms against 3.2. (2) The kz DFT of FP32 and FP64 spectra with the grid size as a template parameter.
 //
 // Included at the end of sse_spectral.cuh (it uses that file's loaders, stores, CT, launch_fft and SSE_TIMED).
 #pragma once
@@ -236,6 +236,22 @@ cudaError_t launch_e4_t(const char* name, const double2* tw, Load ld, Store sv, 
     return cudaGetLastError();
 }
 
+// profile labels of the register-codelet kernels (plain, prefetching) for a transform the drivers name
+// "fft_e_kernel(X)"
+inline const char* e4_label(const char* name, bool prefetch) {
+    static const char* const labels[][3] = {
+        {"fft_e_kernel(G)", "fft_e4_kernel(G)", "fft_e4p_kernel(G)"},
+        {"fft_e_kernel(K)", "fft_e4_kernel(K)", "fft_e4p_kernel(K)"},
+        {"fft_e_kernel(S)", "fft_e4_kernel(S)", "fft_e4p_kernel(S)"},
+        {"fft_e_kernel(W)", "fft_e4_kernel(W)", "fft_e4p_kernel(W)"},
+        {"fft_e_kernel(H)", "fft_e4_kernel(H)", "fft_e4p_kernel(H)"},
+        {"fft_e_kernel(R)", "fft_e4_kernel(R)", "fft_e4p_kernel(R)"},
+        {"fft_e_kernel(C)", "fft_e4_kernel(C)", "fft_e4p_kernel(C)"}};
+    for (const auto& l : labels)
+        if (strcmp(l[0], name) == 0) return l[prefetch ? 2 : 1];
+    return name;
+}
+
 // The same transform in a persistent CTA that copies the next tile into a raw staging buffer (cp.async, the
 // loader's own element type) while it transforms the current one, for loaders that read one global element per
 // (batch, row, column): the tile's loads are no longer a wait between the CTA's compute phases.
@@ -368,22 +384,11 @@ cudaError_t launch_e4_any(const char* name, const double2* tw, Load ld, Store sv
                           cudaStream_t st) {
     if constexpr (HasRawSrc<Load>::value && sizeof(typename HasRawSrcType<Load>::type) == 16) {
         if (e4p_smem<L1, L2>(ld) <= (size_t)kE4pSmemMax)
-            return launch_e4p_t<L1, L2>(name, tw, ld, sv, ncols, batches, st);
+            return launch_e4p_t<L1, L2>(e4_label(name, true), tw, ld, sv, ncols, batches, st);
     }
-    return launch_e4_t<L1, L2>(name, tw, ld, sv, ncols, batches, st);
+    return launch_e4_t<L1, L2>(e4_label(name, false), tw, ld, sv, ncols, batches, st);
 }
 
-// profile label of the register-codelet kernel for a transform the drivers name "fft_e_kernel(X)"
-inline const char* e4_label(const char* name) {
-    static const char* const labels[][2] = {
-        {"fft_e_kernel(G)", "fft_e4_kernel(G)"}, {"fft_e_kernel(K)", "fft_e4_kernel(K)"},
-        {"fft_e_kernel(S)", "fft_e4_kernel(S)"}, {"fft_e_kernel(W)", "fft_e4_kernel(W)"},
-        {"fft_e_kernel(H)", "fft_e4_kernel(H)"}, {"fft_e_kernel(R)", "fft_e4_kernel(R)"},
-        {"fft_e_kernel(C)", "fft_e4_kernel(C)"}};
-    for (const auto& l : labels)
-        if (strcmp(l[0], name) == 0) return l[1];
-    return name;
-}
 
 // FP32 E-transforms at the lengths with an instantiation (those of the stated workloads and of the small test
 // shapes); every other length, and the FP64 transforms, take fft_e_kernel.
@@ -392,11 +397,11 @@ cudaError_t launch_fft32(const char* name, const FftPlan& p, const double2* tw, 
                          int batches, cudaStream_t st) {
     if constexpr (std::is_same<typename Load::C, float2>::value) {
         switch (p.L) {
-            case 36: return launch_e4_any<6, 6>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 54: return launch_e4_any<6, 9>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 288: return launch_e4_any<16, 18>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 576: return launch_e4_any<24, 24>(e4_label(name), tw, ld, sv, ncols, batches, st);
-            case 1152: return launch_e4_any<32, 36>(e4_label(name), tw, ld, sv, ncols, batches, st);
+            case 36: return launch_e4_any<6, 6>(name, tw, ld, sv, ncols, batches, st);
+            case 54: return launch_e4_any<6, 9>(name, tw, ld, sv, ncols, batches, st);
+            case 288: return launch_e4_any<16, 18>(name, tw, ld, sv, ncols, batches, st);
+            case 576: return launch_e4_any<24, 24>(name, tw, ld, sv, ncols, batches, st);
+            case 1152: return launch_e4_any<32, 36>(name, tw, ld, sv, ncols, batches, st);
             default: break;
         }
     }

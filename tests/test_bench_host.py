@@ -91,7 +91,8 @@ def test_half_spectrum_count_is_one_per_pair(Nkz, NE, Nw):
 
 
 def test_kernel_sources_resolve():
-    for k in list(bench.NCU_TRAFFIC) + ["spec_prod_kernel", "fft_e_kernel", "dft_k_kernel", "spec_gradg_kernel"]:
+    for k in list(bench.NCU_TRAFFIC) + ["spec_prod_kernel", "fft_e_kernel", "fft_e4_kernel", "fft_e4p_kernel",
+                                        "dft_kz_kernel", "spec_gradg_kernel"]:
         assert len(bench.kernel_source_sha(k)) == 16, k
     assert bench.kernel_source_sha("no_such_kernel") == ""
     assert bench.ncu_traffic("no_such_kernel", 1.0) is None

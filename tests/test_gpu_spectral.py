@@ -207,3 +207,17 @@ def test_maximum_lengths(dims):
     ref = oracle.sigma_grad(inp.nbr, inp.dH, inp.D_less, inp.D_greater, inp.G_less, inp.G_greater, SCALE, W, V)
     for x, y in zip(got, ref):
         assert normwise(x.cpu().numpy(), y) <= TOL
+
+
+@pytest.mark.parametrize("Nkz", list(range(1, 17)))
+def test_every_kz_grid(Nkz):
+    """The kz DFT has one kernel instantiation per grid size (1 .. 16, the pairing of k with Nkz - k differs between
+    odd and even sizes): Sigma in FP64_FFT and FP32_FFT against the oracle for each, with Nqz < Nkz where possible
+    (the lag kernel's zero slices) and L = 36 (the register-codelet FP32 E-transform)."""
+    d = Dims(NA=3, NB=2, Norb=2, NE=32, Nkz=Nkz, Nqz=max(1, Nkz - 1), Nw=4)
+    inp = make_inputs(d, seed=300 + Nkz, nbr=ring_neighbours(d.NA, d.NB))
+    g = inp.to("cuda")
+    Ol, Og = oracle_sigma(inp)
+    for mode, bound in (("fp64_fft", TOL), ("fp32_fft", 2e-6)):
+        Sl, Sg = B.sigma(g.G_less, g.G_greater, g.dH, g.D_less, g.D_greater, g.nbr, mode=mode, check=True)
+        assert max(normwise(Sl.cpu().numpy(), Ol), normwise(Sg.cpu().numpy(), Og)) <= bound, (mode, Nkz)
