@@ -192,7 +192,8 @@ SSE_API int sse_sigma_fwd_host(const sse_dims* d, const int32_t* nbr, const doub
  * summed over frequencies in a fixed order), mode FP32_FFT the same steps with FP32
  * transforms and block products, the coupling-gradient partial sums and all inputs and
  * outputs in FP64 (normwise error about 1e-6, bound 1e-5 at the workloads tested);
- * TF32 and BF16X3 return SSE_ERR_UNSUPPORTED.
+ * TF32, BF16X3 and F16X3_FFT return SSE_ERR_UNSUPPORTED (after an F16X3_FFT forward,
+ * take the FP32_FFT adjoint).
  * For the loss
  *   L = sum_t sum_{a in range, E, k} Re tr( gS^t_a(E,k)^H Sigma^t_a(E,k) )
  * it writes the gradients w.r.t. dH, D^< and D^> in the PyTorch convention
@@ -216,8 +217,8 @@ SSE_API int sse_sigma_bwd(const sse_dims* d, const int32_t* nbr, const double* d
  *                     sum_ij conj(i*scale * D^tau_ij(q,w,a,s)) dH_i(a,s)^H gS^t_a(E,k) dH_j(a,s).
  * g_G_less / g_G_greater have the layout of G and are fully overwritten for every atom (zero where
  * no bond in range reaches). Through the transforms, in FP64 (modes FP64 and FP64_FFT) or with FP32
- * transforms and block products (mode FP32_FFT; FP64 inputs and outputs); TF32 and BF16X3 return
- * SSE_ERR_UNSUPPORTED. Per atom and frequency, the bonds into it in (a, s) order from a list built on
+ * transforms and block products (mode FP32_FFT; FP64 inputs and outputs); TF32, BF16X3 and
+ * F16X3_FFT return SSE_ERR_UNSUPPORTED. Per atom and frequency, the bonds into it in (a, s) order from a list built on
  * the device (deterministic sums).
  * SYMMETRIZE projects gS as in sse_sigma_bwd. Workspace: sse_sigma_bwd_g_workspace_bytes(). */
 SSE_API size_t sse_sigma_bwd_g_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);
@@ -238,8 +239,8 @@ SSE_API int sse_sigma_bwd_g(const sse_dims* d, const int32_t* nbr, const double*
  * Modes FP64 and FP64_FFT evaluate it with the convolution theorem in FP64 (per
  * frequency 6 block products and 9 traces per bond, then one inverse transform per
  * (bond, i, j)); mode FP32_FFT takes the same steps with FP32 transforms and block
- * products (FP64 inputs and outputs; normwise error a few 1e-7); TF32 and BF16X3
- * return SSE_ERR_UNSUPPORTED.
+ * products (FP64 inputs and outputs; normwise error a few 1e-7); TF32, BF16X3 and
+ * F16X3_FFT return SSE_ERR_UNSUPPORTED.
  * Flags: SYMMETRIZE replaces each 3x3 block B by (B - B^H)/2; CHECK, PROFILE as above.
  * Rows of other atoms are untouched. Workspace: sse_pi_workspace_bytes(). */
 SSE_API size_t sse_pi_workspace_bytes(const sse_dims* d, int mode, uint32_t flags);

@@ -234,9 +234,7 @@ def test_tensor_core_transform_mode_limits_are_checked_on_host():
         assert entries[name](B.sse_dims(16, 4, 10, 64, 4, 1, 4, 0, 16), m) == 2, name
     # FP32_FFT's workspace
     d = B.sse_dims(256, 4, 10, 256, 5, 5, 16, 0, 256)
-    assert B.sse_workspace_bytes(d, m, 0) == B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0) - (
-        B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0) - B.sse_workspace_bytes(d, m, 0))
-    assert 0 < B.sse_workspace_bytes(d, m, 0) <= B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0)
+    assert 0 < B.sse_workspace_bytes(d, m, 0) == B.sse_workspace_bytes(d, B.SSE_MODE_FP32_FFT, 0)
 
 
 def test_direct_fp64_adjoint_has_no_transform_limits():
